@@ -1,0 +1,933 @@
+/*
+ * FP64 CPU oracle for multi-view differentiable Gaussian splatting.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * CPU-baseline leg of bench.py load this library.  The product path (the CUDA
+ * library under paper_2510_26358_gb300/csrc) never calls it, and the two share
+ * no code, header, table or constant generator.
+ *
+ * Everything is computed in double precision, one pixel and one Gaussian at a
+ * time, in the order the method defines it, with no blocking or fusion.
+ * Paper: AgriGS-SLAM, Sec. III-B (multi-view 3DGS, Eqs. 2-4) and Sec. III-C
+ * (losses, Eqs. 6-8).  The paper defers the rasteriser itself to standard
+ * 3D Gaussian Splatting; the constants it leaves open are taken as
+ *   dilation 0.3 px, alpha = min(0.99, o*exp(-d^T Sigma'^-1 d / 2)),
+ *   skip alpha < 1/255, stop before blending when T would drop below 1e-4,
+ * and the readings below.
+ *
+ * Readings (where the paper is silent):
+ *   R1  quaternion order (w,x,y,z), normalised before use; |q| = 0 culls.
+ *   R2  cameras use OpenCV axes; W_b is the world->camera [R|t].
+ *   R3  near plane: a pair is visible only if view-space z > near_z.
+ *   R4  Jacobian of the pinhole with the tangent x/z clamped to
+ *       +-jac_clamp*max(cx, W-cx)/fx (same for y); derivative taken of the
+ *       clamped function as written.
+ *   R5  pixel (i,j) is sampled at its centre (i+0.5, j+0.5).
+ *   R6  support: a Gaussian contributes to a pixel iff alpha >= alpha_min there;
+ *       its tile rectangle covers the pixel centres inside the padded
+ *       axis-aligned extent of the ellipse {d : d^T Q d <= 2 ln(o/alpha_min)}.
+ *       Images therefore do not depend on the tile size.
+ *   R7  colour: real orthonormal SH basis without Condon-Shortley phase,
+ *       ordered by l then m=-l..l, evaluated at the unit direction from the
+ *       camera centre to the mean; rgb = max(0.5 + sum_k c_k Y_k, 0).
+ *   R8  opacity o = sigmoid(omega).
+ *   R9  compositing order: ascending (fp32-rounded view depth, Gaussian index);
+ *       depth output is the alpha-weighted view-space z, not normalised.
+ *   R10 depth is exact: p = R mu + t summed as ((R0 mu0 + R1 mu1) + R2 mu2) + t
+ *       in double (products of float inputs are exact), then z32 = (float)p_z.
+ *   R11 pose tangent: left perturbation T_cw <- exp(xi^) T_cw, xi = (rho, phi).
+ *   R12 depth loss (Eq. 7): nearest pixel of each LiDAR return; fixed sigma_u;
+ *       points are valid if inside the image, z_L > near_z and alpha > 0.
+ *   R13 image loss (Eq. 6 with lambda = 0): mean |C - I| over all channels,
+ *       pixels and views.
+ *   R14 densification statistic: per view where the pair is visible,
+ *       acc += ||(dL/du, dL/dv)|| in pixels and cnt += 1.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* interface types                                                          */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int32_t width, height, submap, pad_;
+    double fx, fy, cx, cy;
+    double T[12]; /* row-major [R | t], world -> camera */
+} oc_camera;
+
+typedef struct {
+    int32_t tile_w, tile_h;
+    double near_z, dilation, alpha_min, alpha_max, t_min, jac_clamp;
+    double ext_rel_pad, ext_abs_pad; /* padding of the extent used for tile rectangles */
+    double rect_eps_abs, rect_eps_rel; /* width of the ambiguity band for rect decisions */
+} oc_config;
+
+/* columns of a projected record (one row of OC_NCOL doubles per pair) */
+enum {
+    C_VIS = 0, C_TX0, C_TY0, C_TX1, C_TY1, /* tile rectangle, inclusive */
+    C_U, C_V, C_Z, C_Z32,                 /* pixel mean, view depth, depth as float */
+    C_SA, C_SB, C_SC,                     /* Sigma' (2x2, with dilation) */
+    C_QA, C_QB, C_QC,                     /* Q = Sigma'^-1 */
+    C_OPA, C_E, C_EX, C_EY,               /* opacity, support threshold, padded extents */
+    C_R, C_G, C_B,                        /* colour */
+    C_CLR, C_CLG, C_CLB,                  /* 1 where the colour is clamped at 0 */
+    C_RGB_MARGIN,                         /* min |0.5 + sum c Y| over channels */
+    C_RECT_AMBIG,                         /* 1 if a rect decision lies inside the eps band */
+    C_GAUSS, C_VIEW,                      /* Gaussian index, view index */
+    OC_NCOL
+};
+
+/* columns of the per-pair image-space gradient */
+enum { G_U = 0, G_V, G_QA, G_QB, G_QC, G_LNO, G_R, G_G, G_B, G_Z, OC_NGRAD };
+
+/* layout check for the Python wrapper: OC_NCOL*100 + OC_NGRAD */
+int64_t oracle_layout(void) { return (int64_t)OC_NCOL * 100 + OC_NGRAD; }
+
+/* ------------------------------------------------------------------------ */
+/* small helpers                                                            */
+/* ------------------------------------------------------------------------ */
+
+static void mat3_mul(const double A[9], const double B[9], double C[9]) {
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < 3; ++k) s += A[3 * i + k] * B[3 * k + j];
+            C[3 * i + j] = s;
+        }
+}
+
+static void mat3_transpose(const double A[9], double B[9]) {
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) B[3 * j + i] = A[3 * i + j];
+}
+
+/* rotation of a unit quaternion (w,x,y,z) */
+static void quat_to_rot(const double q[4], double R[9]) {
+    double w = q[0], x = q[1], y = q[2], z = q[3];
+    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+    R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+    R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+}
+
+/* dR/dq_k for the same formula, k = w,x,y,z (q need not be unit here) */
+static void quat_to_rot_jac(const double q[4], double dR[4][9]) {
+    double w = q[0], x = q[1], y = q[2], z = q[3];
+    double Dw[9] = {0, -2 * z, 2 * y, 2 * z, 0, -2 * x, -2 * y, 2 * x, 0};
+    double Dx[9] = {0, 2 * y, 2 * z, 2 * y, -4 * x, -2 * w, 2 * z, 2 * w, -4 * x};
+    double Dy[9] = {-4 * y, 2 * x, 2 * w, 2 * x, 0, 2 * z, -2 * w, 2 * z, -4 * y};
+    double Dz[9] = {-4 * z, -2 * w, 2 * x, 2 * w, -4 * z, 2 * y, 2 * x, 2 * y, 0};
+    memcpy(dR[0], Dw, sizeof Dw);
+    memcpy(dR[1], Dx, sizeof Dx);
+    memcpy(dR[2], Dy, sizeof Dy);
+    memcpy(dR[3], Dz, sizeof Dz);
+}
+
+/* real orthonormal SH basis (R7) and its gradient w.r.t. the direction */
+static void sh_basis(int deg, const double d[3], double Y[16], double dY[16][3]) {
+    const double PI = 3.14159265358979323846;
+    double x = d[0], y = d[1], z = d[2];
+    double c0 = 0.5 * sqrt(1.0 / PI);
+    double c1 = sqrt(3.0 / (4.0 * PI));
+    double c2a = 0.5 * sqrt(15.0 / PI), c2b = 0.25 * sqrt(5.0 / PI), c2c = 0.25 * sqrt(15.0 / PI);
+    double c3a = 0.25 * sqrt(35.0 / (2.0 * PI)), c3b = 0.5 * sqrt(105.0 / PI);
+    double c3c = 0.25 * sqrt(21.0 / (2.0 * PI)), c3d = 0.25 * sqrt(7.0 / PI);
+    double c3e = 0.25 * sqrt(105.0 / PI);
+    memset(dY, 0, sizeof(double) * 16 * 3);
+    Y[0] = c0;
+    if (deg < 1) return;
+    Y[1] = c1 * y; dY[1][1] = c1;
+    Y[2] = c1 * z; dY[2][2] = c1;
+    Y[3] = c1 * x; dY[3][0] = c1;
+    if (deg < 2) return;
+    Y[4] = c2a * x * y;               dY[4][0] = c2a * y; dY[4][1] = c2a * x;
+    Y[5] = c2a * y * z;               dY[5][1] = c2a * z; dY[5][2] = c2a * y;
+    Y[6] = c2b * (2 * z * z - x * x - y * y);
+    dY[6][0] = -2 * c2b * x; dY[6][1] = -2 * c2b * y; dY[6][2] = 4 * c2b * z;
+    Y[7] = c2a * x * z;               dY[7][0] = c2a * z; dY[7][2] = c2a * x;
+    Y[8] = c2c * (x * x - y * y);     dY[8][0] = 2 * c2c * x; dY[8][1] = -2 * c2c * y;
+    if (deg < 3) return;
+    Y[9] = c3a * y * (3 * x * x - y * y);
+    dY[9][0] = c3a * 6 * x * y; dY[9][1] = c3a * (3 * x * x - 3 * y * y);
+    Y[10] = c3b * x * y * z;
+    dY[10][0] = c3b * y * z; dY[10][1] = c3b * x * z; dY[10][2] = c3b * x * y;
+    Y[11] = c3c * y * (4 * z * z - x * x - y * y);
+    dY[11][0] = c3c * (-2 * x * y); dY[11][1] = c3c * (4 * z * z - x * x - 3 * y * y);
+    dY[11][2] = c3c * 8 * y * z;
+    Y[12] = c3d * z * (2 * z * z - 3 * x * x - 3 * y * y);
+    dY[12][0] = c3d * (-6 * x * z); dY[12][1] = c3d * (-6 * y * z);
+    dY[12][2] = c3d * (6 * z * z - 3 * x * x - 3 * y * y);
+    Y[13] = c3c * x * (4 * z * z - x * x - y * y);
+    dY[13][0] = c3c * (4 * z * z - 3 * x * x - y * y); dY[13][1] = c3c * (-2 * x * y);
+    dY[13][2] = c3c * 8 * x * z;
+    Y[14] = c3e * z * (x * x - y * y);
+    dY[14][0] = c3e * 2 * x * z; dY[14][1] = -c3e * 2 * y * z; dY[14][2] = c3e * (x * x - y * y);
+    Y[15] = c3a * x * (x * x - 3 * y * y);
+    dY[15][0] = c3a * (3 * x * x - 3 * y * y); dY[15][1] = c3a * (-6 * x * y);
+}
+
+static double dmin(double a, double b) { return a < b ? a : b; }
+static double dmax(double a, double b) { return a > b ? a : b; }
+
+/* ------------------------------------------------------------------------ */
+/* view layout                                                              */
+/* ------------------------------------------------------------------------ */
+
+/* Pairs are laid out view-major: view v owns pairs [pair_off[v], pair_off[v] +
+ * N_s) for its submap s, in Gaussian order.  Tiles of view v are numbered
+ * tile_off[v] + ty*ntx + tx; pixels pix_off[v] + y*W + x. */
+typedef struct {
+    int64_t pair_off, tile_off, pix_off;
+    int64_t g0, ng;
+    int32_t ntx, nty;
+} oc_view;
+
+static void make_views(int n_views, const oc_camera *cams, const int64_t *sub_off,
+                       const oc_config *cfg, oc_view *V) {
+    int64_t po = 0, to = 0, xo = 0;
+    for (int v = 0; v < n_views; ++v) {
+        int s = cams[v].submap;
+        V[v].g0 = sub_off[s];
+        V[v].ng = sub_off[s + 1] - sub_off[s];
+        V[v].pair_off = po;
+        V[v].tile_off = to;
+        V[v].pix_off = xo;
+        V[v].ntx = (cams[v].width + cfg->tile_w - 1) / cfg->tile_w;
+        V[v].nty = (cams[v].height + cfg->tile_h - 1) / cfg->tile_h;
+        po += V[v].ng;
+        to += (int64_t)V[v].ntx * V[v].nty;
+        xo += (int64_t)cams[v].width * cams[v].height;
+    }
+}
+
+int64_t oracle_count_pairs(int n_views, const oc_camera *cams, const int64_t *sub_off) {
+    int64_t p = 0;
+    for (int v = 0; v < n_views; ++v) p += sub_off[cams[v].submap + 1] - sub_off[cams[v].submap];
+    return p;
+}
+
+int64_t oracle_count_tiles(int n_views, const oc_camera *cams, const oc_config *cfg) {
+    int64_t t = 0;
+    for (int v = 0; v < n_views; ++v)
+        t += (int64_t)((cams[v].width + cfg->tile_w - 1) / cfg->tile_w) *
+             ((cams[v].height + cfg->tile_h - 1) / cfg->tile_h);
+    return t;
+}
+
+/* ------------------------------------------------------------------------ */
+/* 3-D covariance, Eq. (3)                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* Sigma = R S S^T R^T with S = diag(exp(log_scale)), R from the normalised
+ * quaternion.  Output: full 3x3 row-major. Returns 0 if |q| = 0. */
+int oracle_cov3d(const double *quat, const double *log_scale, double *Sigma) {
+    double qn = sqrt(quat[0] * quat[0] + quat[1] * quat[1] + quat[2] * quat[2] + quat[3] * quat[3]);
+    if (!(qn > 0.0)) return 0;
+    double qh[4] = {quat[0] / qn, quat[1] / qn, quat[2] / qn, quat[3] / qn};
+    double R[9];
+    quat_to_rot(qh, R);
+    double S2[3] = {exp(2 * log_scale[0]), exp(2 * log_scale[1]), exp(2 * log_scale[2])};
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0;
+            for (int k = 0; k < 3; ++k) s += R[3 * i + k] * S2[k] * R[3 * j + k];
+            Sigma[3 * i + j] = s;
+        }
+    return 1;
+}
+
+void oracle_sh_basis(int deg, const double *dir, double *Y) {
+    double dY[16][3];
+    double Yl[16] = {0};
+    sh_basis(deg, dir, Yl, dY);
+    int K = (deg + 1) * (deg + 1);
+    for (int k = 0; k < K; ++k) Y[k] = Yl[k];
+}
+
+/* ------------------------------------------------------------------------ */
+/* projection, Eqs. (2)-(4)                                                  */
+/* ------------------------------------------------------------------------ */
+
+/* tile index of the first covered pixel for a lower extent argument a:
+ * first pixel = ceil(a) clipped to >= 0 */
+static int64_t lo_tile(double a, int tw) {
+    double p = ceil(a);
+    if (p < 0) p = 0;
+    return (int64_t)p / tw;
+}
+static int64_t hi_tile(double a, int W, int tw) {
+    double p = floor(a);
+    if (p > W - 1) p = W - 1;
+    return (int64_t)p / tw;
+}
+
+static void project_pair(const double *mu, const double *ls, const double *q, double omega,
+                         const double *sh, int sh_degree, const oc_camera *cam,
+                         const oc_config *cfg, double *rec) {
+    memset(rec, 0, sizeof(double) * OC_NCOL);
+    const double *T = cam->T;
+    /* R10: view-space point, fixed summation order */
+    double p[3];
+    for (int i = 0; i < 3; ++i)
+        p[i] = ((T[4 * i + 0] * mu[0] + T[4 * i + 1] * mu[1]) + T[4 * i + 2] * mu[2]) + T[4 * i + 3];
+    rec[C_Z] = p[2];
+    rec[C_Z32] = (double)(float)p[2];
+    if (!(p[2] > cfg->near_z)) return; /* R3 */
+    double qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    if (!(qn > 0.0)) return; /* R1 */
+
+    /* Eq. (3): Sigma = R S S^T R^T */
+    double Sigma[9];
+    oracle_cov3d(q, ls, Sigma);
+    /* W Sigma W^T with W the rotation of the world->camera transform */
+    double Rb[9] = {T[0], T[1], T[2], T[4], T[5], T[6], T[8], T[9], T[10]};
+    double RbT[9], tmp[9], Sc[9];
+    mat3_transpose(Rb, RbT);
+    mat3_mul(Rb, Sigma, tmp);
+    mat3_mul(tmp, RbT, Sc);
+    /* R4: Jacobian of the pinhole with clamped tangents */
+    double W = cam->width, H = cam->height;
+    double limx = cfg->jac_clamp * dmax(cam->cx, W - cam->cx) / cam->fx;
+    double limy = cfg->jac_clamp * dmax(cam->cy, H - cam->cy) / cam->fy;
+    double tx = dmin(dmax(p[0] / p[2], -limx), limx) * p[2];
+    double ty = dmin(dmax(p[1] / p[2], -limy), limy) * p[2];
+    double J[6] = {cam->fx / p[2], 0.0, -cam->fx * tx / (p[2] * p[2]),
+                   0.0, cam->fy / p[2], -cam->fy * ty / (p[2] * p[2])};
+    /* Eq. (4): Sigma' = J W Sigma W^T J^T, top-left 2x2, plus dilation */
+    double S2[4];
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+            double s = 0;
+            for (int k = 0; k < 3; ++k)
+                for (int l = 0; l < 3; ++l) s += J[3 * i + k] * Sc[3 * k + l] * J[3 * j + l];
+            S2[2 * i + j] = s;
+        }
+    double a = S2[0] + cfg->dilation, b = S2[1], c = S2[3] + cfg->dilation;
+    double det = a * c - b * b;
+    rec[C_SA] = a; rec[C_SB] = b; rec[C_SC] = c;
+    if (!(det > 0.0)) return;
+    rec[C_QA] = c / det; rec[C_QB] = -b / det; rec[C_QC] = a / det;
+    /* R5: pixel-space mean */
+    double u = cam->fx * p[0] / p[2] + cam->cx;
+    double v = cam->fy * p[1] / p[2] + cam->cy;
+    rec[C_U] = u; rec[C_V] = v;
+    /* R8 */
+    double o = 1.0 / (1.0 + exp(-omega));
+    rec[C_OPA] = o;
+    /* R6: support threshold and padded axis-aligned extent */
+    double E = 2.0 * log(o / cfg->alpha_min);
+    rec[C_E] = E;
+    if (!(E > 0.0)) return;
+    double ex = sqrt(E * a) * (1.0 + cfg->ext_rel_pad) + cfg->ext_abs_pad;
+    double ey = sqrt(E * c) * (1.0 + cfg->ext_rel_pad) + cfg->ext_abs_pad;
+    rec[C_EX] = ex; rec[C_EY] = ey;
+    double xa = u - ex - 0.5, xb = u + ex - 0.5, ya = v - ey - 0.5, yb = v + ey - 0.5;
+    int tw = cfg->tile_w, th = cfg->tile_h;
+    int vis = ceil(xa) <= floor(xb) && ceil(xa) <= W - 1 && floor(xb) >= 0 &&
+              ceil(ya) <= floor(yb) && ceil(ya) <= H - 1 && floor(yb) >= 0;
+    /* ambiguity band: does a small perturbation of the arguments change a
+     * tile index or the visibility decision? */
+    {
+        double epsx = cfg->rect_eps_abs + cfg->rect_eps_rel * ex;
+        double epsy = cfg->rect_eps_abs + cfg->rect_eps_rel * ey;
+        int amb = 0;
+        for (int sgn = -1; sgn <= 1; sgn += 2) {
+            double dxa = xa + sgn * epsx, dxb = xb - sgn * epsx;
+            double dya = ya + sgn * epsy, dyb = yb - sgn * epsy;
+            int vis2 = ceil(dxa) <= floor(dxb) && ceil(dxa) <= W - 1 && floor(dxb) >= 0 &&
+                       ceil(dya) <= floor(dyb) && ceil(dya) <= H - 1 && floor(dyb) >= 0;
+            if (vis2 != vis) amb = 1;
+            if (vis && vis2) {
+                if (lo_tile(dxa, tw) != lo_tile(xa, tw) || hi_tile(dxb, cam->width, tw) != hi_tile(xb, cam->width, tw) ||
+                    lo_tile(dya, th) != lo_tile(ya, th) || hi_tile(dyb, cam->height, th) != hi_tile(yb, cam->height, th))
+                    amb = 1;
+            }
+        }
+        rec[C_RECT_AMBIG] = amb;
+    }
+    if (!vis) return;
+    rec[C_TX0] = (double)lo_tile(xa, tw);
+    rec[C_TX1] = (double)hi_tile(xb, cam->width, tw);
+    rec[C_TY0] = (double)lo_tile(ya, th);
+    rec[C_TY1] = (double)hi_tile(yb, cam->height, th);
+    rec[C_VIS] = 1.0;
+    /* R7: view-dependent colour from the camera centre C = -R^T t */
+    double Cb[3];
+    for (int i = 0; i < 3; ++i) Cb[i] = -(RbT[3 * i + 0] * T[3] + RbT[3 * i + 1] * T[7] + RbT[3 * i + 2] * T[11]);
+    double w[3] = {mu[0] - Cb[0], mu[1] - Cb[1], mu[2] - Cb[2]};
+    double wn = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+    double dir[3] = {w[0] / wn, w[1] / wn, w[2] / wn};
+    double Y[16], dY[16][3];
+    sh_basis(sh_degree, dir, Y, dY);
+    int K = (sh_degree + 1) * (sh_degree + 1);
+    double margin = 1e300;
+    for (int ch = 0; ch < 3; ++ch) {
+        double s = 0.5;
+        for (int k = 0; k < K; ++k) s += sh[3 * k + ch] * Y[k];
+        rec[C_R + ch] = s < 0 ? 0.0 : s;
+        rec[C_CLR + ch] = s < 0 ? 1.0 : 0.0;
+        margin = dmin(margin, fabs(s));
+    }
+    rec[C_RGB_MARGIN] = margin;
+}
+
+/* Project every (view, Gaussian) pair.  Inputs are the float parameters
+ * widened to double.  rec: [n_pairs][OC_NCOL]. */
+int oracle_project(int64_t n, const double *means, const double *log_scales, const double *quats,
+                   const double *opacity_logits, const double *sh, int sh_degree,
+                   int n_views, const oc_camera *cams, const int64_t *submap_offsets,
+                   const oc_config *cfg, double *rec) {
+    (void)n;
+    oc_view *V = (oc_view *)malloc(sizeof(oc_view) * (n_views > 0 ? n_views : 1));
+    make_views(n_views, cams, submap_offsets, cfg, V);
+    int K = (sh_degree + 1) * (sh_degree + 1);
+    for (int v = 0; v < n_views; ++v)
+        for (int64_t k = 0; k < V[v].ng; ++k) {
+            int64_t g = V[v].g0 + k;
+            double *r = rec + (V[v].pair_off + k) * OC_NCOL;
+            project_pair(means + 3 * g, log_scales + 3 * g, quats + 4 * g, opacity_logits[g],
+                         sh + (int64_t)3 * K * g, sh_degree, &cams[v], cfg, r);
+            r[C_GAUSS] = (double)g;
+            r[C_VIEW] = (double)v;
+        }
+    free(V);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* binning: 64-bit (tile | depth) keys, stable sort, per-tile ranges         */
+/* ------------------------------------------------------------------------ */
+
+typedef struct { uint64_t key; int64_t seq; int64_t pair; } oc_inst;
+
+static int inst_cmp(const void *pa, const void *pb) {
+    const oc_inst *a = (const oc_inst *)pa, *b = (const oc_inst *)pb;
+    if (a->key != b->key) return a->key < b->key ? -1 : 1;
+    return (a->seq > b->seq) - (a->seq < b->seq); /* stable: emission order */
+}
+
+static uint32_t float_bits(float f) { uint32_t u; memcpy(&u, &f, 4); return u; }
+
+/* Count instances: sum over visible pairs of their rectangle areas. */
+int64_t oracle_count_instances(int64_t n_pairs, const double *rec) {
+    int64_t total = 0;
+    for (int64_t p = 0; p < n_pairs; ++p) {
+        const double *r = rec + p * OC_NCOL;
+        if (r[C_VIS] == 0.0) continue;
+        total += (int64_t)(r[C_TX1] - r[C_TX0] + 1) * (int64_t)(r[C_TY1] - r[C_TY0] + 1);
+    }
+    return total;
+}
+
+/* Emit one key per (visible pair, covered tile) in pair order with the tiles of
+ * a rectangle row-major, key = (global tile << 32) | bits(z32); stable sort by
+ * key; ranges[2t], ranges[2t+1] = [first, end) of tile t (0,0 when empty). */
+int oracle_bin(int n_views, const oc_camera *cams, const int64_t *submap_offsets,
+               const oc_config *cfg, const double *rec, uint64_t *keys_out, int64_t *vals_out,
+               int64_t *ranges) {
+    oc_view *V = (oc_view *)malloc(sizeof(oc_view) * (n_views > 0 ? n_views : 1));
+    make_views(n_views, cams, submap_offsets, cfg, V);
+    int64_t n_pairs = oracle_count_pairs(n_views, cams, submap_offsets);
+    int64_t n_tiles = oracle_count_tiles(n_views, cams, cfg);
+    int64_t n_inst = oracle_count_instances(n_pairs, rec);
+    oc_inst *I = (oc_inst *)malloc(sizeof(oc_inst) * (n_inst > 0 ? n_inst : 1));
+    int64_t m = 0;
+    for (int v = 0; v < n_views; ++v)
+        for (int64_t k = 0; k < V[v].ng; ++k) {
+            int64_t p = V[v].pair_off + k;
+            const double *r = rec + p * OC_NCOL;
+            if (r[C_VIS] == 0.0) continue;
+            uint32_t zb = float_bits((float)r[C_Z32]);
+            for (int64_t ty = (int64_t)r[C_TY0]; ty <= (int64_t)r[C_TY1]; ++ty)
+                for (int64_t tx = (int64_t)r[C_TX0]; tx <= (int64_t)r[C_TX1]; ++tx) {
+                    uint64_t tile = (uint64_t)(V[v].tile_off + ty * V[v].ntx + tx);
+                    I[m].key = (tile << 32) | zb;
+                    I[m].seq = m;
+                    I[m].pair = p;
+                    ++m;
+                }
+        }
+    qsort(I, (size_t)n_inst, sizeof(oc_inst), inst_cmp);
+    for (int64_t t = 0; t < 2 * n_tiles; ++t) ranges[t] = 0;
+    for (int64_t i = 0; i < n_inst; ++i) {
+        keys_out[i] = I[i].key;
+        vals_out[i] = I[i].pair;
+        int64_t t = (int64_t)(I[i].key >> 32);
+        if (i == 0 || (I[i - 1].key >> 32) != (uint64_t)t) ranges[2 * t] = i;
+        if (i == n_inst - 1 || (I[i + 1].key >> 32) != (uint64_t)t) ranges[2 * t + 1] = i + 1;
+    }
+    free(I);
+    free(V);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* forward compositing                                                      */
+/* ------------------------------------------------------------------------ */
+
+/* alpha of pair record r at pixel centre (px, py); *raw gets o*exp(pw) */
+static double frag_alpha(const double *r, double px, double py, const oc_config *cfg, double *raw) {
+    double dx = px - r[C_U], dy = py - r[C_V];
+    double pw = -0.5 * (r[C_QA] * dx * dx + 2.0 * r[C_QB] * dx * dy + r[C_QC] * dy * dy);
+    double al = r[C_OPA] * exp(pw);
+    *raw = al;
+    return dmin(cfg->alpha_max, al);
+}
+
+typedef struct {
+    double C[3], D, T;
+    int64_t last;    /* list position of the last blended fragment, -1 if none */
+    int64_t n_blend; /* number of blended fragments */
+    double margin;   /* min log-distance of a discrete decision to its threshold */
+    double clamp_margin;
+    uint64_t sig;    /* order-sensitive signature of the blended set */
+} oc_pix;
+
+/* Composite the candidate pairs cand[0..n) (already in compositing order) at
+ * pixel centre (px, py).  pos[i] is the list position reported as `last`. */
+static void composite(const double *rec, const int64_t *cand, const int64_t *pos, int64_t n,
+                      double px, double py, const oc_config *cfg, oc_pix *out) {
+    double T = 1.0, C[3] = {0, 0, 0}, D = 0.0, margin = 1e300, cm = 1e300;
+    int64_t last = -1, nb = 0;
+    uint64_t sig = 1469598103934665603ull;
+    double lmin = log(cfg->alpha_min), ltmin = log(cfg->t_min), lmax = log(cfg->alpha_max);
+    for (int64_t i = 0; i < n; ++i) {
+        const double *r = rec + cand[i] * OC_NCOL;
+        double raw, al = frag_alpha(r, px, py, cfg, &raw);
+        if (raw > 0) {
+            margin = dmin(margin, fabs(log(raw) - lmin));
+            cm = dmin(cm, fabs(log(raw) - lmax));
+        }
+        if (al < cfg->alpha_min) continue;
+        double Tn = T * (1.0 - al);
+        margin = dmin(margin, fabs(log(Tn) - ltmin));
+        if (Tn < cfg->t_min) break; /* stop before blending this fragment */
+        double w = al * T;
+        for (int ch = 0; ch < 3; ++ch) C[ch] += w * r[C_R + ch];
+        D += w * r[C_Z];
+        T = Tn;
+        last = pos[i];
+        ++nb;
+        sig = (sig ^ (uint64_t)cand[i]) * 1099511628211ull;
+    }
+    memcpy(out->C, C, sizeof C);
+    out->D = D; out->T = T; out->last = last; out->n_blend = nb;
+    out->margin = margin; out->clamp_margin = cm; out->sig = sig;
+}
+
+static void write_pix(const oc_pix *o, int64_t pix, int64_t W, int64_t H, int64_t pix_off,
+                      double *rgb, double *depth, double *alpha, double *Tfin, int64_t *last,
+                      int64_t *nblend, double *margin, uint64_t *sig) {
+    int64_t local = pix - pix_off;
+    for (int ch = 0; ch < 3; ++ch) rgb[3 * pix_off + ch * W * H + local] = o->C[ch];
+    depth[pix] = o->D;
+    alpha[pix] = 1.0 - o->T;
+    if (Tfin) Tfin[pix] = o->T;
+    if (last) last[pix] = o->last;
+    if (nblend) nblend[pix] = o->n_blend;
+    if (margin) margin[pix] = o->margin;
+    if (sig) sig[pix] = o->sig;
+}
+
+/* Tiled forward: every pixel walks the sorted list of its tile.
+ * rgb is planar per view: view v occupies [3*pix_off, 3*pix_off + 3*W*H).
+ * last holds the list position of the last blended fragment (-1 if none). */
+int oracle_render_fwd(int n_views, const oc_camera *cams, const int64_t *submap_offsets,
+                      const oc_config *cfg, const double *rec, const int64_t *vals,
+                      const int64_t *ranges, double *rgb, double *depth, double *alpha,
+                      double *Tfin, int64_t *last, int64_t *nblend, double *margin, uint64_t *sig) {
+    oc_view *V = (oc_view *)malloc(sizeof(oc_view) * (n_views > 0 ? n_views : 1));
+    make_views(n_views, cams, submap_offsets, cfg, V);
+    for (int v = 0; v < n_views; ++v) {
+        int64_t W = cams[v].width, H = cams[v].height;
+        for (int64_t y = 0; y < H; ++y)
+            for (int64_t x = 0; x < W; ++x) {
+                int64_t t = V[v].tile_off + (y / cfg->tile_h) * V[v].ntx + x / cfg->tile_w;
+                int64_t s = ranges[2 * t], e = ranges[2 * t + 1];
+                int64_t n = e - s;
+                int64_t *pos = (int64_t *)malloc(sizeof(int64_t) * (n > 0 ? n : 1));
+                for (int64_t i = 0; i < n; ++i) pos[i] = s + i;
+                oc_pix o;
+                composite(rec, vals + s, pos, n, x + 0.5, y + 0.5, cfg, &o);
+                free(pos);
+                write_pix(&o, V[v].pix_off + y * W + x, W, H, V[v].pix_off, rgb, depth, alpha,
+                          Tfin, last, nblend, margin, sig);
+            }
+    }
+    free(V);
+    return 0;
+}
+
+/* Brute-force forward without tiles: every pixel composites all visible pairs
+ * of its view in ascending (z32, Gaussian index) order; membership is decided
+ * by alpha alone.  `last` here is the index into that per-view order. */
+typedef struct { double z32; int64_t g; int64_t pair; } oc_zs;
+static int zs_cmp(const void *pa, const void *pb) {
+    const oc_zs *a = (const oc_zs *)pa, *b = (const oc_zs *)pb;
+    if (a->z32 != b->z32) return a->z32 < b->z32 ? -1 : 1;
+    return (a->g > b->g) - (a->g < b->g);
+}
+
+int oracle_render_brute(int n_views, const oc_camera *cams, const int64_t *submap_offsets,
+                        const oc_config *cfg, const double *rec, double *rgb, double *depth,
+                        double *alpha, double *Tfin, int64_t *nblend, uint64_t *sig) {
+    oc_view *V = (oc_view *)malloc(sizeof(oc_view) * (n_views > 0 ? n_views : 1));
+    make_views(n_views, cams, submap_offsets, cfg, V);
+    for (int v = 0; v < n_views; ++v) {
+        int64_t W = cams[v].width, H = cams[v].height;
+        oc_zs *Z = (oc_zs *)malloc(sizeof(oc_zs) * (V[v].ng > 0 ? V[v].ng : 1));
+        int64_t n = 0;
+        for (int64_t k = 0; k < V[v].ng; ++k) {
+            int64_t p = V[v].pair_off + k;
+            const double *r = rec + p * OC_NCOL;
+            /* every projected pair in front of the camera is a candidate; the
+             * rectangle is not consulted */
+            if (!(r[C_Z] > cfg->near_z) || !(r[C_E] > 0.0) || r[C_QA] == 0.0) continue;
+            Z[n].z32 = r[C_Z32]; Z[n].g = (int64_t)r[C_GAUSS]; Z[n].pair = p; ++n;
+        }
+        qsort(Z, (size_t)n, sizeof(oc_zs), zs_cmp);
+        int64_t *cand = (int64_t *)malloc(sizeof(int64_t) * (n > 0 ? n : 1));
+        int64_t *pos = (int64_t *)malloc(sizeof(int64_t) * (n > 0 ? n : 1));
+        for (int64_t i = 0; i < n; ++i) { cand[i] = Z[i].pair; pos[i] = i; }
+        for (int64_t y = 0; y < H; ++y)
+            for (int64_t x = 0; x < W; ++x) {
+                oc_pix o;
+                composite(rec, cand, pos, n, x + 0.5, y + 0.5, cfg, &o);
+                write_pix(&o, V[v].pix_off + y * W + x, W, H, V[v].pix_off, rgb, depth, alpha,
+                          Tfin, NULL, nblend, NULL, sig);
+            }
+        free(cand); free(pos); free(Z);
+    }
+    free(V);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* losses, Eqs. (6)-(7)                                                      */
+/* ------------------------------------------------------------------------ */
+
+/* R13: L = mean |C - I| over n values; dL/dC = sign(C - I)/n (sign(0) = 0). */
+double oracle_image_l1(int64_t n, const double *C, const double *I, double *grad) {
+    double s = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        double d = C[i] - I[i];
+        s += fabs(d);
+        if (grad) grad[i] = (d > 0 ? 1.0 : (d < 0 ? -1.0 : 0.0)) / (double)n;
+    }
+    return n > 0 ? s / (double)n : 0.0;
+}
+
+/* KL(N(m1, s1^2) || N(m2, s2^2)) */
+double oracle_kl_normal(double m1, double s1, double m2, double s2) {
+    return log(s2 / s1) + (s1 * s1 + (m1 - m2) * (m1 - m2)) / (2.0 * s2 * s2) - 0.5;
+}
+
+/* R12 / Eq. (7).  lidar rows (u, v, z, view).  mode 0: mean |D - z|;
+ * mode 1: mean KL(N(z, sigma_L^2) || N(D, sigma_U^2)); scaled by lambda.
+ * grad (nullable) receives dL/dD per pixel (accumulated over points). */
+double oracle_depth_loss(int n_views, const oc_camera *cams, const int64_t *submap_offsets,
+                         const oc_config *cfg, const double *depth, const double *alpha,
+                         int64_t n_pts, const double *lidar, int mode, double sigma_L,
+                         double sigma_U, double lambda, double *grad, int64_t *n_valid) {
+    oc_view *V = (oc_view *)malloc(sizeof(oc_view) * (n_views > 0 ? n_views : 1));
+    make_views(n_views, cams, submap_offsets, cfg, V);
+    double s = 0;
+    int64_t nv = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int64_t i = 0; i < n_pts; ++i) {
+            const double *L = lidar + 4 * i;
+            int v = (int)L[3];
+            if (v < 0 || v >= n_views) continue;
+            double W = cams[v].width, H = cams[v].height;
+            if (!(L[0] >= 0 && L[0] < W && L[1] >= 0 && L[1] < H && L[2] > cfg->near_z)) continue;
+            int64_t pix = V[v].pix_off + (int64_t)floor(L[1]) * cams[v].width + (int64_t)floor(L[0]);
+            if (!(alpha[pix] > 0)) continue;
+            double Dh = depth[pix], z = L[2];
+            if (pass == 0) {
+                ++nv;
+                s += mode == 0 ? fabs(Dh - z) : oracle_kl_normal(z, sigma_L, Dh, sigma_U);
+            } else if (grad) {
+                double g = mode == 0 ? (Dh > z ? 1.0 : (Dh < z ? -1.0 : 0.0))
+                                     : (Dh - z) / (sigma_U * sigma_U);
+                grad[pix] += lambda * g / (double)nv;
+            }
+        }
+        if (nv == 0) break;
+    }
+    free(V);
+    if (n_valid) *n_valid = nv;
+    return nv > 0 ? lambda * s / (double)nv : 0.0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* backward                                                                 */
+/* ------------------------------------------------------------------------ */
+
+/* Raster adjoint for one pixel: replay the forward to list the blended
+ * fragments with their alpha and transmittance, then apply
+ *   dL/dc_j = w_j gC, dL/dz_j = w_j gD,
+ *   dL/dalpha_j = T_j h_j - (sum_{k>j} w_k h_k) / (1 - alpha_j),
+ * with w_k = alpha_k T_k and h_k = gC.c_k + gD z_k + gA (A = sum_k w_k). */
+static void pixel_adjoint(const double *rec, const int64_t *cand, int64_t n, double px, double py,
+                          const oc_config *cfg, const double gC[3], double gD, double gA,
+                          double *g2d) {
+    int64_t *bl = (int64_t *)malloc(sizeof(int64_t) * (n > 0 ? n : 1));
+    double *al = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
+    double *raw = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
+    double *Tb = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
+    int64_t m = 0;
+    double T = 1.0;
+    for (int64_t i = 0; i < n; ++i) {
+        const double *r = rec + cand[i] * OC_NCOL;
+        double rw, a = frag_alpha(r, px, py, cfg, &rw);
+        if (a < cfg->alpha_min) continue;
+        double Tn = T * (1.0 - a);
+        if (Tn < cfg->t_min) break;
+        bl[m] = cand[i]; al[m] = a; raw[m] = rw; Tb[m] = T; ++m;
+        T = Tn;
+    }
+    double suffix = 0.0;
+    for (int64_t j = m - 1; j >= 0; --j) {
+        const double *r = rec + bl[j] * OC_NCOL;
+        double *g = g2d + bl[j] * OC_NGRAD;
+        double w = al[j] * Tb[j];
+        double h = gC[0] * r[C_R] + gC[1] * r[C_G] + gC[2] * r[C_B] + gD * r[C_Z] + gA;
+        double dal = Tb[j] * h - suffix / (1.0 - al[j]);
+        suffix += w * h;
+        g[G_R] += w * gC[0]; g[G_G] += w * gC[1]; g[G_B] += w * gC[2];
+        g[G_Z] += w * gD;
+        if (raw[j] > cfg->alpha_max) continue; /* clamped: no dependence on o, pw */
+        /* alpha = o exp(pw): dalpha/dln(o) = alpha, dalpha/dpw = alpha */
+        double gpw = dal * al[j];
+        g[G_LNO] += gpw;
+        double dx = px - r[C_U], dy = py - r[C_V];
+        /* pw = -1/2 (qa dx^2 + 2 qb dx dy + qc dy^2), d = pixel - mean */
+        g[G_QA] += -0.5 * gpw * dx * dx;
+        g[G_QB] += -gpw * dx * dy;
+        g[G_QC] += -0.5 * gpw * dy * dy;
+        g[G_U] += gpw * (r[C_QA] * dx + r[C_QB] * dy);
+        g[G_V] += gpw * (r[C_QB] * dx + r[C_QC] * dy);
+    }
+    free(bl); free(al); free(raw); free(Tb);
+}
+
+/* Projection adjoint for one visible pair: from the image-space gradient g to
+ * the Gaussian parameters (accumulated) and the pose twist of the view. */
+static void project_adjoint(const double *mu, const double *ls, const double *q, double omega,
+                            const double *sh, int sh_degree, const oc_camera *cam,
+                            const oc_config *cfg, const double *rec, const double *g,
+                            double *g_mu, double *g_ls, double *g_q, double *g_om, double *g_sh,
+                            double *g_pose) {
+    (void)omega; /* the opacity enters through rec[C_OPA] */
+    const double *T = cam->T;
+    double p[3];
+    for (int i = 0; i < 3; ++i)
+        p[i] = ((T[4 * i + 0] * mu[0] + T[4 * i + 1] * mu[1]) + T[4 * i + 2] * mu[2]) + T[4 * i + 3];
+    double Rb[9] = {T[0], T[1], T[2], T[4], T[5], T[6], T[8], T[9], T[10]};
+    double RbT[9];
+    mat3_transpose(Rb, RbT);
+    double fx = cam->fx, fy = cam->fy;
+    double gp[3] = {0, 0, 0};   /* dL/dp, p the view-space mean */
+    double gw[3] = {0, 0, 0};   /* dL/dw, w = mu - C the SH viewing vector */
+
+    /* colour: rgb_c = max(0.5 + sum_k sh_kc Y_k(dir), 0), dir = w/|w| */
+    double Cb[3];
+    for (int i = 0; i < 3; ++i) Cb[i] = -(RbT[3 * i + 0] * T[3] + RbT[3 * i + 1] * T[7] + RbT[3 * i + 2] * T[11]);
+    double w[3] = {mu[0] - Cb[0], mu[1] - Cb[1], mu[2] - Cb[2]};
+    double wn = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+    double dir[3] = {w[0] / wn, w[1] / wn, w[2] / wn};
+    double Y[16], dY[16][3];
+    sh_basis(sh_degree, dir, Y, dY);
+    int K = (sh_degree + 1) * (sh_degree + 1);
+    double gdir[3] = {0, 0, 0};
+    for (int ch = 0; ch < 3; ++ch) {
+        if (rec[C_CLR + ch] != 0.0) continue;
+        double gc = g[G_R + ch];
+        for (int k = 0; k < K; ++k) {
+            g_sh[3 * k + ch] += gc * Y[k];
+            for (int i = 0; i < 3; ++i) gdir[i] += gc * sh[3 * k + ch] * dY[k][i];
+        }
+    }
+    /* dir = w/|w|: dL/dw = (I - dir dir^T) gdir / |w| */
+    double dd = dir[0] * gdir[0] + dir[1] * gdir[1] + dir[2] * gdir[2];
+    for (int i = 0; i < 3; ++i) gw[i] = (gdir[i] - dir[i] * dd) / wn;
+
+    /* depth output: z = p_z */
+    gp[2] += g[G_Z];
+    /* pixel mean: u = fx p_x/p_z + cx, v = fy p_y/p_z + cy */
+    gp[0] += g[G_U] * fx / p[2];
+    gp[1] += g[G_V] * fy / p[2];
+    gp[2] += -(g[G_U] * fx * p[0] + g[G_V] * fy * p[1]) / (p[2] * p[2]);
+
+    /* conic Q = Sigma'^-1: with G the symmetric matrix of dL/dQ (off-diagonal
+     * halved, since qb appears twice), dL/dSigma' = -Q G Q */
+    double Q[4] = {rec[C_QA], rec[C_QB], rec[C_QB], rec[C_QC]};
+    double G[4] = {g[G_QA], 0.5 * g[G_QB], 0.5 * g[G_QB], g[G_QC]};
+    double QG[4], M[4];
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) QG[2 * i + j] = Q[2 * i] * G[j] + Q[2 * i + 1] * G[2 + j];
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) M[2 * i + j] = -(QG[2 * i] * Q[j] + QG[2 * i + 1] * Q[2 + j]);
+    /* M is dL/dSigma' as a symmetric matrix (full-matrix convention) */
+
+    /* Sigma' = J Sc J^T + dil I with Sc = Rb Sigma Rb^T */
+    double Sigma[9], tmp[9], Sc[9];
+    oracle_cov3d(q, ls, Sigma);
+    mat3_mul(Rb, Sigma, tmp);
+    mat3_mul(tmp, RbT, Sc);
+    double W = cam->width, H = cam->height;
+    double limx = cfg->jac_clamp * dmax(cam->cx, W - cam->cx) / fx;
+    double limy = cfg->jac_clamp * dmax(cam->cy, H - cam->cy) / fy;
+    double xr = p[0] / p[2], yr = p[1] / p[2];
+    int clx = xr < -limx || xr > limx, cly = yr < -limy || yr > limy;
+    double tx = dmin(dmax(xr, -limx), limx) * p[2];
+    double ty = dmin(dmax(yr, -limy), limy) * p[2];
+    double J[6] = {fx / p[2], 0.0, -fx * tx / (p[2] * p[2]),
+                   0.0, fy / p[2], -fy * ty / (p[2] * p[2])};
+    /* dL/dSc = J^T M J ; dL/dJ = 2 M J Sc */
+    double gSc[9];
+    for (int k = 0; k < 3; ++k)
+        for (int l = 0; l < 3; ++l) {
+            double s = 0;
+            for (int i = 0; i < 2; ++i)
+                for (int j = 0; j < 2; ++j) s += J[3 * i + k] * M[2 * i + j] * J[3 * j + l];
+            gSc[3 * k + l] = s;
+        }
+    double gJ[6];
+    for (int i = 0; i < 2; ++i)
+        for (int k = 0; k < 3; ++k) {
+            double s = 0;
+            for (int j = 0; j < 2; ++j)
+                for (int l = 0; l < 3; ++l) s += M[2 * i + j] * J[3 * j + l] * Sc[3 * l + k];
+            gJ[3 * i + k] = 2.0 * s;
+        }
+    /* J entries as functions of p (clamped tangent: tx = c*p_z, J02 = -fx c/p_z) */
+    double z2 = p[2] * p[2], z3 = z2 * p[2];
+    gp[2] += gJ[0] * (-fx / z2) + gJ[4] * (-fy / z2);
+    if (!clx) {
+        gp[0] += gJ[2] * (-fx / z2);
+        gp[2] += gJ[2] * (2.0 * fx * p[0] / z3);
+    } else {
+        double cx_ = tx / p[2];
+        gp[2] += gJ[2] * (fx * cx_ / z2);
+    }
+    if (!cly) {
+        gp[1] += gJ[5] * (-fy / z2);
+        gp[2] += gJ[5] * (2.0 * fy * p[1] / z3);
+    } else {
+        double cy_ = ty / p[2];
+        gp[2] += gJ[5] * (fy * cy_ / z2);
+    }
+
+    /* Sc = Rb Sigma Rb^T: dL/dSigma = Rb^T gSc Rb */
+    double gSig[9], t2[9];
+    mat3_mul(RbT, gSc, t2);
+    mat3_mul(t2, Rb, gSig);
+    /* Sigma = R diag(S^2) R^T = M3 M3^T with M3 = R diag(S): dL/dM3 = (G + G^T) M3 */
+    double qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    double qh[4] = {q[0] / qn, q[1] / qn, q[2] / qn, q[3] / qn};
+    double R[9];
+    quat_to_rot(qh, R);
+    double S[3] = {exp(ls[0]), exp(ls[1]), exp(ls[2])};
+    double gM3[9];
+    for (int i = 0; i < 3; ++i)
+        for (int k = 0; k < 3; ++k) {
+            double s = 0;
+            for (int j = 0; j < 3; ++j) s += (gSig[3 * i + j] + gSig[3 * j + i]) * R[3 * j + k] * S[k];
+            gM3[3 * i + k] = s;
+        }
+    /* M3_ik = R_ik S_k with S_k = exp(ls_k): dL/dls_k = sum_i gM3_ik R_ik S_k */
+    double gR[9];
+    for (int k = 0; k < 3; ++k) {
+        double s = 0;
+        for (int i = 0; i < 3; ++i) {
+            s += gM3[3 * i + k] * R[3 * i + k];
+            gR[3 * i + k] = gM3[3 * i + k] * S[k];
+        }
+        g_ls[k] += s * S[k];
+    }
+    /* R from the normalised quaternion, then the normalisation */
+    double dR[4][9];
+    quat_to_rot_jac(qh, dR);
+    double gqh[4];
+    for (int a = 0; a < 4; ++a) {
+        double s = 0;
+        for (int e = 0; e < 9; ++e) s += gR[e] * dR[a][e];
+        gqh[a] = s;
+    }
+    double dq = qh[0] * gqh[0] + qh[1] * gqh[1] + qh[2] * gqh[2] + qh[3] * gqh[3];
+    for (int a = 0; a < 4; ++a) g_q[a] += (gqh[a] - qh[a] * dq) / qn;
+
+    /* opacity: ln o = -ln(1 + e^-omega), d ln o / d omega = 1 - o */
+    *g_om += g[G_LNO] * (1.0 - rec[C_OPA]);
+
+    /* mean: p = Rb mu + t and w = mu - C */
+    for (int i = 0; i < 3; ++i)
+        g_mu[i] += RbT[3 * i + 0] * gp[0] + RbT[3 * i + 1] * gp[1] + RbT[3 * i + 2] * gp[2] + gw[i];
+
+    /* pose, left perturbation (R11): p -> p + rho + phi x p, Rb -> (I + [phi]x) Rb,
+     * w -> w + Rb^T rho.  dL/drho = gp + Rb gw; dL/dphi = p x gp + cov term. */
+    double gw_c[3];
+    for (int i = 0; i < 3; ++i) gw_c[i] = Rb[3 * i + 0] * gw[0] + Rb[3 * i + 1] * gw[1] + Rb[3 * i + 2] * gw[2];
+    g_pose[0] += gp[0] + gw_c[0];
+    g_pose[1] += gp[1] + gw_c[1];
+    g_pose[2] += gp[2] + gw_c[2];
+    g_pose[3] += p[1] * gp[2] - p[2] * gp[1];
+    g_pose[4] += p[2] * gp[0] - p[0] * gp[2];
+    g_pose[5] += p[0] * gp[1] - p[1] * gp[0];
+    /* Sc -> Sc + [phi]x Sc - Sc [phi]x: dL/dphi = 2 * axial(A - A^T)/..., A = Sc gSc */
+    double A[9];
+    mat3_mul(Sc, gSc, A);
+    g_pose[3] += 2.0 * (A[5] - A[7]);
+    g_pose[4] += 2.0 * (A[6] - A[2]);
+    g_pose[5] += 2.0 * (A[1] - A[3]);
+}
+
+/* Full backward: raster adjoint for every pixel (using the oracle's own sorted
+ * lists), then the projection adjoint of every visible pair.
+ * dC: planar like rgb; dD, dA per pixel (dA nullable).
+ * Outputs (accumulated, caller zeroes): g2d [n_pairs][OC_NGRAD], parameter
+ * gradients, pose [n_views][6], densify acc/cnt [n]. */
+int oracle_render_bwd(int64_t n, const double *means, const double *log_scales, const double *quats,
+                      const double *opacity_logits, const double *sh, int sh_degree,
+                      int n_views, const oc_camera *cams, const int64_t *submap_offsets,
+                      const oc_config *cfg, const double *rec, const int64_t *vals,
+                      const int64_t *ranges, const double *dC, const double *dD, const double *dA,
+                      double *g2d, double *g_means, double *g_ls, double *g_quats, double *g_om,
+                      double *g_sh, double *g_pose, double *dens_acc, double *dens_cnt) {
+    (void)n;
+    oc_view *V = (oc_view *)malloc(sizeof(oc_view) * (n_views > 0 ? n_views : 1));
+    make_views(n_views, cams, submap_offsets, cfg, V);
+    for (int v = 0; v < n_views; ++v) {
+        int64_t W = cams[v].width, H = cams[v].height;
+        for (int64_t y = 0; y < H; ++y)
+            for (int64_t x = 0; x < W; ++x) {
+                int64_t pix = V[v].pix_off + y * W + x, local = y * W + x;
+                double gC[3];
+                for (int ch = 0; ch < 3; ++ch) gC[ch] = dC[3 * V[v].pix_off + ch * W * H + local];
+                double gD = dD ? dD[pix] : 0.0, gA = dA ? dA[pix] : 0.0;
+                if (gC[0] == 0 && gC[1] == 0 && gC[2] == 0 && gD == 0 && gA == 0) continue;
+                int64_t t = V[v].tile_off + (y / cfg->tile_h) * V[v].ntx + x / cfg->tile_w;
+                int64_t s = ranges[2 * t], e = ranges[2 * t + 1];
+                pixel_adjoint(rec, vals + s, e - s, x + 0.5, y + 0.5, cfg, gC, gD, gA, g2d);
+            }
+    }
+    int K = (sh_degree + 1) * (sh_degree + 1);
+    for (int v = 0; v < n_views; ++v)
+        for (int64_t k = 0; k < V[v].ng; ++k) {
+            int64_t p = V[v].pair_off + k, g = V[v].g0 + k;
+            const double *r = rec + p * OC_NCOL;
+            if (r[C_VIS] == 0.0) continue;
+            const double *gg = g2d + p * OC_NGRAD;
+            project_adjoint(means + 3 * g, log_scales + 3 * g, quats + 4 * g, opacity_logits[g],
+                            sh + (int64_t)3 * K * g, sh_degree, &cams[v], cfg, r, gg,
+                            g_means + 3 * g, g_ls + 3 * g, g_quats + 4 * g, g_om + g,
+                            g_sh + (int64_t)3 * K * g, g_pose + 6 * v);
+            if (dens_acc) dens_acc[g] += sqrt(gg[G_U] * gg[G_U] + gg[G_V] * gg[G_V]);
+            if (dens_cnt) dens_cnt[g] += 1.0;
+        }
+    free(V);
+    return 0;
+}

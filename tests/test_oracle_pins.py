@@ -1,0 +1,467 @@
+"""Pins for the FP64 oracle against facts that do not come from the oracle itself.
+
+Each test ties one part of the oracle to a closed form, an invariant, an
+independent library routine or brute force, so that a dropped term, a wrong
+sign, a transposed operand or a wrong index in the oracle fails at least one:
+
+  covariance (Eq. 3)        eigen-structure; scipy's quaternion rotation
+  projection (Eq. 4)        isotropic on-axis closed form; pinhole; J by FD
+  colour                    SH orthonormality by quadrature; DC reproduces rgb
+  compositing               single-Gaussian closed form; stacked-alpha closed
+                            form with the stop rule; sum of weights = alpha
+  binning                   keys rebuilt with numpy's stable sort; brute-force
+                            renderer (no tiles) equal bitwise for 3 tile sizes
+  backward                  central differences of every parameter type and
+                            every pose twist; translation identity
+  losses (Eqs. 6-7)         KL by numerical integration; FD of both losses
+"""
+import copy
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2510_26358_gb300 import scenes as S
+
+scipy = pytest.importorskip("scipy")
+from scipy.spatial.transform import Rotation  # noqa: E402
+
+
+CFG = O.Config()
+
+
+def _cam(W=64, H=48, f=60.0, T=None, cx=None, cy=None):
+    T = np.concatenate([np.eye(3), np.zeros((3, 1))], 1) if T is None else T
+    return S.Camera(W, H, f, f, W / 2 if cx is None else cx, H / 2 if cy is None else cy, T, 0)
+
+
+def _params(means, log_scales, quats, omega, sh, deg=0):
+    n = len(means)
+    return O.Params(np.asarray(means, np.float64).reshape(n, 3),
+                    np.asarray(log_scales, np.float64).reshape(n, 3),
+                    np.asarray(quats, np.float64).reshape(n, 4),
+                    np.asarray(omega, np.float64).reshape(n),
+                    np.asarray(sh, np.float64).reshape(n, (deg + 1) ** 2, 3), deg,
+                    np.array([0, n], np.int64))
+
+
+# ---------------------------------------------------------------------------
+# covariance, Eq. (3)
+# ---------------------------------------------------------------------------
+
+def test_cov3d_eigenvalues_and_rotation():
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        q = rng.normal(size=4) * rng.uniform(0.1, 5.0)   # not unit on purpose
+        s = rng.normal(-2, 1, 3)
+        Sig = O.cov3d(q, s)
+        assert np.allclose(Sig, Sig.T, atol=1e-15)
+        ev = np.sort(np.linalg.eigvalsh(Sig))
+        assert np.allclose(ev, np.sort(np.exp(2 * s)), rtol=1e-10, atol=1e-15)
+        # scipy's rotation of the same quaternion (scipy order is x,y,z,w)
+        R = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()
+        assert np.allclose(Sig, R @ np.diag(np.exp(2 * s)) @ R.T, rtol=1e-10, atol=1e-14)
+
+
+def test_cov3d_zero_quaternion_is_rejected():
+    # a zero quaternion culls the pair (reading R1)
+    cam = _cam()
+    P = _params([[0, 0, 3]], [[-2, -2, -2]], [[0, 0, 0, 0]], [2.0], [[0, 0, 0]])
+    rec = O.project(P, [cam], CFG)
+    assert rec[0, O.C_VIS] == 0
+
+
+# ---------------------------------------------------------------------------
+# projection, Eq. (4)
+# ---------------------------------------------------------------------------
+
+def test_isotropic_on_axis_image_covariance():
+    f, z, s = 60.0, 3.0, math.log(0.05)
+    cam = _cam(f=f)
+    P = _params([[0, 0, z]], [[s, s, s]], [[0.3, -0.2, 0.5, 0.7]], [1.0], [[0, 0, 0]])
+    r = O.project(P, [cam], CFG)[0]
+    var = (f * 0.05 / z) ** 2 + float(np.float32(0.3))
+    assert r[O.C_SA] == pytest.approx(var, rel=1e-12)
+    assert r[O.C_SC] == pytest.approx(var, rel=1e-12)
+    assert abs(r[O.C_SB]) < 1e-15
+    assert r[O.C_U] == pytest.approx(32.0, abs=1e-12) and r[O.C_V] == pytest.approx(24.0, abs=1e-12)
+    assert r[O.C_QA] == pytest.approx(1 / var, rel=1e-12)
+    assert r[O.C_Z] == z and r[O.C_Z32] == z
+
+
+def test_pinhole_mean_and_pose():
+    # a rotated, translated camera: the mean lands where the pinhole model says
+    R = Rotation.from_euler("xyz", [0.1, -0.2, 0.3]).as_matrix()
+    t = np.array([0.2, -0.1, 0.5])
+    cam = S.Camera(80, 60, 70.0, 65.0, 41.0, 29.0, np.concatenate([R, t[:, None]], 1), 0)
+    mu = np.array([0.3, 0.2, 2.5])
+    P = _params([mu], [[-3, -3, -3]], [[1, 0, 0, 0]], [1.0], [[0, 0, 0]])
+    r = O.project(P, [cam], CFG)[0]
+    pc = R @ mu + t
+    assert r[O.C_U] == pytest.approx(70.0 * pc[0] / pc[2] + 41.0, rel=1e-13)
+    assert r[O.C_V] == pytest.approx(65.0 * pc[1] / pc[2] + 29.0, rel=1e-13)
+    assert r[O.C_Z] == pytest.approx(pc[2], rel=1e-15)
+
+
+def test_image_covariance_is_linearised_pinhole():
+    # Sigma' - dil*I = J (R Sigma R^T) J^T with J the derivative of the pinhole
+    # map, here taken by central differences of (fx x/z + cx, fy y/z + cy)
+    rng = np.random.default_rng(5)
+    R = Rotation.from_euler("xyz", [0.05, 0.1, -0.3]).as_matrix()
+    t = np.array([0.1, 0.0, 0.2])
+    cam = S.Camera(100, 80, 90.0, 85.0, 50.0, 40.0, np.concatenate([R, t[:, None]], 1), 0)
+    for _ in range(10):
+        mu = np.array([rng.uniform(-0.5, 0.5), rng.uniform(-0.4, 0.4), rng.uniform(1.5, 4)])
+        q = rng.normal(size=4)
+        s = rng.normal(-2.5, 0.5, 3)
+        P = _params([mu], [s], [q], [1.0], [[0, 0, 0]])
+        r = O.project(P, [cam], CFG)[0]
+        pc = R @ mu + t
+
+        def pin(p):
+            return np.array([90.0 * p[0] / p[2] + 50.0, 85.0 * p[1] / p[2] + 40.0])
+        J = np.zeros((2, 3))
+        for k in range(3):
+            e = np.zeros(3); e[k] = 1e-6
+            J[:, k] = (pin(pc + e) - pin(pc - e)) / 2e-6
+        Sc = R @ O.cov3d(q, s) @ R.T
+        S2 = J @ Sc @ J.T
+        dil = float(np.float32(0.3))
+        assert np.allclose([r[O.C_SA] - dil, r[O.C_SB], r[O.C_SC] - dil],
+                           [S2[0, 0], S2[0, 1], S2[1, 1]], rtol=1e-7, atol=1e-9)
+
+
+def test_near_plane_culls():
+    cam = _cam()
+    P = _params([[0, 0, 0.19], [0, 0, 0.21]], [[-3] * 3] * 2, [[1, 0, 0, 0]] * 2, [2.0, 2.0],
+                [[0, 0, 0]] * 2)
+    rec = O.project(P, [cam], CFG)
+    assert rec[0, O.C_VIS] == 0 and rec[1, O.C_VIS] == 1
+
+
+# ---------------------------------------------------------------------------
+# colour
+# ---------------------------------------------------------------------------
+
+def test_sh_basis_orthonormal():
+    # Gauss-Legendre in cos(theta) x uniform phi: exact for the degree <= 6
+    # products of degree-3 harmonics
+    xg, wg = np.polynomial.legendre.leggauss(16)
+    nphi = 32
+    phis = 2 * np.pi * np.arange(nphi) / nphi
+    G = np.zeros((16, 16))
+    for ct, w in zip(xg, wg):
+        st = math.sqrt(1 - ct * ct)
+        for ph in phis:
+            d = np.array([st * math.cos(ph), st * math.sin(ph), ct])
+            Y = O.sh_basis(3, d)
+            G += w * (2 * np.pi / nphi) * np.outer(Y, Y)
+    assert np.allclose(G, np.eye(16), atol=1e-12)
+
+
+def test_sh_degree0_reproduces_rgb():
+    cam = _cam()
+    rgb = np.array([0.1, 0.6, 0.95])
+    sh0 = (rgb - 0.5) * 2 * math.sqrt(math.pi)
+    P = _params([[0.1, 0.05, 2.0]], [[-3] * 3], [[1, 0, 0, 0]], [2.0], [sh0])
+    r = O.project(P, [cam], CFG)[0]
+    assert np.allclose(r[[O.C_R, O.C_G, O.C_B]], rgb, atol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# compositing
+# ---------------------------------------------------------------------------
+
+def test_single_isotropic_gaussian_closed_form():
+    W, H, f, z, sc = 40, 32, 50.0, 2.0, 0.04
+    cam = _cam(W, H, f)
+    omega, rgb = 1.3, np.array([0.2, 0.7, 0.4])
+    sh0 = (rgb - 0.5) * 2 * math.sqrt(math.pi)
+    P = _params([[0, 0, z]], [[math.log(sc)] * 3], [[1, 0, 0, 0]], [omega], [sh0])
+    rec, keys, vals, ranges, out = O.forward(P, [cam], CFG)
+    o = 1 / (1 + math.exp(-omega))
+    var = (f * sc / z) ** 2 + float(np.float32(0.3))
+    amin, amax = float(np.float32(1 / 255)), float(np.float32(0.99))
+    ys, xs = np.mgrid[0:H, 0:W]
+    d2 = (xs + 0.5 - W / 2) ** 2 + (ys + 0.5 - H / 2) ** 2
+    raw = o * np.exp(-0.5 * d2 / var)
+    al = np.where(raw >= amin, np.minimum(amax, raw), 0.0).ravel()
+    assert np.allclose(out["alpha"], al, atol=1e-14)
+    assert np.allclose(out["depth"], al * z, atol=1e-13)
+    for c in range(3):
+        assert np.allclose(out["rgb"][c * W * H:(c + 1) * W * H], al * rgb[c], atol=1e-14)
+    assert (out["alpha"] > 0).sum() > 20
+
+
+def test_stacked_alphas_and_stop_rule():
+    # k identical opaque discs at increasing depth: T after j blends = (1-a)^j;
+    # the fragment that would take T below t_min is not blended
+    cam = _cam(16, 16, 20.0)
+    a = 0.95
+    omega = math.log(a / (1 - a))
+    n = 6
+    P = _params([[0, 0, 1.0 + 0.1 * i] for i in range(n)], [[math.log(0.5)] * 3] * n,
+                [[1, 0, 0, 0]] * n, [omega] * n, [[1.0, 1.0, 1.0]] * n)
+    rec, keys, vals, ranges, out = O.forward(P, [cam], CFG)
+    pix = 8 * 16 + 8
+    # near the centre alpha ~ a; T: 0.05, 2.5e-3, 1.25e-4, then 6.25e-6 < 1e-4 stops
+    assert out["nblend"][pix] == 3
+    T = out["T"][pix]
+    assert 1e-4 <= T < 2e-4
+    assert out["alpha"][pix] == pytest.approx(1 - T, rel=0, abs=1e-15)
+
+
+def test_weights_sum_to_alpha():
+    # with every colour equal to 1, each channel equals the accumulated alpha
+    sc = S.random_box_scene(300, 48, 40, 45.0, seed=2)
+    sh = np.zeros_like(sc.sh)
+    sh[:, 0, :] = 0.5 * 2 * math.sqrt(math.pi)
+    P = O.Params(sc.means, sc.log_scales, sc.quats, sc.opacity_logits, sh, 0, sc.submap_offsets)
+    cams = O.as_float32_cameras(sc.cameras)
+    rec, keys, vals, ranges, out = O.forward(P, cams, CFG)
+    npx = 48 * 40
+    for c in range(3):
+        assert np.allclose(out["rgb"][c * npx:(c + 1) * npx], out["alpha"], atol=1e-13)
+    assert np.all(out["T"] >= float(np.float32(1e-4)))
+    assert np.allclose(out["alpha"], 1 - out["T"], atol=0)
+    # the alpha-weighted depth lies between the nearest and farthest blended depth
+    zs = rec[rec[:, O.C_VIS] > 0, O.C_Z]
+    m = out["alpha"] > 0
+    dn = out["depth"][m] / out["alpha"][m]
+    assert dn.min() >= zs.min() - 1e-12 and dn.max() <= zs.max() + 1e-12
+
+
+# ---------------------------------------------------------------------------
+# binning and tiling
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("tile", [(8, 8), (16, 16), (16, 32)])
+def test_tiled_equals_brute_force(tile):
+    cfg = O.Config(tile_w=tile[0], tile_h=tile[1])
+    sc = S.random_box_scene(500, 72, 56, 60.0, seed=11, sh_degree=3)
+    P = O.Params.from_scene(sc)
+    cams = O.as_float32_cameras(sc.cameras)
+    rec, keys, vals, ranges, out = O.forward(P, cams, cfg)
+    br = O.render_brute(P, cams, cfg, rec)
+    for k in ("rgb", "depth", "alpha", "T", "nblend", "sig"):
+        assert np.array_equal(out[k], br[k]), k
+    assert out["nblend"].max() >= 3
+
+
+def test_keys_rebuilt_with_numpy_stable_sort():
+    cfg = O.Config(tile_w=8, tile_h=8)
+    sc = S.uneven_submaps(3, 200, 800, seed=4, scale=1.0, resolutions=((48, 40), (64, 32)))
+    P = O.Params.from_scene(sc)
+    cams = O.as_float32_cameras(sc.cameras)
+    rec = O.project(P, cams, cfg)
+    keys, vals, ranges = O.bin(P, cams, cfg, rec)
+    # independent rebuild: per view, per visible pair, per tile; then argsort
+    ek, ev = [], []
+    toff, poff = 0, 0
+    for v, c in enumerate(cams):
+        ntx, nty = -(-c.width // 8), -(-c.height // 8)
+        ng = int(sc.submap_offsets[c.submap + 1] - sc.submap_offsets[c.submap])
+        for k in range(ng):
+            r = rec[poff + k]
+            if r[O.C_VIS] == 0:
+                continue
+            zb = np.array([r[O.C_Z32]], np.float32).view(np.uint32)[0]
+            for ty in range(int(r[O.C_TY0]), int(r[O.C_TY1]) + 1):
+                for tx in range(int(r[O.C_TX0]), int(r[O.C_TX1]) + 1):
+                    ek.append((np.uint64(toff + ty * ntx + tx) << np.uint64(32)) | np.uint64(zb))
+                    ev.append(poff + k)
+        toff += ntx * nty
+        poff += ng
+    ek, ev = np.array(ek, np.uint64), np.array(ev, np.int64)
+    order = np.argsort(ek, kind="stable")
+    assert np.array_equal(keys, ek[order]) and np.array_equal(vals, ev[order])
+    tiles = (keys >> np.uint64(32)).astype(np.int64)
+    for t in range(ranges.shape[0]):
+        idx = np.nonzero(tiles == t)[0]
+        if len(idx):
+            assert ranges[t, 0] == idx[0] and ranges[t, 1] == idx[-1] + 1
+        else:
+            assert ranges[t, 0] == ranges[t, 1] == 0
+    # views only see the Gaussians of their own submap
+    g = rec[:, O.C_GAUSS].astype(int)
+    vw = rec[:, O.C_VIEW].astype(int)
+    for v, c in enumerate(cams):
+        gs = g[vw == v]
+        assert gs.min() >= sc.submap_offsets[c.submap] and gs.max() < sc.submap_offsets[c.submap + 1]
+
+
+# ---------------------------------------------------------------------------
+# backward: central differences and the translation identity
+# ---------------------------------------------------------------------------
+
+def _se3_left(T, xi):
+    rho, phi = xi[:3], xi[3:]
+    th = np.linalg.norm(phi)
+    K = np.array([[0, -phi[2], phi[1]], [phi[2], 0, -phi[0]], [-phi[1], phi[0], 0]])
+    if th < 1e-12:
+        R, V = np.eye(3) + K, np.eye(3) + 0.5 * K
+    else:
+        R = np.eye(3) + math.sin(th) / th * K + (1 - math.cos(th)) / th ** 2 * K @ K
+        V = np.eye(3) + (1 - math.cos(th)) / th ** 2 * K + (th - math.sin(th)) / th ** 3 * K @ K
+    return np.concatenate([R @ T[:, :3], (R @ T[:, 3] + V @ rho)[:, None]], 1)
+
+
+def _fd_case(scene, cams, n_samples, seed, h=1e-7):
+    P = O.Params.from_scene(scene)
+    rng = np.random.default_rng(seed)
+    npx = sum(c.width * c.height for c in cams)
+    wC, wD, wA = rng.normal(size=3 * npx), 0.1 * rng.normal(size=npx), rng.normal(size=npx)
+    rec = O.project(P, cams, CFG)
+    vis = np.unique(rec[rec[:, O.C_VIS] > 0, O.C_GAUSS].astype(int))
+    pix_view = np.concatenate([np.full(c.width * c.height, v) for v, c in enumerate(cams)])
+    rgb_pix = np.concatenate([np.tile(np.arange(c.width * c.height) + sum(d.width * d.height for d in cams[:v]), 3)
+                              for v, c in enumerate(cams)])
+    del pix_view
+
+    def run(Pp, cc):
+        return O.forward(Pp, cc, CFG)[4]
+
+    def masked(flip):
+        keep = ~flip
+        return wC * keep[rgb_pix], wD * keep, wA * keep
+
+    def check(Pp, Pm, cp, cm, pick):
+        op, om = run(Pp, cp), run(Pm, cm)
+        flip = op["sig"] != om["sig"]
+        mC, mD, mA = masked(flip)
+        fd = (mC @ (op["rgb"] - om["rgb"]) + mD @ (op["depth"] - om["depth"]) +
+              mA @ (op["alpha"] - om["alpha"])) / (2 * h)
+        r0, k0, v0, rg0, o0 = O.forward(P, cams, CFG)
+        g = O.render_bwd(P, cams, CFG, r0, v0, rg0, mC, mD, mA)
+        return fd, pick(g), int(flip.sum())
+
+    results = []
+    for name in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+        for _ in range(n_samples):
+            gi = int(rng.choice(vis))
+            A = getattr(P, name)
+            idx = (gi,) + tuple(int(rng.integers(0, s)) for s in A.shape[1:])
+            Pp, Pm = P.copy(), P.copy()
+            getattr(Pp, name)[idx] += h
+            getattr(Pm, name)[idx] -= h
+            fd, an, nf = check(Pp, Pm, cams, cams, lambda g: g[name][idx])
+            results.append((name, fd, an, nf))
+    for v in range(len(cams)):
+        for k in range(6):
+            xi = np.zeros(6); xi[k] = h
+            cp, cm = copy.deepcopy(cams), copy.deepcopy(cams)
+            cp[v].T_cw = _se3_left(cams[v].T_cw, xi)
+            cm[v].T_cw = _se3_left(cams[v].T_cw, -xi)
+            fd, an, nf = check(P, P, cp, cm, lambda g: g["pose"][v, k])
+            results.append((f"pose{v}.{k}", fd, an, nf))
+    return results
+
+
+def _assert_fd(results, rtol=1e-5):
+    scale = {}
+    for name, fd, an, _ in results:
+        key = name.split(".")[0].rstrip("0123456789") if name.startswith("pose") else name
+        scale[key] = max(scale.get(key, 0.0), abs(an))
+    for name, fd, an, nf in results:
+        key = name.split(".")[0].rstrip("0123456789") if name.startswith("pose") else name
+        # relative to the gradient and, for near-zero entries, to the tensor's scale
+        tol = rtol * max(abs(an), 1e-3 * scale[key]) + 1e-9
+        assert abs(fd - an) <= tol, (name, fd, an, nf)
+
+
+def test_fd_box_scene_sh3():
+    sc = S.random_box_scene(250, 48, 40, 45.0, seed=7, sh_degree=3)
+    cams = O.as_float32_cameras(sc.cameras)
+    _assert_fd(_fd_case(sc, cams, 4, seed=1))
+
+
+def test_fd_orchard_crop_posed_rig():
+    # the pose-gradient workload at toy size: orchard rows, a perturbed 4-camera
+    # rig, every camera cropped to a 64x48 window around its principal point
+    sc = S.orchard_scene(6_000, 3, 4, 1440, 1080, rear=True, pose_noise=True,
+                         lidar_per_view=0, seed=3)
+    cams = [c.crop(int(c.cx) - 32, int(c.cy) - 24, 64, 48) for c in sc.cameras]
+    cams = O.as_float32_cameras(cams)
+    res = _fd_case(sc, cams, 3, seed=2)
+    _assert_fd(res)
+    assert sum(1 for r in res if r[0].startswith("pose")) == 24
+
+
+def test_translation_identity():
+    # shifting every mean by delta equals moving the camera by -delta:
+    # dL/drho = R_b sum_g dL/dmu_g for a single view
+    sc = S.random_box_scene(300, 48, 40, 45.0, seed=9, sh_degree=3)
+    P = O.Params.from_scene(sc)
+    cams = O.as_float32_cameras(sc.cameras)
+    R = np.array([[0.96, -0.2, 0.19], [0.21, 0.98, -0.03], [-0.18, 0.07, 0.98]])
+    u, _, vt = np.linalg.svd(R)
+    cams[0].T_cw = np.concatenate([u @ vt, np.array([[0.1], [-0.05], [0.3]])], 1)
+    rng = np.random.default_rng(0)
+    npx = 48 * 40
+    rec, keys, vals, ranges, out = O.forward(P, cams, CFG)
+    g = O.render_bwd(P, cams, CFG, rec, vals, ranges, rng.normal(size=3 * npx),
+                     rng.normal(size=npx), rng.normal(size=npx))
+    lhs = cams[0].T_cw[:, :3] @ g["means"].sum(0)
+    assert np.allclose(g["pose"][0, :3], lhs, rtol=1e-10, atol=1e-10)
+    assert np.abs(g["pose"][0, 3:]).max() > 0
+
+
+# ---------------------------------------------------------------------------
+# losses, Eqs. (6)-(7)
+# ---------------------------------------------------------------------------
+
+def test_kl_closed_form_by_integration():
+    from scipy.integrate import quad
+    for (m1, s1, m2, s2) in [(3.0, 0.05, 3.1, 0.05), (2.0, 0.1, 1.7, 0.3), (5.0, 0.5, 5.0, 0.2)]:
+        p = lambda x: math.exp(-0.5 * ((x - m1) / s1) ** 2) / (s1 * math.sqrt(2 * math.pi))
+        q = lambda x: math.exp(-0.5 * ((x - m2) / s2) ** 2) / (s2 * math.sqrt(2 * math.pi))
+        val, _ = quad(lambda x: p(x) * (math.log(p(x)) - math.log(q(x))) if p(x) > 0 else 0.0,
+                      m1 - 12 * s1, m1 + 12 * s1, limit=200, epsabs=1e-13, epsrel=1e-12)
+        assert O.kl_normal(m1, s1, m2, s2) == pytest.approx(val, rel=1e-8, abs=1e-10)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_depth_loss_gradient_and_validity(mode):
+    rng = np.random.default_rng(1)
+    cams = [_cam(20, 16, 20.0), _cam(12, 10, 15.0)]
+    P = O.Params(np.zeros((1, 3)), np.zeros((1, 3)), np.ones((1, 4)), np.zeros(1),
+                 np.zeros((1, 1, 3)), 0, np.array([0, 1]))
+    npx = 20 * 16 + 12 * 10
+    depth = rng.uniform(1, 5, npx)
+    alpha = rng.uniform(0, 1, npx)
+    alpha[rng.random(npx) < 0.2] = 0.0
+    lid = np.stack([rng.uniform(-2, 22, 300), rng.uniform(-2, 18, 300), rng.uniform(0.1, 6, 300),
+                    rng.integers(0, 2, 300)], 1)
+    loss, grad, nv = O.depth_loss(P, cams, CFG, depth, alpha, lid, mode=mode, sigma_L=0.05,
+                                  sigma_U=0.08, lam=0.7)
+    # count of valid points by the stated rule
+    cnt = 0
+    for u, v, z, vw in lid:
+        c = cams[int(vw)]
+        if 0 <= u < c.width and 0 <= v < c.height and z > 0.2:
+            off = 0 if vw == 0 else 320
+            if alpha[off + int(v) * c.width + int(u)] > 0:
+                cnt += 1
+    assert nv == cnt and nv > 50
+    h = 1e-6
+    for pix in rng.choice(np.nonzero(grad)[0], 10, replace=False):
+        dp, dm = depth.copy(), depth.copy()
+        dp[pix] += h
+        dm[pix] -= h
+        fd = (O.depth_loss(P, cams, CFG, dp, alpha, lid, mode, 0.05, 0.08, 0.7)[0] -
+              O.depth_loss(P, cams, CFG, dm, alpha, lid, mode, 0.05, 0.08, 0.7)[0]) / (2 * h)
+        assert fd == pytest.approx(grad[pix], rel=1e-6, abs=1e-9)
+
+
+def test_image_l1_gradient():
+    rng = np.random.default_rng(2)
+    C, I = rng.random(50), rng.random(50)
+    loss, g = O.image_l1(C, I)
+    assert loss == pytest.approx(np.abs(C - I).sum() / 50)
+    h = 1e-7
+    for i in range(0, 50, 7):
+        Cp, Cm = C.copy(), C.copy()
+        Cp[i] += h
+        Cm[i] -= h
+        assert (O.image_l1(Cp, I)[0] - O.image_l1(Cm, I)[0]) / (2 * h) == pytest.approx(g[i], rel=1e-6)
