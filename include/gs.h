@@ -1,0 +1,192 @@
+/*
+ * gs.h - C ABI of the GB300 multi-view Gaussian-splatting library
+ * (libgsraster.so, built from paper_2510_26358_gb300/csrc).
+ *
+ * The library renders B cameras of one shared set of 3-D Gaussians and
+ * back-propagates to every Gaussian parameter and to each camera's SE(3)
+ * pose, as the multi-view mapping of AgriGS-SLAM describes (Sec. III-B,
+ * Eqs. 2-4: a single shared splat set, per-camera EWA projection
+ * Sigma' = J W Sigma W^T J^T; Sec. III-C, Eqs. 6-8: photometric and
+ * probabilistic LiDAR depth losses whose gradients also refine the poses).
+ *
+ * Conventions
+ *  - Every pointer marked (device) is CUDA device memory owned by the caller.
+ *    The library owns only the workspace, which gs_workspace_create allocates
+ *    once; no other call allocates, frees or synchronises.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream). All work of a call is enqueued on it, in order.
+ *  - Gaussians are float32 structure-of-arrays: means [N][3], log_scales
+ *    [N][3], quats [N][4] as (w,x,y,z) (normalised inside), opacity_logits
+ *    [N], sh [N][K][3] with K = (sh_degree+1)^2 (real orthonormal basis,
+ *    ordered by l then m = -l..l, no Condon-Shortley phase).
+ *  - Submaps: the Gaussian array is partitioned by submap_offsets [S+1];
+ *    camera v renders only the Gaussians of its submap.
+ *  - Cameras: OpenCV axes (x right, y down, z forward); T_cw is the row-major
+ *    3x4 world->camera transform [R | t]. Pixel (i,j) is sampled at its centre.
+ *  - Images are planar float32, views concatenated: view v's RGB occupies
+ *    rgb[3*pix_off[v] .. 3*pix_off[v] + 3*W*H) as [3][H][W]; depth and alpha
+ *    occupy [pix_off[v] .. pix_off[v] + W*H) as [H][W]; pix_off[v] is the sum
+ *    of W*H over the views before v.
+ *  - Gradients are accumulated (+=) into the caller's buffers.
+ *  - Errors: argument errors return at once and enqueue nothing. Conditions
+ *    found on the device (instance capacity exceeded) set a flag in the
+ *    workspace that lasts until the next gs_bin_sort; the kernels that follow
+ *    then work on empty lists (blank images, zero gradients) and
+ *    gs_workspace_status reports the flag. Nothing traps or aborts.
+ */
+#ifndef GS_H
+#define GS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GS_MAX_VIEWS 64
+#define GS_MAX_SUBMAPS 64
+
+typedef enum {
+    GS_OK = 0,
+    GS_ERR_INVALID_ARG = 1, /* a pointer, size or configuration value is out of range */
+    GS_ERR_CAPACITY = 2,    /* more (view, Gaussian, tile) instances than the workspace holds */
+    GS_ERR_CUDA = 3,        /* a CUDA runtime call failed (message: gs_last_error) */
+    GS_ERR_STATE = 4        /* calls out of order (e.g. gs_render_fwd before gs_bin_sort) */
+} gs_status;
+
+/* One pinhole camera (80 bytes). */
+typedef struct {
+    int32_t width, height; /* image size in pixels, 1..16384 */
+    int32_t submap;        /* index of the submap this camera renders */
+    int32_t reserved;      /* must be 0 */
+    float fx, fy, cx, cy;  /* focal lengths and principal point, pixels */
+    float T_cw[12];        /* row-major [R | t], world -> camera */
+} gs_camera;
+
+/* Renderer constants (the paper leaves them to standard 3DGS). */
+typedef struct {
+    int32_t tile_w, tile_h; /* tile size in pixels: 8x8, 16x16, 16x32 or 32x16 */
+    int32_t batch_depth;    /* Gaussians staged per shared-memory batch: 32..256, multiple of 32 */
+    int32_t depth_mode;     /* gs_depth_loss: 0 = L1 |D - z|, 1 = KL of Eq. (7) with fixed sigma_U */
+    float near_z;           /* pairs with view-space z <= near_z are culled (0.2 m) */
+    float dilation;         /* added to the diagonal of Sigma' (0.3 px^2) */
+    float alpha_min;        /* fragments with alpha < alpha_min are skipped (1/255) */
+    float alpha_max;        /* alpha = min(alpha_max, o*exp(-d^T Sigma'^-1 d / 2)) (0.99) */
+    float t_min;            /* a fragment that would take T below t_min ends the pixel (1e-4) */
+    float jac_clamp;        /* tangent clamp of the projection Jacobian, x max(cx,W-cx)/fx (1.3) */
+    float ext_rel_pad;      /* relative padding of the support extent used for tiles (1e-3) */
+    float ext_abs_pad;      /* absolute padding of that extent, pixels (1e-2) */
+    float sigma_L;          /* LiDAR standard deviation of Eq. (7), metres (0.05) */
+    float sigma_U;          /* rendered-depth standard deviation of Eq. (7), metres (0.05) */
+    float lambda_L;         /* weight lambda_L of Eq. (7) (1) */
+    float reserved;         /* must be 0 */
+} gs_config;
+
+/* Gaussian parameters (device, float32, C-contiguous). */
+typedef struct {
+    const float *means, *log_scales, *quats, *opacity_logits, *sh;
+    int64_t n; /* must equal submap_offsets[n_submaps] given at workspace creation */
+} gs_gaussians;
+
+/* Gradient outputs (device, accumulated). pose, densify_acc and densify_cnt
+ * may be NULL. densify_acc[g] += ||dL/d(u,v)|| (pixels) and densify_cnt[g] += 1
+ * for every view in which Gaussian g is visible. */
+typedef struct {
+    float *means, *log_scales, *quats, *opacity_logits, *sh;
+    float *pose;        /* [n_views][6]: dL/d(rho, phi) of the left perturbation exp(xi^) T_cw */
+    float *densify_acc; /* [N] */
+    int32_t *densify_cnt; /* [N] */
+} gs_grads;
+
+typedef struct gs_workspace gs_workspace;
+
+/* Fill *cfg with the defaults quoted above (16x16 tiles, depth 256, L1 depth loss). */
+void gs_config_default(gs_config *cfg);
+
+/* Create a workspace for a fixed camera geometry and submap partition.
+ * cams (host, n_views entries, 1..GS_MAX_VIEWS): sizes and submap ids are
+ *   fixed here; intrinsics and poses are read from the device copy given to
+ *   each call, so poses may change between calls (and CUDA-graph replays).
+ * submap_offsets (host, n_submaps+1 entries, 1..GS_MAX_SUBMAPS, nondecreasing,
+ *   offsets[0] = 0).
+ * sh_degree 0..3. inst_capacity: maximum (view, Gaussian, tile) instances per
+ * iteration (gs_workspace_status reports the number needed).
+ * Allocates all device memory the other calls use (on the current device). */
+gs_status gs_workspace_create(const gs_camera *cams, int32_t n_views, const int64_t *submap_offsets,
+                              int32_t n_submaps, int32_t sh_degree, const gs_config *cfg,
+                              int64_t inst_capacity, gs_workspace **out);
+void gs_workspace_destroy(gs_workspace *ws);
+
+/* Per-camera projection (Eqs. 3-4): for every (view, Gaussian) pair of the
+ * same submap, Sigma = R S S^T R^T from the normalised quaternion and
+ * exp(log_scale), p = W mu + t, near-plane cull, Sigma' = J W Sigma W^T J^T
+ * + dilation*I, its inverse, opacity sigmoid(omega), the extent of the
+ * alpha >= alpha_min ellipse and the tiles it covers, and the SH colour seen
+ * from the camera centre.  cams_dev: (device) n_views gs_camera, same sizes
+ * and submaps as at creation. */
+gs_status gs_project(gs_workspace *ws, const gs_gaussians *g, const gs_camera *cams_dev, void *stream);
+
+/* Binning: one instance per (visible pair, covered tile), ordered by the
+ * 64-bit key (global tile id << 32 | float bits of the view depth), ties by
+ * (view, Gaussian index); per-tile [start, end) ranges. Stable on-device
+ * radix sorts (depth of the visible pairs, then tile id of the instances). */
+gs_status gs_bin_sort(gs_workspace *ws, void *stream);
+
+/* Front-to-back alpha compositing of every tile's list into rgb (device,
+ * planar, 3*N_pix), depth (device, N_pix: sum of alpha*T*z, not normalised)
+ * and alpha (device, N_pix: 1 - T).  Keeps, per pixel, the number of list
+ * entries up to the last blended fragment and the final T for the backward. */
+gs_status gs_render_fwd(gs_workspace *ws, float *rgb, float *depth, float *alpha, void *stream);
+
+/* LiDAR depth consistency (Eq. 7).  lidar (device, [n_pts][4] float32 rows
+ * u, v, z, view): pixel (floor u, floor v) of view `view`; a point is valid if
+ * it lies inside the image, z > near_z and alpha > 0 there.  depth_mode 0:
+ * mean |D - z|; 1: mean KL(N(z, sigma_L^2) || N(D, sigma_U^2)).  Times
+ * lambda_L.  loss (device, 1 float) receives the value; dL_ddepth (device,
+ * N_pix, nullable) is accumulated with dL/dD.  Zero valid points give 0. */
+gs_status gs_depth_loss(gs_workspace *ws, const float *depth, const float *alpha, const float *lidar,
+                        int64_t n_pts, float *loss, float *dL_ddepth, void *stream);
+
+/* L1 photometric term of Eq. (6) (with the SSIM weight lambda = 0):
+ * loss = mean |rgb - target| over 3*N_pix values, dL_drgb += sign(rgb -
+ * target) / (3*N_pix) (nullable). rgb, target, dL_drgb: (device) planar. */
+gs_status gs_image_l1(gs_workspace *ws, const float *rgb, const float *target, float *loss,
+                      float *dL_drgb, void *stream);
+
+/* Backward of gs_render_fwd and gs_project: walks each tile's list back to
+ * front from the last blended fragment, recomputing alpha, reduces each
+ * Gaussian's contributions across the warp before one atomic per component,
+ * then chains to the parameters and, through the projection, to each
+ * camera's pose twist.  dL_drgb, dL_ddepth (device, planar like the outputs),
+ * dL_dalpha (device, nullable).  g and cams_dev must be those of the
+ * preceding gs_project. */
+gs_status gs_render_bwd(gs_workspace *ws, const gs_gaussians *g, const gs_camera *cams_dev,
+                        const float *dL_drgb, const float *dL_ddepth, const float *dL_dalpha,
+                        const gs_grads *out, void *stream);
+
+/* Synchronise `stream` and report device-side conditions: returns
+ * GS_ERR_CAPACITY if the last gs_bin_sort needed more instances than the
+ * capacity. Any out pointer may be NULL. */
+gs_status gs_workspace_status(gs_workspace *ws, void *stream, int64_t *n_instances, int64_t *n_visible);
+
+/* Sizes of the workspace: info[0] n_pairs, [1] n_tiles, [2] n_pix, [3]
+ * inst_capacity, [4] n_views, [5] N, [6] bytes of device memory held. */
+gs_status gs_workspace_info(gs_workspace *ws, int64_t *info, int32_t n_info);
+
+/* Copy an internal buffer to `dst` (device) for inspection; bytes must equal
+ * the buffer size reported through *bytes when dst is NULL.
+ * which: 0 records [n_pairs][12] f32, 1 pair depth keys [n_pairs] u32,
+ * 2 tile rectangles [n_pairs][4] i16, 3 sorted instance tile ids [capacity]
+ * u32, 4 sorted instance pair ids [capacity] u32, 5 tile ranges [n_tiles][2]
+ * u32, 6 per-pixel list count up to the last blended fragment [N_pix] u32,
+ * 7 per-pixel final T [N_pix] f32, 8 image-space gradients [n_pairs][10] f32. */
+gs_status gs_workspace_copy(gs_workspace *ws, int32_t which, void *dst, int64_t *bytes, void *stream);
+
+const char *gs_status_string(gs_status s);
+/* Text of the last CUDA error seen by this thread's calls ("" if none). */
+const char *gs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GS_H */

@@ -1,0 +1,175 @@
+// Losses of Sec. III-C.
+//
+// Depth consistency (Eq. 7): each LiDAR return (u, v, z, view) reads the
+// rendered depth at pixel (floor u, floor v).  A return is valid when it lies
+// inside the image, z > near_z and the pixel's alpha > 0.  Mode 0 averages
+// |D - z|; mode 1 averages KL(N(z, sigma_L^2) || N(D, sigma_U^2)) =
+// ln(sigma_U/sigma_L) + (sigma_L^2 + (z - D)^2) / (2 sigma_U^2) - 1/2; both are
+// scaled by lambda_L.  The gradient dL/dD = lambda_L/|Omega| dl/dD is added to
+// the pixel (atomically: several returns may share a pixel).
+//
+// Photometric L1 (Eq. 6 with lambda = 0): mean |C - I| over every channel of
+// every pixel of every view, gradient sign(C - I)/n.
+//
+// Sums are deterministic: per-block partials in double, then one block adds
+// them in block order.
+#include "gs_internal.cuh"
+
+namespace gs {
+namespace {
+
+constexpr int LT = 256;
+
+__device__ __forceinline__ double block_sum_d(double v, double *sm) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sm[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sm[i];
+    return t;
+}
+
+struct DepthArgs {
+    const ViewInfo *views;
+    int32_t n_views, mode;
+    float near_z, sigma_L, sigma_U, lambda;
+    const float *depth, *alpha, *lidar;
+    int64_t n_pts;
+    double *part;  // [2][nb]
+    int nb;
+    float *loss;
+    float *grad;
+    DevState *st;
+};
+
+// returns the pixel index or -1 if the return is not valid
+__device__ __forceinline__ int64_t lidar_pixel(const DepthArgs &A, int64_t i, float &z) {
+    const float4 L = reinterpret_cast<const float4 *>(A.lidar)[i];
+    int v = (int)L.w;
+    z = L.z;
+    if (!(L.w >= 0.f) || v >= A.n_views) return -1;
+    const ViewInfo vi = A.views[v];
+    if (!(L.x >= 0.f && L.x < (float)vi.W && L.y >= 0.f && L.y < (float)vi.H && L.z > A.near_z)) return -1;
+    int64_t pix = vi.pix_off + (int64_t)floorf(L.y) * vi.W + (int64_t)floorf(L.x);
+    if (!(A.alpha[pix] > 0.f)) return -1;
+    return pix;
+}
+
+__global__ void __launch_bounds__(LT) k_depth_partial(DepthArgs A) {
+    __shared__ double sm[32];
+    double s = 0.0, c = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * LT + threadIdx.x; i < A.n_pts; i += (int64_t)gridDim.x * LT) {
+        float z;
+        int64_t pix = lidar_pixel(A, i, z);
+        if (pix < 0) continue;
+        double D = A.depth[pix], d = D - (double)z;
+        if (A.mode == 0) {
+            s += fabs(d);
+        } else {
+            double sl = A.sigma_L, su = A.sigma_U;
+            s += log(su / sl) + (sl * sl + d * d) / (2.0 * su * su) - 0.5;
+        }
+        c += 1.0;
+    }
+    double ts = block_sum_d(s, sm);
+    double tc = block_sum_d(c, sm);
+    if (threadIdx.x == 0) {
+        A.part[blockIdx.x] = ts;
+        A.part[A.nb + blockIdx.x] = tc;
+    }
+}
+
+__global__ void __launch_bounds__(LT) k_depth_final(DepthArgs A) {
+    __shared__ double sm[32];
+    double s = 0.0, c = 0.0;
+    // fixed order: each thread a fixed strided set, then a fixed tree
+    for (int i = threadIdx.x; i < A.nb; i += LT) {
+        s += A.part[i];
+        c += A.part[A.nb + i];
+    }
+    double ts = block_sum_d(s, sm);
+    double tc = block_sum_d(c, sm);
+    if (threadIdx.x == 0) {
+        double scale = tc > 0.0 ? (double)A.lambda / tc : 0.0;
+        *A.loss = (float)(ts * scale);
+        A.st->depth_scale = (float)scale;
+        A.st->depth_valid = (uint32_t)tc;
+    }
+}
+
+__global__ void __launch_bounds__(LT) k_depth_grad(DepthArgs A) {
+    const float scale = A.st->depth_scale;
+    if (scale == 0.f) return;
+    const float iv = 1.f / (A.sigma_U * A.sigma_U);
+    for (int64_t i = (int64_t)blockIdx.x * LT + threadIdx.x; i < A.n_pts; i += (int64_t)gridDim.x * LT) {
+        float z;
+        int64_t pix = lidar_pixel(A, i, z);
+        if (pix < 0) continue;
+        float d = A.depth[pix] - z;
+        float g = A.mode == 0 ? (d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f)) : d * iv;
+        atomicAdd(A.grad + pix, scale * g);
+    }
+}
+
+__global__ void __launch_bounds__(LT) k_l1_partial(const float *rgb, const float *target, int64_t n,
+                                                  float *grad, double *part) {
+    __shared__ double sm[32];
+    double s = 0.0;
+    const float inv = (float)(1.0 / (double)n);
+    for (int64_t i = (int64_t)blockIdx.x * LT + threadIdx.x; i < n; i += (int64_t)gridDim.x * LT) {
+        float d = rgb[i] - target[i];
+        s += fabs((double)d);
+        if (grad) grad[i] += d > 0.f ? inv : (d < 0.f ? -inv : 0.f);
+    }
+    double t = block_sum_d(s, sm);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(LT) k_l1_final(const double *part, int nb, int64_t n, float *loss) {
+    __shared__ double sm[32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nb; i += LT) s += part[i];
+    double t = block_sum_d(s, sm);
+    if (threadIdx.x == 0) *loss = (float)(t / (double)n);
+}
+
+}  // namespace
+
+gs_status launch_depth_loss(gs_workspace *ws, const float *depth, const float *alpha, const float *lidar,
+                            int64_t n_pts, float *loss, float *dL_ddepth, cudaStream_t s) {
+    DepthArgs A{};
+    A.views = ws->views;
+    A.n_views = ws->n_views;
+    A.mode = ws->cfg.depth_mode;
+    A.near_z = ws->cfg.near_z;
+    A.sigma_L = ws->cfg.sigma_L;
+    A.sigma_U = ws->cfg.sigma_U;
+    A.lambda = ws->cfg.lambda_L;
+    A.depth = depth;
+    A.alpha = alpha;
+    A.lidar = lidar;
+    A.n_pts = n_pts;
+    A.part = ws->red_part;
+    A.nb = ws->sort_blocks;
+    A.loss = loss;
+    A.grad = dL_ddepth;
+    A.st = ws->st;
+    k_depth_partial<<<A.nb, LT, 0, s>>>(A);
+    k_depth_final<<<1, LT, 0, s>>>(A);
+    if (dL_ddepth && n_pts > 0) k_depth_grad<<<A.nb, LT, 0, s>>>(A);
+    return check_launch("depth_loss");
+}
+
+gs_status launch_image_l1(gs_workspace *ws, const float *rgb, const float *target, float *loss,
+                          float *dL_drgb, cudaStream_t s) {
+    int64_t n = 3 * ws->n_pix;
+    int nb = ws->sort_blocks;
+    k_l1_partial<<<nb, LT, 0, s>>>(rgb, target, n, dL_drgb, ws->red_part);
+    k_l1_final<<<1, LT, 0, s>>>(ws->red_part, nb, n, loss);
+    return check_launch("image_l1");
+}
+
+}  // namespace gs

@@ -1,0 +1,672 @@
+// Per-camera EWA projection of the shared Gaussian set and its adjoint.
+//
+// Forward (Sec. III-B, Eqs. 3-4): for every (view, Gaussian) pair of the same
+// submap, Sigma = R S S^T R^T, p = W mu + t, Sigma' = J W Sigma W^T J^T +
+// dilation*I, the scaled Cholesky factor of Sigma'^-1, opacity, the extent of
+// the alpha >= alpha_min ellipse and its tile rectangle, and the SH colour.
+// One thread per Gaussian loops over the cameras of its submap, so the 3-D
+// covariance and the parameter loads are shared by all views.
+//
+// Precision: the view-space depth is the double-precision dot product
+// ((R0 mu0 + R1 mu1) + R2 mu2) + t (exact products of float inputs), rounded to
+// float for the sort key, so keys are reproducible bit for bit.  The pixel
+// mean is formed in double and kept as an integer pixel plus a small float
+// offset, so that per-fragment offsets are exact integers plus that offset.
+// The image covariance is built from the rows of J W R S, its determinant
+// through the Lagrange identity (a sum of squares), so no step cancels.
+//
+// Backward (chain rule through the same steps): one thread per Gaussian
+// accumulates the parameter gradients of all its views in registers and
+// writes them once; the pose twist of each view is reduced over the block
+// (blocks never straddle a submap) and summed per view by a second kernel in
+// a fixed order.
+#include "gs_internal.cuh"
+
+namespace gs {
+namespace {
+
+// real orthonormal SH, no Condon-Shortley phase, ordered by l then m = -l..l
+constexpr float kC0 = 0.28209479177387814f;
+constexpr float kC1 = 0.48860251190291992f;
+constexpr float kC2a = 1.09254843059207907f;
+constexpr float kC2b = 0.31539156525252001f;
+constexpr float kC2c = 0.54627421529603954f;
+constexpr float kC3a = 0.59004358992664352f;
+constexpr float kC3b = 2.89061144264055405f;
+constexpr float kC3c = 0.45704579946446572f;
+constexpr float kC3d = 0.37317633259011540f;
+constexpr float kC3e = 1.44530572132027729f;
+
+template <int DEG>
+__device__ __forceinline__ void sh_basis(float x, float y, float z, float Y[16]) {
+    Y[0] = kC0;
+    if (DEG >= 1) {
+        Y[1] = kC1 * y;
+        Y[2] = kC1 * z;
+        Y[3] = kC1 * x;
+    }
+    if (DEG >= 2) {
+        Y[4] = kC2a * x * y;
+        Y[5] = kC2a * y * z;
+        Y[6] = kC2b * (2.f * z * z - x * x - y * y);
+        Y[7] = kC2a * x * z;
+        Y[8] = kC2c * (x * x - y * y);
+    }
+    if (DEG >= 3) {
+        Y[9] = kC3a * y * (3.f * x * x - y * y);
+        Y[10] = kC3b * x * y * z;
+        Y[11] = kC3c * y * (4.f * z * z - x * x - y * y);
+        Y[12] = kC3d * z * (2.f * z * z - 3.f * x * x - 3.f * y * y);
+        Y[13] = kC3c * x * (4.f * z * z - x * x - y * y);
+        Y[14] = kC3e * z * (x * x - y * y);
+        Y[15] = kC3a * x * (x * x - 3.f * y * y);
+    }
+}
+
+// d Y_k / d(x, y, z)
+template <int DEG>
+__device__ __forceinline__ void sh_basis_grad(float x, float y, float z, float dY[16][3]) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) dY[k][0] = dY[k][1] = dY[k][2] = 0.f;
+    if (DEG >= 1) {
+        dY[1][1] = kC1;
+        dY[2][2] = kC1;
+        dY[3][0] = kC1;
+    }
+    if (DEG >= 2) {
+        dY[4][0] = kC2a * y; dY[4][1] = kC2a * x;
+        dY[5][1] = kC2a * z; dY[5][2] = kC2a * y;
+        dY[6][0] = -2.f * kC2b * x; dY[6][1] = -2.f * kC2b * y; dY[6][2] = 4.f * kC2b * z;
+        dY[7][0] = kC2a * z; dY[7][2] = kC2a * x;
+        dY[8][0] = 2.f * kC2c * x; dY[8][1] = -2.f * kC2c * y;
+    }
+    if (DEG >= 3) {
+        dY[9][0] = kC3a * 6.f * x * y; dY[9][1] = kC3a * 3.f * (x * x - y * y);
+        dY[10][0] = kC3b * y * z; dY[10][1] = kC3b * x * z; dY[10][2] = kC3b * x * y;
+        dY[11][0] = -2.f * kC3c * x * y;
+        dY[11][1] = kC3c * (4.f * z * z - x * x - 3.f * y * y);
+        dY[11][2] = 8.f * kC3c * y * z;
+        dY[12][0] = -6.f * kC3d * x * z; dY[12][1] = -6.f * kC3d * y * z;
+        dY[12][2] = kC3d * (6.f * z * z - 3.f * x * x - 3.f * y * y);
+        dY[13][0] = kC3c * (4.f * z * z - 3.f * x * x - y * y);
+        dY[13][1] = -2.f * kC3c * x * y;
+        dY[13][2] = 8.f * kC3c * x * z;
+        dY[14][0] = 2.f * kC3e * x * z; dY[14][1] = -2.f * kC3e * y * z;
+        dY[14][2] = kC3e * (x * x - y * y);
+        dY[15][0] = 3.f * kC3a * (x * x - y * y); dY[15][1] = -6.f * kC3a * x * y;
+    }
+}
+
+// a*b - c*d with one rounding error (Kahan's difference of products)
+__device__ __forceinline__ float diff_prod(float a, float b, float c, float d) {
+    float w = c * d;
+    float e = __fmaf_rn(-c, d, w);
+    float f = __fmaf_rn(a, b, -w);
+    return f + e;
+}
+
+struct Cam {
+    float fx, fy, cx, cy;
+    float T[12];
+};
+
+__device__ __forceinline__ Cam load_cam(const gs_camera *cams, int v) {
+    Cam c;
+    const gs_camera *cp = cams + v;
+    c.fx = __ldg(&cp->fx);
+    c.fy = __ldg(&cp->fy);
+    c.cx = __ldg(&cp->cx);
+    c.cy = __ldg(&cp->cy);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) c.T[i] = __ldg(&cp->T_cw[i]);
+    return c;
+}
+
+// p = W mu + t in double with the fixed summation order
+__device__ __forceinline__ double view_coord(const float *Ti, float m0, float m1, float m2) {
+    double s = __fma_rn((double)Ti[1], (double)m1, (double)Ti[0] * (double)m0);
+    s = __fma_rn((double)Ti[2], (double)m2, s);
+    return s + (double)Ti[3];
+}
+
+__device__ __forceinline__ int submap_of(const SubmapInfo *subs, int n_submaps, int64_t g) {
+    int lo = 0, hi = n_submaps - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (subs[mid].g0 <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// quaternion (w,x,y,z) -> rotation of the normalised quaternion; returns |q|
+__device__ __forceinline__ float quat_rot(const float q[4], float qh[4], float R[9]) {
+    float n2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+    float qn = sqrtf(n2);
+    float inv = qn > 0.f ? 1.f / qn : 0.f;
+    float w = q[0] * inv, x = q[1] * inv, y = q[2] * inv, z = q[3] * inv;
+    qh[0] = w; qh[1] = x; qh[2] = y; qh[3] = z;
+    R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z); R[2] = 2.f * (x * z + w * y);
+    R[3] = 2.f * (x * y + w * z); R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
+    R[6] = 2.f * (x * z - w * y); R[7] = 2.f * (y * z + w * x); R[8] = 1.f - 2.f * (x * x + y * y);
+    return qn;
+}
+
+struct ProjArgs {
+    const float *means, *log_scales, *quats, *opac, *sh;
+    int64_t n;
+    const gs_camera *cams;
+    const ViewInfo *views;
+    const SubmapInfo *subs;
+    const int32_t *sub_views;
+    int32_t n_submaps, maxv;
+    Consts c;
+    float4 *rec;
+    uint32_t *pkey;
+    short4 *rect;
+    // backward
+    const float *g2d;
+    float *gm, *gls, *gq, *gom, *gsh, *pose_part, *dens_acc;
+    int32_t *dens_cnt;
+};
+
+// Projection of one pair in float after the exact depth: Jacobian, image
+// covariance rows T2 = J W R S, and the derived quantities.
+struct PairGeom {
+    float pxf, pyf, pzf;          // view-space mean (rounded from double)
+    float J00, J02, J11, J12;     // projection Jacobian
+    bool clx, cly;                // tangent clamped
+    float txc, tyc;               // clamped tangent times z
+    float WM[9];                  // W R S
+    float r0[3], r1[3];           // rows of J W R S
+    float a, b, c, det;           // Sigma' and its determinant
+};
+
+__device__ __forceinline__ void pair_geom(const Cam &cam, int W, int H, const Consts &k, double px,
+                                          double py, double pz, const float M[9], PairGeom &G) {
+    G.pxf = (float)px;
+    G.pyf = (float)py;
+    G.pzf = (float)pz;
+    float limx = k.jac_clamp * fmaxf(cam.cx, (float)W - cam.cx) / cam.fx;
+    float limy = k.jac_clamp * fmaxf(cam.cy, (float)H - cam.cy) / cam.fy;
+    float xr = G.pxf / G.pzf, yr = G.pyf / G.pzf;
+    G.clx = xr < -limx || xr > limx;
+    G.cly = yr < -limy || yr > limy;
+    G.txc = fminf(fmaxf(xr, -limx), limx) * G.pzf;
+    G.tyc = fminf(fmaxf(yr, -limy), limy) * G.pzf;
+    float iz = 1.f / G.pzf;
+    float iz2 = iz * iz;
+    G.J00 = cam.fx * iz;
+    G.J02 = -cam.fx * G.txc * iz2;
+    G.J11 = cam.fy * iz;
+    G.J12 = -cam.fy * G.tyc * iz2;
+    const float *T = cam.T;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            G.WM[3 * i + j] = T[4 * i + 0] * M[j] + T[4 * i + 1] * M[3 + j] + T[4 * i + 2] * M[6 + j];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        G.r0[j] = G.J00 * G.WM[j] + G.J02 * G.WM[6 + j];
+        G.r1[j] = G.J11 * G.WM[3 + j] + G.J12 * G.WM[6 + j];
+    }
+    float n0 = G.r0[0] * G.r0[0] + G.r0[1] * G.r0[1] + G.r0[2] * G.r0[2];
+    float n1 = G.r1[0] * G.r1[0] + G.r1[1] * G.r1[1] + G.r1[2] * G.r1[2];
+    G.b = G.r0[0] * G.r1[0] + G.r0[1] * G.r1[1] + G.r0[2] * G.r1[2];
+    G.a = n0 + k.dilation;
+    G.c = n1 + k.dilation;
+    float cx = diff_prod(G.r0[1], G.r1[2], G.r0[2], G.r1[1]);
+    float cy = diff_prod(G.r0[2], G.r1[0], G.r0[0], G.r1[2]);
+    float cz = diff_prod(G.r0[0], G.r1[1], G.r0[1], G.r1[0]);
+    G.det = (cx * cx + cy * cy + cz * cz) + k.dilation * (n0 + n1) + k.dilation * k.dilation;
+}
+
+template <int DEG>
+__device__ __forceinline__ void load_sh(const float *sh, int64_t g, float C[16][3]) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    const float *p = sh + g * (3 * K);
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) C[k][ch] = __ldg(p + 3 * k + ch);
+}
+
+// unit viewing direction mu - C, C = -R^T t the camera centre
+__device__ __forceinline__ void view_dir(const Cam &cam, const float mu[3], float w[3], float &wn) {
+    const float *T = cam.T;
+    float C0 = -(T[0] * T[3] + T[4] * T[7] + T[8] * T[11]);
+    float C1 = -(T[1] * T[3] + T[5] * T[7] + T[9] * T[11]);
+    float C2 = -(T[2] * T[3] + T[6] * T[7] + T[10] * T[11]);
+    w[0] = mu[0] - C0;
+    w[1] = mu[1] - C1;
+    w[2] = mu[2] - C2;
+    wn = sqrtf(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+}
+
+template <int DEG>
+__global__ void __launch_bounds__(kProjThreads) k_project_fwd(ProjArgs A) {
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= A.n) return;
+    const Consts &k = A.c;
+    int s = submap_of(A.subs, A.n_submaps, g);
+    const SubmapInfo sub = A.subs[s];
+
+    float mu[3] = {__ldg(A.means + 3 * g), __ldg(A.means + 3 * g + 1), __ldg(A.means + 3 * g + 2)};
+    float ls[3] = {__ldg(A.log_scales + 3 * g), __ldg(A.log_scales + 3 * g + 1),
+                   __ldg(A.log_scales + 3 * g + 2)};
+    float q[4] = {__ldg(A.quats + 4 * g), __ldg(A.quats + 4 * g + 1), __ldg(A.quats + 4 * g + 2),
+                  __ldg(A.quats + 4 * g + 3)};
+    float om = __ldg(A.opac + g);
+    float qh[4], R[9];
+    float qn = quat_rot(q, qh, R);
+    float S[3] = {expf(ls[0]), expf(ls[1]), expf(ls[2])};
+    float M[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) M[3 * i + j] = R[3 * i + j] * S[j];
+    // ln o = -ln(1 + e^-omega); support threshold E = 2 ln(o / alpha_min)
+    float lno = -log1pf(expf(-om));
+    float log2o = lno * kLog2e;
+    float E = 2.f * (lno - k.ln_alpha_min);
+    float C[16][3];
+    load_sh<DEG>(A.sh, g, C);
+    constexpr int K = (DEG + 1) * (DEG + 1);
+
+    for (int kv = 0; kv < sub.nviews; ++kv) {
+        int v = A.sub_views[s * A.maxv + kv];
+        const ViewInfo vi = A.views[v];
+        int64_t pair = (int64_t)vi.pair_off + (g - vi.g0);
+        Cam cam = load_cam(A.cams, v);
+        double px = view_coord(cam.T, mu[0], mu[1], mu[2]);
+        double py = view_coord(cam.T + 4, mu[0], mu[1], mu[2]);
+        double pz = view_coord(cam.T + 8, mu[0], mu[1], mu[2]);
+        bool vis = pz > (double)k.near_z && qn > 0.f && E > 0.f;
+        PairGeom G;
+        float4 r0 = make_float4(0, 0, 0, 0), r1 = r0, r2 = r0;
+        short4 rc = make_short4(1, 1, 0, 0);
+        if (vis) {
+            pair_geom(cam, vi.W, vi.H, k, px, py, pz, M, G);
+            vis = G.det > 0.f;
+        }
+        if (vis) {
+            // pixel mean in double, split into integer pixel + offset
+            double iz = 1.0 / pz;
+            double u = (double)cam.fx * px * iz + (double)cam.cx;
+            double vv = (double)cam.fy * py * iz + (double)cam.cy;
+            double Uf = floor(u), Vf = floor(vv);
+            float hx = (float)(0.5 - (u - Uf));
+            float hy = (float)(0.5 - (vv - Vf));
+            // padded axis-aligned extent of {d : d^T Sigma'^-1 d <= E}
+            float ex = sqrtf(E * G.a) * (1.f + k.ext_rel_pad) + k.ext_abs_pad;
+            float ey = sqrtf(E * G.c) * (1.f + k.ext_rel_pad) + k.ext_abs_pad;
+            double xlo = ceil(u - (double)ex - 0.5), xhi = floor(u + (double)ex - 0.5);
+            double ylo = ceil(vv - (double)ey - 0.5), yhi = floor(vv + (double)ey - 0.5);
+            xlo = fmax(xlo, 0.0);
+            ylo = fmax(ylo, 0.0);
+            xhi = fmin(xhi, (double)(vi.W - 1));
+            yhi = fmin(yhi, (double)(vi.H - 1));
+            vis = xlo <= xhi && ylo <= yhi;
+            if (vis) {
+                rc = make_short4((short)((int)xlo / k.tile_w), (short)((int)ylo / k.tile_h),
+                                 (short)((int)xhi / k.tile_w), (short)((int)yhi / k.tile_h));
+                // Cholesky factor L (upper) of Sigma'^-1 = L^T L, scaled by kCholScale
+                float l22 = kCholScale / sqrtf(G.c);
+                float l11 = kCholScale * sqrtf(G.c / G.det);
+                float l12 = -kCholScale * G.b / sqrtf(G.c * G.det);
+                // colour seen from the camera centre
+                float w[3], wn;
+                view_dir(cam, mu, w, wn);
+                float iw = 1.f / wn;
+                float Y[16];
+                sh_basis<DEG>(w[0] * iw, w[1] * iw, w[2] * iw, Y);
+                float rgb[3];
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) {
+                    float acc = 0.5f;
+#pragma unroll
+                    for (int kk = 0; kk < K; ++kk) acc = __fmaf_rn(C[kk][ch], Y[kk], acc);
+                    rgb[ch] = fmaxf(acc, 0.f);
+                }
+                r0 = make_float4((float)Uf, (float)Vf, hx, hy);
+                r1 = make_float4(l11, l12, l22, log2o);
+                r2 = make_float4(rgb[0], rgb[1], rgb[2], __double2float_rn(pz));
+            }
+        }
+        if (vis) {
+            A.rec[3 * pair + 0] = r0;
+            A.rec[3 * pair + 1] = r1;
+            A.rec[3 * pair + 2] = r2;
+        }
+        A.rect[pair] = rc;
+        A.pkey[pair] = vis ? __float_as_uint(r2.w) : kInvalidKey;
+    }
+}
+
+// block-wide sum of v (all threads of the block must call); result valid in all threads
+__device__ __forceinline__ float block_sum(float v, float *scratch) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) scratch[w] = v;
+    __syncthreads();
+    float t = 0.f;
+    int nw = blockDim.x >> 5;
+    for (int i = 0; i < nw; ++i) t += scratch[i];
+    return t;
+}
+
+template <int DEG>
+__global__ void __launch_bounds__(kProjThreads) k_project_bwd(ProjArgs A) {
+    __shared__ float red[32];
+    const Consts &k = A.c;
+    // blocks are laid out per submap
+    int b = blockIdx.x;
+    int s = 0;
+    {
+        int lo = 0, hi = A.n_submaps - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (A.subs[mid].block0 <= b) lo = mid; else hi = mid - 1;
+        }
+        s = lo;
+    }
+    const SubmapInfo sub = A.subs[s];
+    int64_t local = (int64_t)(b - sub.block0) * blockDim.x + threadIdx.x;
+    bool live = local < sub.ng;
+    int64_t g = sub.g0 + (live ? local : 0);
+    constexpr int K = (DEG + 1) * (DEG + 1);
+
+    float mu[3] = {0, 0, 0}, ls[3] = {0, 0, 0}, q[4] = {1, 0, 0, 0}, om = 0.f;
+    float C[16][3];
+    if (live) {
+        mu[0] = __ldg(A.means + 3 * g); mu[1] = __ldg(A.means + 3 * g + 1); mu[2] = __ldg(A.means + 3 * g + 2);
+        ls[0] = __ldg(A.log_scales + 3 * g); ls[1] = __ldg(A.log_scales + 3 * g + 1);
+        ls[2] = __ldg(A.log_scales + 3 * g + 2);
+        q[0] = __ldg(A.quats + 4 * g); q[1] = __ldg(A.quats + 4 * g + 1);
+        q[2] = __ldg(A.quats + 4 * g + 2); q[3] = __ldg(A.quats + 4 * g + 3);
+        om = __ldg(A.opac + g);
+        load_sh<DEG>(A.sh, g, C);
+    } else {
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) C[kk][0] = C[kk][1] = C[kk][2] = 0.f;
+    }
+    float qh[4], R[9];
+    float qn = quat_rot(q, qh, R);
+    float S[3] = {expf(ls[0]), expf(ls[1]), expf(ls[2])};
+    float M[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) M[3 * i + j] = R[3 * i + j] * S[j];
+    float o = 1.f / (1.f + expf(-om));
+
+    float gmu[3] = {0, 0, 0}, gM[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, gom = 0.f;
+    float gC[16][3];
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) gC[kk][0] = gC[kk][1] = gC[kk][2] = 0.f;
+    float dacc = 0.f;
+    int dcnt = 0;
+
+    for (int kv = 0; kv < sub.nviews; ++kv) {
+        int v = A.sub_views[s * A.maxv + kv];
+        const ViewInfo vi = A.views[v];
+        int64_t pair = (int64_t)vi.pair_off + (g - vi.g0);
+        float gpose[6] = {0, 0, 0, 0, 0, 0};
+        bool vis = live && A.pkey[pair] != kInvalidKey;
+        if (vis) {
+            const float *gg = A.g2d + pair * kGrad;
+            float gu = gg[G_U], gv = gg[G_V], gqa = gg[G_QA], gqb = gg[G_QB], gqc = gg[G_QC];
+            float glno = gg[G_LNO], gz = gg[G_Z];
+            float grgb[3] = {gg[G_R], gg[G_G], gg[G_B]};
+            Cam cam = load_cam(A.cams, v);
+            double pxd = view_coord(cam.T, mu[0], mu[1], mu[2]);
+            double pyd = view_coord(cam.T + 4, mu[0], mu[1], mu[2]);
+            double pzd = view_coord(cam.T + 8, mu[0], mu[1], mu[2]);
+            PairGeom G;
+            pair_geom(cam, vi.W, vi.H, k, pxd, pyd, pzd, M, G);
+            const float p[3] = {G.pxf, G.pyf, G.pzf};
+            const float *T = cam.T;
+            float gp[3] = {0.f, 0.f, gz};
+            // pixel mean
+            float iz = 1.f / p[2], iz2 = iz * iz;
+            gp[0] += gu * cam.fx * iz;
+            gp[1] += gv * cam.fy * iz;
+            gp[2] -= (gu * cam.fx * p[0] + gv * cam.fy * p[1]) * iz2;
+            // colour
+            float w[3], wn;
+            view_dir(cam, mu, w, wn);
+            float iw = 1.f / wn;
+            float d[3] = {w[0] * iw, w[1] * iw, w[2] * iw};
+            float Y[16], dY[16][3];
+            sh_basis<DEG>(d[0], d[1], d[2], Y);
+            sh_basis_grad<DEG>(d[0], d[1], d[2], dY);
+            float gdir[3] = {0, 0, 0};
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                float acc = 0.5f;
+#pragma unroll
+                for (int kk = 0; kk < K; ++kk) acc = __fmaf_rn(C[kk][ch], Y[kk], acc);
+                if (acc < 0.f) continue;  // clamped colour
+#pragma unroll
+                for (int kk = 0; kk < K; ++kk) {
+                    gC[kk][ch] += grgb[ch] * Y[kk];
+                    float t = grgb[ch] * C[kk][ch];
+                    gdir[0] += t * dY[kk][0];
+                    gdir[1] += t * dY[kk][1];
+                    gdir[2] += t * dY[kk][2];
+                }
+            }
+            float dd = d[0] * gdir[0] + d[1] * gdir[1] + d[2] * gdir[2];
+            float gw[3] = {(gdir[0] - d[0] * dd) * iw, (gdir[1] - d[1] * dd) * iw, (gdir[2] - d[2] * dd) * iw};
+            // dL/dSigma' = -Q G Q with Q = Sigma'^-1, G = [[gqa, gqb/2], [gqb/2, gqc]]
+            float idet = 1.f / G.det;
+            float Qa = G.c * idet, Qb = -G.b * idet, Qc = G.a * idet;
+            float hb = 0.5f * gqb;
+            float QG00 = Qa * gqa + Qb * hb, QG01 = Qa * hb + Qb * gqc;
+            float QG10 = Qb * gqa + Qc * hb, QG11 = Qb * hb + Qc * gqc;
+            float Ma = -(QG00 * Qa + QG01 * Qb);
+            float Mb = -(QG00 * Qb + QG01 * Qc);
+            float Mc = -(QG10 * Qb + QG11 * Qc);
+            // Sigma' = T2 T2^T + dil I with T2 = J W M (rows r0, r1):
+            // dL/dT2 = 2 Msym T2 (Msym = [[Ma, Mb], [Mb, Mc]])
+            float gr0[3], gr1[3];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                gr0[j] = 2.f * (Ma * G.r0[j] + Mb * G.r1[j]);
+                gr1[j] = 2.f * (Mb * G.r0[j] + Mc * G.r1[j]);
+            }
+            // T2 = J WM: rows r0 = J00 WM0 + J02 WM2, r1 = J11 WM1 + J12 WM2
+            float gJ00 = gr0[0] * G.WM[0] + gr0[1] * G.WM[1] + gr0[2] * G.WM[2];
+            float gJ02 = gr0[0] * G.WM[6] + gr0[1] * G.WM[7] + gr0[2] * G.WM[8];
+            float gJ11 = gr1[0] * G.WM[3] + gr1[1] * G.WM[4] + gr1[2] * G.WM[5];
+            float gJ12 = gr1[0] * G.WM[6] + gr1[1] * G.WM[7] + gr1[2] * G.WM[8];
+            float gWM[9];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                gWM[j] = G.J00 * gr0[j];
+                gWM[3 + j] = G.J11 * gr1[j];
+                gWM[6 + j] = G.J02 * gr0[j] + G.J12 * gr1[j];
+            }
+            // J as a function of p (clamped tangent: J02 = -fx c / z)
+            gp[2] += -(gJ00 * cam.fx + gJ11 * cam.fy) * iz2;
+            if (!G.clx) {
+                gp[0] += -gJ02 * cam.fx * iz2;
+                gp[2] += 2.f * gJ02 * cam.fx * p[0] * iz2 * iz;
+            } else {
+                gp[2] += gJ02 * cam.fx * (G.txc * iz) * iz2;
+            }
+            if (!G.cly) {
+                gp[1] += -gJ12 * cam.fy * iz2;
+                gp[2] += 2.f * gJ12 * cam.fy * p[1] * iz2 * iz;
+            } else {
+                gp[2] += gJ12 * cam.fy * (G.tyc * iz) * iz2;
+            }
+            // WM = Rb M: dL/dM += Rb^T gWM ; pose rotation: Rb -> (I + [phi]x) Rb
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+                    gM[3 * i + j] += T[i] * gWM[j] + T[4 + i] * gWM[3 + j] + T[8 + i] * gWM[6 + j];
+            // dL/dphi from WM: delta WM = [phi]x WM -> dL/dphi = sum_j WM_j x gWM_j (columns)
+            float A_[9];  // A = gWM WM^T
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+                    A_[3 * i + j] = gWM[3 * i] * G.WM[3 * j] + gWM[3 * i + 1] * G.WM[3 * j + 1] +
+                                    gWM[3 * i + 2] * G.WM[3 * j + 2];
+            // tr(A^T [phi]x WM...) : dL = sum_ij gWM_ij ([phi]x WM)_ij = tr(gWM^T [phi]x WM)
+            //   = tr([phi]x WM gWM^T) = tr([phi]x A^T); axial part
+            gpose[3] += A_[7] - A_[5];
+            gpose[4] += A_[2] - A_[6];
+            gpose[5] += A_[3] - A_[1];
+            // mean and pose translation: p = Rb mu + t
+            gmu[0] += T[0] * gp[0] + T[4] * gp[1] + T[8] * gp[2] + gw[0];
+            gmu[1] += T[1] * gp[0] + T[5] * gp[1] + T[9] * gp[2] + gw[1];
+            gmu[2] += T[2] * gp[0] + T[6] * gp[1] + T[10] * gp[2] + gw[2];
+            float gwc[3] = {T[0] * gw[0] + T[1] * gw[1] + T[2] * gw[2],
+                            T[4] * gw[0] + T[5] * gw[1] + T[6] * gw[2],
+                            T[8] * gw[0] + T[9] * gw[1] + T[10] * gw[2]};
+            gpose[0] += gp[0] + gwc[0];
+            gpose[1] += gp[1] + gwc[1];
+            gpose[2] += gp[2] + gwc[2];
+            gpose[3] += p[1] * gp[2] - p[2] * gp[1];
+            gpose[4] += p[2] * gp[0] - p[0] * gp[2];
+            gpose[5] += p[0] * gp[1] - p[1] * gp[0];
+            // opacity: d ln o / d omega = 1 - o
+            gom += glno * (1.f - o);
+            dacc += sqrtf(gu * gu + gv * gv);
+            dcnt += 1;
+        }
+        // pose twist of this view: block reduce, one partial per block and view slot
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            float t = block_sum(gpose[i], red);
+            if (threadIdx.x == 0) A.pose_part[((int64_t)b * A.maxv + kv) * 6 + i] = t;
+        }
+    }
+    if (!live) return;
+    // M = R diag(S): dL/dS_k = sum_i gM_ik R_ik, dL/dls_k = dL/dS_k S_k; dL/dR_ik = gM_ik S_k
+    float gR[9];
+    float gls[3];
+#pragma unroll
+    for (int kk = 0; kk < 3; ++kk) {
+        gls[kk] = (gM[kk] * R[kk] + gM[3 + kk] * R[3 + kk] + gM[6 + kk] * R[6 + kk]) * S[kk];
+        gR[kk] = gM[kk] * S[kk];
+        gR[3 + kk] = gM[3 + kk] * S[kk];
+        gR[6 + kk] = gM[6 + kk] * S[kk];
+    }
+    // rotation of the normalised quaternion, then the normalisation
+    float w = qh[0], x = qh[1], y = qh[2], z = qh[3];
+    float gw_ = 2.f * (-z * gR[1] + y * gR[2] + z * gR[3] - x * gR[5] - y * gR[6] + x * gR[7]);
+    float gx_ = 2.f * (y * gR[1] + z * gR[2] + y * gR[3] - 2.f * x * gR[4] - w * gR[5] + z * gR[6] +
+                       w * gR[7] - 2.f * x * gR[8]);
+    float gy_ = 2.f * (-2.f * y * gR[0] + x * gR[1] + w * gR[2] + x * gR[3] + z * gR[5] - w * gR[6] +
+                       z * gR[7] - 2.f * y * gR[8]);
+    float gz_ = 2.f * (-2.f * z * gR[0] - w * gR[1] + x * gR[2] + w * gR[3] - 2.f * z * gR[4] +
+                       y * gR[5] + x * gR[6] + y * gR[7]);
+    float dq = w * gw_ + x * gx_ + y * gy_ + z * gz_;
+    float iq = qn > 0.f ? 1.f / qn : 0.f;
+    float gq[4] = {(gw_ - w * dq) * iq, (gx_ - x * dq) * iq, (gy_ - y * dq) * iq, (gz_ - z * dq) * iq};
+
+#pragma unroll
+    for (int i = 0; i < 3; ++i) A.gm[3 * g + i] += gmu[i];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) A.gls[3 * g + i] += gls[i];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) A.gq[4 * g + i] += gq[i];
+    A.gom[g] += gom;
+    float *gs = A.gsh + g * (3 * K);
+#pragma unroll
+    for (int kk = 0; kk < K; ++kk)
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) gs[3 * kk + ch] += gC[kk][ch];
+    if (A.dens_acc) A.dens_acc[g] += dacc;
+    if (A.dens_cnt) A.dens_cnt[g] += dcnt;
+}
+
+// pose[v] += sum over the blocks of v's submap of the partials of v's slot
+__global__ void k_pose_reduce(const float *pose_part, const ViewInfo *views, const SubmapInfo *subs,
+                              int maxv, int n_views, float *pose) {
+    int v = blockIdx.x;
+    if (v >= n_views) return;
+    int i = threadIdx.x;
+    if (i >= 6) return;
+    const ViewInfo vi = views[v];
+    const SubmapInfo sub = subs[vi.submap];
+    double acc = 0.0;
+    for (int b = sub.block0; b < sub.block0 + sub.nblocks; ++b)
+        acc += (double)pose_part[((int64_t)b * maxv + vi.k_in_submap) * 6 + i];
+    pose[6 * v + i] += (float)acc;
+}
+
+ProjArgs make_args(gs_workspace *ws, const gs_gaussians *g, const gs_camera *cams) {
+    ProjArgs A{};
+    A.means = g->means;
+    A.log_scales = g->log_scales;
+    A.quats = g->quats;
+    A.opac = g->opacity_logits;
+    A.sh = g->sh;
+    A.n = g->n;
+    A.cams = cams;
+    A.views = ws->views;
+    A.subs = ws->subs;
+    A.sub_views = ws->sub_views;
+    A.n_submaps = ws->n_submaps;
+    A.maxv = ws->max_views_per_submap;
+    A.c = ws->consts;
+    A.rec = ws->rec;
+    A.pkey = ws->pkey;
+    A.rect = ws->rect;
+    A.g2d = ws->g2d;
+    return A;
+}
+
+}  // namespace
+
+gs_status launch_project_fwd(gs_workspace *ws, const gs_gaussians *g, const gs_camera *cams,
+                             cudaStream_t s) {
+    ProjArgs A = make_args(ws, g, cams);
+    if (ws->n == 0) return GS_OK;
+    int grid = (int)((ws->n + kProjThreads - 1) / kProjThreads);
+    switch (ws->sh_degree) {
+        case 0: k_project_fwd<0><<<grid, kProjThreads, 0, s>>>(A); break;
+        case 1: k_project_fwd<1><<<grid, kProjThreads, 0, s>>>(A); break;
+        case 2: k_project_fwd<2><<<grid, kProjThreads, 0, s>>>(A); break;
+        default: k_project_fwd<3><<<grid, kProjThreads, 0, s>>>(A); break;
+    }
+    return check_launch("project_fwd");
+}
+
+gs_status launch_project_bwd(gs_workspace *ws, const gs_gaussians *g, const gs_camera *cams,
+                             const gs_grads *out, cudaStream_t s) {
+    ProjArgs A = make_args(ws, g, cams);
+    A.gm = out->means;
+    A.gls = out->log_scales;
+    A.gq = out->quats;
+    A.gom = out->opacity_logits;
+    A.gsh = out->sh;
+    A.pose_part = ws->pose_part;
+    A.dens_acc = out->densify_acc;
+    A.dens_cnt = out->densify_cnt;
+    if (ws->proj_blocks > 0) {
+        switch (ws->sh_degree) {
+            case 0: k_project_bwd<0><<<ws->proj_blocks, kProjThreads, 0, s>>>(A); break;
+            case 1: k_project_bwd<1><<<ws->proj_blocks, kProjThreads, 0, s>>>(A); break;
+            case 2: k_project_bwd<2><<<ws->proj_blocks, kProjThreads, 0, s>>>(A); break;
+            default: k_project_bwd<3><<<ws->proj_blocks, kProjThreads, 0, s>>>(A); break;
+        }
+        gs_status st = check_launch("project_bwd");
+        if (st != GS_OK) return st;
+    }
+    if (out->pose) {
+        k_pose_reduce<<<ws->n_views, 32, 0, s>>>(ws->pose_part, ws->views, ws->subs,
+                                                 ws->max_views_per_submap, ws->n_views, out->pose);
+        return check_launch("pose_reduce");
+    }
+    return GS_OK;
+}
+
+}  // namespace gs

@@ -1,0 +1,357 @@
+// Tile rasteriser: forward alpha compositing and its adjoint.
+//
+// One CTA owns one tile at a time (one thread per pixel) and pulls tiles of
+// every view from a global work counter, so a single persistent launch covers
+// all cameras of the batch, whatever their sizes.  Gaussians of the tile's
+// depth-sorted list are staged `batch_depth` at a time in shared memory; each
+// thread walks them for its pixel.
+//
+// Forward (front to back):  alpha = min(alpha_max, o e^{pw}); skip alpha <
+// alpha_min; a fragment that would take T below t_min ends the pixel before it
+// is blended; C += alpha T c, D += alpha T z, T *= (1 - alpha).  The CTA leaves
+// a tile as soon as every pixel has ended.  Per pixel it keeps the list count
+// up to the last blended fragment and the final T.
+//
+// Backward (back to front from that count): alpha is recomputed with the same
+// instructions, T is recovered by division, and with h = gC.c + gD z + gA
+//   dL/dalpha_j = T_j h_j - (sum_{k>j} w_k h_k) / (1 - alpha_j).
+// The 10 image-space gradient components of each Gaussian are summed over the
+// warp's 32 pixels with shuffles before one atomic per component.
+#include "gs_internal.cuh"
+
+namespace gs {
+namespace {
+
+struct RasterArgs {
+    const ViewInfo *views;
+    int32_t n_views, n_tiles, depth;
+    Consts c;
+    const float4 *rec;
+    const uint32_t *vals;
+    const uint2 *ranges;
+    uint32_t *counter;
+    uint32_t *last;
+    float *tfin;
+    // forward outputs
+    float *rgb, *depth_out, *alpha_out;
+    // backward inputs / outputs
+    const float *dL_drgb, *dL_ddepth, *dL_dalpha;
+    float *g2d;
+};
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW * TH) k_raster_fwd(RasterArgs A) {
+    constexpr int NT = TW * TH;
+    extern __shared__ float4 smem[];
+    float4 *sA = smem, *sB = smem + A.depth, *sC = smem + 2 * A.depth;
+    __shared__ int s_tile;
+    const int tid = threadIdx.x;
+    const float amax = A.c.alpha_max, tmin = A.c.t_min, l2amin = A.c.log2_alpha_min;
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_tile = (int)atomicAdd(A.counter, 1u);
+        __syncthreads();
+        const int tile = s_tile;
+        if (tile >= A.n_tiles) break;
+        const int v = view_of_tile(A.views, A.n_views, tile);
+        const ViewInfo vi = A.views[v];
+        const int lt = tile - vi.tile_off;
+        const int px = (lt % vi.ntx) * TW + tid % TW;
+        const int py = (lt / vi.ntx) * TH + tid / TW;
+        const bool inside = px < vi.W && py < vi.H;
+        const float pxf = (float)px, pyf = (float)py;
+        const uint2 rg = A.ranges[tile];
+        float T = 1.f, Cr = 0.f, Cg = 0.f, Cb = 0.f, D = 0.f;
+        uint32_t cnt = 0;
+        bool done = !inside;
+        for (uint32_t b0 = rg.x; b0 < rg.y; b0 += A.depth) {
+            if (__syncthreads_and(done)) break;
+            const int nb = min((int)(rg.y - b0), A.depth);
+            for (int j = tid; j < nb; j += NT) {
+                uint32_t pair = A.vals[b0 + j];
+                float4 r0 = A.rec[3 * (size_t)pair], r1 = A.rec[3 * (size_t)pair + 1];
+                float4 a, bb;
+                stage_record(r0, r1, a, bb);
+                sA[j] = a;
+                sB[j] = bb;
+                sC[j] = A.rec[3 * (size_t)pair + 2];
+            }
+            __syncthreads();
+            if (!done) {
+                for (int j = 0; j < nb; ++j) {
+                    float t1, t2, dxi, dyi;
+                    const float e = frag_log2_alpha(sA[j], sB[j], pxf, pyf, t1, t2, dxi, dyi);
+                    if (e < l2amin) continue;
+                    const float al = fminf(amax, ex2_approx(e));
+                    const float Tn = __fmaf_rn(-T, al, T);
+                    if (Tn < tmin) {
+                        done = true;
+                        break;
+                    }
+                    const float wgt = al * T;
+                    const float4 c = sC[j];
+                    Cr = __fmaf_rn(wgt, c.x, Cr);
+                    Cg = __fmaf_rn(wgt, c.y, Cg);
+                    Cb = __fmaf_rn(wgt, c.z, Cb);
+                    D = __fmaf_rn(wgt, c.w, D);
+                    T = Tn;
+                    cnt = b0 + j - rg.x + 1;
+                }
+            }
+        }
+        if (inside) {
+            const int64_t pl = (int64_t)py * vi.W + px;
+            const int64_t pix = vi.pix_off + pl;
+            const int64_t hw = (int64_t)vi.W * vi.H;
+            float *rgb = A.rgb + 3 * (int64_t)vi.pix_off;
+            rgb[pl] = Cr;
+            rgb[hw + pl] = Cg;
+            rgb[2 * hw + pl] = Cb;
+            A.depth_out[pix] = D;
+            A.alpha_out[pix] = 1.f - T;
+            A.last[pix] = cnt;
+            A.tfin[pix] = T;
+        }
+    }
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW * TH) k_raster_bwd(RasterArgs A) {
+    constexpr int NT = TW * TH;
+    constexpr int NW = NT / 32;
+    extern __shared__ float4 smem[];
+    float4 *sA = smem, *sB = smem + A.depth, *sC = smem + 2 * A.depth;
+    float2 *sH = reinterpret_cast<float2 *>(smem + 3 * A.depth);
+    uint32_t *sP = reinterpret_cast<uint32_t *>(sH + A.depth);
+    __shared__ int s_tile;
+    __shared__ uint32_t s_max[NW];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const float amax = A.c.alpha_max, l2amin = A.c.log2_alpha_min;
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_tile = (int)atomicAdd(A.counter, 1u);
+        __syncthreads();
+        const int tile = s_tile;
+        if (tile >= A.n_tiles) break;
+        const int v = view_of_tile(A.views, A.n_views, tile);
+        const ViewInfo vi = A.views[v];
+        const int lt = tile - vi.tile_off;
+        const int px = (lt % vi.ntx) * TW + tid % TW;
+        const int py = (lt / vi.ntx) * TH + tid / TW;
+        const bool inside = px < vi.W && py < vi.H;
+        const float pxf = (float)px, pyf = (float)py;
+        const uint2 rg = A.ranges[tile];
+        uint32_t cnt = 0;
+        float T = 1.f, gR = 0.f, gG = 0.f, gB = 0.f, gD = 0.f, gA = 0.f;
+        if (inside) {
+            const int64_t pl = (int64_t)py * vi.W + px;
+            const int64_t pix = vi.pix_off + pl;
+            const int64_t hw = (int64_t)vi.W * vi.H;
+            const float *g = A.dL_drgb + 3 * (int64_t)vi.pix_off;
+            cnt = A.last[pix];
+            T = A.tfin[pix];
+            gR = g[pl];
+            gG = g[hw + pl];
+            gB = g[2 * hw + pl];
+            gD = A.dL_ddepth ? A.dL_ddepth[pix] : 0.f;
+            gA = A.dL_dalpha ? A.dL_dalpha[pix] : 0.f;
+        }
+        uint32_t m = cnt;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) s_max[wid] = m;
+        __syncthreads();
+        uint32_t maxcnt = 0;
+#pragma unroll
+        for (int i = 0; i < NW; ++i) maxcnt = max(maxcnt, s_max[i]);
+        float acc = 0.f;  // sum over later blended fragments of w_k h_k
+        for (int64_t hi = (int64_t)rg.x + maxcnt; hi > (int64_t)rg.x; hi -= A.depth) {
+            const int64_t lo = max((int64_t)rg.x, hi - A.depth);
+            const int nb = (int)(hi - lo);
+            __syncthreads();
+            for (int j = tid; j < nb; j += NT) {
+                uint32_t pair = A.vals[lo + j];
+                float4 r0 = A.rec[3 * (size_t)pair], r1 = A.rec[3 * (size_t)pair + 1];
+                float4 a, bb;
+                stage_record(r0, r1, a, bb);
+                sA[j] = a;
+                sB[j] = bb;
+                sC[j] = A.rec[3 * (size_t)pair + 2];
+                sH[j] = make_float2(r0.z, r0.w);
+                sP[j] = pair;
+            }
+            __syncthreads();
+            for (int j = nb - 1; j >= 0; --j) {
+                const uint32_t rel = (uint32_t)(lo + j - rg.x);
+                float t1, t2, dxi, dyi;
+                const float4 sa = sA[j], sb = sB[j];
+                const float e = frag_log2_alpha(sa, sb, pxf, pyf, t1, t2, dxi, dyi);
+                const bool contrib = rel < cnt && e >= l2amin;
+                float gu = 0.f, gv = 0.f, gqa = 0.f, gqb = 0.f, gqc = 0.f, glno = 0.f;
+                float gr = 0.f, gg = 0.f, gb = 0.f, gz = 0.f;
+                if (contrib) {
+                    const float araw = ex2_approx(e);
+                    const float al = fminf(amax, araw);
+                    const float r1m = 1.f / (1.f - al);
+                    T = T * r1m;  // transmittance before this fragment
+                    const float4 c = sC[j];
+                    const float wgt = al * T;
+                    const float h = gR * c.x + gG * c.y + gB * c.z + gD * c.w + gA;
+                    const float dLda = T * h - acc * r1m;
+                    acc = __fmaf_rn(wgt, h, acc);
+                    gr = wgt * gR;
+                    gg = wgt * gG;
+                    gb = wgt * gB;
+                    gz = wgt * gD;
+                    if (araw <= amax) {
+                        const float gpw = dLda * al;  // dL/dpw, pw = -d^T Q d / 2 (natural log)
+                        const float2 hh = sH[j];
+                        const float dx = dxi + hh.x, dy = dyi + hh.y;
+                        glno = gpw;
+                        gqa = -0.5f * gpw * dx * dx;
+                        gqb = -gpw * dx * dy;
+                        gqc = -0.5f * gpw * dy * dy;
+                        // dpw/du = (Q d)_x = l11 t1 / s^2, dpw/dv = (l12 t1 + l22 t2) / s^2
+                        gu = gpw * kTwoLn2 * (sb.x * t1);
+                        gv = gpw * kTwoLn2 * (sb.y * t1 + sb.z * t2);
+                    }
+                }
+                if (__any_sync(0xffffffffu, contrib)) {
+                    gu = warp_sum(gu);
+                    gv = warp_sum(gv);
+                    gqa = warp_sum(gqa);
+                    gqb = warp_sum(gqb);
+                    gqc = warp_sum(gqc);
+                    glno = warp_sum(glno);
+                    gr = warp_sum(gr);
+                    gg = warp_sum(gg);
+                    gb = warp_sum(gb);
+                    gz = warp_sum(gz);
+                    if (lane < kGrad) {
+                        float val = lane == G_U ? gu : lane == G_V ? gv : lane == G_QA ? gqa :
+                                    lane == G_QB ? gqb : lane == G_QC ? gqc : lane == G_LNO ? glno :
+                                    lane == G_R ? gr : lane == G_G ? gg : lane == G_B ? gb : gz;
+                        atomicAdd(A.g2d + (size_t)sP[j] * kGrad + lane, val);
+                    }
+                }
+            }
+        }
+    }
+}
+
+// zero the image-space gradients of the visible pairs
+__global__ void k_zero_g2d(const uint32_t *vis_pair, const DevState *st, float *g2d) {
+    uint32_t n = st->n_vis;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n * kGrad; i += gridDim.x * blockDim.x)
+        g2d[(size_t)vis_pair[i / kGrad] * kGrad + i % kGrad] = 0.f;
+}
+
+template <int TW, int TH>
+size_t fwd_smem(int depth) { return (size_t)depth * 3 * sizeof(float4); }
+template <int TW, int TH>
+size_t bwd_smem(int depth) {
+    return (size_t)depth * (3 * sizeof(float4) + sizeof(float2) + sizeof(uint32_t));
+}
+
+template <int TW, int TH>
+gs_status configure_one(gs_workspace *ws) {
+    int depth = ws->cfg.batch_depth;
+    cudaError_t e;
+    e = cudaFuncSetAttribute(k_raster_fwd<TW, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)fwd_smem<TW, TH>(256));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_raster_bwd<TW, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)bwd_smem<TW, TH>(256));
+    int occ_f = 0, occ_b = 0;
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_f, k_raster_fwd<TW, TH>, TW * TH,
+                                                          fwd_smem<TW, TH>(depth));
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, k_raster_bwd<TW, TH>, TW * TH,
+                                                          bwd_smem<TW, TH>(depth));
+    if (e != cudaSuccess) {
+        set_last_error(std::string("raster_configure: ") + cudaGetErrorString(e));
+        return GS_ERR_CUDA;
+    }
+    ws->raster_grid_fwd = std::max(1, occ_f) * ws->num_sms;
+    ws->raster_grid_bwd = std::max(1, occ_b) * ws->num_sms;
+    return GS_OK;
+}
+
+RasterArgs make_args(gs_workspace *ws) {
+    RasterArgs A{};
+    A.views = ws->views;
+    A.n_views = ws->n_views;
+    A.n_tiles = (int32_t)ws->n_tiles;
+    A.depth = ws->cfg.batch_depth;
+    A.c = ws->consts;
+    A.rec = ws->rec;
+    A.vals = ws->inst_val;
+    A.ranges = ws->ranges;
+    A.last = ws->last;
+    A.tfin = ws->tfin;
+    return A;
+}
+
+template <int TW, int TH>
+gs_status run_fwd(gs_workspace *ws, RasterArgs A, cudaStream_t s) {
+    k_raster_fwd<TW, TH><<<ws->raster_grid_fwd, TW * TH, fwd_smem<TW, TH>(A.depth), s>>>(A);
+    return check_launch("raster_fwd");
+}
+template <int TW, int TH>
+gs_status run_bwd(gs_workspace *ws, RasterArgs A, cudaStream_t s) {
+    k_raster_bwd<TW, TH><<<ws->raster_grid_bwd, TW * TH, bwd_smem<TW, TH>(A.depth), s>>>(A);
+    return check_launch("raster_bwd");
+}
+
+}  // namespace
+
+gs_status raster_configure(gs_workspace *ws) {
+    int tw = ws->cfg.tile_w, th = ws->cfg.tile_h;
+    if (tw == 8 && th == 8) return configure_one<8, 8>(ws);
+    if (tw == 16 && th == 16) return configure_one<16, 16>(ws);
+    if (tw == 16 && th == 32) return configure_one<16, 32>(ws);
+    if (tw == 32 && th == 16) return configure_one<32, 16>(ws);
+    return GS_ERR_INVALID_ARG;
+}
+
+gs_status launch_raster_fwd(gs_workspace *ws, float *rgb, float *depth, float *alpha, cudaStream_t s) {
+    RasterArgs A = make_args(ws);
+    A.counter = &ws->st->fwd_counter;
+    A.rgb = rgb;
+    A.depth_out = depth;
+    A.alpha_out = alpha;
+    cudaMemsetAsync(A.counter, 0, sizeof(uint32_t), s);
+    int tw = ws->cfg.tile_w, th = ws->cfg.tile_h;
+    if (tw == 8 && th == 8) return run_fwd<8, 8>(ws, A, s);
+    if (tw == 16 && th == 16) return run_fwd<16, 16>(ws, A, s);
+    if (tw == 16 && th == 32) return run_fwd<16, 32>(ws, A, s);
+    return run_fwd<32, 16>(ws, A, s);
+}
+
+gs_status launch_raster_bwd(gs_workspace *ws, const float *dL_drgb, const float *dL_ddepth,
+                            const float *dL_dalpha, cudaStream_t s) {
+    RasterArgs A = make_args(ws);
+    A.counter = &ws->st->bwd_counter;
+    A.dL_drgb = dL_drgb;
+    A.dL_ddepth = dL_ddepth;
+    A.dL_dalpha = dL_dalpha;
+    A.g2d = ws->g2d;
+    k_zero_g2d<<<ws->num_sms * 4, 256, 0, s>>>(ws->vis_pair, ws->st, ws->g2d);
+    gs_status r = check_launch("zero_g2d");
+    if (r != GS_OK) return r;
+    cudaMemsetAsync(A.counter, 0, sizeof(uint32_t), s);
+    int tw = ws->cfg.tile_w, th = ws->cfg.tile_h;
+    if (tw == 8 && th == 8) return run_bwd<8, 8>(ws, A, s);
+    if (tw == 16 && th == 16) return run_bwd<16, 16>(ws, A, s);
+    if (tw == 16 && th == 32) return run_bwd<16, 32>(ws, A, s);
+    return run_bwd<32, 16>(ws, A, s);
+}
+
+}  // namespace gs

@@ -1,0 +1,405 @@
+// Binning: one instance per (visible pair, covered tile), ordered by the
+// 64-bit key (global tile << 32 | float bits of depth), ties by pair order.
+//
+// Instead of radix-sorting 64-bit keys over every instance, the visible pairs
+// are first sorted by their 32-bit depth key (N_vis elements), the instances
+// are then emitted in that order, and a stable sort by tile id alone (only the
+// ceil(log2 n_tiles) bits that can be set) finishes the job.  Stability makes
+// the result identical to the stable 64-bit sort: within a tile the instances
+// stay in (depth, pair) order.  Per-tile ranges come from key changes.
+//
+// Every count lives on the device (capacity overflow sets a flag), so the
+// sequence needs no host round trip and can be captured in a CUDA graph.  All
+// kernels run a fixed grid of `sort_blocks` blocks, each owning a contiguous
+// chunk of ceil(n / blocks) rounded to a whole tile.
+//
+// The radix sort is a reduce-then-scan LSD sort with 8-bit digits:
+//   hist     per-block digit counts -> table[digit][block]
+//   scan     exclusive scan of the table (digit-major) -> global offsets
+//   scatter  per block, tile by tile in order: stable in-tile ranks from warp
+//            match masks and per-warp digit counts, a local reorder in shared
+//            memory, then coalesced runs written at the global offsets.
+#include "gs_internal.cuh"
+
+namespace gs {
+namespace {
+
+constexpr int T = kSortThreads;
+constexpr int W = T / 32;
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// block-wide exclusive scan of one value per thread (blockDim == T); returns
+// the exclusive prefix and writes the block total to *total
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *sm, uint32_t *total) {
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sm[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t s = lane < W ? sm[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < W) sm[lane] = s;  // inclusive warp totals
+    }
+    __syncthreads();
+    uint32_t base = w > 0 ? sm[w - 1] : 0u;
+    *total = sm[W - 1];
+    __syncthreads();
+    return base + x - v;
+}
+
+// ---------------------------------------------------------------------------
+// visible-pair compaction
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(T) k_count_visible(const uint32_t *pkey, uint32_t n, uint32_t *part,
+                                                    int nb) {
+    __shared__ uint32_t sm[32];
+    uint32_t lo, hi;
+    chunk_range(n, blockIdx.x, nb, T, lo, hi);
+    uint32_t c = 0;
+    for (uint32_t i = lo + threadIdx.x; i < hi; i += T) c += pkey[i] != kInvalidKey;
+    uint32_t tot;
+    block_exclusive_scan(c, sm, &tot);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+// exclusive scan of part[0..nb) in place by one block; the total goes to *total
+// and, when cap > 0, is checked against the capacity
+__global__ void k_scan_parts(uint32_t *part, int nb, uint32_t *total, DevState *st, uint64_t cap,
+                             int mode) {
+    __shared__ uint32_t sm[32];
+    __shared__ unsigned long long carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nb; base += T) {
+        int i = base + threadIdx.x;
+        uint32_t v = i < nb ? part[i] : 0u;
+        uint32_t tot;
+        uint32_t ex = block_exclusive_scan(v, sm, &tot);
+        if (i < nb) part[i] = (uint32_t)(carry + ex);
+        __syncthreads();
+        if (threadIdx.x == 0) carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        unsigned long long t = carry;
+        if (mode == 0) {
+            *total = (uint32_t)t;
+        } else {
+            st->n_inst_needed = t;
+            if (t > cap) {
+                st->flags |= kFlagCapacity;
+                st->n_inst = 0;
+            } else {
+                st->n_inst = (uint32_t)t;
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(T) k_compact_visible(const uint32_t *pkey, uint32_t n, const uint32_t *part,
+                                                      int nb, uint32_t *vis_key, uint32_t *vis_pair) {
+    __shared__ uint32_t sm[32];
+    uint32_t lo, hi;
+    chunk_range(n, blockIdx.x, nb, T, lo, hi);
+    uint32_t base = part[blockIdx.x];
+    for (uint32_t t0 = lo; t0 < hi; t0 += T) {
+        uint32_t i = t0 + threadIdx.x;
+        uint32_t k = i < hi ? pkey[i] : kInvalidKey;
+        uint32_t f = k != kInvalidKey;
+        uint32_t tot;
+        uint32_t ex = block_exclusive_scan(f, sm, &tot);
+        if (f) {
+            vis_key[base + ex] = k;
+            vis_pair[base + ex] = i;
+        }
+        base += tot;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// radix sort passes (count n read from the device)
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(T) k_radix_hist(const uint32_t *keys, const uint32_t *n_ptr, int shift,
+                                                 uint32_t *hist, int nb) {
+    __shared__ uint32_t h[W][256];
+    for (int i = threadIdx.x; i < W * 256; i += T) (&h[0][0])[i] = 0;
+    __syncthreads();
+    uint32_t lo, hi;
+    chunk_range(*n_ptr, blockIdx.x, nb, kSortTile, lo, hi);
+    int w = threadIdx.x >> 5;
+    for (uint32_t i = lo + threadIdx.x; i < hi; i += T) atomicAdd(&h[w][(keys[i] >> shift) & 255u], 1u);
+    __syncthreads();
+    uint32_t s = 0;
+#pragma unroll
+    for (int j = 0; j < W; ++j) s += h[j][threadIdx.x];
+    hist[threadIdx.x * nb + blockIdx.x] = s;
+}
+
+// exclusive scan of the 256 x nb table, one block of 1024 threads
+__global__ void __launch_bounds__(1024) k_radix_scan(uint32_t *hist, int count) {
+    __shared__ uint32_t sm[32];
+    int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    int per = (count + 1023) / 1024;
+    int lo = t * per, hi = min(count, lo + per);
+    uint32_t s = 0;
+    for (int i = lo; i < hi; ++i) s += hist[i];
+    uint32_t x = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sm[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t v = sm[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        sm[lane] = v;
+    }
+    __syncthreads();
+    uint32_t run = (w > 0 ? sm[w - 1] : 0u) + x - s;
+    for (int i = lo; i < hi; ++i) {
+        uint32_t c = hist[i];
+        hist[i] = run;
+        run += c;
+    }
+}
+
+struct ScatterSmem {
+    uint32_t key[kSortTile];
+    uint32_t val[kSortTile];
+    uint32_t wcnt[W][256];
+    uint32_t wpre[W][256];
+    uint32_t base[256], tcnt[256], tstart[256];
+    uint32_t scan[32];
+};
+
+__global__ void __launch_bounds__(T) k_radix_scatter(const uint32_t *kin, const uint32_t *vin,
+                                                    uint32_t *kout, uint32_t *vout,
+                                                    const uint32_t *n_ptr, int shift,
+                                                    const uint32_t *hist, int nb) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ScatterSmem &S = *reinterpret_cast<ScatterSmem *>(smem_raw);
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    uint32_t lo, hi;
+    chunk_range(*n_ptr, blockIdx.x, nb, kSortTile, lo, hi);
+    S.base[t] = hist[t * nb + blockIdx.x];
+    S.tcnt[t] = 0;
+#pragma unroll
+    for (int j = 0; j < W; ++j) S.wcnt[j][t] = 0;
+    __syncthreads();
+    const uint32_t lt = lanemask_lt();
+    for (uint32_t t0 = lo; t0 < hi; t0 += kSortTile) {
+        uint32_t tn = min((uint32_t)kSortTile, hi - t0);
+        uint32_t key[kSortRounds], val[kSortRounds], rank[kSortRounds];
+#pragma unroll
+        for (int r = 0; r < kSortRounds; ++r) {
+            uint32_t i = r * T + t;
+            key[r] = i < tn ? kin[t0 + i] : 0u;
+            val[r] = i < tn ? vin[t0 + i] : 0u;
+        }
+#pragma unroll
+        for (int r = 0; r < kSortRounds; ++r) {
+            bool valid = (uint32_t)(r * T + t) < tn;
+            uint32_t d = (key[r] >> shift) & 255u;
+            // invalid lanes get a private tag so that they match nobody
+            uint32_t tag = valid ? d : (0x100u | (uint32_t)lane);
+            uint32_t m = __match_any_sync(0xffffffffu, tag);
+            uint32_t below = m & lt;
+            if (valid && below == 0) S.wcnt[w][d] = __popc(m);
+            __syncthreads();
+            {
+                uint32_t run = S.tcnt[t];
+#pragma unroll
+                for (int j = 0; j < W; ++j) {
+                    uint32_t c = S.wcnt[j][t];
+                    S.wpre[j][t] = run;
+                    S.wcnt[j][t] = 0;
+                    run += c;
+                }
+                S.tcnt[t] = run;
+            }
+            __syncthreads();
+            rank[r] = valid ? S.wpre[w][d] + __popc(below) : 0u;
+        }
+        __syncthreads();
+        uint32_t tot;
+        uint32_t ex = block_exclusive_scan(S.tcnt[t], S.scan, &tot);
+        S.tstart[t] = ex;
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kSortRounds; ++r) {
+            if ((uint32_t)(r * T + t) < tn) {
+                uint32_t d = (key[r] >> shift) & 255u;
+                uint32_t lp = S.tstart[d] + rank[r];
+                S.key[lp] = key[r];
+                S.val[lp] = val[r];
+            }
+        }
+        __syncthreads();
+        for (uint32_t j = t; j < tn; j += T) {
+            uint32_t k = S.key[j];
+            uint32_t d = (k >> shift) & 255u;
+            uint32_t o = S.base[d] + (j - S.tstart[d]);
+            kout[o] = k;
+            vout[o] = S.val[j];
+        }
+        __syncthreads();
+        S.base[t] += S.tcnt[t];
+        S.tcnt[t] = 0;
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// instance emission and ranges
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t rect_tiles(short4 r) {
+    int nx = (int)r.z - (int)r.x + 1, ny = (int)r.w - (int)r.y + 1;
+    return (nx > 0 && ny > 0) ? (uint32_t)(nx * ny) : 0u;
+}
+
+__global__ void __launch_bounds__(T) k_count_instances(const uint32_t *vis_pair, const short4 *rect,
+                                                      const DevState *st, uint32_t *part, int nb) {
+    __shared__ uint32_t sm[32];
+    uint32_t n = st->n_vis;
+    uint32_t lo, hi;
+    chunk_range(n, blockIdx.x, nb, T, lo, hi);
+    uint32_t c = 0;
+    for (uint32_t i = lo + threadIdx.x; i < hi; i += T) c += rect_tiles(rect[vis_pair[i]]);
+    uint32_t tot;
+    block_exclusive_scan(c, sm, &tot);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(T) k_emit_instances(const uint32_t *vis_pair, const short4 *rect,
+                                                     const ViewInfo *views, int n_views,
+                                                     const DevState *st, const uint32_t *part, int nb,
+                                                     uint32_t *inst_tile, uint32_t *inst_val) {
+    __shared__ uint32_t sm[32];
+    if (st->flags & kFlagCapacity) return;
+    uint32_t n = st->n_vis;
+    uint32_t lo, hi;
+    chunk_range(n, blockIdx.x, nb, T, lo, hi);
+    uint32_t base = part[blockIdx.x];
+    for (uint32_t t0 = lo; t0 < hi; t0 += T) {
+        uint32_t i = t0 + threadIdx.x;
+        uint32_t pair = 0, cnt = 0;
+        short4 r = make_short4(1, 1, 0, 0);
+        if (i < hi) {
+            pair = vis_pair[i];
+            r = rect[pair];
+            cnt = rect_tiles(r);
+        }
+        uint32_t tot;
+        uint32_t off = base + block_exclusive_scan(cnt, sm, &tot);
+        if (cnt) {
+            // the view owning this pair: largest v with pair_off <= pair
+            int lo_v = 0, hi_v = n_views - 1;
+            while (lo_v < hi_v) {
+                int mid = (lo_v + hi_v + 1) >> 1;
+                if ((uint32_t)views[mid].pair_off <= pair) lo_v = mid; else hi_v = mid - 1;
+            }
+            const ViewInfo vi = views[lo_v];
+            for (int ty = r.y; ty <= r.w; ++ty)
+                for (int tx = r.x; tx <= r.z; ++tx) {
+                    inst_tile[off] = (uint32_t)(vi.tile_off + ty * vi.ntx + tx);
+                    inst_val[off] = pair;
+                    ++off;
+                }
+        }
+        base += tot;
+    }
+}
+
+__global__ void k_ranges(const uint32_t *tile, const DevState *st, uint2 *ranges) {
+    uint32_t n = st->n_inst;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        uint32_t t = tile[i];
+        if (i == 0 || tile[i - 1] != t) ranges[t].x = i;
+        if (i + 1 == n || tile[i + 1] != t) ranges[t].y = i + 1;
+    }
+}
+
+// One stable pass over bits [shift, shift+8); swaps in/out.
+gs_status radix_pass(gs_workspace *ws, uint32_t *&k, uint32_t *&v, uint32_t *&k2, uint32_t *&v2,
+                     const uint32_t *n_ptr, int shift, cudaStream_t s) {
+    int nb = ws->sort_blocks;
+    k_radix_hist<<<nb, T, 0, s>>>(k, n_ptr, shift, ws->hist, nb);
+    k_radix_scan<<<1, 1024, 0, s>>>(ws->hist, 256 * nb);
+    k_radix_scatter<<<nb, T, sizeof(ScatterSmem), s>>>(k, v, k2, v2, n_ptr, shift, ws->hist, nb);
+    std::swap(k, k2);
+    std::swap(v, v2);
+    return check_launch("radix_pass");
+}
+
+}  // namespace
+
+gs_status sort_configure() {
+    cudaError_t e = cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(ScatterSmem));
+    if (e != cudaSuccess) {
+        set_last_error(std::string("sort_configure: ") + cudaGetErrorString(e));
+        return GS_ERR_CUDA;
+    }
+    return GS_OK;
+}
+
+gs_status launch_bin_sort(gs_workspace *ws, cudaStream_t s) {
+    int nb = ws->sort_blocks;
+    uint32_t n_pairs = (uint32_t)ws->n_pairs;
+    DevState *st = ws->st;
+    cudaMemsetAsync(&st->n_vis, 0, sizeof(uint32_t) * 2 + sizeof(unsigned long long) + sizeof(uint32_t), s);
+    // 1. compaction of visible pairs
+    k_count_visible<<<nb, T, 0, s>>>(ws->pkey, n_pairs, ws->part, nb);
+    k_scan_parts<<<1, T, 0, s>>>(ws->part, nb, &st->n_vis, st, 0, 0);
+    k_compact_visible<<<nb, T, 0, s>>>(ws->pkey, n_pairs, ws->part, nb, ws->vis_key, ws->vis_pair);
+    gs_status r = check_launch("compact");
+    if (r != GS_OK) return r;
+    // 2. stable sort of the visible pairs by depth key (32 bits)
+    uint32_t *k = ws->vis_key, *v = ws->vis_pair, *k2 = ws->vis_key_alt, *v2 = ws->vis_pair_alt;
+    for (int sh = 0; sh < 32; sh += 8)
+        if ((r = radix_pass(ws, k, v, k2, v2, &st->n_vis, sh, s)) != GS_OK) return r;
+    // after 4 passes the sorted data are back in vis_key / vis_pair
+    // 3. instance offsets, capacity check, emission in depth order
+    // emit into whichever buffer makes the last tile pass end in inst_tile/inst_val
+    int passes = (ws->tile_bits + 7) / 8;
+    uint32_t *tk = (passes & 1) ? ws->inst_tile_alt : ws->inst_tile;
+    uint32_t *tv = (passes & 1) ? ws->inst_val_alt : ws->inst_val;
+    uint32_t *tk2 = (passes & 1) ? ws->inst_tile : ws->inst_tile_alt;
+    uint32_t *tv2 = (passes & 1) ? ws->inst_val : ws->inst_val_alt;
+    k_count_instances<<<nb, T, 0, s>>>(v, ws->rect, st, ws->part, nb);
+    k_scan_parts<<<1, T, 0, s>>>(ws->part, nb, nullptr, st, (uint64_t)ws->inst_cap, 1);
+    k_emit_instances<<<nb, T, 0, s>>>(v, ws->rect, ws->views, ws->n_views, st, ws->part, nb, tk, tv);
+    if ((r = check_launch("emit")) != GS_OK) return r;
+    // 4. stable sort of the instances by tile id
+    for (int p = 0; p < passes; ++p)
+        if ((r = radix_pass(ws, tk, tv, tk2, tv2, &st->n_inst, 8 * p, s)) != GS_OK) return r;
+    // 5. ranges
+    cudaMemsetAsync(ws->ranges, 0, sizeof(uint2) * ws->n_tiles, s);
+    k_ranges<<<ws->num_sms * 8, 256, 0, s>>>(ws->inst_tile, st, ws->ranges);
+    return check_launch("ranges");
+}
+
+}  // namespace gs

@@ -1,0 +1,368 @@
+"""Thin Python binding of libgsraster (include/gs.h).
+
+Argument marshalling only: every step of the hot path runs in the library's
+CUDA kernels.  The functions below carry the C names and raise ``GsError`` on
+a non-OK status.  ``Renderer`` holds a workspace plus the device copy of the
+cameras and passes torch tensors' device pointers and the current CUDA
+stream; ``GSRender`` wraps forward and backward as a torch.autograd.Function.
+
+There is no fallback: if ``libgsraster.so`` has not been built, loading fails
+with an error that says so.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libgsraster.so")
+
+GS_OK, GS_ERR_INVALID_ARG, GS_ERR_CAPACITY, GS_ERR_CUDA, GS_ERR_STATE = range(5)
+GS_MAX_VIEWS = 64
+GS_MAX_SUBMAPS = 64
+# gs_workspace_copy buffer ids
+BUF_RECORDS, BUF_PAIR_KEYS, BUF_RECTS, BUF_INST_TILES, BUF_INST_PAIRS, BUF_RANGES, BUF_LAST, BUF_TFIN, BUF_G2D = range(9)
+
+EXPORTED = ("gs_config_default", "gs_workspace_create", "gs_workspace_destroy", "gs_project",
+            "gs_bin_sort", "gs_render_fwd", "gs_depth_loss", "gs_image_l1", "gs_render_bwd",
+            "gs_workspace_status", "gs_workspace_info", "gs_workspace_copy", "gs_status_string",
+            "gs_last_error")
+
+
+class GsError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} ({status})" + (f": {detail}" if detail else ""))
+
+
+class GsCamera(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("submap", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("fx", ctypes.c_float), ("fy", ctypes.c_float),
+                ("cx", ctypes.c_float), ("cy", ctypes.c_float), ("T_cw", ctypes.c_float * 12)]
+
+
+class GsConfig(ctypes.Structure):
+    _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("batch_depth", ctypes.c_int32),
+                ("depth_mode", ctypes.c_int32), ("near_z", ctypes.c_float), ("dilation", ctypes.c_float),
+                ("alpha_min", ctypes.c_float), ("alpha_max", ctypes.c_float), ("t_min", ctypes.c_float),
+                ("jac_clamp", ctypes.c_float), ("ext_rel_pad", ctypes.c_float),
+                ("ext_abs_pad", ctypes.c_float), ("sigma_L", ctypes.c_float), ("sigma_U", ctypes.c_float),
+                ("lambda_L", ctypes.c_float), ("reserved", ctypes.c_float)]
+
+
+class GsGaussians(ctypes.Structure):
+    _fields_ = [("means", ctypes.c_void_p), ("log_scales", ctypes.c_void_p), ("quats", ctypes.c_void_p),
+                ("opacity_logits", ctypes.c_void_p), ("sh", ctypes.c_void_p), ("n", ctypes.c_int64)]
+
+
+class GsGrads(ctypes.Structure):
+    _fields_ = [("means", ctypes.c_void_p), ("log_scales", ctypes.c_void_p), ("quats", ctypes.c_void_p),
+                ("opacity_logits", ctypes.c_void_p), ("sh", ctypes.c_void_p), ("pose", ctypes.c_void_p),
+                ("densify_acc", ctypes.c_void_p), ("densify_cnt", ctypes.c_void_p)]
+
+
+assert ctypes.sizeof(GsCamera) == 80 and ctypes.sizeof(GsConfig) == 64
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libgsraster.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; "
+                           "g.build()'` (no CPU fallback exists)")
+    L = ctypes.CDLL(LIB_PATH)
+    P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    L.gs_config_default.argtypes = [ctypes.POINTER(GsConfig)]
+    L.gs_config_default.restype = None
+    L.gs_workspace_create.argtypes = [ctypes.POINTER(GsCamera), i32, ctypes.POINTER(ctypes.c_int64), i32, i32,
+                                      ctypes.POINTER(GsConfig), i64, ctypes.POINTER(ctypes.c_void_p)]
+    L.gs_workspace_destroy.argtypes = [P]
+    L.gs_workspace_destroy.restype = None
+    L.gs_project.argtypes = [P, ctypes.POINTER(GsGaussians), P, P]
+    L.gs_bin_sort.argtypes = [P, P]
+    L.gs_render_fwd.argtypes = [P, P, P, P, P]
+    L.gs_depth_loss.argtypes = [P, P, P, P, i64, P, P, P]
+    L.gs_image_l1.argtypes = [P, P, P, P, P, P]
+    L.gs_render_bwd.argtypes = [P, ctypes.POINTER(GsGaussians), P, P, P, P, ctypes.POINTER(GsGrads), P]
+    L.gs_workspace_status.argtypes = [P, P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+    L.gs_workspace_info.argtypes = [P, ctypes.POINTER(ctypes.c_int64), i32]
+    L.gs_workspace_copy.argtypes = [P, i32, P, ctypes.POINTER(ctypes.c_int64), P]
+    L.gs_status_string.argtypes = [i32]
+    L.gs_status_string.restype = ctypes.c_char_p
+    L.gs_last_error.argtypes = []
+    L.gs_last_error.restype = ctypes.c_char_p
+    for name in ("gs_workspace_create", "gs_project", "gs_bin_sort", "gs_render_fwd", "gs_depth_loss",
+                 "gs_image_l1", "gs_render_bwd", "gs_workspace_status", "gs_workspace_info",
+                 "gs_workspace_copy"):
+        getattr(L, name).restype = i32
+    _lib = L
+    return L
+
+
+def status_string(s: int) -> str:
+    return lib().gs_status_string(int(s)).decode()
+
+
+def last_error() -> str:
+    return lib().gs_last_error().decode()
+
+
+def _check(st: int, where: str):
+    if st != GS_OK:
+        raise GsError(st, where, last_error())
+
+
+# ---------------------------------------------------------------------------
+# C names
+# ---------------------------------------------------------------------------
+
+def gs_config_default(**overrides) -> GsConfig:
+    c = GsConfig()
+    lib().gs_config_default(ctypes.byref(c))
+    for k, v in overrides.items():
+        setattr(c, k, v)
+    return c
+
+
+def gs_workspace_create(cams, n_views, submap_offsets, n_submaps, sh_degree, cfg, inst_capacity):
+    out = ctypes.c_void_p()
+    offs = (ctypes.c_int64 * (n_submaps + 1))(*[int(x) for x in submap_offsets])
+    _check(lib().gs_workspace_create(cams, n_views, offs, n_submaps, sh_degree, ctypes.byref(cfg),
+                                     int(inst_capacity), ctypes.byref(out)), "gs_workspace_create")
+    return out
+
+
+def gs_workspace_destroy(ws):
+    lib().gs_workspace_destroy(ws)
+
+
+def gs_project(ws, g: GsGaussians, cams_dev, stream):
+    _check(lib().gs_project(ws, ctypes.byref(g), cams_dev, stream), "gs_project")
+
+
+def gs_bin_sort(ws, stream):
+    _check(lib().gs_bin_sort(ws, stream), "gs_bin_sort")
+
+
+def gs_render_fwd(ws, rgb, depth, alpha, stream):
+    _check(lib().gs_render_fwd(ws, rgb, depth, alpha, stream), "gs_render_fwd")
+
+
+def gs_depth_loss(ws, depth, alpha, lidar, n_pts, loss, dL_ddepth, stream):
+    _check(lib().gs_depth_loss(ws, depth, alpha, lidar, int(n_pts), loss, dL_ddepth, stream), "gs_depth_loss")
+
+
+def gs_image_l1(ws, rgb, target, loss, dL_drgb, stream):
+    _check(lib().gs_image_l1(ws, rgb, target, loss, dL_drgb, stream), "gs_image_l1")
+
+
+def gs_render_bwd(ws, g: GsGaussians, cams_dev, dL_drgb, dL_ddepth, dL_dalpha, grads: GsGrads, stream):
+    _check(lib().gs_render_bwd(ws, ctypes.byref(g), cams_dev, dL_drgb, dL_ddepth, dL_dalpha,
+                               ctypes.byref(grads), stream), "gs_render_bwd")
+
+
+def gs_workspace_status(ws, stream):
+    """Returns (status, n_instances_needed, n_visible); does not raise on capacity."""
+    ni, nv = ctypes.c_int64(0), ctypes.c_int64(0)
+    st = lib().gs_workspace_status(ws, stream, ctypes.byref(ni), ctypes.byref(nv))
+    if st not in (GS_OK, GS_ERR_CAPACITY):
+        _check(st, "gs_workspace_status")
+    return st, int(ni.value), int(nv.value)
+
+
+def gs_workspace_info(ws) -> dict:
+    v = (ctypes.c_int64 * 7)()
+    _check(lib().gs_workspace_info(ws, v, 7), "gs_workspace_info")
+    keys = ("n_pairs", "n_tiles", "n_pix", "inst_capacity", "n_views", "n", "bytes")
+    return dict(zip(keys, [int(x) for x in v]))
+
+
+def gs_workspace_copy(ws, which, dst, nbytes, stream):
+    b = ctypes.c_int64(nbytes)
+    _check(lib().gs_workspace_copy(ws, int(which), dst, ctypes.byref(b), stream), "gs_workspace_copy")
+    return b.value
+
+
+def gs_workspace_buffer_bytes(ws, which) -> int:
+    b = ctypes.c_int64(0)
+    _check(lib().gs_workspace_copy(ws, int(which), None, ctypes.byref(b), None), "gs_workspace_copy")
+    return int(b.value)
+
+
+# ---------------------------------------------------------------------------
+# torch convenience layer (marshalling only)
+# ---------------------------------------------------------------------------
+
+def camera_structs(cameras) -> ctypes.Array:
+    """ctypes array of GsCamera from objects with width/height/submap/fx/fy/cx/cy/T_cw."""
+    arr = (GsCamera * len(cameras))()
+    for i, c in enumerate(cameras):
+        arr[i].width, arr[i].height, arr[i].submap, arr[i].reserved = int(c.width), int(c.height), int(c.submap), 0
+        arr[i].fx, arr[i].fy, arr[i].cx, arr[i].cy = float(c.fx), float(c.fy), float(c.cx), float(c.cy)
+        T = np.asarray(c.T_cw, np.float64).reshape(12)
+        for k in range(12):
+            arr[i].T_cw[k] = float(T[k])
+    return arr
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Renderer:
+    """A workspace for a fixed rig (camera sizes, submap partition, SH degree)
+    and the device copy of the cameras.  All tensors are float32 CUDA tensors."""
+
+    def __init__(self, cameras, submap_offsets, sh_degree, config: GsConfig | None = None,
+                 inst_capacity: int | None = None, device=None):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device or "cuda")
+        self.cameras = list(cameras)
+        self.n_views = len(self.cameras)
+        self.submap_offsets = [int(x) for x in submap_offsets]
+        self.n = self.submap_offsets[-1]
+        self.sh_degree = int(sh_degree)
+        self.config = config or gs_config_default()
+        cams = camera_structs(self.cameras)
+        self.n_pix = sum(c.width * c.height for c in self.cameras)
+        if inst_capacity is None:
+            inst_capacity = max(1 << 20, 16 * self.n * max(1, self.n_views))
+            inst_capacity = min(inst_capacity, (1 << 31) - 1)
+        with torch.cuda.device(self.device):
+            self.ws = gs_workspace_create(cams, self.n_views, self.submap_offsets, len(self.submap_offsets) - 1,
+                                          self.sh_degree, self.config, inst_capacity)
+        self.info = gs_workspace_info(self.ws)
+        self.cams_dev = torch.empty(ctypes.sizeof(cams), dtype=torch.uint8, device=self.device)
+        self.set_cameras(self.cameras)
+
+    def close(self):
+        if getattr(self, "ws", None):
+            gs_workspace_destroy(self.ws)
+            self.ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_cameras(self, cameras):
+        """Upload intrinsics and poses (sizes and submaps must not change)."""
+        cams = camera_structs(cameras)
+        host = self.torch.frombuffer(bytearray(bytes(cams)), dtype=self.torch.uint8)
+        self.cams_dev.copy_(host.to(self.device, non_blocking=False))
+        self.cameras = list(cameras)
+
+    @staticmethod
+    def gaussians(means, log_scales, quats, opacity_logits, sh) -> GsGaussians:
+        return GsGaussians(means.data_ptr(), log_scales.data_ptr(), quats.data_ptr(),
+                           opacity_logits.data_ptr(), sh.data_ptr(), means.shape[0])
+
+    def forward(self, means, log_scales, quats, opacity_logits, sh, stream=None, outputs=None):
+        """project -> bin/sort -> rasterise. Returns (rgb [3*N_pix], depth [N_pix], alpha [N_pix])."""
+        torch = self.torch
+        s = _stream(stream)
+        g = self.gaussians(means, log_scales, quats, opacity_logits, sh)
+        if outputs is None:
+            outputs = (torch.empty(3 * self.n_pix, device=self.device), torch.empty(self.n_pix, device=self.device),
+                       torch.empty(self.n_pix, device=self.device))
+        rgb, depth, alpha = outputs
+        gs_project(self.ws, g, _ptr(self.cams_dev), s)
+        gs_bin_sort(self.ws, s)
+        gs_render_fwd(self.ws, _ptr(rgb), _ptr(depth), _ptr(alpha), s)
+        return rgb, depth, alpha
+
+    def backward(self, means, log_scales, quats, opacity_logits, sh, dL_drgb, dL_ddepth, dL_dalpha=None,
+                 grads=None, stream=None, pose=True, densify=True):
+        """Accumulates gradients into ``grads`` (dict of tensors; allocated zeroed if None)."""
+        torch = self.torch
+        s = _stream(stream)
+        g = self.gaussians(means, log_scales, quats, opacity_logits, sh)
+        if grads is None:
+            grads = dict(means=torch.zeros_like(means), log_scales=torch.zeros_like(log_scales),
+                         quats=torch.zeros_like(quats), opacity_logits=torch.zeros_like(opacity_logits),
+                         sh=torch.zeros_like(sh))
+            if pose:
+                grads["pose"] = torch.zeros(self.n_views, 6, device=self.device)
+            if densify:
+                grads["densify_acc"] = torch.zeros(self.n, device=self.device)
+                grads["densify_cnt"] = torch.zeros(self.n, dtype=torch.int32, device=self.device)
+        gg = GsGrads(grads["means"].data_ptr(), grads["log_scales"].data_ptr(), grads["quats"].data_ptr(),
+                     grads["opacity_logits"].data_ptr(), grads["sh"].data_ptr(),
+                     grads["pose"].data_ptr() if "pose" in grads else None,
+                     grads["densify_acc"].data_ptr() if "densify_acc" in grads else None,
+                     grads["densify_cnt"].data_ptr() if "densify_cnt" in grads else None)
+        gs_render_bwd(self.ws, g, _ptr(self.cams_dev), _ptr(dL_drgb), _ptr(dL_ddepth), _ptr(dL_dalpha), gg, s)
+        return grads
+
+    def depth_loss(self, depth, alpha, lidar, dL_ddepth=None, stream=None):
+        loss = self.torch.zeros(1, device=self.device)
+        gs_depth_loss(self.ws, _ptr(depth), _ptr(alpha), _ptr(lidar), lidar.shape[0], _ptr(loss),
+                      _ptr(dL_ddepth), _stream(stream))
+        return loss
+
+    def image_l1(self, rgb, target, dL_drgb=None, stream=None):
+        loss = self.torch.zeros(1, device=self.device)
+        gs_image_l1(self.ws, _ptr(rgb), _ptr(target), _ptr(loss), _ptr(dL_drgb), _stream(stream))
+        return loss
+
+    def status(self, stream=None):
+        return gs_workspace_status(self.ws, _stream(stream))
+
+    def buffer(self, which, dtype):
+        torch = self.torch
+        nb = gs_workspace_buffer_bytes(self.ws, which)
+        out = torch.empty(nb, dtype=torch.uint8, device=self.device)
+        gs_workspace_copy(self.ws, which, _ptr(out), nb, _stream())
+        return out.view(dtype)
+
+
+def _make_render_function():
+    import torch
+
+    class GSRender(torch.autograd.Function):
+        """(rgb, depth, alpha) = GSRender.apply(renderer, means, log_scales, quats, opacity_logits, sh,
+        pose_delta).  ``pose_delta`` is a [V, 6] tensor whose gradient is the pose twist gradient
+        dL/d(rho, phi) at zero (its value is not used: poses come from the renderer's cameras)."""
+
+        @staticmethod
+        def forward(ctx, renderer, means, log_scales, quats, opacity_logits, sh, pose_delta):
+            rgb, depth, alpha = renderer.forward(means, log_scales, quats, opacity_logits, sh)
+            ctx.renderer = renderer
+            ctx.save_for_backward(means, log_scales, quats, opacity_logits, sh)
+            return rgb, depth, alpha
+
+        @staticmethod
+        def backward(ctx, g_rgb, g_depth, g_alpha):
+            means, log_scales, quats, opacity_logits, sh = ctx.saved_tensors
+            r = ctx.renderer
+            z = lambda t, n: t.contiguous() if t is not None else torch.zeros(n, device=r.device)
+            grads = r.backward(means, log_scales, quats, opacity_logits, sh, z(g_rgb, 3 * r.n_pix),
+                               z(g_depth, r.n_pix), z(g_alpha, r.n_pix), densify=False)
+            return (None, grads["means"], grads["log_scales"], grads["quats"], grads["opacity_logits"],
+                    grads["sh"], grads["pose"])
+
+    return GSRender
+
+
+_GSRender = None
+
+
+def GSRender():
+    global _GSRender
+    if _GSRender is None:
+        _GSRender = _make_render_function()
+    return _GSRender

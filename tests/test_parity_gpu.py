@@ -1,0 +1,146 @@
+"""CUDA path vs the FP64 oracle, element by element, on seeded scenes.
+
+Tolerances (from the benchmark spec of the method's bar):
+  * sort keys, instance order and tile ranges: bit-exact;
+  * forward images: within 1e-5 absolute;
+  * gradients: within 1e-4 relative (per-tensor L2).
+Pixels where the oracle sees a discrete decision (alpha >= 1/255, the T stop)
+within MARGIN of its threshold are left out of the image comparison and
+counted; their upstream gradients are zeroed on both sides.  Pairs whose tile
+rectangle has a decision inside the oracle's ambiguity band are left out of
+the key comparison and counted.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2510_26358_gb300 import scenes as S
+from tests.gpu_helpers import decode_records, pixel_weights, rel_l2, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+FWD_TOL = 1e-5
+GRAD_TOL = 1e-4
+MARGIN = 1e-4
+
+
+def _scenes():
+    return {
+        "box10k": S.random_box_scene(10_000, 320, 240, 300.0, seed=0),
+        "orchard_rig": S.orchard_scene(40_000, 3, 4, 200, 120, rear=True, pose_noise=True,
+                                       lidar_per_view=3000, seed=1, name="orchard_rig"),
+        "submaps": S.uneven_submaps(4, 3000, 30000, seed=2, scale=1.0,
+                                    resolutions=((96, 64), (160, 96), (128, 128))),
+    }
+
+
+SCENES = _scenes()
+
+
+@pytest.fixture(scope="module", params=list(SCENES))
+def case(request):
+    sc = SCENES[request.param]
+    ocfg = O.Config()
+    P, cams, rec, keys, vals, ranges, out = run_oracle(sc, ocfg)
+    keep = out["margin"] > MARGIN
+    rng = np.random.default_rng(7)
+    rgbmask, pmask = pixel_weights(sc, keep)
+    gC = rng.normal(size=3 * sc.n_pix) * rgbmask
+    gD = 0.1 * rng.normal(size=sc.n_pix) * pmask
+    gA = rng.normal(size=sc.n_pix) * pmask
+    g = run_gpu(sc, ocfg, gC, gD, gA)
+    go = O.render_bwd(P, cams, ocfg, rec, vals, ranges, gC, gD, gA)
+    yield dict(name=request.param, sc=sc, ocfg=ocfg, rec=rec, keys=keys, vals=vals, ranges=ranges,
+               out=out, keep=keep, gpu=g, go=go)
+    g["renderer"].close()
+
+
+def test_status_ok(case):
+    g = case["gpu"]
+    assert g["status"] == 0
+    assert g["n_vis"] == int(case["rec"][:, O.C_VIS].sum()) or case["rec"][:, O.C_RECT_AMBIG].any()
+    assert g["n_inst"] > 0
+
+
+def test_projection(case):
+    rec, g = case["rec"], case["gpu"]
+    amb = rec[:, O.C_RECT_AMBIG] > 0
+    vis_o = rec[:, O.C_VIS] > 0
+    vis_g = g["pkey"] != 0xFFFFFFFF
+    assert np.array_equal(vis_o[~amb], vis_g[~amb]), "visibility differs"
+    both = vis_o & vis_g
+    d = decode_records(g["rec"][both])
+    r = rec[both]
+    # depth keys: bit-exact
+    z32_o = r[:, O.C_Z32].astype(np.float32)
+    assert np.array_equal(d["z"].view(np.uint32), z32_o.view(np.uint32))
+    assert np.array_equal(g["pkey"][both], z32_o.view(np.uint32))
+    # pixel mean
+    assert np.abs(d["u"] - r[:, O.C_U]).max() < 1e-6 * (1 + np.abs(r[:, O.C_U]).max())
+    assert np.abs(d["v"] - r[:, O.C_V]).max() < 1e-6 * (1 + np.abs(r[:, O.C_V]).max())
+    # conic, relative to its scale
+    sc = np.sqrt(r[:, O.C_QA] * r[:, O.C_QC])
+    for k, c in (("qa", O.C_QA), ("qb", O.C_QB), ("qc", O.C_QC)):
+        assert (np.abs(d[k] - r[:, c]) / sc).max() < 1e-5, k
+    assert np.abs(d["log2o"] - np.log2(r[:, O.C_OPA])).max() < 2e-6
+    assert np.abs(d["rgb"] - r[:, O.C_R:O.C_B + 1]).max() < 2e-6
+    # tile rectangles, except pairs in the ambiguity band
+    ok = both & ~amb
+    rect_o = rec[ok][:, [O.C_TX0, O.C_TY0, O.C_TX1, O.C_TY1]].astype(np.int64)
+    assert np.array_equal(g["rect"][ok].astype(np.int64), rect_o)
+    print(f"[{case['name']}] visible {both.sum()}, ambiguous rects {amb.sum()}")
+
+
+def test_keys_and_ranges_bit_exact(case):
+    rec, g = case["rec"], case["gpu"]
+    amb_pairs = np.nonzero(rec[:, O.C_RECT_AMBIG] > 0)[0]
+    gp = g["inst_pair"].astype(np.int64)
+    gt = g["inst_tile"].astype(np.uint64)
+    gz = g["pkey"][gp].astype(np.uint64)
+    gkeys = (gt << np.uint64(32)) | gz
+    okeys, ovals = case["keys"], case["vals"]
+    keep_g = ~np.isin(gp, amb_pairs)
+    keep_o = ~np.isin(ovals, amb_pairs)
+    assert np.array_equal(gkeys[keep_g], okeys[keep_o]), "sorted keys differ"
+    assert np.array_equal(gp[keep_g], ovals[keep_o]), "instance order differs"
+    if len(amb_pairs) == 0:
+        assert np.array_equal(g["ranges"].astype(np.int64), case["ranges"])
+    else:
+        # ranges must still describe the GPU's own sorted tile ids exactly
+        tiles = g["inst_tile"].astype(np.int64)
+        for t in range(g["ranges"].shape[0]):
+            s, e = g["ranges"][t]
+            assert np.all(tiles[s:e] == t)
+        assert g["ranges"][:, 1].astype(np.int64).sum() - g["ranges"][:, 0].astype(np.int64).sum() == len(tiles)
+    print(f"[{case['name']}] instances {len(gkeys)}, ambiguous pairs {len(amb_pairs)}")
+
+
+def test_forward_images(case):
+    out, g, keep = case["out"], case["gpu"], case["keep"]
+    rgbmask, pmask = pixel_weights(case["sc"], keep)
+    e_rgb = np.abs(g["rgb"].astype(np.float64) - out["rgb"])[rgbmask].max()
+    e_d = np.abs(g["depth"].astype(np.float64) - out["depth"])[pmask].max()
+    e_a = np.abs(g["alpha"].astype(np.float64) - out["alpha"])[pmask].max()
+    e_t = np.abs(g["tfin"].astype(np.float64) - out["T"])[pmask].max()
+    print(f"[{case['name']}] excluded pixels {(~keep).sum()} of {keep.size}; max err rgb {e_rgb:.2e} "
+          f"depth {e_d:.2e} alpha {e_a:.2e} T {e_t:.2e}")
+    assert e_rgb <= FWD_TOL and e_a <= FWD_TOL and e_t <= FWD_TOL
+    # depth is alpha-weighted metres: same absolute bound per metre of depth
+    zmax = case["rec"][case["rec"][:, O.C_VIS] > 0, O.C_Z].max()
+    assert e_d <= FWD_TOL * max(1.0, zmax)
+    assert (~keep).sum() <= 0.01 * keep.size
+
+
+def test_gradients(case):
+    g, go = case["gpu"], case["go"]
+    res = {}
+    for k in ("means", "log_scales", "quats", "opacity_logits", "sh", "pose", "dens_acc"):
+        gk = "g_densify_acc" if k == "dens_acc" else "g_" + k
+        res[k] = rel_l2(g[gk], go[k])
+    vis = case["rec"][:, O.C_VIS] > 0
+    res["g2d"] = rel_l2(g["g2d"][vis], go["g2d"][vis])
+    cnt = g["g_densify_cnt"].astype(np.float64)
+    print(f"[{case['name']}] " + " ".join(f"{k} {v:.1e}" for k, v in res.items()))
+    assert np.array_equal(cnt, go["dens_cnt"]) or case["rec"][:, O.C_RECT_AMBIG].any()
+    for k, v in res.items():
+        assert v <= GRAD_TOL, (k, v)
