@@ -1,0 +1,509 @@
+#!/usr/bin/env python3
+"""Benchmark of the batched multi-view Gaussian-splatting mapping step.
+
+One step = one mapping iteration of a keyframe (Sec. III-B/C): project every
+(view, Gaussian) pair, bin and sort, rasterise RGB + depth + alpha for all
+cameras, the L1 photometric loss (Eq. 6, lambda = 0) and the LiDAR depth loss
+(Eq. 7), then the full backward to every Gaussian parameter and every camera
+pose.  The metric is rendered megapixels per second over the whole step.
+
+Default workload: the 500k-Gaussian orchard (3 rows of 8 trees, trunk
+cylinders + canopy balls, SH degree 3) seen by a 3-camera rig of 1280x720,
+with 20k LiDAR returns per view and an L1 depth term.  Synthetic, seeded.
+
+Arms:
+  default            the batched path: one CUDA graph per step covering every
+                     kernel of every view; L2 flushed between timed steps.
+  --impl reference   the FP64 CPU oracle on a bounded sample of the same
+                     workload (this paper ships no code to compare against).
+
+Multi-GPU (--gpus N under torchrun): the path does not exchange anything
+between keyframes, so each rank runs an independent replica (weak scaling);
+value = pixels of all ranks / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd rendered Mpix/s (RGB+depth, multi-view batch)"
+UNIT = "Mpix/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="orchard500k")
+    ap.add_argument("--tile", default="16x16")
+    ap.add_argument("--depth", type=int, default=256)
+    ap.add_argument("--no-per-view", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=640, help="crop width (px) per view for the oracle sample")
+    return ap.parse_args()
+
+
+def workload_config(sc, args, tile=None, depth=None):
+    W = sorted({(c.width, c.height) for c in sc.cameras})
+    return {"workload": sc.name, "n_gaussians": sc.n, "views": len(sc.cameras),
+            "resolutions": [f"{w}x{h}" for w, h in W], "n_pix": sc.n_pix, "sh_degree": sc.sh_degree,
+            "lidar_points": int(sc.lidar.shape[0]), "losses": "L1 rgb + L1 depth",
+            "tile": tile or args.tile, "batch_depth": depth or args.depth,
+            "l2": "flushed (512 MiB write) before every timed step", "graph": True,
+            "parallelism": "replicas", "seed": 0}
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), float(parts[2]), parts[3], parts[4:8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[i] for r in rows for i, f in enumerate(r[4]) if f.lower().startswith("active")})
+        return {"sm_mhz": float(np.median([r[0] for r in rows])), "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": reasons}
+
+
+def gpu_uuid(torch):
+    try:
+        u = torch.cuda.get_device_properties(torch.cuda.current_device()).uuid
+        return "GPU-" + str(u)
+    except Exception:
+        return str(torch.cuda.current_device())
+
+
+# ---------------------------------------------------------------------------
+# the step
+# ---------------------------------------------------------------------------
+
+class Step:
+    """All device buffers of one mapping step plus the calls that make it."""
+
+    def __init__(self, G, torch, sc, cfg, dev, inst_capacity=None):
+        self.G, self.torch, self.sc, self.dev = G, torch, sc, dev
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+        self.P = [t(sc.means), t(sc.log_scales), t(sc.quats), t(sc.opacity_logits), t(sc.sh)]
+        self.target = t(sc.target)
+        self.lidar = t(sc.lidar)
+        self.r = G.Renderer(sc.cameras, sc.submap_offsets, sc.sh_degree, config=cfg,
+                            inst_capacity=inst_capacity or max(1 << 22, 8 * sc.n))
+        npx = self.r.n_pix
+        self.rgb = torch.empty(3 * npx, device=dev)
+        self.depth = torch.empty(npx, device=dev)
+        self.alpha = torch.empty(npx, device=dev)
+        self.g_rgb = torch.zeros(3 * npx, device=dev)
+        self.g_depth = torch.zeros(npx, device=dev)
+        self.grads = dict(means=torch.zeros_like(self.P[0]), log_scales=torch.zeros_like(self.P[1]),
+                          quats=torch.zeros_like(self.P[2]), opacity_logits=torch.zeros_like(self.P[3]),
+                          sh=torch.zeros_like(self.P[4]), pose=torch.zeros(len(sc.cameras), 6, device=dev),
+                          densify_acc=torch.zeros(sc.n, device=dev),
+                          densify_cnt=torch.zeros(sc.n, dtype=torch.int32, device=dev))
+        self.loss_rgb = torch.zeros(1, device=dev)
+        self.loss_depth = torch.zeros(1, device=dev)
+
+    def zero(self):
+        self.g_rgb.zero_()
+        self.g_depth.zero_()
+        for v in self.grads.values():
+            v.zero_()
+
+    # stage-by-stage so that the breakdown can put events between them
+    def stages(self):
+        G, r = self.G, self.r
+        torch = self.torch
+
+        def project():
+            s = G._stream()
+            G.gs_project(r.ws, r.gaussians(*self.P), G._ptr(r.cams_dev), s)
+
+        def binsort():
+            G.gs_bin_sort(r.ws, G._stream())
+
+        def fwd():
+            G.gs_render_fwd(r.ws, G._ptr(self.rgb), G._ptr(self.depth), G._ptr(self.alpha), G._stream())
+
+        def losses():
+            s = G._stream()
+            G.gs_image_l1(r.ws, G._ptr(self.rgb), G._ptr(self.target), G._ptr(self.loss_rgb), G._ptr(self.g_rgb), s)
+            G.gs_depth_loss(r.ws, G._ptr(self.depth), G._ptr(self.alpha), G._ptr(self.lidar), self.lidar.shape[0],
+                            G._ptr(self.loss_depth), G._ptr(self.g_depth), s)
+
+        def bwd():
+            gg = self.grads
+            grads = G.GsGrads(*(gg[k].data_ptr() for k in ("means", "log_scales", "quats", "opacity_logits", "sh",
+                                                            "pose", "densify_acc", "densify_cnt")))
+            G.gs_render_bwd(r.ws, r.gaussians(*self.P), G._ptr(r.cams_dev), G._ptr(self.g_rgb),
+                            G._ptr(self.g_depth), None, grads, G._stream())
+        return [("zero", self.zero), ("project", project), ("bin_sort", binsort), ("raster_fwd", fwd),
+                ("losses", losses), ("backward", bwd)]
+
+    def run(self):
+        for _, f in self.stages():
+            f()
+
+
+def make_graph(torch, step):
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        for _ in range(2):
+            step.run()
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        step.run()
+    return g
+
+
+def time_steps(torch, fn, steps, warmup, flush):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        times.append((e0, e1))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in times]
+
+
+def stage_breakdown(torch, step, steps, flush):
+    names = [n for n, _ in step.stages()]
+    acc = {n: [] for n in names}
+    for _ in range(steps):
+        flush.zero_()
+        evs = []
+        for n, f in step.stages():
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            f()
+            e1.record()
+            evs.append((n, e0, e1))
+        torch.cuda.synchronize()
+        for n, a, b in evs:
+            acc[n].append(a.elapsed_time(b))
+    return {n: float(np.mean(v)) for n, v in acc.items()}
+
+
+def kernel_breakdown(torch, G, step, steps, flush):
+    """Mean CUDA-event duration of every library stage (events recorded by the
+    library itself around each kernel group, on the launching stream)."""
+    G.gs_workspace_set_profiling(step.r.ws, True)
+    acc = {}
+    for _ in range(steps):
+        flush.zero_()
+        step.run()
+        for k, v in G.gs_workspace_stage_ms(step.r.ws).items():
+            acc.setdefault(k, []).append(v)
+    G.gs_workspace_set_profiling(step.r.ws, False)
+    return {k: float(np.mean(v)) for k, v in acc.items()}
+
+
+# ---------------------------------------------------------------------------
+# reference arm and CPU baseline: the FP64 oracle on a bounded sample
+# ---------------------------------------------------------------------------
+
+def oracle_sample(sc, crop_w):
+    """The workload's cameras cropped to a centred window crop_w wide (same
+    aspect ratio): same scene, same Gaussians, fewer pixels."""
+    cams = []
+    for c in sc.cameras:
+        w = min(crop_w, c.width)
+        h = max(1, int(round(w * c.height / c.width)))
+        cams.append(c.crop(int(c.cx) - w // 2, int(c.cy) - h // 2, w, h))
+    return cams
+
+
+def run_oracle_step(O, P, cams, cfg, lidar_full, sc):
+    """project -> bin -> forward -> L1 image + L1 depth losses -> backward, in FP64."""
+    rec = O.project(P, cams, cfg)
+    keys, vals, ranges = O.bin(P, cams, cfg, rec)
+    out = O.render_fwd(P, cams, cfg, rec, vals, ranges)
+    npx = sum(c.width * c.height for c in cams)
+    target = np.zeros(3 * npx)
+    _, gC = O.image_l1(out["rgb"], target)
+    _, gD, _ = O.depth_loss(P, cams, cfg, out["depth"], out["alpha"], lidar_full, mode=0)
+    O.render_bwd(P, cams, cfg, rec, vals, ranges, gC, gD)
+    return npx
+
+
+def cpu_baseline(sc, args, reps=1):
+    import oracle as O
+    O.build()
+    cams = O.as_float32_cameras(oracle_sample(sc, args.cpu_sample))
+    P = O.Params.from_scene(sc)
+    # LiDAR returns re-expressed in the crops' pixel coordinates
+    lid = sc.lidar.astype(np.float64).copy()
+    for v, (c, cc) in enumerate(zip(sc.cameras, cams)):
+        m = lid[:, 3] == v
+        lid[m, 0] -= (c.cx - cc.cx)
+        lid[m, 1] -= (c.cy - cc.cy)
+    cfg = O.Config()
+    t0 = time.perf_counter()
+    npx = 0
+    for _ in range(reps):
+        npx += run_oracle_step(O, P, cams, cfg, lid, sc)
+    dt = time.perf_counter() - t0
+    sample = (f"FP64 oracle, full step (project all {sc.n} Gaussians x {len(cams)} views, bin, forward, "
+              f"L1 rgb + L1 depth, backward) on centred {cams[0].width}x{cams[0].height} crops of every view, "
+              f"{reps} step(s), {dt:.1f} s")
+    return {"value": npx / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+            "seconds": dt, "pixels": npx}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_2510_26358_gb300 import scenes
+    sc = scenes.workload(args.workload)
+    # warm-up and timed steps, each a bounded sample of the workload
+    cb = None
+    for _ in range(args.warmup):
+        cpu_baseline(sc, args)
+    vals, secs, pix = [], 0.0, 0
+    for _ in range(args.steps):
+        cb = cpu_baseline(sc, args)
+        secs += cb["seconds"]
+        pix += cb["pixels"]
+    value = pix / secs / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(sc, args),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cb["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2510_26358_gb300 import gsraster as G
+    from paper_2510_26358_gb300 import scenes
+
+    sc = scenes.workload(args.workload, seed=rank)
+    tw, th = (int(x) for x in args.tile.split("x"))
+    cfg = G.gs_config_default(tile_w=tw, tile_h=th, batch_depth=args.depth)
+    step = Step(G, torch, sc, cfg, dev)
+    # size the instance capacity from a first run
+    step.run()
+    st, need, nvis = step.r.status()
+    if st == G.GS_ERR_CAPACITY or need > step.r.info["inst_capacity"]:
+        step.r.close()
+        step = Step(G, torch, sc, cfg, dev, inst_capacity=int(need * 1.25) + 1024)
+        step.run()
+        st, need, nvis = step.r.status()
+    assert st == G.GS_OK, G.status_string(st)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    # launches per step, from the library's own counter
+    k0 = G.gs_workspace_info(step.r.ws)["kernel_launches"]
+    step.run()
+    launches_per_step = G.gs_workspace_info(step.r.ws)["kernel_launches"] - k0
+
+    graph = make_graph(torch, step)
+    # timed region: graph replays, clocks sampled meanwhile
+    sampler = ClockSampler(gpu_uuid(torch))
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    times = time_steps(torch, graph.replay, args.steps, args.warmup, flush)
+    clocks = sampler.stop()
+    ms = float(np.mean(times))
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    npx_total = sc.n_pix * world
+    value = npx_total / (ms * 1e-3) / 1e6
+
+    # correctness of the timed state (status after the replays)
+    st, need2, _ = step.r.status()
+    assert st == G.GS_OK
+
+    breakdown = stage_breakdown(torch, step, max(3, args.steps // 2), flush)
+    kern = kernel_breakdown(torch, G, step, max(3, args.steps // 2), flush)
+
+    # per-view plain version: one workspace per camera, no graph
+    per_view = None
+    if not args.no_per_view:
+        from copy import copy
+        pv_steps = []
+        for v, c in enumerate(sc.cameras):
+            sub = copy(sc)
+            c1 = copy(c)
+            c1.submap = 0
+            s0, s1 = int(sc.submap_offsets[c.submap]), int(sc.submap_offsets[c.submap + 1])
+            sub.means, sub.log_scales, sub.quats = sc.means[s0:s1], sc.log_scales[s0:s1], sc.quats[s0:s1]
+            sub.opacity_logits, sub.sh = sc.opacity_logits[s0:s1], sc.sh[s0:s1]
+            sub.submap_offsets = np.array([0, s1 - s0], np.int64)
+            sub.cameras = [c1]
+            off = sum(cc.width * cc.height for cc in sc.cameras[:v])
+            hw = c.width * c.height
+            sub.target = sc.target[3 * off:3 * (off + hw)]
+            m = sc.lidar[:, 3] == v
+            lid = sc.lidar[m].copy()
+            lid[:, 3] = 0
+            sub.lidar = lid
+            pv_steps.append(Step(G, torch, sub, G.gs_config_default(), dev, inst_capacity=need + 1024))
+        run_all = lambda: [s.run() for s in pv_steps]
+        pv_times = time_steps(torch, run_all, max(3, args.steps // 2), 3, flush)
+        pv_ms = float(np.mean(pv_times))
+        per_view = {"value": sc.n_pix / (pv_ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": pv_ms,
+                    "how": "one workspace and launch sequence per camera, 16x16 tiles, no CUDA graph",
+                    "batched_over_per_view": (sc.n_pix / (ms * 1e-3) / 1e6) / (sc.n_pix / (pv_ms * 1e-3) / 1e6)}
+        for s in pv_steps:
+            s.r.close()
+
+    # end to end through the C ABI with host buffers: every step copies the
+    # Gaussians, targets, LiDAR and cameras from pinned host memory and reads
+    # both losses back
+    e2e = None
+    if not args.no_e2e:
+        host = [p.cpu().pin_memory() for p in step.P] + [step.target.cpu().pin_memory(),
+                                                        step.lidar.cpu().pin_memory(),
+                                                        step.r.cams_dev.cpu().pin_memory()]
+        dst = list(step.P) + [step.target, step.lidar, step.r.cams_dev]
+        loss_h = torch.empty(2, pin_memory=True)
+        h2d = sum(h.numel() * h.element_size() for h in host)
+
+        def e2e_step():
+            for h, d in zip(host, dst):
+                d.copy_(h, non_blocking=True)
+            graph.replay()
+            loss_h[0:1].copy_(step.loss_rgb, non_blocking=True)
+            loss_h[1:2].copy_(step.loss_depth, non_blocking=True)
+        e_times = time_steps(torch, e2e_step, max(3, args.steps // 2), 3, flush)
+        e_ms = float(np.mean(e_times))
+        e2e = {"value": sc.n_pix * world / (e_ms * 1e-3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": 8, "ms_per_step": e_ms}
+
+    # roofline of the dominant kernel (the raster backward)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    n_inst = need
+    npx = sc.n_pix
+    n_tiles = step.r.info["n_tiles"]
+    # algorithmic bytes of one raster-backward launch: instance pair ids (4 B),
+    # visible records read once (48 B), per-pixel inputs (3 rgb + depth grads,
+    # list count, final T = 24 B), tile ranges (8 B), image-space gradients of
+    # the visible pairs accumulated (40 B written)
+    alg_bytes = 4 * n_inst + 48 * nvis + 24 * npx + 8 * n_tiles + 40 * nvis
+    bwd_ms = kern["raster_bwd"]
+    achieved = alg_bytes / (bwd_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "k_raster_bwd",
+                "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                "traffic": None, "algorithmic_bytes": int(alg_bytes), "ms": bwd_ms,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6800 GB/s"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(sc, args, f"{tw}x{th}", args.depth),
+            "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches_per_step * args.steps),
+            "launches_per_step": int(launches_per_step), "roofline": roofline,
+            "per_view": per_view, "breakdown_ms": breakdown, "kernel_ms": kern,
+            "counts": {"visible_pairs": nvis, "instances": n_inst, "tiles": n_tiles}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = {k: v for k, v in cpu_baseline(sc, args, reps=2).items()
+                                if k not in ("seconds", "pixels")}
+    elif rank == 0:
+        line["cpu_baseline"] = None
+    step.r.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -170,7 +170,8 @@ gs_status gs_render_bwd(gs_workspace *ws, const gs_gaussians *g, const gs_camera
 gs_status gs_workspace_status(gs_workspace *ws, void *stream, int64_t *n_instances, int64_t *n_visible);
 
 /* Sizes of the workspace: info[0] n_pairs, [1] n_tiles, [2] n_pix, [3]
- * inst_capacity, [4] n_views, [5] N, [6] bytes of device memory held. */
+ * inst_capacity, [4] n_views, [5] N, [6] bytes of device memory held,
+ * [7] kernels this workspace's calls have enqueued so far. */
 gs_status gs_workspace_info(gs_workspace *ws, int64_t *info, int32_t n_info);
 
 /* Copy an internal buffer to `dst` (device) for inspection; bytes must equal
@@ -181,6 +182,29 @@ gs_status gs_workspace_info(gs_workspace *ws, int64_t *info, int32_t n_info);
  * u32, 6 per-pixel list count up to the last blended fragment [N_pix] u32,
  * 7 per-pixel final T [N_pix] f32, 8 image-space gradients [n_pairs][10] f32. */
 gs_status gs_workspace_copy(gs_workspace *ws, int32_t which, void *dst, int64_t *bytes, void *stream);
+
+/* Optional per-stage timing. With profiling on, each call records CUDA
+ * events on its stream around every stage below (do not enable it while
+ * capturing a CUDA graph); gs_workspace_stage_ms synchronises on the events
+ * and writes the last duration of each stage in milliseconds (-1 if the
+ * stage has not run since profiling was enabled). */
+enum {
+    GS_STAGE_PROJECT = 0,    /* gs_project */
+    GS_STAGE_COMPACT = 1,    /* visible-pair compaction */
+    GS_STAGE_DEPTH_SORT = 2, /* radix sort of visible pairs by depth */
+    GS_STAGE_EMIT = 3,       /* instance counting, capacity check, emission */
+    GS_STAGE_TILE_SORT = 4,  /* radix sort of instances by tile */
+    GS_STAGE_RANGES = 5,     /* per-tile ranges */
+    GS_STAGE_RASTER_FWD = 6, /* forward compositing */
+    GS_STAGE_IMAGE_L1 = 7,   /* gs_image_l1 */
+    GS_STAGE_DEPTH_LOSS = 8, /* gs_depth_loss */
+    GS_STAGE_ZERO_GRAD = 9,  /* clearing the image-space gradients */
+    GS_STAGE_RASTER_BWD = 10, /* backward compositing */
+    GS_STAGE_PROJECT_BWD = 11, /* projection adjoint and pose reduction */
+    GS_NUM_STAGES = 12
+};
+gs_status gs_workspace_set_profiling(gs_workspace *ws, int32_t on);
+gs_status gs_workspace_stage_ms(gs_workspace *ws, float *ms, int32_t n);
 
 const char *gs_status_string(gs_status s);
 /* Text of the last CUDA error seen by this thread's calls ("" if none). */

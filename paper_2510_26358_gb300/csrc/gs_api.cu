@@ -93,6 +93,31 @@ void gs_config_default(gs_config *cfg) {
     cfg->lambda_L = 1.f;
 }
 
+gs_status gs_workspace_set_profiling(gs_workspace *ws, int32_t on) {
+    if (!ws) return fail(GS_ERR_INVALID_ARG, "NULL workspace");
+    if (on && !ws->ev[0]) {
+        for (cudaEvent_t &e : ws->ev) {
+            cudaError_t r = cudaEventCreate(&e);
+            if (r != cudaSuccess) return fail(GS_ERR_CUDA, std::string("event: ") + cudaGetErrorString(r));
+        }
+    }
+    ws->profiling = on != 0;
+    for (bool &u : ws->ev_used) u = false;
+    return GS_OK;
+}
+
+gs_status gs_workspace_stage_ms(gs_workspace *ws, float *ms, int32_t n) {
+    if (!ws || !ms || n < 0) return fail(GS_ERR_INVALID_ARG, "NULL argument");
+    for (int i = 0; i < n && i < GS_NUM_STAGES; ++i) {
+        ms[i] = -1.f;
+        if (!ws->ev_used[i]) continue;
+        cudaError_t r = cudaEventSynchronize(ws->ev[2 * i + 1]);
+        if (r == cudaSuccess) r = cudaEventElapsedTime(&ms[i], ws->ev[2 * i], ws->ev[2 * i + 1]);
+        if (r != cudaSuccess) return fail(GS_ERR_CUDA, std::string("stage timing: ") + cudaGetErrorString(r));
+    }
+    return GS_OK;
+}
+
 const char *gs_status_string(gs_status s) {
     switch (s) {
         case GS_OK: return "ok";
@@ -114,6 +139,8 @@ void gs_workspace_destroy(gs_workspace *ws) {
                     ws->last, ws->tfin, ws->hist, ws->part, ws->pose_part, ws->red_part, ws->st};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    for (cudaEvent_t e : ws->ev)
+        if (e) cudaEventDestroy(e);
     delete ws;
 }
 
@@ -345,8 +372,9 @@ gs_status gs_workspace_status(gs_workspace *ws, void *stream, int64_t *n_instanc
 
 gs_status gs_workspace_info(gs_workspace *ws, int64_t *info, int32_t n_info) {
     if (!ws || !info || n_info < 0) return fail(GS_ERR_INVALID_ARG, "NULL argument");
-    int64_t v[7] = {ws->n_pairs, ws->n_tiles, ws->n_pix, ws->inst_cap, ws->n_views, ws->n, (int64_t)ws->bytes};
-    for (int i = 0; i < n_info && i < 7; ++i) info[i] = v[i];
+    int64_t v[8] = {ws->n_pairs, ws->n_tiles, ws->n_pix,   ws->inst_cap,
+                    ws->n_views, ws->n,       (int64_t)ws->bytes, ws->kernel_launches};
+    for (int i = 0; i < n_info && i < 8; ++i) info[i] = v[i];
     return GS_OK;
 }
 

@@ -84,6 +84,7 @@ struct gs_workspace {
     int32_t tile_bits = 0, sort_blocks = 0, proj_blocks = 0, max_views_per_submap = 0;
     int32_t raster_grid_fwd = 0, raster_grid_bwd = 0;
     size_t bytes = 0;
+    int64_t kernel_launches = 0;  // kernels enqueued by this workspace so far
     std::vector<gs::ViewInfo> views_h;
     std::vector<gs::SubmapInfo> subs_h;
     std::vector<int32_t> sub_views_h;  // [n_submaps][max_views_per_submap]
@@ -112,6 +113,10 @@ struct gs_workspace {
     gs::DevState *st = nullptr;
     // host-side order checks
     bool projected = false, binned = false, rendered = false;
+    // optional per-stage timing (events recorded around each kernel group)
+    bool profiling = false;
+    cudaEvent_t ev[2 * GS_NUM_STAGES] = {};
+    bool ev_used[GS_NUM_STAGES] = {};
 };
 
 namespace gs {
@@ -122,6 +127,22 @@ namespace gs {
 
 void set_last_error(const std::string &msg);
 gs_status check_launch(const char *what);
+
+// Brackets the kernels of one stage with timing events when profiling is on.
+struct StageTimer {
+    gs_workspace *ws;
+    int id;
+    cudaStream_t s;
+    StageTimer(gs_workspace *w, int stage, cudaStream_t st) : ws(w), id(stage), s(st) {
+        if (ws->profiling) cudaEventRecord(ws->ev[2 * id], s);
+    }
+    ~StageTimer() {
+        if (ws->profiling) {
+            cudaEventRecord(ws->ev[2 * id + 1], s);
+            ws->ev_used[id] = true;
+        }
+    }
+};
 
 // ---------------------------------------------------------------------------
 // stage launchers (one translation unit each)

@@ -157,9 +157,13 @@ gs_status launch_depth_loss(gs_workspace *ws, const float *depth, const float *a
     A.loss = loss;
     A.grad = dL_ddepth;
     A.st = ws->st;
-    k_depth_partial<<<A.nb, LT, 0, s>>>(A);
-    k_depth_final<<<1, LT, 0, s>>>(A);
-    if (dL_ddepth && n_pts > 0) k_depth_grad<<<A.nb, LT, 0, s>>>(A);
+    StageTimer timer(ws, GS_STAGE_DEPTH_LOSS, s);
+    ++ws->kernel_launches; k_depth_partial<<<A.nb, LT, 0, s>>>(A);
+    ++ws->kernel_launches; k_depth_final<<<1, LT, 0, s>>>(A);
+    if (dL_ddepth && n_pts > 0) {
+        ++ws->kernel_launches;
+        k_depth_grad<<<A.nb, LT, 0, s>>>(A);
+    }
     return check_launch("depth_loss");
 }
 
@@ -167,8 +171,9 @@ gs_status launch_image_l1(gs_workspace *ws, const float *rgb, const float *targe
                           float *dL_drgb, cudaStream_t s) {
     int64_t n = 3 * ws->n_pix;
     int nb = ws->sort_blocks;
-    k_l1_partial<<<nb, LT, 0, s>>>(rgb, target, n, dL_drgb, ws->red_part);
-    k_l1_final<<<1, LT, 0, s>>>(ws->red_part, nb, n, loss);
+    StageTimer timer(ws, GS_STAGE_IMAGE_L1, s);
+    ++ws->kernel_launches; k_l1_partial<<<nb, LT, 0, s>>>(rgb, target, n, dL_drgb, ws->red_part);
+    ++ws->kernel_launches; k_l1_final<<<1, LT, 0, s>>>(ws->red_part, nb, n, loss);
     return check_launch("image_l1");
 }
 

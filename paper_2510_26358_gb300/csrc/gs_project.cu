@@ -630,12 +630,13 @@ gs_status launch_project_fwd(gs_workspace *ws, const gs_gaussians *g, const gs_c
                              cudaStream_t s) {
     ProjArgs A = make_args(ws, g, cams);
     if (ws->n == 0) return GS_OK;
+    StageTimer timer(ws, GS_STAGE_PROJECT, s);
     int grid = (int)((ws->n + kProjThreads - 1) / kProjThreads);
     switch (ws->sh_degree) {
-        case 0: k_project_fwd<0><<<grid, kProjThreads, 0, s>>>(A); break;
-        case 1: k_project_fwd<1><<<grid, kProjThreads, 0, s>>>(A); break;
-        case 2: k_project_fwd<2><<<grid, kProjThreads, 0, s>>>(A); break;
-        default: k_project_fwd<3><<<grid, kProjThreads, 0, s>>>(A); break;
+        case 0: ++ws->kernel_launches; k_project_fwd<0><<<grid, kProjThreads, 0, s>>>(A); break;
+        case 1: ++ws->kernel_launches; k_project_fwd<1><<<grid, kProjThreads, 0, s>>>(A); break;
+        case 2: ++ws->kernel_launches; k_project_fwd<2><<<grid, kProjThreads, 0, s>>>(A); break;
+        default: ++ws->kernel_launches; k_project_fwd<3><<<grid, kProjThreads, 0, s>>>(A); break;
     }
     return check_launch("project_fwd");
 }
@@ -651,18 +652,19 @@ gs_status launch_project_bwd(gs_workspace *ws, const gs_gaussians *g, const gs_c
     A.pose_part = ws->pose_part;
     A.dens_acc = out->densify_acc;
     A.dens_cnt = out->densify_cnt;
+    StageTimer timer(ws, GS_STAGE_PROJECT_BWD, s);
     if (ws->proj_blocks > 0) {
         switch (ws->sh_degree) {
-            case 0: k_project_bwd<0><<<ws->proj_blocks, kProjThreads, 0, s>>>(A); break;
-            case 1: k_project_bwd<1><<<ws->proj_blocks, kProjThreads, 0, s>>>(A); break;
-            case 2: k_project_bwd<2><<<ws->proj_blocks, kProjThreads, 0, s>>>(A); break;
-            default: k_project_bwd<3><<<ws->proj_blocks, kProjThreads, 0, s>>>(A); break;
+            case 0: ++ws->kernel_launches; k_project_bwd<0><<<ws->proj_blocks, kProjThreads, 0, s>>>(A); break;
+            case 1: ++ws->kernel_launches; k_project_bwd<1><<<ws->proj_blocks, kProjThreads, 0, s>>>(A); break;
+            case 2: ++ws->kernel_launches; k_project_bwd<2><<<ws->proj_blocks, kProjThreads, 0, s>>>(A); break;
+            default: ++ws->kernel_launches; k_project_bwd<3><<<ws->proj_blocks, kProjThreads, 0, s>>>(A); break;
         }
         gs_status st = check_launch("project_bwd");
         if (st != GS_OK) return st;
     }
     if (out->pose) {
-        k_pose_reduce<<<ws->n_views, 32, 0, s>>>(ws->pose_part, ws->views, ws->subs,
+        ++ws->kernel_launches; k_pose_reduce<<<ws->n_views, 32, 0, s>>>(ws->pose_part, ws->views, ws->subs,
                                                  ws->max_views_per_submap, ws->n_views, out->pose);
         return check_launch("pose_reduce");
     }

@@ -301,12 +301,14 @@ RasterArgs make_args(gs_workspace *ws) {
 
 template <int TW, int TH>
 gs_status run_fwd(gs_workspace *ws, RasterArgs A, cudaStream_t s) {
-    k_raster_fwd<TW, TH><<<ws->raster_grid_fwd, TW * TH, fwd_smem<TW, TH>(A.depth), s>>>(A);
+    StageTimer timer(ws, GS_STAGE_RASTER_FWD, s);
+    ++ws->kernel_launches; k_raster_fwd<TW, TH><<<ws->raster_grid_fwd, TW * TH, fwd_smem<TW, TH>(A.depth), s>>>(A);
     return check_launch("raster_fwd");
 }
 template <int TW, int TH>
 gs_status run_bwd(gs_workspace *ws, RasterArgs A, cudaStream_t s) {
-    k_raster_bwd<TW, TH><<<ws->raster_grid_bwd, TW * TH, bwd_smem<TW, TH>(A.depth), s>>>(A);
+    StageTimer timer(ws, GS_STAGE_RASTER_BWD, s);
+    ++ws->kernel_launches; k_raster_bwd<TW, TH><<<ws->raster_grid_bwd, TW * TH, bwd_smem<TW, TH>(A.depth), s>>>(A);
     return check_launch("raster_bwd");
 }
 
@@ -343,7 +345,11 @@ gs_status launch_raster_bwd(gs_workspace *ws, const float *dL_drgb, const float 
     A.dL_ddepth = dL_ddepth;
     A.dL_dalpha = dL_dalpha;
     A.g2d = ws->g2d;
-    k_zero_g2d<<<ws->num_sms * 4, 256, 0, s>>>(ws->vis_pair, ws->st, ws->g2d);
+    {
+        StageTimer timer(ws, GS_STAGE_ZERO_GRAD, s);
+        ++ws->kernel_launches;
+        k_zero_g2d<<<ws->num_sms * 4, 256, 0, s>>>(ws->vis_pair, ws->st, ws->g2d);
+    }
     gs_status r = check_launch("zero_g2d");
     if (r != GS_OK) return r;
     cudaMemsetAsync(A.counter, 0, sizeof(uint32_t), s);

@@ -346,9 +346,9 @@ __global__ void k_ranges(const uint32_t *tile, const DevState *st, uint2 *ranges
 gs_status radix_pass(gs_workspace *ws, uint32_t *&k, uint32_t *&v, uint32_t *&k2, uint32_t *&v2,
                      const uint32_t *n_ptr, int shift, cudaStream_t s) {
     int nb = ws->sort_blocks;
-    k_radix_hist<<<nb, T, 0, s>>>(k, n_ptr, shift, ws->hist, nb);
-    k_radix_scan<<<1, 1024, 0, s>>>(ws->hist, 256 * nb);
-    k_radix_scatter<<<nb, T, sizeof(ScatterSmem), s>>>(k, v, k2, v2, n_ptr, shift, ws->hist, nb);
+    ++ws->kernel_launches; k_radix_hist<<<nb, T, 0, s>>>(k, n_ptr, shift, ws->hist, nb);
+    ++ws->kernel_launches; k_radix_scan<<<1, 1024, 0, s>>>(ws->hist, 256 * nb);
+    ++ws->kernel_launches; k_radix_scatter<<<nb, T, sizeof(ScatterSmem), s>>>(k, v, k2, v2, n_ptr, shift, ws->hist, nb);
     std::swap(k, k2);
     std::swap(v, v2);
     return check_launch("radix_pass");
@@ -372,15 +372,22 @@ gs_status launch_bin_sort(gs_workspace *ws, cudaStream_t s) {
     DevState *st = ws->st;
     cudaMemsetAsync(&st->n_vis, 0, sizeof(uint32_t) * 2 + sizeof(unsigned long long) + sizeof(uint32_t), s);
     // 1. compaction of visible pairs
-    k_count_visible<<<nb, T, 0, s>>>(ws->pkey, n_pairs, ws->part, nb);
-    k_scan_parts<<<1, T, 0, s>>>(ws->part, nb, &st->n_vis, st, 0, 0);
-    k_compact_visible<<<nb, T, 0, s>>>(ws->pkey, n_pairs, ws->part, nb, ws->vis_key, ws->vis_pair);
-    gs_status r = check_launch("compact");
+    gs_status r;
+    {
+    StageTimer timer(ws, GS_STAGE_COMPACT, s);
+    ++ws->kernel_launches; k_count_visible<<<nb, T, 0, s>>>(ws->pkey, n_pairs, ws->part, nb);
+    ++ws->kernel_launches; k_scan_parts<<<1, T, 0, s>>>(ws->part, nb, &st->n_vis, st, 0, 0);
+    ++ws->kernel_launches; k_compact_visible<<<nb, T, 0, s>>>(ws->pkey, n_pairs, ws->part, nb, ws->vis_key, ws->vis_pair);
+    r = check_launch("compact");
     if (r != GS_OK) return r;
+    }
     // 2. stable sort of the visible pairs by depth key (32 bits)
     uint32_t *k = ws->vis_key, *v = ws->vis_pair, *k2 = ws->vis_key_alt, *v2 = ws->vis_pair_alt;
+    {
+    StageTimer timer(ws, GS_STAGE_DEPTH_SORT, s);
     for (int sh = 0; sh < 32; sh += 8)
         if ((r = radix_pass(ws, k, v, k2, v2, &st->n_vis, sh, s)) != GS_OK) return r;
+    }
     // after 4 passes the sorted data are back in vis_key / vis_pair
     // 3. instance offsets, capacity check, emission in depth order
     // emit into whichever buffer makes the last tile pass end in inst_tile/inst_val
@@ -389,16 +396,23 @@ gs_status launch_bin_sort(gs_workspace *ws, cudaStream_t s) {
     uint32_t *tv = (passes & 1) ? ws->inst_val_alt : ws->inst_val;
     uint32_t *tk2 = (passes & 1) ? ws->inst_tile : ws->inst_tile_alt;
     uint32_t *tv2 = (passes & 1) ? ws->inst_val : ws->inst_val_alt;
-    k_count_instances<<<nb, T, 0, s>>>(v, ws->rect, st, ws->part, nb);
-    k_scan_parts<<<1, T, 0, s>>>(ws->part, nb, nullptr, st, (uint64_t)ws->inst_cap, 1);
-    k_emit_instances<<<nb, T, 0, s>>>(v, ws->rect, ws->views, ws->n_views, st, ws->part, nb, tk, tv);
+    {
+    StageTimer timer(ws, GS_STAGE_EMIT, s);
+    ++ws->kernel_launches; k_count_instances<<<nb, T, 0, s>>>(v, ws->rect, st, ws->part, nb);
+    ++ws->kernel_launches; k_scan_parts<<<1, T, 0, s>>>(ws->part, nb, nullptr, st, (uint64_t)ws->inst_cap, 1);
+    ++ws->kernel_launches; k_emit_instances<<<nb, T, 0, s>>>(v, ws->rect, ws->views, ws->n_views, st, ws->part, nb, tk, tv);
     if ((r = check_launch("emit")) != GS_OK) return r;
+    }
     // 4. stable sort of the instances by tile id
+    {
+    StageTimer timer(ws, GS_STAGE_TILE_SORT, s);
     for (int p = 0; p < passes; ++p)
         if ((r = radix_pass(ws, tk, tv, tk2, tv2, &st->n_inst, 8 * p, s)) != GS_OK) return r;
+    }
     // 5. ranges
+    StageTimer timer(ws, GS_STAGE_RANGES, s);
     cudaMemsetAsync(ws->ranges, 0, sizeof(uint2) * ws->n_tiles, s);
-    k_ranges<<<ws->num_sms * 8, 256, 0, s>>>(ws->inst_tile, st, ws->ranges);
+    ++ws->kernel_launches; k_ranges<<<ws->num_sms * 8, 256, 0, s>>>(ws->inst_tile, st, ws->ranges);
     return check_launch("ranges");
 }
 

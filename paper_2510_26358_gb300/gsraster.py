@@ -27,8 +27,10 @@ BUF_RECORDS, BUF_PAIR_KEYS, BUF_RECTS, BUF_INST_TILES, BUF_INST_PAIRS, BUF_RANGE
 
 EXPORTED = ("gs_config_default", "gs_workspace_create", "gs_workspace_destroy", "gs_project",
             "gs_bin_sort", "gs_render_fwd", "gs_depth_loss", "gs_image_l1", "gs_render_bwd",
-            "gs_workspace_status", "gs_workspace_info", "gs_workspace_copy", "gs_status_string",
-            "gs_last_error")
+            "gs_workspace_status", "gs_workspace_info", "gs_workspace_copy", "gs_workspace_set_profiling",
+            "gs_workspace_stage_ms", "gs_status_string", "gs_last_error")
+STAGES = ("project", "compact", "depth_sort", "emit", "tile_sort", "ranges", "raster_fwd", "image_l1",
+          "depth_loss", "zero_grad", "raster_bwd", "project_bwd")
 
 
 class GsError(RuntimeError):
@@ -93,13 +95,15 @@ def lib() -> ctypes.CDLL:
     L.gs_workspace_status.argtypes = [P, P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
     L.gs_workspace_info.argtypes = [P, ctypes.POINTER(ctypes.c_int64), i32]
     L.gs_workspace_copy.argtypes = [P, i32, P, ctypes.POINTER(ctypes.c_int64), P]
+    L.gs_workspace_set_profiling.argtypes = [P, i32]
+    L.gs_workspace_stage_ms.argtypes = [P, ctypes.POINTER(ctypes.c_float), i32]
     L.gs_status_string.argtypes = [i32]
     L.gs_status_string.restype = ctypes.c_char_p
     L.gs_last_error.argtypes = []
     L.gs_last_error.restype = ctypes.c_char_p
     for name in ("gs_workspace_create", "gs_project", "gs_bin_sort", "gs_render_fwd", "gs_depth_loss",
                  "gs_image_l1", "gs_render_bwd", "gs_workspace_status", "gs_workspace_info",
-                 "gs_workspace_copy"):
+                 "gs_workspace_copy", "gs_workspace_set_profiling", "gs_workspace_stage_ms"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -177,9 +181,9 @@ def gs_workspace_status(ws, stream):
 
 
 def gs_workspace_info(ws) -> dict:
-    v = (ctypes.c_int64 * 7)()
-    _check(lib().gs_workspace_info(ws, v, 7), "gs_workspace_info")
-    keys = ("n_pairs", "n_tiles", "n_pix", "inst_capacity", "n_views", "n", "bytes")
+    v = (ctypes.c_int64 * 8)()
+    _check(lib().gs_workspace_info(ws, v, 8), "gs_workspace_info")
+    keys = ("n_pairs", "n_tiles", "n_pix", "inst_capacity", "n_views", "n", "bytes", "kernel_launches")
     return dict(zip(keys, [int(x) for x in v]))
 
 
@@ -187,6 +191,17 @@ def gs_workspace_copy(ws, which, dst, nbytes, stream):
     b = ctypes.c_int64(nbytes)
     _check(lib().gs_workspace_copy(ws, int(which), dst, ctypes.byref(b), stream), "gs_workspace_copy")
     return b.value
+
+
+def gs_workspace_set_profiling(ws, on: bool):
+    _check(lib().gs_workspace_set_profiling(ws, 1 if on else 0), "gs_workspace_set_profiling")
+
+
+def gs_workspace_stage_ms(ws) -> dict:
+    """Last duration (ms) of each stage; stages that did not run are omitted."""
+    v = (ctypes.c_float * len(STAGES))()
+    _check(lib().gs_workspace_stage_ms(ws, v, len(STAGES)), "gs_workspace_stage_ms")
+    return {n: float(x) for n, x in zip(STAGES, v) if x >= 0}
 
 
 def gs_workspace_buffer_bytes(ws, which) -> int:
