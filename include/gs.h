@@ -183,6 +183,27 @@ gs_status gs_workspace_info(gs_workspace *ws, int64_t *info, int32_t n_info);
  * 7 per-pixel final T [N_pix] f32, 8 image-space gradients [n_pairs][10] f32. */
 gs_status gs_workspace_copy(gs_workspace *ws, int32_t which, void *dst, int64_t *bytes, void *stream);
 
+/* gs_image_l1 for callers that cannot allocate device memory (the paper has
+ * no counterpart: this is a deployment variant of the L1 term of Eq. (6)).
+ * Some callers may not call cudaMalloc: a hard real-time mapping loop whose
+ * memory is fixed at start-up (cudaMalloc can block and synchronise the
+ * device), or code embedded in a host program that only hands over its
+ * buffers.  This call needs no workspace and allocates nothing: its only
+ * scratch is a file-scope device array of GS_IMAGE_L1_NOALLOC_BLOCKS doubles
+ * (8 KiB) that every GPU which loads the library holds until exit.
+ * rgb, target (device, n floats), loss (device, 1 float) receives
+ * mean |rgb - target| (0 when n = 0), dL_drgb (device, n floats, nullable)
+ * is accumulated with sign(rgb - target)/n.
+ * n beyond GS_IMAGE_L1_NOALLOC_BLOCKS * GS_IMAGE_L1_NOALLOC_CHUNK returns
+ * GS_ERR_INVALID_ARG without launching anything.  The first call on a device
+ * (made with that device current) resolves the array's address once; make
+ * it before any stream capture.  All calls share the array: calls whose
+ * kernels overlap on the GPU race on it. */
+#define GS_IMAGE_L1_NOALLOC_BLOCKS 1024
+#define GS_IMAGE_L1_NOALLOC_CHUNK 65536
+gs_status gs_image_l1_noalloc(const float *rgb, const float *target, int64_t n, float *loss,
+                              float *dL_drgb, void *stream);
+
 /* Optional per-stage timing. With profiling on, each call records CUDA
  * events on its stream around every stage below (do not enable it while
  * capturing a CUDA graph); gs_workspace_stage_ms synchronises on the events

@@ -28,7 +28,8 @@ BUF_RECORDS, BUF_PAIR_KEYS, BUF_RECTS, BUF_INST_TILES, BUF_INST_PAIRS, BUF_RANGE
 EXPORTED = ("gs_config_default", "gs_workspace_create", "gs_workspace_destroy", "gs_project",
             "gs_bin_sort", "gs_render_fwd", "gs_depth_loss", "gs_image_l1", "gs_render_bwd",
             "gs_workspace_status", "gs_workspace_info", "gs_workspace_copy", "gs_workspace_set_profiling",
-            "gs_workspace_stage_ms", "gs_status_string", "gs_last_error")
+            "gs_workspace_stage_ms", "gs_image_l1_noalloc", "gs_status_string", "gs_last_error")
+IMAGE_L1_NOALLOC_MAX = 1024 * 65536  # GS_IMAGE_L1_NOALLOC_BLOCKS * GS_IMAGE_L1_NOALLOC_CHUNK
 STAGES = ("project", "compact", "depth_sort", "emit", "tile_sort", "ranges", "raster_fwd", "image_l1",
           "depth_loss", "zero_grad", "raster_bwd", "project_bwd")
 
@@ -95,6 +96,7 @@ def lib() -> ctypes.CDLL:
     L.gs_workspace_status.argtypes = [P, P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
     L.gs_workspace_info.argtypes = [P, ctypes.POINTER(ctypes.c_int64), i32]
     L.gs_workspace_copy.argtypes = [P, i32, P, ctypes.POINTER(ctypes.c_int64), P]
+    L.gs_image_l1_noalloc.argtypes = [P, P, i64, P, P, P]
     L.gs_workspace_set_profiling.argtypes = [P, i32]
     L.gs_workspace_stage_ms.argtypes = [P, ctypes.POINTER(ctypes.c_float), i32]
     L.gs_status_string.argtypes = [i32]
@@ -103,7 +105,8 @@ def lib() -> ctypes.CDLL:
     L.gs_last_error.restype = ctypes.c_char_p
     for name in ("gs_workspace_create", "gs_project", "gs_bin_sort", "gs_render_fwd", "gs_depth_loss",
                  "gs_image_l1", "gs_render_bwd", "gs_workspace_status", "gs_workspace_info",
-                 "gs_workspace_copy", "gs_workspace_set_profiling", "gs_workspace_stage_ms"):
+                 "gs_workspace_copy", "gs_workspace_set_profiling", "gs_workspace_stage_ms",
+                 "gs_image_l1_noalloc"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -164,6 +167,11 @@ def gs_depth_loss(ws, depth, alpha, lidar, n_pts, loss, dL_ddepth, stream):
 
 def gs_image_l1(ws, rgb, target, loss, dL_drgb, stream):
     _check(lib().gs_image_l1(ws, rgb, target, loss, dL_drgb, stream), "gs_image_l1")
+
+
+def gs_image_l1_noalloc(rgb, target, n, loss, dL_drgb, stream):
+    """L1 image loss without a workspace; see include/gs.h for its static scratch."""
+    _check(lib().gs_image_l1_noalloc(rgb, target, int(n), loss, dL_drgb, stream), "gs_image_l1_noalloc")
 
 
 def gs_render_bwd(ws, g: GsGaussians, cams_dev, dL_drgb, dL_ddepth, dL_dalpha, grads: GsGrads, stream):
