@@ -136,7 +136,8 @@ void gs_workspace_destroy(gs_workspace *ws) {
     void *ptrs[] = {ws->views, ws->subs, ws->sub_views, ws->rec, ws->pkey, ws->rect, ws->g2d,
                     ws->vis_key, ws->vis_pair, ws->vis_key_alt, ws->vis_pair_alt, ws->ioff,
                     ws->inst_tile, ws->inst_val, ws->inst_tile_alt, ws->inst_val_alt, ws->ranges,
-                    ws->last, ws->tfin, ws->hist, ws->part, ws->pose_part, ws->red_part, ws->st};
+                    ws->last, ws->tfin, ws->hist, ws->part, ws->digit_tot, ws->pose_part, ws->red_part,
+                    ws->st};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : ws->ev)
@@ -232,7 +233,7 @@ gs_status gs_workspace_create(const gs_camera *cams, int32_t n_views, const int6
         ws->subs_h.push_back(si);
     }
     ws->proj_blocks = blocks;
-    ws->sort_blocks = std::min(1024, 2 * ws->num_sms);
+    ws->sort_blocks = std::min(4 * kSortThreads, 2 * ws->num_sms);
 
     // constants
     Consts &k = ws->consts;
@@ -275,6 +276,7 @@ gs_status gs_workspace_create(const gs_camera *cams, int32_t n_views, const int6
     GS_ALLOC(ws->tfin, (size_t)ws->n_pix);
     GS_ALLOC(ws->hist, (size_t)256 * ws->sort_blocks);
     GS_ALLOC(ws->part, (size_t)ws->sort_blocks + 1);
+    GS_ALLOC(ws->digit_tot, (size_t)256);
     GS_ALLOC(ws->pose_part, (size_t)std::max(1, blocks) * maxv * 6);
     GS_ALLOC(ws->red_part, (size_t)2 * ws->sort_blocks);
     GS_ALLOC(ws->st, 1);

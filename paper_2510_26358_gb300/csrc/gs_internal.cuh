@@ -108,6 +108,7 @@ struct gs_workspace {
     // scratch
     uint32_t *hist = nullptr;      // [256][sort_blocks]
     uint32_t *part = nullptr;      // [sort_blocks + 1]
+    uint32_t *digit_tot = nullptr; // [256] digit totals of the current radix pass
     float *pose_part = nullptr;    // [proj_blocks][max_views_per_submap][6]
     double *red_part = nullptr;    // [2][sort_blocks] loss partials
     gs::DevState *st = nullptr;

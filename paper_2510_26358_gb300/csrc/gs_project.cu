@@ -266,6 +266,8 @@ __global__ void __launch_bounds__(kProjThreads) k_project_fwd(ProjArgs A) {
 #pragma unroll
         for (int j = 0; j < 3; ++j) M[3 * i + j] = R[3 * i + j] * S[j];
     // ln o = -ln(1 + e^-omega); support threshold E = 2 ln(o / alpha_min)
+    // largest axis scale, for the conservative frustum test below
+    const float smax = fmaxf(S[0], fmaxf(S[1], S[2]));
     float lno = -log1pf(expf(-om));
     float log2o = lno * kLog2e;
     float E = 2.f * (lno - k.ln_alpha_min);
@@ -285,6 +287,26 @@ __global__ void __launch_bounds__(kProjThreads) k_project_fwd(ProjArgs A) {
         PairGeom G;
         float4 r0 = make_float4(0, 0, 0, 0), r1 = r0, r2 = r0;
         short4 rc = make_short4(1, 1, 0, 0);
+        if (vis) {
+            // The rows of W R S have norm <= smax, so Sigma'_xx <= (|J00| + |J02|)^2 smax^2 + dil:
+            // a pair whose mean lies farther outside the image than that bound on the
+            // support's half-extent (plus a margin for this float estimate) has no pixel.
+            float zf = (float)pz, xf = (float)px, yf = (float)py;
+            float iz = 1.f / zf;
+            float limx = k.jac_clamp * fmaxf(cam.cx, (float)vi.W - cam.cx) / cam.fx;
+            float limy = k.jac_clamp * fmaxf(cam.cy, (float)vi.H - cam.cy) / cam.fy;
+            float tx = fminf(fmaxf(xf * iz, -limx), limx), ty = fminf(fmaxf(yf * iz, -limy), limy);
+            float jx = cam.fx * iz * (1.f + fabsf(tx)), jy = cam.fy * iz * (1.f + fabsf(ty));
+            float bx = sqrtf(E * (jx * jx * smax * smax + k.dilation)) * 1.01f * (1.f + k.ext_rel_pad) +
+                       k.ext_abs_pad + 1.f;
+            float by = sqrtf(E * (jy * jy * smax * smax + k.dilation)) * 1.01f * (1.f + k.ext_rel_pad) +
+                       k.ext_abs_pad + 1.f;
+            float uf = cam.fx * xf * iz + cam.cx, vf = cam.fy * yf * iz + cam.cy;
+            float mu_ = 1e-4f * (fabsf(uf) + fabsf(vf));
+            if (uf < 0.5f - bx - mu_ || uf > (float)vi.W - 0.5f + bx + mu_ ||
+                vf < 0.5f - by - mu_ || vf > (float)vi.H - 0.5f + by + mu_)
+                vis = false;
+        }
         if (vis) {
             pair_geom(cam, vi.W, vi.H, k, px, py, pz, M, G);
             vis = G.det > 0.f;
@@ -343,23 +365,9 @@ __global__ void __launch_bounds__(kProjThreads) k_project_fwd(ProjArgs A) {
     }
 }
 
-// block-wide sum of v (all threads of the block must call); result valid in all threads
-__device__ __forceinline__ float block_sum(float v, float *scratch) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) scratch[w] = v;
-    __syncthreads();
-    float t = 0.f;
-    int nw = blockDim.x >> 5;
-    for (int i = 0; i < nw; ++i) t += scratch[i];
-    return t;
-}
-
 template <int DEG>
 __global__ void __launch_bounds__(kProjThreads) k_project_bwd(ProjArgs A) {
-    __shared__ float red[32];
+    extern __shared__ float red[];  // [views of the submap][warps][6]
     const Consts &k = A.c;
     // blocks are laid out per submap
     int b = blockIdx.x;
@@ -378,9 +386,17 @@ __global__ void __launch_bounds__(kProjThreads) k_project_bwd(ProjArgs A) {
     int64_t g = sub.g0 + (live ? local : 0);
     constexpr int K = (DEG + 1) * (DEG + 1);
 
+    // which of the submap's views see this Gaussian
+    uint32_t vis_mask = 0;
+    for (int kv = 0; kv < sub.nviews; ++kv) {
+        const ViewInfo vi = A.views[A.sub_views[s * A.maxv + kv]];
+        if (live && A.pkey[(int64_t)vi.pair_off + (g - vi.g0)] != kInvalidKey) vis_mask |= 1u << kv;
+    }
+    const bool any_vis = vis_mask != 0;
+
     float mu[3] = {0, 0, 0}, ls[3] = {0, 0, 0}, q[4] = {1, 0, 0, 0}, om = 0.f;
     float C[16][3];
-    if (live) {
+    if (any_vis) {
         mu[0] = __ldg(A.means + 3 * g); mu[1] = __ldg(A.means + 3 * g + 1); mu[2] = __ldg(A.means + 3 * g + 2);
         ls[0] = __ldg(A.log_scales + 3 * g); ls[1] = __ldg(A.log_scales + 3 * g + 1);
         ls[2] = __ldg(A.log_scales + 3 * g + 2);
@@ -409,12 +425,13 @@ __global__ void __launch_bounds__(kProjThreads) k_project_bwd(ProjArgs A) {
     float dacc = 0.f;
     int dcnt = 0;
 
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int kv = 0; kv < sub.nviews; ++kv) {
         int v = A.sub_views[s * A.maxv + kv];
         const ViewInfo vi = A.views[v];
         int64_t pair = (int64_t)vi.pair_off + (g - vi.g0);
         float gpose[6] = {0, 0, 0, 0, 0, 0};
-        bool vis = live && A.pkey[pair] != kInvalidKey;
+        bool vis = (vis_mask >> kv) & 1u;
         if (vis) {
             const float *gg = A.g2d + pair * kGrad;
             float gu = gg[G_U], gv = gg[G_V], gqa = gg[G_QA], gqb = gg[G_QB], gqc = gg[G_QC];
@@ -540,14 +557,26 @@ __global__ void __launch_bounds__(kProjThreads) k_project_bwd(ProjArgs A) {
             dacc += sqrtf(gu * gu + gv * gv);
             dcnt += 1;
         }
-        // pose twist of this view: block reduce, one partial per block and view slot
+        // pose twist of this view: warp sums into shared memory, one slot per
+        // (view, warp); the block sums them after the loop
+        if (__any_sync(0xffffffffu, vis)) {
 #pragma unroll
-        for (int i = 0; i < 6; ++i) {
-            float t = block_sum(gpose[i], red);
-            if (threadIdx.x == 0) A.pose_part[((int64_t)b * A.maxv + kv) * 6 + i] = t;
+            for (int i = 0; i < 6; ++i)
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) gpose[i] += __shfl_xor_sync(0xffffffffu, gpose[i], o);
         }
+        if (lane == 0)
+#pragma unroll
+            for (int i = 0; i < 6; ++i) red[(kv * (kProjThreads / 32) + wid) * 6 + i] = gpose[i];
     }
-    if (!live) return;
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < sub.nviews * 6; idx += blockDim.x) {
+        int kv = idx / 6, i = idx % 6;
+        float t = 0.f;
+        for (int w = 0; w < kProjThreads / 32; ++w) t += red[(kv * (kProjThreads / 32) + w) * 6 + i];
+        A.pose_part[((int64_t)b * A.maxv + kv) * 6 + i] = t;
+    }
+    if (!any_vis) return;
     // M = R diag(S): dL/dS_k = sum_i gM_ik R_ik, dL/dls_k = dL/dS_k S_k; dL/dR_ik = gM_ik S_k
     float gR[9];
     float gls[3];
@@ -587,19 +616,26 @@ __global__ void __launch_bounds__(kProjThreads) k_project_bwd(ProjArgs A) {
     if (A.dens_cnt) A.dens_cnt[g] += dcnt;
 }
 
-// pose[v] += sum over the blocks of v's submap of the partials of v's slot
-__global__ void k_pose_reduce(const float *pose_part, const ViewInfo *views, const SubmapInfo *subs,
-                              int maxv, int n_views, float *pose) {
-    int v = blockIdx.x;
-    if (v >= n_views) return;
-    int i = threadIdx.x;
-    if (i >= 6) return;
+// pose[v][i] += sum over the blocks of v's submap of the partials of v's slot;
+// one block per (view, component), fixed summation order
+__global__ void __launch_bounds__(256) k_pose_reduce(const float *pose_part, const ViewInfo *views,
+                                                    const SubmapInfo *subs, int maxv, float *pose) {
+    __shared__ double sm[8];
+    const int v = blockIdx.x / 6, i = blockIdx.x % 6;
     const ViewInfo vi = views[v];
     const SubmapInfo sub = subs[vi.submap];
     double acc = 0.0;
-    for (int b = sub.block0; b < sub.block0 + sub.nblocks; ++b)
+    for (int b = sub.block0 + threadIdx.x; b < sub.block0 + sub.nblocks; b += 256)
         acc += (double)pose_part[((int64_t)b * maxv + vi.k_in_submap) * 6 + i];
-    pose[6 * v + i] += (float)acc;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += sm[w];
+        pose[6 * v + i] += (float)t;
+    }
 }
 
 ProjArgs make_args(gs_workspace *ws, const gs_gaussians *g, const gs_camera *cams) {
@@ -654,18 +690,20 @@ gs_status launch_project_bwd(gs_workspace *ws, const gs_gaussians *g, const gs_c
     A.dens_cnt = out->densify_cnt;
     StageTimer timer(ws, GS_STAGE_PROJECT_BWD, s);
     if (ws->proj_blocks > 0) {
+        size_t smem = sizeof(float) * ws->max_views_per_submap * (kProjThreads / 32) * 6;
         switch (ws->sh_degree) {
-            case 0: ++ws->kernel_launches; k_project_bwd<0><<<ws->proj_blocks, kProjThreads, 0, s>>>(A); break;
-            case 1: ++ws->kernel_launches; k_project_bwd<1><<<ws->proj_blocks, kProjThreads, 0, s>>>(A); break;
-            case 2: ++ws->kernel_launches; k_project_bwd<2><<<ws->proj_blocks, kProjThreads, 0, s>>>(A); break;
-            default: ++ws->kernel_launches; k_project_bwd<3><<<ws->proj_blocks, kProjThreads, 0, s>>>(A); break;
+            case 0: ++ws->kernel_launches; k_project_bwd<0><<<ws->proj_blocks, kProjThreads, smem, s>>>(A); break;
+            case 1: ++ws->kernel_launches; k_project_bwd<1><<<ws->proj_blocks, kProjThreads, smem, s>>>(A); break;
+            case 2: ++ws->kernel_launches; k_project_bwd<2><<<ws->proj_blocks, kProjThreads, smem, s>>>(A); break;
+            default: ++ws->kernel_launches; k_project_bwd<3><<<ws->proj_blocks, kProjThreads, smem, s>>>(A); break;
         }
         gs_status st = check_launch("project_bwd");
         if (st != GS_OK) return st;
     }
     if (out->pose) {
-        ++ws->kernel_launches; k_pose_reduce<<<ws->n_views, 32, 0, s>>>(ws->pose_part, ws->views, ws->subs,
-                                                 ws->max_views_per_submap, ws->n_views, out->pose);
+        ++ws->kernel_launches;
+        k_pose_reduce<<<6 * ws->n_views, 256, 0, s>>>(ws->pose_part, ws->views, ws->subs,
+                                                      ws->max_views_per_submap, out->pose);
         return check_launch("pose_reduce");
     }
     return GS_OK;

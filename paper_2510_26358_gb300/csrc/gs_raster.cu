@@ -115,10 +115,48 @@ __global__ void __launch_bounds__(TW * TH) k_raster_fwd(RasterArgs A) {
     }
 }
 
-__device__ __forceinline__ float warp_sum(float v) {
+// Sums ten per-lane values over the warp by recursive halving: at each of the
+// five butterfly levels a lane keeps half of its remaining components and
+// sends the other half to its partner, so 12 shuffles replace 50.  Afterwards
+// lane l holds the warp total of component
+//   comp(l) = 5*b4 + 3*b3 + 2*b2 + b1      (bK = bit K of l),
+// valid when (b3 == 0 and not (b2 and b1)) or (b3 == 1 and b2 == 0); lanes l
+// and l^1 hold the same total.  reduce10_component gives comp(l) or -1.
+__device__ __forceinline__ float warp_reduce_scatter10(const float v[10], int lane) {
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+    float a[5];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+    for (int i = 0; i < 5; ++i) {
+        float send = b4 ? v[i] : v[i + 5];
+        float keep = b4 ? v[i + 5] : v[i];
+        a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+    float c[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        float hiv = i + 3 < 5 ? a[i + 3] : 0.f;
+        float send = b3 ? a[i] : hiv;
+        float keep = b3 ? hiv : a[i];
+        c[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    float d[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        float hiv = i + 2 < 3 ? c[i + 2] : 0.f;
+        float send = b2 ? c[i] : hiv;
+        float keep = b2 ? hiv : c[i];
+        d[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    float send = b1 ? d[0] : d[1];
+    float keep = b1 ? d[1] : d[0];
+    float e = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    return e + __shfl_xor_sync(0xffffffffu, e, 1);
+}
+
+__device__ __forceinline__ int reduce10_component(int lane) {
+    const int b4 = (lane >> 4) & 1, b3 = (lane >> 3) & 1, b2 = (lane >> 2) & 1, b1 = (lane >> 1) & 1;
+    const bool ok = b3 == 0 ? !(b2 && b1) : b2 == 0;
+    return ok ? 5 * b4 + 3 * b3 + 2 * b2 + b1 : -1;
 }
 
 template <int TW, int TH>
@@ -133,6 +171,8 @@ __global__ void __launch_bounds__(TW * TH) k_raster_bwd(RasterArgs A) {
     __shared__ uint32_t s_max[NW];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const float amax = A.c.alpha_max, l2amin = A.c.log2_alpha_min;
+    // component this lane adds after the reduction (even lanes only)
+    const int my_comp = (lane & 1) ? -1 : reduce10_component(lane);
     for (;;) {
         __syncthreads();
         if (tid == 0) s_tile = (int)atomicAdd(A.counter, 1u);
@@ -193,8 +233,9 @@ __global__ void __launch_bounds__(TW * TH) k_raster_bwd(RasterArgs A) {
                 const float4 sa = sA[j], sb = sB[j];
                 const float e = frag_log2_alpha(sa, sb, pxf, pyf, t1, t2, dxi, dyi);
                 const bool contrib = rel < cnt && e >= l2amin;
-                float gu = 0.f, gv = 0.f, gqa = 0.f, gqb = 0.f, gqc = 0.f, glno = 0.f;
-                float gr = 0.f, gg = 0.f, gb = 0.f, gz = 0.f;
+                float gv10[kGrad];
+#pragma unroll
+                for (int q = 0; q < kGrad; ++q) gv10[q] = 0.f;
                 if (contrib) {
                     const float araw = ex2_approx(e);
                     const float al = fminf(amax, araw);
@@ -205,40 +246,26 @@ __global__ void __launch_bounds__(TW * TH) k_raster_bwd(RasterArgs A) {
                     const float h = gR * c.x + gG * c.y + gB * c.z + gD * c.w + gA;
                     const float dLda = T * h - acc * r1m;
                     acc = __fmaf_rn(wgt, h, acc);
-                    gr = wgt * gR;
-                    gg = wgt * gG;
-                    gb = wgt * gB;
-                    gz = wgt * gD;
+                    gv10[G_R] = wgt * gR;
+                    gv10[G_G] = wgt * gG;
+                    gv10[G_B] = wgt * gB;
+                    gv10[G_Z] = wgt * gD;
                     if (araw <= amax) {
                         const float gpw = dLda * al;  // dL/dpw, pw = -d^T Q d / 2 (natural log)
                         const float2 hh = sH[j];
                         const float dx = dxi + hh.x, dy = dyi + hh.y;
-                        glno = gpw;
-                        gqa = -0.5f * gpw * dx * dx;
-                        gqb = -gpw * dx * dy;
-                        gqc = -0.5f * gpw * dy * dy;
+                        gv10[G_LNO] = gpw;
+                        gv10[G_QA] = -0.5f * gpw * dx * dx;
+                        gv10[G_QB] = -gpw * dx * dy;
+                        gv10[G_QC] = -0.5f * gpw * dy * dy;
                         // dpw/du = (Q d)_x = l11 t1 / s^2, dpw/dv = (l12 t1 + l22 t2) / s^2
-                        gu = gpw * kTwoLn2 * (sb.x * t1);
-                        gv = gpw * kTwoLn2 * (sb.y * t1 + sb.z * t2);
+                        gv10[G_U] = gpw * kTwoLn2 * (sb.x * t1);
+                        gv10[G_V] = gpw * kTwoLn2 * (sb.y * t1 + sb.z * t2);
                     }
                 }
                 if (__any_sync(0xffffffffu, contrib)) {
-                    gu = warp_sum(gu);
-                    gv = warp_sum(gv);
-                    gqa = warp_sum(gqa);
-                    gqb = warp_sum(gqb);
-                    gqc = warp_sum(gqc);
-                    glno = warp_sum(glno);
-                    gr = warp_sum(gr);
-                    gg = warp_sum(gg);
-                    gb = warp_sum(gb);
-                    gz = warp_sum(gz);
-                    if (lane < kGrad) {
-                        float val = lane == G_U ? gu : lane == G_V ? gv : lane == G_QA ? gqa :
-                                    lane == G_QB ? gqb : lane == G_QC ? gqc : lane == G_LNO ? glno :
-                                    lane == G_R ? gr : lane == G_G ? gg : lane == G_B ? gb : gz;
-                        atomicAdd(A.g2d + (size_t)sP[j] * kGrad + lane, val);
-                    }
+                    const float tot = warp_reduce_scatter10(gv10, lane);
+                    if (my_comp >= 0) atomicAdd(A.g2d + (size_t)sP[j] * kGrad + my_comp, tot);
                 }
             }
         }

@@ -151,38 +151,31 @@ __global__ void __launch_bounds__(T) k_radix_hist(const uint32_t *keys, const ui
     hist[threadIdx.x * nb + blockIdx.x] = s;
 }
 
-// exclusive scan of the 256 x nb table, one block of 1024 threads
-__global__ void __launch_bounds__(1024) k_radix_scan(uint32_t *hist, int count) {
+// Exclusive scan of each digit's row of the [256][nb] table: block d turns
+// row d into offsets relative to the digit's first slot and writes the row
+// total to dtot[d].  The digit bases (prefix of dtot) are added by the
+// scatter kernel.  nb <= 4 * T.
+__global__ void __launch_bounds__(T) k_radix_scan(uint32_t *hist, int nb, uint32_t *dtot) {
     __shared__ uint32_t sm[32];
-    int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    int per = (count + 1023) / 1024;
-    int lo = t * per, hi = min(count, lo + per);
+    uint32_t *row = hist + (size_t)blockIdx.x * nb;
+    const int t = threadIdx.x;
+    uint32_t v[4];
     uint32_t s = 0;
-    for (int i = lo; i < hi; ++i) s += hist[i];
-    uint32_t x = s;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
+    for (int k = 0; k < 4; ++k) {
+        int i = 4 * t + k;
+        v[k] = i < nb ? row[i] : 0u;
+        s += v[k];
     }
-    if (lane == 31) sm[w] = x;
-    __syncthreads();
-    if (w == 0) {
-        uint32_t v = sm[lane];
+    uint32_t tot;
+    uint32_t run = block_exclusive_scan(s, sm, &tot);
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
-            if (lane >= o) v += y;
-        }
-        sm[lane] = v;
+    for (int k = 0; k < 4; ++k) {
+        int i = 4 * t + k;
+        if (i < nb) row[i] = run;
+        run += v[k];
     }
-    __syncthreads();
-    uint32_t run = (w > 0 ? sm[w - 1] : 0u) + x - s;
-    for (int i = lo; i < hi; ++i) {
-        uint32_t c = hist[i];
-        hist[i] = run;
-        run += c;
-    }
+    if (t == 0) dtot[blockIdx.x] = tot;
 }
 
 struct ScatterSmem {
@@ -197,13 +190,18 @@ struct ScatterSmem {
 __global__ void __launch_bounds__(T) k_radix_scatter(const uint32_t *kin, const uint32_t *vin,
                                                     uint32_t *kout, uint32_t *vout,
                                                     const uint32_t *n_ptr, int shift,
-                                                    const uint32_t *hist, int nb) {
+                                                    const uint32_t *hist, const uint32_t *dtot, int nb) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ScatterSmem &S = *reinterpret_cast<ScatterSmem *>(smem_raw);
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     uint32_t lo, hi;
     chunk_range(*n_ptr, blockIdx.x, nb, kSortTile, lo, hi);
-    S.base[t] = hist[t * nb + blockIdx.x];
+    if (lo >= hi) return;
+    {
+        uint32_t tot;
+        uint32_t digit_base = block_exclusive_scan(dtot[t], S.scan, &tot);
+        S.base[t] = digit_base + hist[t * nb + blockIdx.x];
+    }
     S.tcnt[t] = 0;
 #pragma unroll
     for (int j = 0; j < W; ++j) S.wcnt[j][t] = 0;
@@ -347,8 +345,9 @@ gs_status radix_pass(gs_workspace *ws, uint32_t *&k, uint32_t *&v, uint32_t *&k2
                      const uint32_t *n_ptr, int shift, cudaStream_t s) {
     int nb = ws->sort_blocks;
     ++ws->kernel_launches; k_radix_hist<<<nb, T, 0, s>>>(k, n_ptr, shift, ws->hist, nb);
-    ++ws->kernel_launches; k_radix_scan<<<1, 1024, 0, s>>>(ws->hist, 256 * nb);
-    ++ws->kernel_launches; k_radix_scatter<<<nb, T, sizeof(ScatterSmem), s>>>(k, v, k2, v2, n_ptr, shift, ws->hist, nb);
+    ++ws->kernel_launches; k_radix_scan<<<256, T, 0, s>>>(ws->hist, nb, ws->digit_tot);
+    ++ws->kernel_launches;
+    k_radix_scatter<<<nb, T, sizeof(ScatterSmem), s>>>(k, v, k2, v2, n_ptr, shift, ws->hist, ws->digit_tot, nb);
     std::swap(k, k2);
     std::swap(v, v2);
     return check_launch("radix_pass");
