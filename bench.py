@@ -128,6 +128,23 @@ def gpu_uuid(torch):
         return str(torch.cuda.current_device())
 
 
+def max_over_ranks(ms: float, device) -> float:
+    """Slowest rank's step time (the job's time); no-op without a process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def job_throughput(pix_per_rank: int, ms: float, world: int) -> float:
+    """Whole-job Mpix/s: every rank renders its own replica in `ms`."""
+    return pix_per_rank * world / (ms * 1e-3) / 1e6
+
+
 # ---------------------------------------------------------------------------
 # the step
 # ---------------------------------------------------------------------------
@@ -392,14 +409,8 @@ def main():
     time.sleep(0.3)
     times = time_steps(torch, graph.replay, args.steps, args.warmup, flush)
     clocks = sampler.stop()
-    ms = float(np.mean(times))
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dist.barrier()
-    npx_total = sc.n_pix * world
-    value = npx_total / (ms * 1e-3) / 1e6
+    ms = max_over_ranks(float(np.mean(times)), dev)
+    value = job_throughput(sc.n_pix, ms, world)
 
     # correctness of the timed state (status after the replays)
     st, need2, _ = step.r.status()

@@ -104,6 +104,7 @@ def lib():
         _lib.oracle_count_instances.restype = i64
         _lib.oracle_render_fwd.argtypes = [i32, P, P, P, P, P, P, P, P, P, P, P, P, P, P]
         _lib.oracle_render_brute.argtypes = [i32, P, P, P, P, P, P, P, P, P, P]
+        _lib.oracle_render_fwd_pixels.argtypes = [i32, P, P, P, P, P, P, i64, P, P, P, P, P, P, P]
         _lib.oracle_render_bwd.argtypes = [i64, P, P, P, P, P, i32, i32, P, P, P, P, P, P, P, P, P,
                                            P, P, P, P, P, P, P, P, P]
         _lib.oracle_image_l1.argtypes = [i64, P, P, P]
@@ -232,6 +233,21 @@ def render_fwd(P: Params, cams, cfg: Config, rec, vals, ranges) -> dict:
                             _p(out["alpha"]), _p(out["T"]), _p(out["last"]), _p(out["nblend"]),
                             _p(out["margin"]), _p(out["sig"]))
     return out
+
+
+def render_fwd_pixels(P: Params, cams, cfg: Config, rec, vals, ranges, pix) -> dict:
+    """Tiled forward of the listed global pixel indices only."""
+    ca, cc = cameras(cams), cfg.c()
+    pix = np.ascontiguousarray(pix, np.int64)
+    n = pix.size
+    out = dict(rgb=np.zeros((max(n, 1), 3)), depth=np.zeros(max(n, 1)), alpha=np.zeros(max(n, 1)),
+               T=np.zeros(max(n, 1)), last=np.zeros(max(n, 1), np.int64), margin=np.zeros(max(n, 1)))
+    lib().oracle_render_fwd_pixels(len(cams), ca, _p(P.submap_offsets), ctypes.byref(cc),
+                                   _p(np.ascontiguousarray(rec)), _p(np.ascontiguousarray(vals, np.int64)),
+                                   _p(np.ascontiguousarray(ranges, np.int64)), n, _p(pix), _p(out["rgb"]),
+                                   _p(out["depth"]), _p(out["alpha"]), _p(out["T"]), _p(out["last"]),
+                                   _p(out["margin"]))
+    return {k: v[:n] for k, v in out.items()}
 
 
 def render_brute(P: Params, cams, cfg: Config, rec) -> dict:

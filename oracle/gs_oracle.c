@@ -560,6 +560,41 @@ int oracle_render_fwd(int n_views, const oc_camera *cams, const int64_t *submap_
     return 0;
 }
 
+/* Tiled forward for a list of pixels only (global pixel indices), for
+ * sampled checks of full-size images; outputs are per listed pixel:
+ * rgb [n_sel][3], depth, alpha, T, last, margin. */
+int oracle_render_fwd_pixels(int n_views, const oc_camera *cams, const int64_t *submap_offsets,
+                             const oc_config *cfg, const double *rec, const int64_t *vals,
+                             const int64_t *ranges, int64_t n_sel, const int64_t *pix,
+                             double *rgb, double *depth, double *alpha, double *Tfin,
+                             int64_t *last, double *margin) {
+    oc_view *V = (oc_view *)malloc(sizeof(oc_view) * (n_views > 0 ? n_views : 1));
+    make_views(n_views, cams, submap_offsets, cfg, V);
+    for (int64_t k = 0; k < n_sel; ++k) {
+        int v = 0;
+        while (v + 1 < n_views && V[v + 1].pix_off <= pix[k]) ++v;
+        int64_t W = cams[v].width;
+        int64_t local = pix[k] - V[v].pix_off;
+        int64_t y = local / W, x = local % W;
+        int64_t t = V[v].tile_off + (y / cfg->tile_h) * V[v].ntx + x / cfg->tile_w;
+        int64_t s = ranges[2 * t], e = ranges[2 * t + 1];
+        int64_t n = e - s;
+        int64_t *pos = (int64_t *)malloc(sizeof(int64_t) * (n > 0 ? n : 1));
+        for (int64_t i = 0; i < n; ++i) pos[i] = s + i;
+        oc_pix o;
+        composite(rec, vals + s, pos, n, x + 0.5, y + 0.5, cfg, &o);
+        free(pos);
+        for (int ch = 0; ch < 3; ++ch) rgb[3 * k + ch] = o.C[ch];
+        depth[k] = o.D;
+        alpha[k] = 1.0 - o.T;
+        Tfin[k] = o.T;
+        last[k] = o.last;
+        margin[k] = o.margin;
+    }
+    free(V);
+    return 0;
+}
+
 /* Brute-force forward without tiles: every pixel composites all visible pairs
  * of its view in ascending (z32, Gaussian index) order; membership is decided
  * by alpha alone.  `last` here is the index into that per-view order. */

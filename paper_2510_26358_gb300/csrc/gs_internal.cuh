@@ -31,9 +31,9 @@ constexpr float kTwoLn2 = 1.38629436111989061883f;
 constexpr float kLog2e = 1.44269504088896340736f;
 
 constexpr int kSortThreads = 256;
-constexpr int kSortRounds = 16;
-constexpr int kSortTile = kSortThreads * kSortRounds;  // 4096 keys per block tile
 constexpr int kProjThreads = 256;
+constexpr int kOrderBuckets = 64;     // list-length buckets of the raster work order
+constexpr int kOrderShift = 5;        // bucket = min(63, length >> 5)
 
 // ---------------------------------------------------------------------------
 // tables
@@ -103,6 +103,8 @@ struct gs_workspace {
     uint32_t *inst_tile = nullptr, *inst_val = nullptr, *inst_tile_alt = nullptr, *inst_val_alt = nullptr;
     // per-tile / per-pixel
     uint2 *ranges = nullptr;       // [n_tiles]
+    uint32_t *tile_order = nullptr; // [n_tiles] tiles by decreasing list length (raster work order)
+    uint32_t *tile_buckets = nullptr; // [2][kOrderBuckets] histogram and cursors for tile_order
     uint32_t *last = nullptr;      // [n_pix]
     float *tfin = nullptr;         // [n_pix]
     // scratch
@@ -171,6 +173,12 @@ gs_status sort_configure();
 // device helpers
 // ---------------------------------------------------------------------------
 
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -192,12 +200,23 @@ __device__ __forceinline__ void stage_record(const float4 r0, const float4 r1, f
 
 // log2 of the unclamped alpha of a staged Gaussian at integer pixel (px, py):
 // d = (px - U + hx, py - V + hy), t1 = l11 dx + l12 dy, t2 = l22 dy,
-// e = log2 o - t1^2 - t2^2.  The same instruction sequence serves both passes.
-__device__ __forceinline__ float frag_log2_alpha(const float4 a, const float4 b, float pxf, float pyf,
-                                                 float &t1, float &t2, float &dxi, float &dyi) {
+// e = log2 o - t1^2 - t2^2, evaluated as
+//   column part (shared by the pixels of one column):  dxi = px - U,
+//                                                      u1 = l11 dxi + k1
+//   pixel part:   dyi = py - V,  t1 = l12 dyi + u1,  t2 = l22 dyi + k2,
+//                 e = log2 o - t1^2 - t2^2
+// with exact integer offsets dxi, dyi.  Both passes call these functions, so
+// the backward recomputes exactly the forward's alpha and decisions, for any
+// tile size and any number of pixels per thread.
+__device__ __forceinline__ void frag_column(const float4 a, const float4 b, float pxf, float &dxi, float &u1) {
     dxi = __fsub_rn(pxf, a.x);
+    u1 = __fmaf_rn(b.x, dxi, a.z);
+}
+
+__device__ __forceinline__ float frag_pixel(const float4 a, const float4 b, float u1, float pyf, float &t1,
+                                            float &t2, float &dyi) {
     dyi = __fsub_rn(pyf, a.y);
-    t1 = __fmaf_rn(b.x, dxi, __fmaf_rn(b.y, dyi, a.z));
+    t1 = __fmaf_rn(b.y, dyi, u1);
     t2 = __fmaf_rn(b.z, dyi, a.w);
     return __fmaf_rn(-t1, t1, __fmaf_rn(-t2, t2, b.w));
 }

@@ -114,15 +114,35 @@ __global__ void __launch_bounds__(LT) k_depth_grad(DepthArgs A) {
     }
 }
 
+__device__ __forceinline__ float l1_term(float c, float t, float inv, float &g) {
+    float d = c - t;
+    g += d > 0.f ? inv : (d < 0.f ? -inv : 0.f);
+    return fabsf(d);
+}
+
+// Four terms are added in float, each group of four into a double; the
+// block and grid sums are in double and in a fixed order.
 __global__ void __launch_bounds__(LT) k_l1_partial(const float *rgb, const float *target, int64_t n,
                                                   float *grad, double *part) {
     __shared__ double sm[32];
     double s = 0.0;
     const float inv = (float)(1.0 / (double)n);
-    for (int64_t i = (int64_t)blockIdx.x * LT + threadIdx.x; i < n; i += (int64_t)gridDim.x * LT) {
-        float d = rgb[i] - target[i];
-        s += fabs((double)d);
-        if (grad) grad[i] += d > 0.f ? inv : (d < 0.f ? -inv : 0.f);
+    const bool vec = ((((uintptr_t)rgb) | ((uintptr_t)target) | ((uintptr_t)grad)) & 15) == 0;
+    const int64_t n4 = vec ? n / 4 : 0;
+    const int64_t stride = (int64_t)gridDim.x * LT;
+    for (int64_t i = (int64_t)blockIdx.x * LT + threadIdx.x; i < n4; i += stride) {
+        const float4 c = reinterpret_cast<const float4 *>(rgb)[i];
+        const float4 t = reinterpret_cast<const float4 *>(target)[i];
+        float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (grad) g = reinterpret_cast<float4 *>(grad)[i];
+        s += (double)(l1_term(c.x, t.x, inv, g.x) + l1_term(c.y, t.y, inv, g.y) +
+                      l1_term(c.z, t.z, inv, g.z) + l1_term(c.w, t.w, inv, g.w));
+        if (grad) reinterpret_cast<float4 *>(grad)[i] = g;
+    }
+    for (int64_t i = 4 * n4 + (int64_t)blockIdx.x * LT + threadIdx.x; i < n; i += stride) {
+        float g = grad ? grad[i] : 0.f;
+        s += (double)l1_term(rgb[i], target[i], inv, g);
+        if (grad) grad[i] = g;
     }
     double t = block_sum_d(s, sm);
     if (threadIdx.x == 0) part[blockIdx.x] = t;

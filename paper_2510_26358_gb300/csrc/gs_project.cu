@@ -271,19 +271,26 @@ __global__ void __launch_bounds__(kProjThreads) k_project_fwd(ProjArgs A) {
     float lno = -log1pf(expf(-om));
     float log2o = lno * kLog2e;
     float E = 2.f * (lno - k.ln_alpha_min);
-    float C[16][3];
-    load_sh<DEG>(A.sh, g, C);
     constexpr int K = (DEG + 1) * (DEG + 1);
+    const float *shg = A.sh + g * (3 * K);
+    const float mabs = fabsf(mu[0]) + fabsf(mu[1]) + fabsf(mu[2]);
 
     for (int kv = 0; kv < sub.nviews; ++kv) {
         int v = A.sub_views[s * A.maxv + kv];
         const ViewInfo vi = A.views[v];
         int64_t pair = (int64_t)vi.pair_off + (g - vi.g0);
         Cam cam = load_cam(A.cams, v);
-        double px = view_coord(cam.T, mu[0], mu[1], mu[2]);
-        double py = view_coord(cam.T + 4, mu[0], mu[1], mu[2]);
-        double pz = view_coord(cam.T + 8, mu[0], mu[1], mu[2]);
-        bool vis = pz > (double)k.near_z && qn > 0.f && E > 0.f;
+        // float estimate of the view depth: pairs clearly behind the near plane
+        // skip the exact double-precision depth (the margin dwarfs the float error)
+        const float z_est = __fmaf_rn(cam.T[10], mu[2], __fmaf_rn(cam.T[9], mu[1], __fmaf_rn(cam.T[8], mu[0], cam.T[11])));
+        bool vis = qn > 0.f && E > 0.f && z_est > k.near_z - 1e-5f * (mabs + fabsf(cam.T[11]) + 1.f);
+        double px = 0.0, py = 0.0, pz = 0.0;
+        if (vis) {
+            px = view_coord(cam.T, mu[0], mu[1], mu[2]);
+            py = view_coord(cam.T + 4, mu[0], mu[1], mu[2]);
+            pz = view_coord(cam.T + 8, mu[0], mu[1], mu[2]);
+            vis = pz > (double)k.near_z;
+        }
         PairGeom G;
         float4 r0 = make_float4(0, 0, 0, 0), r1 = r0, r2 = r0;
         short4 rc = make_short4(1, 1, 0, 0);
@@ -343,13 +350,13 @@ __global__ void __launch_bounds__(kProjThreads) k_project_fwd(ProjArgs A) {
                 float Y[16];
                 sh_basis<DEG>(w[0] * iw, w[1] * iw, w[2] * iw, Y);
                 float rgb[3];
+                float acc[3] = {0.5f, 0.5f, 0.5f};
 #pragma unroll
-                for (int ch = 0; ch < 3; ++ch) {
-                    float acc = 0.5f;
+                for (int kk = 0; kk < K; ++kk)
 #pragma unroll
-                    for (int kk = 0; kk < K; ++kk) acc = __fmaf_rn(C[kk][ch], Y[kk], acc);
-                    rgb[ch] = fmaxf(acc, 0.f);
-                }
+                    for (int ch = 0; ch < 3; ++ch) acc[ch] = __fmaf_rn(__ldg(shg + 3 * kk + ch), Y[kk], acc[ch]);
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) rgb[ch] = fmaxf(acc[ch], 0.f);
                 r0 = make_float4((float)Uf, (float)Vf, hx, hy);
                 r1 = make_float4(l11, l12, l22, log2o);
                 r2 = make_float4(rgb[0], rgb[1], rgb[2], __double2float_rn(pz));

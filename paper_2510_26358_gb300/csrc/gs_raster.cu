@@ -16,7 +16,12 @@
 // instructions, T is recovered by division, and with h = gC.c + gD z + gA
 //   dL/dalpha_j = T_j h_j - (sum_{k>j} w_k h_k) / (1 - alpha_j).
 // The 10 image-space gradient components of each Gaussian are summed over the
-// warp's 32 pixels with shuffles before one atomic per component.
+// thread's pixels and then over the warp with shuffles before one atomic per
+// component.
+//
+// In the backward each thread owns PPT vertically adjacent pixels of one
+// column: the shared memory loads, the loop overhead, the column part of the
+// exponent and the warp reduction are paid once per PPT pixels.
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -29,6 +34,7 @@ struct RasterArgs {
     const float4 *rec;
     const uint32_t *vals;
     const uint2 *ranges;
+    const uint32_t *order;  // tiles in work order
     uint32_t *counter;
     uint32_t *last;
     float *tfin;
@@ -42,6 +48,7 @@ struct RasterArgs {
 template <int TW, int TH>
 __global__ void __launch_bounds__(TW * TH) k_raster_fwd(RasterArgs A) {
     constexpr int NT = TW * TH;
+    static_assert(NT % 32 == 0, "the forward needs whole warps");
     extern __shared__ float4 smem[];
     float4 *sA = smem, *sB = smem + A.depth, *sC = smem + 2 * A.depth;
     __shared__ int s_tile;
@@ -49,10 +56,13 @@ __global__ void __launch_bounds__(TW * TH) k_raster_fwd(RasterArgs A) {
     const float amax = A.c.alpha_max, tmin = A.c.t_min, l2amin = A.c.log2_alpha_min;
     for (;;) {
         __syncthreads();
-        if (tid == 0) s_tile = (int)atomicAdd(A.counter, 1u);
+        if (tid == 0) {
+            const uint32_t w = atomicAdd(A.counter, 1u);
+            s_tile = w < (uint32_t)A.n_tiles ? (int)A.order[w] : -1;
+        }
         __syncthreads();
         const int tile = s_tile;
-        if (tile >= A.n_tiles) break;
+        if (tile < 0) break;
         const int v = view_of_tile(A.views, A.n_views, tile);
         const ViewInfo vi = A.views[v];
         const int lt = tile - vi.tile_off;
@@ -77,26 +87,27 @@ __global__ void __launch_bounds__(TW * TH) k_raster_fwd(RasterArgs A) {
                 sC[j] = A.rec[3 * (size_t)pair + 2];
             }
             __syncthreads();
-            if (!done) {
-                for (int j = 0; j < nb; ++j) {
-                    float t1, t2, dxi, dyi;
-                    const float e = frag_log2_alpha(sA[j], sB[j], pxf, pyf, t1, t2, dxi, dyi);
-                    if (e < l2amin) continue;
-                    const float al = fminf(amax, ex2_approx(e));
-                    const float Tn = __fmaf_rn(-T, al, T);
-                    if (Tn < tmin) {
-                        done = true;
-                        break;
-                    }
-                    const float wgt = al * T;
-                    const float4 c = sC[j];
-                    Cr = __fmaf_rn(wgt, c.x, Cr);
-                    Cg = __fmaf_rn(wgt, c.y, Cg);
-                    Cb = __fmaf_rn(wgt, c.z, Cb);
-                    D = __fmaf_rn(wgt, c.w, D);
-                    T = Tn;
-                    cnt = b0 + j - rg.x + 1;
+            if (done) continue;
+            for (int j = 0; j < nb; ++j) {
+                const float4 a = sA[j], b = sB[j];
+                float dxi, u1, t1, t2, dyi;
+                frag_column(a, b, pxf, dxi, u1);
+                const float e = frag_pixel(a, b, u1, pyf, t1, t2, dyi);
+                if (e < l2amin) continue;
+                const float al = fminf(amax, ex2_approx(e));
+                const float Tn = __fmaf_rn(-T, al, T);
+                if (Tn < tmin) {
+                    done = true;
+                    break;
                 }
+                const float wgt = al * T;
+                const float4 c = sC[j];
+                Cr = __fmaf_rn(wgt, c.x, Cr);
+                Cg = __fmaf_rn(wgt, c.y, Cg);
+                Cb = __fmaf_rn(wgt, c.z, Cb);
+                D = __fmaf_rn(wgt, c.w, D);
+                T = Tn;
+                cnt = b0 + j - rg.x + 1;
             }
         }
         if (inside) {
@@ -159,10 +170,11 @@ __device__ __forceinline__ int reduce10_component(int lane) {
     return ok ? 5 * b4 + 3 * b3 + 2 * b2 + b1 : -1;
 }
 
-template <int TW, int TH>
-__global__ void __launch_bounds__(TW * TH) k_raster_bwd(RasterArgs A) {
-    constexpr int NT = TW * TH;
-    constexpr int NW = NT / 32;
+template <int TW, int TH, int PPT>
+__global__ void __launch_bounds__(TW * TH / PPT) k_raster_bwd(RasterArgs A) {
+    constexpr int NT = TW * TH / PPT;
+    static_assert(NT % 32 == 0, "the backward needs whole warps");
+    constexpr int NW = (NT + 31) / 32;
     extern __shared__ float4 smem[];
     float4 *sA = smem, *sB = smem + A.depth, *sC = smem + 2 * A.depth;
     float2 *sH = reinterpret_cast<float2 *>(smem + 3 * A.depth);
@@ -175,42 +187,51 @@ __global__ void __launch_bounds__(TW * TH) k_raster_bwd(RasterArgs A) {
     const int my_comp = (lane & 1) ? -1 : reduce10_component(lane);
     for (;;) {
         __syncthreads();
-        if (tid == 0) s_tile = (int)atomicAdd(A.counter, 1u);
+        if (tid == 0) {
+            const uint32_t w = atomicAdd(A.counter, 1u);
+            s_tile = w < (uint32_t)A.n_tiles ? (int)A.order[w] : -1;
+        }
         __syncthreads();
         const int tile = s_tile;
-        if (tile >= A.n_tiles) break;
+        if (tile < 0) break;
         const int v = view_of_tile(A.views, A.n_views, tile);
         const ViewInfo vi = A.views[v];
         const int lt = tile - vi.tile_off;
         const int px = (lt % vi.ntx) * TW + tid % TW;
-        const int py = (lt / vi.ntx) * TH + tid / TW;
-        const bool inside = px < vi.W && py < vi.H;
-        const float pxf = (float)px, pyf = (float)py;
+        const int py0 = (lt / vi.ntx) * TH + (tid / TW) * PPT;
+        const float pxf = (float)px;
         const uint2 rg = A.ranges[tile];
-        uint32_t cnt = 0;
-        float T = 1.f, gR = 0.f, gG = 0.f, gB = 0.f, gD = 0.f, gA = 0.f;
-        if (inside) {
-            const int64_t pl = (int64_t)py * vi.W + px;
-            const int64_t pix = vi.pix_off + pl;
-            const int64_t hw = (int64_t)vi.W * vi.H;
-            const float *g = A.dL_drgb + 3 * (int64_t)vi.pix_off;
-            cnt = A.last[pix];
-            T = A.tfin[pix];
-            gR = g[pl];
-            gG = g[hw + pl];
-            gB = g[2 * hw + pl];
-            gD = A.dL_ddepth ? A.dL_ddepth[pix] : 0.f;
-            gA = A.dL_dalpha ? A.dL_dalpha[pix] : 0.f;
-        }
-        uint32_t m = cnt;
+        const int64_t hw = (int64_t)vi.W * vi.H;
+        const float *grgb = A.dL_drgb + 3 * (int64_t)vi.pix_off;
+        uint32_t cnt[PPT], mycnt = 0;
+        float T[PPT], gR[PPT], gG[PPT], gB[PPT], gD[PPT], gA[PPT], acc[PPT];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if (lane == 0) s_max[wid] = m;
+        for (int i = 0; i < PPT; ++i) {
+            const int py = py0 + i;
+            cnt[i] = 0;
+            T[i] = 1.f;
+            gR[i] = gG[i] = gB[i] = gD[i] = gA[i] = acc[i] = 0.f;
+            if (px < vi.W && py < vi.H) {
+                const int64_t pl = (int64_t)py * vi.W + px;
+                const int64_t pix = vi.pix_off + pl;
+                cnt[i] = A.last[pix];
+                T[i] = A.tfin[pix];
+                gR[i] = grgb[pl];
+                gG[i] = grgb[hw + pl];
+                gB[i] = grgb[2 * hw + pl];
+                gD[i] = A.dL_ddepth ? A.dL_ddepth[pix] : 0.f;
+                gA[i] = A.dL_dalpha ? A.dL_dalpha[pix] : 0.f;
+            }
+            mycnt = max(mycnt, cnt[i]);
+        }
+        uint32_t wmax = mycnt;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+        if (lane == 0) s_max[wid] = wmax;
         __syncthreads();
         uint32_t maxcnt = 0;
 #pragma unroll
-        for (int i = 0; i < NW; ++i) maxcnt = max(maxcnt, s_max[i]);
-        float acc = 0.f;  // sum over later blended fragments of w_k h_k
+        for (int w = 0; w < NW; ++w) maxcnt = max(maxcnt, s_max[w]);
         for (int64_t hi = (int64_t)rg.x + maxcnt; hi > (int64_t)rg.x; hi -= A.depth) {
             const int64_t lo = max((int64_t)rg.x, hi - A.depth);
             const int nb = (int)(hi - lo);
@@ -229,42 +250,48 @@ __global__ void __launch_bounds__(TW * TH) k_raster_bwd(RasterArgs A) {
             __syncthreads();
             for (int j = nb - 1; j >= 0; --j) {
                 const uint32_t rel = (uint32_t)(lo + j - rg.x);
-                float t1, t2, dxi, dyi;
-                const float4 sa = sA[j], sb = sB[j];
-                const float e = frag_log2_alpha(sa, sb, pxf, pyf, t1, t2, dxi, dyi);
-                const bool contrib = rel < cnt && e >= l2amin;
-                float gv10[kGrad];
+                if (rel >= wmax) continue;  // no pixel of this warp reached this entry
+                const float4 a = sA[j], b = sB[j];
+                float dxi, u1;
+                frag_column(a, b, pxf, dxi, u1);
+                float g[kGrad];
 #pragma unroll
-                for (int q = 0; q < kGrad; ++q) gv10[q] = 0.f;
-                if (contrib) {
+                for (int q = 0; q < kGrad; ++q) g[q] = 0.f;
+                bool any = false;
+#pragma unroll
+                for (int i = 0; i < PPT; ++i) {
+                    float t1, t2, dyi;
+                    const float e = frag_pixel(a, b, u1, (float)(py0 + i), t1, t2, dyi);
+                    if (!(rel < cnt[i] && e >= l2amin)) continue;
+                    any = true;
                     const float araw = ex2_approx(e);
                     const float al = fminf(amax, araw);
-                    const float r1m = 1.f / (1.f - al);
-                    T = T * r1m;  // transmittance before this fragment
+                    const float r1m = rcp_approx(1.f - al);
+                    T[i] = T[i] * r1m;  // transmittance before this fragment
                     const float4 c = sC[j];
-                    const float wgt = al * T;
-                    const float h = gR * c.x + gG * c.y + gB * c.z + gD * c.w + gA;
-                    const float dLda = T * h - acc * r1m;
-                    acc = __fmaf_rn(wgt, h, acc);
-                    gv10[G_R] = wgt * gR;
-                    gv10[G_G] = wgt * gG;
-                    gv10[G_B] = wgt * gB;
-                    gv10[G_Z] = wgt * gD;
+                    const float wgt = al * T[i];
+                    const float h = gR[i] * c.x + gG[i] * c.y + gB[i] * c.z + gD[i] * c.w + gA[i];
+                    const float dLda = T[i] * h - acc[i] * r1m;
+                    acc[i] = __fmaf_rn(wgt, h, acc[i]);
+                    g[G_R] += wgt * gR[i];
+                    g[G_G] += wgt * gG[i];
+                    g[G_B] += wgt * gB[i];
+                    g[G_Z] += wgt * gD[i];
                     if (araw <= amax) {
                         const float gpw = dLda * al;  // dL/dpw, pw = -d^T Q d / 2 (natural log)
                         const float2 hh = sH[j];
                         const float dx = dxi + hh.x, dy = dyi + hh.y;
-                        gv10[G_LNO] = gpw;
-                        gv10[G_QA] = -0.5f * gpw * dx * dx;
-                        gv10[G_QB] = -gpw * dx * dy;
-                        gv10[G_QC] = -0.5f * gpw * dy * dy;
+                        g[G_LNO] += gpw;
+                        g[G_QA] += -0.5f * gpw * dx * dx;
+                        g[G_QB] += -gpw * dx * dy;
+                        g[G_QC] += -0.5f * gpw * dy * dy;
                         // dpw/du = (Q d)_x = l11 t1 / s^2, dpw/dv = (l12 t1 + l22 t2) / s^2
-                        gv10[G_U] = gpw * kTwoLn2 * (sb.x * t1);
-                        gv10[G_V] = gpw * kTwoLn2 * (sb.y * t1 + sb.z * t2);
+                        g[G_U] += gpw * kTwoLn2 * (b.x * t1);
+                        g[G_V] += gpw * kTwoLn2 * (b.y * t1 + b.z * t2);
                     }
                 }
-                if (__any_sync(0xffffffffu, contrib)) {
-                    const float tot = warp_reduce_scatter10(gv10, lane);
+                if (__any_sync(0xffffffffu, any)) {
+                    const float tot = warp_reduce_scatter10(g, lane);
                     if (my_comp >= 0) atomicAdd(A.g2d + (size_t)sP[j] * kGrad + my_comp, tot);
                 }
             }
@@ -279,9 +306,13 @@ __global__ void k_zero_g2d(const uint32_t *vis_pair, const DevState *st, float *
         g2d[(size_t)vis_pair[i / kGrad] * kGrad + i % kGrad] = 0.f;
 }
 
+// Pixels per thread of the backward (the forward uses one, so that a pixel
+// leaves the list as soon as it saturates).  The backward's shuffles and votes
+// use the full mask: a CTA keeps whole warps.
 template <int TW, int TH>
+constexpr int ppt_bwd() { return 2; }
+
 size_t fwd_smem(int depth) { return (size_t)depth * 3 * sizeof(float4); }
-template <int TW, int TH>
 size_t bwd_smem(int depth) {
     return (size_t)depth * (3 * sizeof(float4) + sizeof(float2) + sizeof(uint32_t));
 }
@@ -291,17 +322,17 @@ gs_status configure_one(gs_workspace *ws) {
     int depth = ws->cfg.batch_depth;
     cudaError_t e;
     e = cudaFuncSetAttribute(k_raster_fwd<TW, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)fwd_smem<TW, TH>(256));
+                             (int)fwd_smem(256));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_raster_bwd<TW, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)bwd_smem<TW, TH>(256));
+        e = cudaFuncSetAttribute(k_raster_bwd<TW, TH, ppt_bwd<TW, TH>()>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)bwd_smem(256));
     int occ_f = 0, occ_b = 0;
     if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_f, k_raster_fwd<TW, TH>, TW * TH,
-                                                          fwd_smem<TW, TH>(depth));
+                                                          fwd_smem(depth));
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, k_raster_bwd<TW, TH>, TW * TH,
-                                                          bwd_smem<TW, TH>(depth));
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, k_raster_bwd<TW, TH, ppt_bwd<TW, TH>()>, TW * TH / ppt_bwd<TW, TH>(),
+                                                          bwd_smem(depth));
     if (e != cudaSuccess) {
         set_last_error(std::string("raster_configure: ") + cudaGetErrorString(e));
         return GS_ERR_CUDA;
@@ -321,6 +352,7 @@ RasterArgs make_args(gs_workspace *ws) {
     A.rec = ws->rec;
     A.vals = ws->inst_val;
     A.ranges = ws->ranges;
+    A.order = ws->tile_order;
     A.last = ws->last;
     A.tfin = ws->tfin;
     return A;
@@ -329,13 +361,15 @@ RasterArgs make_args(gs_workspace *ws) {
 template <int TW, int TH>
 gs_status run_fwd(gs_workspace *ws, RasterArgs A, cudaStream_t s) {
     StageTimer timer(ws, GS_STAGE_RASTER_FWD, s);
-    ++ws->kernel_launches; k_raster_fwd<TW, TH><<<ws->raster_grid_fwd, TW * TH, fwd_smem<TW, TH>(A.depth), s>>>(A);
+    ++ws->kernel_launches;
+    k_raster_fwd<TW, TH><<<ws->raster_grid_fwd, TW * TH, fwd_smem(A.depth), s>>>(A);
     return check_launch("raster_fwd");
 }
 template <int TW, int TH>
 gs_status run_bwd(gs_workspace *ws, RasterArgs A, cudaStream_t s) {
     StageTimer timer(ws, GS_STAGE_RASTER_BWD, s);
-    ++ws->kernel_launches; k_raster_bwd<TW, TH><<<ws->raster_grid_bwd, TW * TH, bwd_smem<TW, TH>(A.depth), s>>>(A);
+    ++ws->kernel_launches;
+    k_raster_bwd<TW, TH, ppt_bwd<TW, TH>()><<<ws->raster_grid_bwd, TW * TH / ppt_bwd<TW, TH>(), bwd_smem(A.depth), s>>>(A);
     return check_launch("raster_bwd");
 }
 

@@ -136,12 +136,12 @@ __global__ void __launch_bounds__(T) k_compact_visible(const uint32_t *pkey, uin
 // ---------------------------------------------------------------------------
 
 __global__ void __launch_bounds__(T) k_radix_hist(const uint32_t *keys, const uint32_t *n_ptr, int shift,
-                                                 uint32_t *hist, int nb) {
+                                                 uint32_t *hist, int nb, int tile) {
     __shared__ uint32_t h[W][256];
     for (int i = threadIdx.x; i < W * 256; i += T) (&h[0][0])[i] = 0;
     __syncthreads();
     uint32_t lo, hi;
-    chunk_range(*n_ptr, blockIdx.x, nb, kSortTile, lo, hi);
+    chunk_range(*n_ptr, blockIdx.x, nb, tile, lo, hi);
     int w = threadIdx.x >> 5;
     for (uint32_t i = lo + threadIdx.x; i < hi; i += T) atomicAdd(&h[w][(keys[i] >> shift) & 255u], 1u);
     __syncthreads();
@@ -178,24 +178,28 @@ __global__ void __launch_bounds__(T) k_radix_scan(uint32_t *hist, int nb, uint32
     if (t == 0) dtot[blockIdx.x] = tot;
 }
 
+template <int R>
 struct ScatterSmem {
-    uint32_t key[kSortTile];
-    uint32_t val[kSortTile];
+    uint32_t key[T * R];
+    uint32_t val[T * R];
     uint32_t wcnt[W][256];
     uint32_t wpre[W][256];
     uint32_t base[256], tcnt[256], tstart[256];
     uint32_t scan[32];
 };
 
+// R rounds of T keys make one block tile; blocks own whole tiles
+template <int R>
 __global__ void __launch_bounds__(T) k_radix_scatter(const uint32_t *kin, const uint32_t *vin,
                                                     uint32_t *kout, uint32_t *vout,
                                                     const uint32_t *n_ptr, int shift,
                                                     const uint32_t *hist, const uint32_t *dtot, int nb) {
+    constexpr int TILE = T * R;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    ScatterSmem &S = *reinterpret_cast<ScatterSmem *>(smem_raw);
+    ScatterSmem<R> &S = *reinterpret_cast<ScatterSmem<R> *>(smem_raw);
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     uint32_t lo, hi;
-    chunk_range(*n_ptr, blockIdx.x, nb, kSortTile, lo, hi);
+    chunk_range(*n_ptr, blockIdx.x, nb, TILE, lo, hi);
     if (lo >= hi) return;
     {
         uint32_t tot;
@@ -207,17 +211,17 @@ __global__ void __launch_bounds__(T) k_radix_scatter(const uint32_t *kin, const 
     for (int j = 0; j < W; ++j) S.wcnt[j][t] = 0;
     __syncthreads();
     const uint32_t lt = lanemask_lt();
-    for (uint32_t t0 = lo; t0 < hi; t0 += kSortTile) {
-        uint32_t tn = min((uint32_t)kSortTile, hi - t0);
-        uint32_t key[kSortRounds], val[kSortRounds], rank[kSortRounds];
+    for (uint32_t t0 = lo; t0 < hi; t0 += TILE) {
+        uint32_t tn = min((uint32_t)TILE, hi - t0);
+        uint32_t key[R], val[R], rank[R];
 #pragma unroll
-        for (int r = 0; r < kSortRounds; ++r) {
+        for (int r = 0; r < R; ++r) {
             uint32_t i = r * T + t;
             key[r] = i < tn ? kin[t0 + i] : 0u;
             val[r] = i < tn ? vin[t0 + i] : 0u;
         }
 #pragma unroll
-        for (int r = 0; r < kSortRounds; ++r) {
+        for (int r = 0; r < R; ++r) {
             bool valid = (uint32_t)(r * T + t) < tn;
             uint32_t d = (key[r] >> shift) & 255u;
             // invalid lanes get a private tag so that they match nobody
@@ -246,7 +250,7 @@ __global__ void __launch_bounds__(T) k_radix_scatter(const uint32_t *kin, const 
         S.tstart[t] = ex;
         __syncthreads();
 #pragma unroll
-        for (int r = 0; r < kSortRounds; ++r) {
+        for (int r = 0; r < R; ++r) {
             if ((uint32_t)(r * T + t) < tn) {
                 uint32_t d = (key[r] >> shift) & 255u;
                 uint32_t lp = S.tstart[d] + rank[r];
@@ -340,14 +344,54 @@ __global__ void k_ranges(const uint32_t *tile, const DevState *st, uint2 *ranges
     }
 }
 
-// One stable pass over bits [shift, shift+8); swaps in/out.
+// Raster work order: tiles by decreasing list length, so that the longest
+// lists start first and the persistent rasterisers finish together.  A
+// counting sort into kOrderBuckets length buckets; the order inside a bucket
+// is whatever the atomics give (tiles are independent, so it does not change
+// any result).
+__global__ void k_order_hist(const uint2 *ranges, int n_tiles, uint32_t *buckets) {
+    __shared__ uint32_t h[kOrderBuckets];
+    if (threadIdx.x < kOrderBuckets) h[threadIdx.x] = 0;
+    __syncthreads();
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += gridDim.x * blockDim.x) {
+        uint32_t len = ranges[t].y - ranges[t].x;
+        uint32_t b = kOrderBuckets - 1 - min((uint32_t)(kOrderBuckets - 1), len >> kOrderShift);
+        atomicAdd(&h[b], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < kOrderBuckets && h[threadIdx.x]) atomicAdd(&buckets[threadIdx.x], h[threadIdx.x]);
+}
+
+__global__ void k_order_scatter(const uint2 *ranges, int n_tiles, uint32_t *buckets, uint32_t *order) {
+    __shared__ uint32_t start[kOrderBuckets];
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int b = 0; b < kOrderBuckets; ++b) {
+            start[b] = run;
+            run += buckets[b];
+        }
+    }
+    __syncthreads();
+    uint32_t *cursor = buckets + kOrderBuckets;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += gridDim.x * blockDim.x) {
+        uint32_t len = ranges[t].y - ranges[t].x;
+        uint32_t b = kOrderBuckets - 1 - min((uint32_t)(kOrderBuckets - 1), len >> kOrderShift);
+        order[start[b] + atomicAdd(&cursor[b], 1u)] = (uint32_t)t;
+    }
+}
+
+// One stable pass over bits [shift, shift+8); swaps in/out.  R = 16 rounds
+// (4096-key tiles, long coalesced runs) for the instance sort, R = 4 for the
+// smaller sort of the visible pairs (more blocks busy, shorter latency).
+template <int R>
 gs_status radix_pass(gs_workspace *ws, uint32_t *&k, uint32_t *&v, uint32_t *&k2, uint32_t *&v2,
                      const uint32_t *n_ptr, int shift, cudaStream_t s) {
     int nb = ws->sort_blocks;
-    ++ws->kernel_launches; k_radix_hist<<<nb, T, 0, s>>>(k, n_ptr, shift, ws->hist, nb);
+    ++ws->kernel_launches; k_radix_hist<<<nb, T, 0, s>>>(k, n_ptr, shift, ws->hist, nb, T * R);
     ++ws->kernel_launches; k_radix_scan<<<256, T, 0, s>>>(ws->hist, nb, ws->digit_tot);
     ++ws->kernel_launches;
-    k_radix_scatter<<<nb, T, sizeof(ScatterSmem), s>>>(k, v, k2, v2, n_ptr, shift, ws->hist, ws->digit_tot, nb);
+    k_radix_scatter<R><<<nb, T, sizeof(ScatterSmem<R>), s>>>(k, v, k2, v2, n_ptr, shift, ws->hist,
+                                                             ws->digit_tot, nb);
     std::swap(k, k2);
     std::swap(v, v2);
     return check_launch("radix_pass");
@@ -356,8 +400,11 @@ gs_status radix_pass(gs_workspace *ws, uint32_t *&k, uint32_t *&v, uint32_t *&k2
 }  // namespace
 
 gs_status sort_configure() {
-    cudaError_t e = cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(ScatterSmem));
+    cudaError_t e = cudaFuncSetAttribute(k_radix_scatter<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(ScatterSmem<16>));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_radix_scatter<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(ScatterSmem<4>));
     if (e != cudaSuccess) {
         set_last_error(std::string("sort_configure: ") + cudaGetErrorString(e));
         return GS_ERR_CUDA;
@@ -385,7 +432,7 @@ gs_status launch_bin_sort(gs_workspace *ws, cudaStream_t s) {
     {
     StageTimer timer(ws, GS_STAGE_DEPTH_SORT, s);
     for (int sh = 0; sh < 32; sh += 8)
-        if ((r = radix_pass(ws, k, v, k2, v2, &st->n_vis, sh, s)) != GS_OK) return r;
+        if ((r = radix_pass<4>(ws, k, v, k2, v2, &st->n_vis, sh, s)) != GS_OK) return r;
     }
     // after 4 passes the sorted data are back in vis_key / vis_pair
     // 3. instance offsets, capacity check, emission in depth order
@@ -406,12 +453,19 @@ gs_status launch_bin_sort(gs_workspace *ws, cudaStream_t s) {
     {
     StageTimer timer(ws, GS_STAGE_TILE_SORT, s);
     for (int p = 0; p < passes; ++p)
-        if ((r = radix_pass(ws, tk, tv, tk2, tv2, &st->n_inst, 8 * p, s)) != GS_OK) return r;
+        if ((r = radix_pass<16>(ws, tk, tv, tk2, tv2, &st->n_inst, 8 * p, s)) != GS_OK) return r;
     }
     // 5. ranges
     StageTimer timer(ws, GS_STAGE_RANGES, s);
     cudaMemsetAsync(ws->ranges, 0, sizeof(uint2) * ws->n_tiles, s);
     ++ws->kernel_launches; k_ranges<<<ws->num_sms * 8, 256, 0, s>>>(ws->inst_tile, st, ws->ranges);
+    // 6. raster work order
+    cudaMemsetAsync(ws->tile_buckets, 0, sizeof(uint32_t) * 2 * kOrderBuckets, s);
+    int ob = (int)std::min<int64_t>(ws->num_sms, (ws->n_tiles + 255) / 256);
+    ++ws->kernel_launches;
+    k_order_hist<<<ob, 256, 0, s>>>(ws->ranges, (int)ws->n_tiles, ws->tile_buckets);
+    ++ws->kernel_launches;
+    k_order_scatter<<<ob, 256, 0, s>>>(ws->ranges, (int)ws->n_tiles, ws->tile_buckets, ws->tile_order);
     return check_launch("ranges");
 }
 
