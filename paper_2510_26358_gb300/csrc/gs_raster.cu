@@ -183,8 +183,15 @@ __global__ void __launch_bounds__(TW * TH / PPT) k_raster_bwd(RasterArgs A) {
     __shared__ uint32_t s_max[NW];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const float amax = A.c.alpha_max, l2amin = A.c.log2_alpha_min;
-    // component this lane adds after the reduction (even lanes only)
+    // component this lane adds after the reduction (even lanes only), and the
+    // factors c0 + c11 l11 + c22 l22 that turn its raw sum into the gradient
     const int my_comp = (lane & 1) ? -1 : reduce10_component(lane);
+    const float sc0 = my_comp == G_QA || my_comp == G_QC ? -0.5f
+                      : my_comp == G_QB                  ? -1.f
+                      : my_comp == G_U || my_comp == G_V ? 0.f
+                                                         : 1.f;
+    const float sc11 = my_comp == G_U ? kTwoLn2 : 0.f;
+    const float sc22 = my_comp == G_V ? kTwoLn2 : 0.f;
     for (;;) {
         __syncthreads();
         if (tid == 0) {
@@ -278,21 +285,31 @@ __global__ void __launch_bounds__(TW * TH / PPT) k_raster_bwd(RasterArgs A) {
                     g[G_B] += wgt * gB[i];
                     g[G_Z] += wgt * gD[i];
                     if (araw <= amax) {
-                        const float gpw = dLda * al;  // dL/dpw, pw = -d^T Q d / 2 (natural log)
+                        // gpw = dL/dpw with pw = -d^T Q d / 2 (natural log).  The warp sums
+                        // the raw moments; the per-Gaussian factors are applied once after
+                        // the reduction (see below).
+                        const float gpw = dLda * al;
                         const float2 hh = sH[j];
                         const float dx = dxi + hh.x, dy = dyi + hh.y;
                         g[G_LNO] += gpw;
-                        g[G_QA] += -0.5f * gpw * dx * dx;
-                        g[G_QB] += -gpw * dx * dy;
-                        g[G_QC] += -0.5f * gpw * dy * dy;
-                        // dpw/du = (Q d)_x = l11 t1 / s^2, dpw/dv = (l12 t1 + l22 t2) / s^2
-                        g[G_U] += gpw * kTwoLn2 * (b.x * t1);
-                        g[G_V] += gpw * kTwoLn2 * (b.y * t1 + b.z * t2);
+                        g[G_U] = __fmaf_rn(gpw, t1, g[G_U]);  // sum gpw t1
+                        g[G_V] = __fmaf_rn(gpw, t2, g[G_V]);  // sum gpw t2
+                        const float gx = gpw * dx, gy = gpw * dy;
+                        g[G_QA] = __fmaf_rn(gx, dx, g[G_QA]);  // sum gpw dx^2
+                        g[G_QB] = __fmaf_rn(gx, dy, g[G_QB]);  // sum gpw dx dy
+                        g[G_QC] = __fmaf_rn(gy, dy, g[G_QC]);  // sum gpw dy^2
                     }
                 }
                 if (__any_sync(0xffffffffu, any)) {
                     const float tot = warp_reduce_scatter10(g, lane);
-                    if (my_comp >= 0) atomicAdd(A.g2d + (size_t)sP[j] * kGrad + my_comp, tot);
+                    if (my_comp >= 0) {
+                        // dL/dQ = -1/2 sum gpw d d^T; dpw/du = (Q d)_x = l11 t1 / s^2,
+                        // dpw/dv = (l12 t1 + l22 t2) / s^2 with 1/s^2 = 2 ln 2: each lane
+                        // scales its sum by c0 + c11 l11 + c22 l22 (constants per lane)
+                        float *gp = A.g2d + (size_t)sP[j] * kGrad;
+                        atomicAdd(gp + my_comp, tot * __fmaf_rn(sc11, b.x, __fmaf_rn(sc22, b.z, sc0)));
+                        if (my_comp == G_U) atomicAdd(gp + G_V, kTwoLn2 * b.y * tot);
+                    }
                 }
             }
         }

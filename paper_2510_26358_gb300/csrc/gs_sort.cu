@@ -182,19 +182,25 @@ template <int R>
 struct ScatterSmem {
     uint32_t key[T * R];
     uint32_t val[T * R];
-    uint32_t wcnt[W][256];
-    uint32_t wpre[W][256];
+    uint32_t wcnt[W][256];  // per-warp digit counts, then per-warp digit offsets
     uint32_t base[256], tcnt[256], tstart[256];
     uint32_t scan[32];
 };
 
-// R rounds of T keys make one block tile; blocks own whole tiles
+// One block tile = T*R keys, split into W contiguous warp sub-tiles of 32*R
+// keys.  Each warp ranks its own sub-tile round by round (match masks give
+// the rank among equal digits of the round, per-warp counters carry it across
+// rounds, no block barrier); one block-wide pass then turns the per-warp
+// counts into offsets, the keys are reordered by digit in shared memory and
+// written out in coalesced runs at the global offsets.  Stable: sub-tiles,
+// rounds and lanes follow the input order.
 template <int R>
 __global__ void __launch_bounds__(T) k_radix_scatter(const uint32_t *kin, const uint32_t *vin,
                                                     uint32_t *kout, uint32_t *vout,
                                                     const uint32_t *n_ptr, int shift,
                                                     const uint32_t *hist, const uint32_t *dtot, int nb) {
     constexpr int TILE = T * R;
+    constexpr int WT = 32 * R;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ScatterSmem<R> &S = *reinterpret_cast<ScatterSmem<R> *>(smem_raw);
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
@@ -206,70 +212,62 @@ __global__ void __launch_bounds__(T) k_radix_scatter(const uint32_t *kin, const 
         uint32_t digit_base = block_exclusive_scan(dtot[t], S.scan, &tot);
         S.base[t] = digit_base + hist[t * nb + blockIdx.x];
     }
-    S.tcnt[t] = 0;
-#pragma unroll
-    for (int j = 0; j < W; ++j) S.wcnt[j][t] = 0;
-    __syncthreads();
     const uint32_t lt = lanemask_lt();
     for (uint32_t t0 = lo; t0 < hi; t0 += TILE) {
-        uint32_t tn = min((uint32_t)TILE, hi - t0);
+        const uint32_t tn = min((uint32_t)TILE, hi - t0);
+#pragma unroll
+        for (int j = 0; j < W; ++j) S.wcnt[j][t] = 0;
+        __syncthreads();
         uint32_t key[R], val[R], rank[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            uint32_t i = r * T + t;
+            const uint32_t i = w * WT + r * 32 + lane;
             key[r] = i < tn ? kin[t0 + i] : 0u;
             val[r] = i < tn ? vin[t0 + i] : 0u;
         }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            bool valid = (uint32_t)(r * T + t) < tn;
-            uint32_t d = (key[r] >> shift) & 255u;
-            // invalid lanes get a private tag so that they match nobody
-            uint32_t tag = valid ? d : (0x100u | (uint32_t)lane);
-            uint32_t m = __match_any_sync(0xffffffffu, tag);
-            uint32_t below = m & lt;
-            if (valid && below == 0) S.wcnt[w][d] = __popc(m);
-            __syncthreads();
-            {
-                uint32_t run = S.tcnt[t];
-#pragma unroll
-                for (int j = 0; j < W; ++j) {
-                    uint32_t c = S.wcnt[j][t];
-                    S.wpre[j][t] = run;
-                    S.wcnt[j][t] = 0;
-                    run += c;
-                }
-                S.tcnt[t] = run;
-            }
-            __syncthreads();
-            rank[r] = valid ? S.wpre[w][d] + __popc(below) : 0u;
+            const bool valid = (uint32_t)(w * WT + r * 32 + lane) < tn;
+            const uint32_t d = (key[r] >> shift) & 255u;
+            const uint32_t m = __match_any_sync(0xffffffffu, valid ? d : (0x100u | (uint32_t)lane));
+            const uint32_t below = m & lt;
+            const uint32_t before = valid ? S.wcnt[w][d] : 0u;
+            rank[r] = before + __popc(below);
+            __syncwarp();
+            if (valid && below == 0) S.wcnt[w][d] = before + __popc(m);
+            __syncwarp();
         }
         __syncthreads();
+        uint32_t run = 0;
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            const uint32_t c = S.wcnt[j][t];
+            S.wcnt[j][t] = run;
+            run += c;
+        }
+        S.tcnt[t] = run;
         uint32_t tot;
-        uint32_t ex = block_exclusive_scan(S.tcnt[t], S.scan, &tot);
-        S.tstart[t] = ex;
+        S.tstart[t] = block_exclusive_scan(run, S.scan, &tot);
         __syncthreads();
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            if ((uint32_t)(r * T + t) < tn) {
-                uint32_t d = (key[r] >> shift) & 255u;
-                uint32_t lp = S.tstart[d] + rank[r];
+            if ((uint32_t)(w * WT + r * 32 + lane) < tn) {
+                const uint32_t d = (key[r] >> shift) & 255u;
+                const uint32_t lp = S.tstart[d] + S.wcnt[w][d] + rank[r];
                 S.key[lp] = key[r];
                 S.val[lp] = val[r];
             }
         }
         __syncthreads();
         for (uint32_t j = t; j < tn; j += T) {
-            uint32_t k = S.key[j];
-            uint32_t d = (k >> shift) & 255u;
-            uint32_t o = S.base[d] + (j - S.tstart[d]);
+            const uint32_t k = S.key[j];
+            const uint32_t d = (k >> shift) & 255u;
+            const uint32_t o = S.base[d] + (j - S.tstart[d]);
             kout[o] = k;
             vout[o] = S.val[j];
         }
         __syncthreads();
         S.base[t] += S.tcnt[t];
-        S.tcnt[t] = 0;
-        __syncthreads();
     }
 }
 
@@ -282,56 +280,105 @@ __device__ __forceinline__ uint32_t rect_tiles(short4 r) {
     return (nx > 0 && ny > 0) ? (uint32_t)(nx * ny) : 0u;
 }
 
+// instance count of every sorted visible pair (into ioff) and of every block's chunk
 __global__ void __launch_bounds__(T) k_count_instances(const uint32_t *vis_pair, const short4 *rect,
-                                                      const DevState *st, uint32_t *part, int nb) {
+                                                      const DevState *st, uint32_t *ioff, uint32_t *part,
+                                                      int nb) {
     __shared__ uint32_t sm[32];
     uint32_t n = st->n_vis;
     uint32_t lo, hi;
     chunk_range(n, blockIdx.x, nb, T, lo, hi);
     uint32_t c = 0;
-    for (uint32_t i = lo + threadIdx.x; i < hi; i += T) c += rect_tiles(rect[vis_pair[i]]);
+    for (uint32_t i = lo + threadIdx.x; i < hi; i += T) {
+        uint32_t k = rect_tiles(rect[vis_pair[i]]);
+        ioff[i] = k;
+        c += k;
+    }
     uint32_t tot;
     block_exclusive_scan(c, sm, &tot);
     if (threadIdx.x == 0) part[blockIdx.x] = tot;
 }
 
-__global__ void __launch_bounds__(T) k_emit_instances(const uint32_t *vis_pair, const short4 *rect,
-                                                     const ViewInfo *views, int n_views,
-                                                     const DevState *st, const uint32_t *part, int nb,
-                                                     uint32_t *inst_tile, uint32_t *inst_val) {
+// ioff[i] <- first output slot of sorted pair i (exclusive scan of the counts)
+__global__ void __launch_bounds__(T) k_instance_offsets(const DevState *st, const uint32_t *part, int nb,
+                                                       uint32_t *ioff) {
     __shared__ uint32_t sm[32];
-    if (st->flags & kFlagCapacity) return;
     uint32_t n = st->n_vis;
     uint32_t lo, hi;
     chunk_range(n, blockIdx.x, nb, T, lo, hi);
     uint32_t base = part[blockIdx.x];
     for (uint32_t t0 = lo; t0 < hi; t0 += T) {
         uint32_t i = t0 + threadIdx.x;
-        uint32_t pair = 0, cnt = 0;
-        short4 r = make_short4(1, 1, 0, 0);
-        if (i < hi) {
-            pair = vis_pair[i];
-            r = rect[pair];
-            cnt = rect_tiles(r);
-        }
+        uint32_t c = i < hi ? ioff[i] : 0u;
         uint32_t tot;
-        uint32_t off = base + block_exclusive_scan(cnt, sm, &tot);
-        if (cnt) {
-            // the view owning this pair: largest v with pair_off <= pair
+        uint32_t ex = block_exclusive_scan(c, sm, &tot);
+        if (i < hi) ioff[i] = base + ex;
+        base += tot;
+    }
+}
+
+// Instances of the depth-sorted visible pairs, in that order, each pair's
+// tiles row-major.  The work is split by output slot, not by pair (pairs in
+// depth order have very uneven rectangles): a block takes a window of
+// kEmitWindow consecutive slots, finds the pairs that cover it by binary
+// search in ioff, stages them in shared memory, and every thread writes one
+// instance per step, locating its pair by binary search in the stage.
+constexpr int kEmitWindow = 1024;
+
+__device__ __forceinline__ uint32_t last_le(const uint32_t *a, uint32_t n, uint32_t x) {
+    // largest i < n with a[i] <= x (a nondecreasing, a[0] <= x)
+    uint32_t lo = 0, hi = n - 1;
+    while (lo < hi) {
+        uint32_t mid = (lo + hi + 1) >> 1;
+        if (a[mid] <= x) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(T) k_emit_instances(const uint32_t *vis_pair, const short4 *rect,
+                                                     const ViewInfo *views, int n_views,
+                                                     const DevState *st, const uint32_t *ioff,
+                                                     uint32_t *inst_tile, uint32_t *inst_val) {
+    __shared__ uint32_t s_off[kEmitWindow];
+    __shared__ uint32_t s_pair[kEmitWindow];
+    __shared__ short4 s_rect[kEmitWindow];
+    __shared__ int2 s_view[kEmitWindow];  // (tile_off, ntx) of the pair's view
+    __shared__ uint32_t s_range[2];
+    if (st->flags & kFlagCapacity) return;
+    const uint32_t n = st->n_vis, total = st->n_inst;
+    const uint32_t windows = (total + kEmitWindow - 1) / kEmitWindow;
+    const int t = threadIdx.x;
+    for (uint32_t wdw = blockIdx.x; wdw < windows; wdw += gridDim.x) {
+        const uint32_t o0 = wdw * kEmitWindow;
+        const uint32_t o1 = min(o0 + kEmitWindow, total);
+        if (t == 0) s_range[0] = last_le(ioff, n, o0);
+        if (t == 1) s_range[1] = last_le(ioff, n, o1 - 1);
+        __syncthreads();
+        const uint32_t s0 = s_range[0], np = s_range[1] - s0 + 1;  // np <= window: every pair has >= 1 slot
+        for (uint32_t k = t; k < np; k += T) {
+            const uint32_t pair = vis_pair[s0 + k];
             int lo_v = 0, hi_v = n_views - 1;
             while (lo_v < hi_v) {
                 int mid = (lo_v + hi_v + 1) >> 1;
                 if ((uint32_t)views[mid].pair_off <= pair) lo_v = mid; else hi_v = mid - 1;
             }
-            const ViewInfo vi = views[lo_v];
-            for (int ty = r.y; ty <= r.w; ++ty)
-                for (int tx = r.x; tx <= r.z; ++tx) {
-                    inst_tile[off] = (uint32_t)(vi.tile_off + ty * vi.ntx + tx);
-                    inst_val[off] = pair;
-                    ++off;
-                }
+            s_off[k] = ioff[s0 + k];
+            s_pair[k] = pair;
+            s_rect[k] = rect[pair];
+            s_view[k] = make_int2(views[lo_v].tile_off, views[lo_v].ntx);
         }
-        base += tot;
+        __syncthreads();
+        for (uint32_t o = o0 + t; o < o1; o += T) {
+            const uint32_t a = last_le(s_off, np, o);
+            const short4 r = s_rect[a];
+            const int2 vw = s_view[a];
+            const int wdt = (int)r.z - (int)r.x + 1;
+            const int local = (int)(o - s_off[a]);
+            const int ty = r.y + local / wdt, tx = r.x + local % wdt;
+            inst_tile[o] = (uint32_t)(vw.x + ty * vw.y + tx);
+            inst_val[o] = s_pair[a];
+        }
+        __syncthreads();
     }
 }
 
@@ -444,9 +491,11 @@ gs_status launch_bin_sort(gs_workspace *ws, cudaStream_t s) {
     uint32_t *tv2 = (passes & 1) ? ws->inst_val : ws->inst_val_alt;
     {
     StageTimer timer(ws, GS_STAGE_EMIT, s);
-    ++ws->kernel_launches; k_count_instances<<<nb, T, 0, s>>>(v, ws->rect, st, ws->part, nb);
+    ++ws->kernel_launches; k_count_instances<<<nb, T, 0, s>>>(v, ws->rect, st, ws->ioff, ws->part, nb);
     ++ws->kernel_launches; k_scan_parts<<<1, T, 0, s>>>(ws->part, nb, nullptr, st, (uint64_t)ws->inst_cap, 1);
-    ++ws->kernel_launches; k_emit_instances<<<nb, T, 0, s>>>(v, ws->rect, ws->views, ws->n_views, st, ws->part, nb, tk, tv);
+    ++ws->kernel_launches; k_instance_offsets<<<nb, T, 0, s>>>(st, ws->part, nb, ws->ioff);
+    ++ws->kernel_launches;
+    k_emit_instances<<<4 * ws->num_sms, T, 0, s>>>(v, ws->rect, ws->views, ws->n_views, st, ws->ioff, tk, tv);
     if ((r = check_launch("emit")) != GS_OK) return r;
     }
     // 4. stable sort of the instances by tile id
