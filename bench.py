@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="orchard500k")
-    ap.add_argument("--tile", default="16x16")
+    ap.add_argument("--tile", default="auto", help="WxH, or auto to let the autotuner pick tile and depth")
     ap.add_argument("--depth", type=int, default=256)
     ap.add_argument("--no-per-view", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -380,19 +380,39 @@ def main():
     from paper_2510_26358_gb300 import scenes
 
     sc = scenes.workload(args.workload, seed=rank)
-    tw, th = (int(x) for x in args.tile.split("x"))
-    cfg = G.gs_config_default(tile_w=tw, tile_h=th, batch_depth=args.depth)
-    step = Step(G, torch, sc, cfg, dev)
-    # size the instance capacity from a first run
-    step.run()
-    st, need, nvis = step.r.status()
-    if st == G.GS_ERR_CAPACITY or need > step.r.info["inst_capacity"]:
-        step.r.close()
-        step = Step(G, torch, sc, cfg, dev, inst_capacity=int(need * 1.25) + 1024)
-        step.run()
-        st, need, nvis = step.r.status()
-    assert st == G.GS_OK, G.status_string(st)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def build_step(tw, th, depth):
+        """A Step whose instance capacity fits the scene (sized from a first run)."""
+        cfg = G.gs_config_default(tile_w=tw, tile_h=th, batch_depth=depth)
+        st_ = Step(G, torch, sc, cfg, dev)
+        st_.run()
+        code, need_, _ = st_.r.status()
+        if code == G.GS_ERR_CAPACITY or need_ > st_.r.info["inst_capacity"]:
+            st_.r.close()
+            st_ = Step(G, torch, sc, cfg, dev, inst_capacity=int(need_ * 1.25) + 1024)
+            st_.run()
+        return st_
+
+    tuned = None
+    if args.tile == "auto":
+        from paper_2510_26358_gb300 import autotune
+
+        def measure(tw, th, depth):
+            st_ = build_step(tw, th, depth)
+            g_ = make_graph(torch, st_)
+            t_ = time_steps(torch, g_.replay, 5, 2, flush)
+            st_.r.close()
+            del g_
+            return float(np.mean(t_))
+        key = autotune.signature(sc.cameras, sc.n, sc.sh_degree, sc.submap_offsets, extra="bench-step")
+        tuned = autotune.tune(measure, key=key)
+        tw, th, args.depth = tuned["tile_w"], tuned["tile_h"], tuned["batch_depth"]
+    else:
+        tw, th = (int(x) for x in args.tile.split("x"))
+    step = build_step(tw, th, args.depth)
+    st, need, nvis = step.r.status()
+    assert st == G.GS_OK, G.status_string(st)
 
     # launches per step, from the library's own counter
     k0 = G.gs_workspace_info(step.r.ws)["kernel_launches"]
@@ -498,7 +518,10 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(sc, args, f"{tw}x{th}", args.depth),
+            "config": dict(workload_config(sc, args, f"{tw}x{th}", args.depth),
+                           autotune=None if tuned is None else {"chosen": f"{tw}x{th}/{args.depth}",
+                                                                "cached": tuned.get("cached"),
+                                                                "ms": tuned["timings"]}),
             "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches_per_step * args.steps),
             "launches_per_step": int(launches_per_step), "roofline": roofline,
             "per_view": per_view, "breakdown_ms": breakdown, "kernel_ms": kern,
