@@ -373,7 +373,7 @@ __global__ void __launch_bounds__(kProjThreads) k_project_fwd(ProjArgs A) {
 }
 
 template <int DEG>
-__global__ void __launch_bounds__(kProjThreads) k_project_bwd(ProjArgs A) {
+__global__ void __launch_bounds__(kProjThreads, 2) k_project_bwd(ProjArgs A) {
     extern __shared__ float red[];  // [views of the submap][warps][6]
     const Consts &k = A.c;
     // blocks are laid out per submap
@@ -402,7 +402,6 @@ __global__ void __launch_bounds__(kProjThreads) k_project_bwd(ProjArgs A) {
     const bool any_vis = vis_mask != 0;
 
     float mu[3] = {0, 0, 0}, ls[3] = {0, 0, 0}, q[4] = {1, 0, 0, 0}, om = 0.f;
-    float C[16][3];
     if (any_vis) {
         mu[0] = __ldg(A.means + 3 * g); mu[1] = __ldg(A.means + 3 * g + 1); mu[2] = __ldg(A.means + 3 * g + 2);
         ls[0] = __ldg(A.log_scales + 3 * g); ls[1] = __ldg(A.log_scales + 3 * g + 1);
@@ -410,11 +409,11 @@ __global__ void __launch_bounds__(kProjThreads) k_project_bwd(ProjArgs A) {
         q[0] = __ldg(A.quats + 4 * g); q[1] = __ldg(A.quats + 4 * g + 1);
         q[2] = __ldg(A.quats + 4 * g + 2); q[3] = __ldg(A.quats + 4 * g + 3);
         om = __ldg(A.opac + g);
-        load_sh<DEG>(A.sh, g, C);
-    } else {
-#pragma unroll
-        for (int kk = 0; kk < 16; ++kk) C[kk][0] = C[kk][1] = C[kk][2] = 0.f;
     }
+    // SH coefficients are read from cache where needed and their gradients
+    // accumulated in place (this thread is the only writer of Gaussian g)
+    const float *shg = A.sh + g * (3 * K);
+    float *gsh = A.gsh + g * (3 * K);
     float qh[4], R[9];
     float qn = quat_rot(q, qh, R);
     float S[3] = {expf(ls[0]), expf(ls[1]), expf(ls[2])};
@@ -426,9 +425,6 @@ __global__ void __launch_bounds__(kProjThreads) k_project_bwd(ProjArgs A) {
     float o = 1.f / (1.f + expf(-om));
 
     float gmu[3] = {0, 0, 0}, gM[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, gom = 0.f;
-    float gC[16][3];
-#pragma unroll
-    for (int kk = 0; kk < 16; ++kk) gC[kk][0] = gC[kk][1] = gC[kk][2] = 0.f;
     float dacc = 0.f;
     int dcnt = 0;
 
@@ -467,20 +463,26 @@ __global__ void __launch_bounds__(kProjThreads) k_project_bwd(ProjArgs A) {
             sh_basis<DEG>(d[0], d[1], d[2], Y);
             sh_basis_grad<DEG>(d[0], d[1], d[2], dY);
             float gdir[3] = {0, 0, 0};
+            // colour of the forward, same FMA order, to take the same clamp decision
+            float acc[3] = {0.5f, 0.5f, 0.5f};
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch) {
-                float acc = 0.5f;
+            for (int kk = 0; kk < K; ++kk)
 #pragma unroll
-                for (int kk = 0; kk < K; ++kk) acc = __fmaf_rn(C[kk][ch], Y[kk], acc);
-                if (acc < 0.f) continue;  // clamped colour
+                for (int ch = 0; ch < 3; ++ch) acc[ch] = __fmaf_rn(__ldg(shg + 3 * kk + ch), Y[kk], acc[ch]);
+            float gcol[3];
 #pragma unroll
-                for (int kk = 0; kk < K; ++kk) {
-                    gC[kk][ch] += grgb[ch] * Y[kk];
-                    float t = grgb[ch] * C[kk][ch];
-                    gdir[0] += t * dY[kk][0];
-                    gdir[1] += t * dY[kk][1];
-                    gdir[2] += t * dY[kk][2];
+            for (int ch = 0; ch < 3; ++ch) gcol[ch] = acc[ch] < 0.f ? 0.f : grgb[ch];  // clamped: no gradient
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) {
+                float t = 0.f;
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) {
+                    gsh[3 * kk + ch] += gcol[ch] * Y[kk];
+                    t = __fmaf_rn(gcol[ch], __ldg(shg + 3 * kk + ch), t);
                 }
+                gdir[0] += t * dY[kk][0];
+                gdir[1] += t * dY[kk][1];
+                gdir[2] += t * dY[kk][2];
             }
             float dd = d[0] * gdir[0] + d[1] * gdir[1] + d[2] * gdir[2];
             float gw[3] = {(gdir[0] - d[0] * dd) * iw, (gdir[1] - d[1] * dd) * iw, (gdir[2] - d[2] * dd) * iw};
@@ -614,11 +616,6 @@ __global__ void __launch_bounds__(kProjThreads) k_project_bwd(ProjArgs A) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) A.gq[4 * g + i] += gq[i];
     A.gom[g] += gom;
-    float *gs = A.gsh + g * (3 * K);
-#pragma unroll
-    for (int kk = 0; kk < K; ++kk)
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) gs[3 * kk + ch] += gC[kk][ch];
     if (A.dens_acc) A.dens_acc[g] += dacc;
     if (A.dens_cnt) A.dens_cnt[g] += dcnt;
 }
