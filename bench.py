@@ -140,6 +140,36 @@ def max_over_ranks(ms: float, device) -> float:
     return float(t.item())
 
 
+RASTER_SOURCES = ("paper_2510_26358_gb300/csrc/gs_raster.cu", "paper_2510_26358_gb300/csrc/gs_internal.cuh")
+
+
+def raster_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha1()
+    for f in RASTER_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel: str, workload: str, config: str):
+    """DRAM bytes (read + write) per launch of `kernel` from the committed ncu
+    summary, if it was captured on this workload and configuration from the
+    current raster sources; otherwise None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            rec = json.load(f)[kernel]
+    except (OSError, KeyError, ValueError):
+        return None, "no ncu capture recorded"
+    if rec.get("source_sha1") != raster_source_hash():
+        return None, "kernel changed since the ncu capture"
+    # the backward stages the same list entries (those up to the last blended
+    # fragment) whatever the batch depth, so the tile size fixes its traffic
+    if rec.get("workload") != workload or rec.get("config", "").split("/")[0] != config.split("/")[0]:
+        return None, f"ncu capture was on {rec.get('workload')} {rec.get('config')}"
+    return int(rec["dram_bytes_per_launch"]), rec.get("command", "")
+
+
 def job_throughput(pix_per_rank: int, ms: float, world: int) -> float:
     """Whole-job Mpix/s: every rank renders its own replica in `ms`."""
     return pix_per_rank * world / (ms * 1e-3) / 1e6
@@ -510,9 +540,11 @@ def main():
     alg_bytes = 4 * n_inst + 48 * nvis + 24 * npx + 8 * n_tiles + 40 * nvis
     bwd_ms = kern["raster_bwd"]
     achieved = alg_bytes / (bwd_ms * 1e-3) / 1e9
+    traffic, traffic_note = measured_traffic("k_raster_bwd", sc.name, f"{tw}x{th}/{args.depth}")
     roofline = {"bound": "hbm", "kernel": "k_raster_bwd",
                 "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                "traffic": None, "algorithmic_bytes": int(alg_bytes), "ms": bwd_ms,
+                "traffic": traffic, "traffic_source": traffic_note,
+                "algorithmic_bytes": int(alg_bytes), "ms": bwd_ms,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6800 GB/s"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
