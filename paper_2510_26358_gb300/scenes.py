@@ -390,19 +390,22 @@ def uneven_submaps(n_submaps=8, n_lo=50_000, n_hi=2_000_000, lidar_per_view=0,
 # named workloads (the five sizes the benchmark and tests are built around)
 # ----------------------------------------------------------------------------
 
-def workload(name: str, seed: int = 0) -> Scene:
+def workload(name: str, seed: int = 0, lidar: bool = True) -> Scene:
+    """The named workloads; ``lidar=False`` skips the LiDAR scan (tests that
+    only check rendering)."""
+    L = lambda k: k if lidar else 0
     if name == "box10k":            # single 320x240 camera, 10k Gaussians, SH 0
         return random_box_scene(10_000, seed=seed)
     if name == "orchard500k":       # 3 rows x 8 trees, 3 x 1280x720, SH 3, 20k LiDAR/view
-        return orchard_scene(500_000, 3, 8, 1280, 720, seed=seed, name=name)
+        return orchard_scene(500_000, 3, 8, 1280, 720, lidar_per_view=L(20_000), seed=seed, name=name)
     if name == "orchard1m_pose":    # 3 rows x 16 trees, 4 x 1440x1080, perturbed poses
         return orchard_scene(1_000_000, 3, 16, 1440, 1080, rear=True, pose_noise=True,
-                             lidar_per_view=20_000, seed=seed, name=name)
+                             lidar_per_view=L(20_000), seed=seed, name=name)
     if name == "submaps8":          # 8 submaps log-U[50k,2M], 24 views of mixed size
-        return uneven_submaps(8, seed=seed, lidar_per_view=20_000)
+        return uneven_submaps(8, seed=seed, lidar_per_view=L(20_000))
     if name == "orchard4m":         # 9 rows x 27 trees, 6 x 1920x1200, 100k LiDAR/view
         return orchard_scene(4_000_000, 9, 27, 1920, 1200, lanes=2,
-                             lidar_per_view=100_000, seed=seed, name=name)
+                             lidar_per_view=L(100_000), seed=seed, name=name)
     raise KeyError(name)
 
 
