@@ -42,6 +42,13 @@
  *       pixels and views.
  *   R14 densification statistic: per view where the pair is visible,
  *       acc += ||(dL/du, dL/dv)|| in pixels and cnt += 1.
+ *   R15 rendered depth distribution (for Eq. 7 with a predicted sigma_u):
+ *       the weights w_k = alpha_k T_k of a pixel's blended fragments, of total
+ *       A, spread over their depths z_k: mean mu = D/A, variance
+ *       m2/A - (m1/A)^2 with m1 = sum w (z - c), m2 = sum w (z - c)^2 about
+ *       c = the depth of the pixel's first blended fragment (the variance does
+ *       not depend on c; the shift only avoids cancellation in float).
+ *       sigma_u^2 = max(variance, 0) + sigma_U^2.
  */
 #include <math.h>
 #include <stdint.h>
@@ -477,7 +484,7 @@ static double frag_alpha(const double *r, double px, double py, const oc_config 
 }
 
 typedef struct {
-    double C[3], D, T;
+    double C[3], D, T, M1, M2;
     int64_t last;    /* list position of the last blended fragment, -1 if none */
     int64_t n_blend; /* number of blended fragments */
     double margin;   /* min log-distance of a discrete decision to its threshold */
@@ -489,7 +496,7 @@ typedef struct {
  * pixel centre (px, py).  pos[i] is the list position reported as `last`. */
 static void composite(const double *rec, const int64_t *cand, const int64_t *pos, int64_t n,
                       double px, double py, const oc_config *cfg, oc_pix *out) {
-    double T = 1.0, C[3] = {0, 0, 0}, D = 0.0, margin = 1e300, cm = 1e300;
+    double T = 1.0, C[3] = {0, 0, 0}, D = 0.0, M1 = 0.0, M2 = 0.0, zc = 0.0, margin = 1e300, cm = 1e300;
     int64_t last = -1, nb = 0;
     uint64_t sig = 1469598103934665603ull;
     double lmin = log(cfg->alpha_min), ltmin = log(cfg->t_min), lmax = log(cfg->alpha_max);
@@ -507,13 +514,16 @@ static void composite(const double *rec, const int64_t *cand, const int64_t *pos
         double w = al * T;
         for (int ch = 0; ch < 3; ++ch) C[ch] += w * r[C_R + ch];
         D += w * r[C_Z];
+        if (nb == 0) zc = r[C_Z];
+        M1 += w * (r[C_Z] - zc);
+        M2 += w * (r[C_Z] - zc) * (r[C_Z] - zc);
         T = Tn;
         last = pos[i];
         ++nb;
         sig = (sig ^ (uint64_t)cand[i]) * 1099511628211ull;
     }
     memcpy(out->C, C, sizeof C);
-    out->D = D; out->T = T; out->last = last; out->n_blend = nb;
+    out->D = D; out->T = T; out->M1 = M1; out->M2 = M2; out->last = last; out->n_blend = nb;
     out->margin = margin; out->clamp_margin = cm; out->sig = sig;
 }
 
@@ -554,6 +564,34 @@ int oracle_render_fwd(int n_views, const oc_camera *cams, const int64_t *submap_
                 free(pos);
                 write_pix(&o, V[v].pix_off + y * W + x, W, H, V[v].pix_off, rgb, depth, alpha,
                           Tfin, last, nblend, margin, sig);
+            }
+    }
+    free(V);
+    return 0;
+}
+
+/* Depth moments of the tiled forward (R15): m1, m2 per pixel about the
+ * depth of the pixel's first blended fragment. */
+int oracle_render_moments(int n_views, const oc_camera *cams, const int64_t *submap_offsets,
+                          const oc_config *cfg, const double *rec, const int64_t *vals,
+                          const int64_t *ranges, double *m1, double *m2) {
+    oc_view *V = (oc_view *)malloc(sizeof(oc_view) * (n_views > 0 ? n_views : 1));
+    make_views(n_views, cams, submap_offsets, cfg, V);
+    for (int v = 0; v < n_views; ++v) {
+        int64_t W = cams[v].width, H = cams[v].height;
+        for (int64_t y = 0; y < H; ++y)
+            for (int64_t x = 0; x < W; ++x) {
+                int64_t t = V[v].tile_off + (y / cfg->tile_h) * V[v].ntx + x / cfg->tile_w;
+                int64_t s = ranges[2 * t], e = ranges[2 * t + 1];
+                int64_t n = e - s;
+                int64_t *pos = (int64_t *)malloc(sizeof(int64_t) * (n > 0 ? n : 1));
+                for (int64_t i = 0; i < n; ++i) pos[i] = s + i;
+                oc_pix o;
+                composite(rec, vals + s, pos, n, x + 0.5, y + 0.5, cfg, &o);
+                free(pos);
+                int64_t pix = V[v].pix_off + y * W + x;
+                m1[pix] = o.M1;
+                m2[pix] = o.M2;
             }
     }
     free(V);
@@ -696,6 +734,56 @@ double oracle_depth_loss(int n_views, const oc_camera *cams, const int64_t *subm
     return nv > 0 ? lambda * s / (double)nv : 0.0;
 }
 
+/* Eq. (7) with the renderer's predicted distribution (R15): mu = D/A,
+ * sigma_u^2 = max(m2/A - (m1/A)^2, 0) + sigma_U^2; mean over valid points of
+ * KL(N(z, sigma_L^2) || N(mu, sigma_u^2)) times lambda.  Gradients (each
+ * accumulated per pixel, nullable) w.r.t. D, A, m1 and m2. */
+double oracle_depth_loss_var(int n_views, const oc_camera *cams, const int64_t *submap_offsets,
+                             const oc_config *cfg, const double *depth, const double *alpha,
+                             const double *m1, const double *m2, int64_t n_pts, const double *lidar,
+                             double sigma_L, double sigma_U, double lambda, double *gD, double *gA,
+                             double *gM1, double *gM2, int64_t *n_valid) {
+    oc_view *V = (oc_view *)malloc(sizeof(oc_view) * (n_views > 0 ? n_views : 1));
+    make_views(n_views, cams, submap_offsets, cfg, V);
+    double s = 0;
+    int64_t nv = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int64_t i = 0; i < n_pts; ++i) {
+            const double *L = lidar + 4 * i;
+            int v = (int)L[3];
+            if (v < 0 || v >= n_views) continue;
+            double W = cams[v].width, H = cams[v].height;
+            if (!(L[0] >= 0 && L[0] < W && L[1] >= 0 && L[1] < H && L[2] > cfg->near_z)) continue;
+            int64_t pix = V[v].pix_off + (int64_t)floor(L[1]) * cams[v].width + (int64_t)floor(L[0]);
+            double A = alpha[pix];
+            if (!(A > 0)) continue;
+            double z = L[2];
+            double mu = depth[pix] / A, a1 = m1[pix] / A;
+            double var = m2[pix] / A - a1 * a1;
+            int clamped = var < 0;
+            double su2 = (clamped ? 0.0 : var) + sigma_U * sigma_U;
+            double e = mu - z;
+            if (pass == 0) {
+                ++nv;
+                s += 0.5 * log(su2) - log(sigma_L) + (sigma_L * sigma_L + e * e) / (2.0 * su2) - 0.5;
+            } else {
+                double k = lambda / (double)nv;
+                double dmu = e / su2;                                                  /* dKL/dmu */
+                double dv = clamped ? 0.0 : 0.5 / su2 - (sigma_L * sigma_L + e * e) / (2.0 * su2 * su2);
+                /* mu = D/A; var = m2/A - (m1/A)^2 */
+                if (gD) gD[pix] += k * dmu / A;
+                if (gM1) gM1[pix] += k * dv * (-2.0 * a1 / A);
+                if (gM2) gM2[pix] += k * dv / A;
+                if (gA) gA[pix] += k * (dmu * (-mu / A) + dv * (-m2[pix] / (A * A) + 2.0 * a1 * a1 / A));
+            }
+        }
+        if (nv == 0) break;
+    }
+    free(V);
+    if (n_valid) *n_valid = nv;
+    return nv > 0 ? lambda * s / (double)nv : 0.0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* backward                                                                 */
 /* ------------------------------------------------------------------------ */
@@ -707,7 +795,7 @@ double oracle_depth_loss(int n_views, const oc_camera *cams, const int64_t *subm
  * with w_k = alpha_k T_k and h_k = gC.c_k + gD z_k + gA (A = sum_k w_k). */
 static void pixel_adjoint(const double *rec, const int64_t *cand, int64_t n, double px, double py,
                           const oc_config *cfg, const double gC[3], double gD, double gA,
-                          double *g2d) {
+                          double gM1, double gM2, double *g2d) {
     int64_t *bl = (int64_t *)malloc(sizeof(int64_t) * (n > 0 ? n : 1));
     double *al = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
     double *raw = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
@@ -723,16 +811,20 @@ static void pixel_adjoint(const double *rec, const int64_t *cand, int64_t n, dou
         bl[m] = cand[i]; al[m] = a; raw[m] = rw; Tb[m] = T; ++m;
         T = Tn;
     }
+    /* the moments' reference depth is a constant of the adjoint (R15) */
+    double zc = m > 0 ? rec[bl[0] * OC_NCOL + C_Z] : 0.0;
     double suffix = 0.0;
     for (int64_t j = m - 1; j >= 0; --j) {
         const double *r = rec + bl[j] * OC_NCOL;
         double *g = g2d + bl[j] * OC_NGRAD;
         double w = al[j] * Tb[j];
-        double h = gC[0] * r[C_R] + gC[1] * r[C_G] + gC[2] * r[C_B] + gD * r[C_Z] + gA;
+        double dz = r[C_Z] - zc;
+        double h = gC[0] * r[C_R] + gC[1] * r[C_G] + gC[2] * r[C_B] + gD * r[C_Z] + gA +
+                   gM1 * dz + gM2 * dz * dz;
         double dal = Tb[j] * h - suffix / (1.0 - al[j]);
         suffix += w * h;
         g[G_R] += w * gC[0]; g[G_G] += w * gC[1]; g[G_B] += w * gC[2];
-        g[G_Z] += w * gD;
+        g[G_Z] += w * (gD + gM1 + 2.0 * gM2 * dz);
         if (raw[j] > cfg->alpha_max) continue; /* clamped: no dependence on o, pw */
         /* alpha = o exp(pw): dalpha/dln(o) = alpha, dalpha/dpw = alpha */
         double gpw = dal * al[j];
@@ -930,7 +1022,7 @@ int oracle_render_bwd(int64_t n, const double *means, const double *log_scales, 
                       int n_views, const oc_camera *cams, const int64_t *submap_offsets,
                       const oc_config *cfg, const double *rec, const int64_t *vals,
                       const int64_t *ranges, const double *dC, const double *dD, const double *dA,
-                      double *g2d, double *g_means, double *g_ls, double *g_quats, double *g_om,
+                      const double *dM1, const double *dM2, double *g2d, double *g_means, double *g_ls, double *g_quats, double *g_om,
                       double *g_sh, double *g_pose, double *dens_acc, double *dens_cnt) {
     (void)n;
     oc_view *V = (oc_view *)malloc(sizeof(oc_view) * (n_views > 0 ? n_views : 1));
@@ -943,10 +1035,12 @@ int oracle_render_bwd(int64_t n, const double *means, const double *log_scales, 
                 double gC[3];
                 for (int ch = 0; ch < 3; ++ch) gC[ch] = dC[3 * V[v].pix_off + ch * W * H + local];
                 double gD = dD ? dD[pix] : 0.0, gA = dA ? dA[pix] : 0.0;
-                if (gC[0] == 0 && gC[1] == 0 && gC[2] == 0 && gD == 0 && gA == 0) continue;
+                double gM1 = dM1 ? dM1[pix] : 0.0, gM2 = dM2 ? dM2[pix] : 0.0;
+                if (gC[0] == 0 && gC[1] == 0 && gC[2] == 0 && gD == 0 && gA == 0 && gM1 == 0 && gM2 == 0)
+                    continue;
                 int64_t t = V[v].tile_off + (y / cfg->tile_h) * V[v].ntx + x / cfg->tile_w;
                 int64_t s = ranges[2 * t], e = ranges[2 * t + 1];
-                pixel_adjoint(rec, vals + s, e - s, x + 0.5, y + 0.5, cfg, gC, gD, gA, g2d);
+                pixel_adjoint(rec, vals + s, e - s, x + 0.5, y + 0.5, cfg, gC, gD, gA, gM1, gM2, g2d);
             }
     }
     int K = (sh_degree + 1) * (sh_degree + 1);

@@ -14,6 +14,10 @@ sign, a transposed operand or a wrong index in the oracle fails at least one:
   backward                  central differences of every parameter type and
                             every pose twist; translation identity
   losses (Eqs. 6-7)         KL by numerical integration; FD of both losses
+  rendered depth variance   two-fragment closed form; zero for equal depths;
+                            Popoviciu bound; KL with the rendered variance by
+                            quadrature, reduced to the fixed-sigma mode, and
+                            FD through the whole render
 """
 import copy
 import math
@@ -465,3 +469,199 @@ def test_image_l1_gradient():
         Cp[i] += h
         Cm[i] -= h
         assert (O.image_l1(Cp, I)[0] - O.image_l1(Cm, I)[0]) / (2 * h) == pytest.approx(g[i], rel=1e-6)
+
+
+# ---------------------------------------------------------------------------
+# rendered depth distribution: Eq. (7) with a predicted variance
+# ---------------------------------------------------------------------------
+
+def _moments(P, cams, cfg=CFG):
+    rec, keys, vals, ranges, out = O.forward(P, cams, cfg)
+    m1, m2 = O.render_moments(P, cams, cfg, rec, vals, ranges)
+    return rec, vals, ranges, out, m1, m2
+
+
+def test_two_fragment_variance_closed_form():
+    # two opaque-ish discs at z1 < z2: w1 = a1, w2 = a2 (1 - a1); the weighted
+    # variance of {z1, z2} is w1 w2 (z2 - z1)^2 / (w1 + w2)^2
+    cam = _cam(16, 16, 20.0)
+    a1, a2, z1, z2 = 0.6, 0.8, 1.3, 1.75
+    P = _params([[0, 0, z1], [0, 0, z2]], [[math.log(0.5)] * 3] * 2, [[1, 0, 0, 0]] * 2,
+                [math.log(a1 / (1 - a1)), math.log(a2 / (1 - a2))], [[1.0, 1.0, 1.0]] * 2)
+    rec, vals, ranges, out, m1, m2 = _moments(P, [cam])
+    pix = 8 * 16 + 8
+    A = out["alpha"][pix]
+    # the two weights from alpha and depth: D = w1 z1 + w2 z2, A = w1 + w2
+    D = out["depth"][pix]
+    w2 = (D - z1 * A) / (z2 - z1)
+    w1 = A - w2
+    assert w1 > 0.5 and w2 > 0.2
+    var = m2[pix] / A - (m1[pix] / A) ** 2
+    assert var == pytest.approx(w1 * w2 * (z2 - z1) ** 2 / A ** 2, rel=1e-12)
+    # the reference depth is the first fragment's: m1 = w2 (z2 - z1)
+    assert m1[pix] == pytest.approx(w2 * (z2 - z1), rel=1e-12)
+
+
+def test_equal_depth_fragments_have_zero_variance():
+    cam = _cam(16, 16, 20.0)
+    n = 4
+    P = _params([[0.01 * i, -0.01 * i, 1.5] for i in range(n)], [[math.log(0.3)] * 3] * n,
+                [[1, 0, 0, 0]] * n, [0.5] * n, [[1.0, 1.0, 1.0]] * n)
+    rec, vals, ranges, out, m1, m2 = _moments(P, [cam])
+    assert (out["nblend"] >= 3).any()
+    assert np.array_equal(m1, np.zeros_like(m1)) and np.array_equal(m2, np.zeros_like(m2))
+
+
+def test_rendered_variance_bounds():
+    # 0 <= variance <= (z_max - z_min)^2 / 4 (Popoviciu), and m1 = D - c A with
+    # c inside the blended depth range
+    sc = S.random_box_scene(400, 48, 40, 45.0, seed=5)
+    P = O.Params.from_scene(sc)
+    cams = O.as_float32_cameras(sc.cameras)
+    rec, vals, ranges, out, m1, m2 = _moments(P, cams)
+    zs = rec[rec[:, O.C_VIS] > 0, O.C_Z]
+    m = out["alpha"] > 0
+    A = out["alpha"][m]
+    var = m2[m] / A - (m1[m] / A) ** 2
+    assert var.min() >= -1e-12
+    assert var.max() <= (zs.max() - zs.min()) ** 2 / 4 + 1e-12
+    c = (out["depth"][m] - m1[m]) / A
+    assert c.min() >= zs.min() - 1e-9 and c.max() <= zs.max() + 1e-9
+    assert (var > 1e-4).sum() > 100
+
+
+def _var_loss_inputs(rng, n_pts=300):
+    # per-pixel (alpha, mean, spread) and LiDAR returns whose depth lies within
+    # a few decimetres of the rendered mean where they land, as in tracking
+    cams = [_cam(20, 16, 20.0), _cam(12, 10, 15.0)]
+    P = O.Params(np.zeros((1, 3)), np.zeros((1, 3)), np.ones((1, 4)), np.zeros(1),
+                 np.zeros((1, 1, 3)), 0, np.array([0, 1]))
+    npx = 20 * 16 + 12 * 10
+    alpha = rng.uniform(0.05, 1, npx)
+    alpha[rng.random(npx) < 0.2] = 0.0
+    mu = rng.uniform(1, 5, npx)
+    depth = mu * alpha
+    c = mu + rng.uniform(-0.3, 0.1, npx)
+    sd = rng.uniform(0.0, 0.2, npx)
+    m1 = alpha * (mu - c)
+    m2 = alpha * (sd ** 2 + (mu - c) ** 2)
+    vw = rng.integers(0, 2, n_pts)
+    u, v = rng.uniform(-2, 22, n_pts), rng.uniform(-2, 18, n_pts)
+    z = rng.uniform(0.1, 6, n_pts)
+    for i in range(n_pts):
+        cm = cams[vw[i]]
+        if 0 <= u[i] < cm.width and 0 <= v[i] < cm.height:
+            pix = (0 if vw[i] == 0 else 320) + int(v[i]) * cm.width + int(u[i])
+            z[i] = mu[pix] + rng.normal(0, 0.2)
+    lid = np.stack([u, v, z, vw], 1)
+    return P, cams, depth, alpha, m1, m2, lid
+
+
+def test_variance_kl_reduces_to_fixed_sigma():
+    # zero rendered variance: sigma_u = sigma_U, so the loss is the fixed-sigma
+    # KL mode evaluated on the normalised depth D / A
+    rng = np.random.default_rng(4)
+    P, cams, depth, alpha, m1, m2, lid = _var_loss_inputs(rng)
+    z = np.zeros_like(depth)
+    lv = O.depth_loss_var(P, cams, CFG, depth, alpha, z, z, lid, 0.05, 0.08, 0.7)
+    dn = np.where(alpha > 0, depth / np.where(alpha > 0, alpha, 1), 0.0)
+    lk, gk, nk = O.depth_loss(P, cams, CFG, dn, alpha, lid, 1, 0.05, 0.08, 0.7)
+    assert lv[0] == pytest.approx(lk, rel=1e-13) and lv[5] == nk
+    m = alpha > 0
+    assert np.allclose(lv[1][m] * alpha[m], gk[m], rtol=1e-12, atol=1e-15)
+
+
+def test_variance_kl_matches_integration():
+    # one point: the loss is KL(N(z, sL^2) || N(mu, var + sU^2)) by quadrature
+    from scipy.integrate import quad
+    cams = [_cam(4, 4, 5.0)]
+    P = O.Params(np.zeros((1, 3)), np.zeros((1, 3)), np.ones((1, 4)), np.zeros(1),
+                 np.zeros((1, 1, 3)), 0, np.array([0, 1]))
+    A, mu, c, sd, z = 0.7, 3.2, 3.05, 0.11, 3.3
+    sL, sU = float(np.float32(0.05)), float(np.float32(0.04))
+    depth = np.full(16, 0.0); alpha = np.zeros(16); m1 = np.zeros(16); m2 = np.zeros(16)
+    depth[5], alpha[5], m1[5], m2[5] = A * mu, A, A * (mu - c), A * (sd ** 2 + (mu - c) ** 2)
+    lid = np.array([[1.5, 1.5, z, 0]])
+    loss = O.depth_loss_var(P, cams, CFG, depth, alpha, m1, m2, lid, sL, sU, 1.0)[0]
+    s2 = math.sqrt(sd ** 2 + sU ** 2)
+    p = lambda x: math.exp(-0.5 * ((x - z) / sL) ** 2) / (sL * math.sqrt(2 * math.pi))
+    lq = lambda x: -0.5 * ((x - mu) / s2) ** 2 - math.log(s2 * math.sqrt(2 * math.pi))
+    val, _ = quad(lambda x: p(x) * (math.log(p(x)) - lq(x)) if p(x) > 0 else 0.0,
+                  z - 12 * sL, z + 12 * sL, limit=200, epsabs=1e-13, epsrel=1e-12)
+    assert loss == pytest.approx(val, rel=1e-8)
+
+
+def test_variance_kl_gradient_fd():
+    rng = np.random.default_rng(6)
+    P, cams, depth, alpha, m1, m2, lid = _var_loss_inputs(rng)
+    args = (0.05, 0.08, 0.7)
+    loss, gD, gA, gM1, gM2, nv = O.depth_loss_var(P, cams, CFG, depth, alpha, m1, m2, lid, *args)
+    assert nv > 50
+    h = 1e-7
+    ins = [depth, alpha, m1, m2]
+    for k, g in enumerate((gD, gA, gM1, gM2)):
+        for pix in rng.choice(np.nonzero(g)[0], 8, replace=False):
+            xp = [x.copy() for x in ins]
+            xm = [x.copy() for x in ins]
+            xp[k][pix] += h
+            xm[k][pix] -= h
+            fd = (O.depth_loss_var(P, cams, CFG, *xp, lid, *args)[0] -
+                  O.depth_loss_var(P, cams, CFG, *xm, lid, *args)[0]) / (2 * h)
+            assert fd == pytest.approx(g[pix], rel=1e-5, abs=1e-8), (k, pix)
+
+
+def test_variance_kl_chain_fd():
+    # loss(render(params)) with the rendered variance: the adjoint through the
+    # depth moments against central differences of every parameter type and
+    # every pose twist
+    sc = S.random_box_scene(250, 48, 40, 45.0, seed=12, sh_degree=1)
+    P = O.Params.from_scene(sc)
+    cams = O.as_float32_cameras(sc.cameras)
+    rng = np.random.default_rng(8)
+    rec, vals, ranges, out, m1, m2 = _moments(P, cams)
+    hit = np.nonzero(out["alpha"] > 0.2)[0]
+    pix = rng.choice(hit, 200, replace=False)
+    mu = out["depth"][pix] / out["alpha"][pix]
+    lid = np.stack([pix % 48 + 0.5, pix // 48 + 0.5, mu + rng.normal(0, 0.1, len(pix)),
+                    np.zeros(len(pix))], 1)
+    args = (0.05, 0.03, 1.0)
+
+    def loss_of(Pp, cc):
+        r, k, v, rg, o = O.forward(Pp, cc, CFG)
+        a, b = O.render_moments(Pp, cc, CFG, r, v, rg)
+        return O.depth_loss_var(Pp, cc, CFG, o["depth"], o["alpha"], a, b, lid, *args)[0], o
+
+    L0, gD, gA, gM1, gM2, nv = O.depth_loss_var(P, cams, CFG, out["depth"], out["alpha"], m1, m2, lid, *args)
+    assert nv == len(pix)
+    z = np.zeros(3 * 48 * 40)
+    g = O.render_bwd(P, cams, CFG, rec, vals, ranges, z, gD, gA, gM1, gM2)
+    h = 1e-7
+    checked = 0
+    vis = np.unique(rec[rec[:, O.C_VIS] > 0, O.C_GAUSS].astype(int))
+    for name in ("means", "log_scales", "quats", "opacity_logits"):
+        for _ in range(4):
+            gi = int(rng.choice(vis))
+            Arr = getattr(P, name)
+            idx = (gi,) + tuple(int(rng.integers(0, s)) for s in Arr.shape[1:])
+            Pp, Pm = P.copy(), P.copy()
+            getattr(Pp, name)[idx] += h
+            getattr(Pm, name)[idx] -= h
+            (lp, op), (lm, om) = loss_of(Pp, cams), loss_of(Pm, cams)
+            if np.any(op["sig"] != om["sig"]):
+                continue  # a support or stop decision flipped inside the step
+            fd = (lp - lm) / (2 * h)
+            assert fd == pytest.approx(g[name][idx], rel=1e-5, abs=1e-7), (name, idx)
+            checked += 1
+    for k in range(6):
+        xi = np.zeros(6); xi[k] = h
+        cp, cm = copy.deepcopy(cams), copy.deepcopy(cams)
+        cp[0].T_cw = _se3_left(cams[0].T_cw, xi)
+        cm[0].T_cw = _se3_left(cams[0].T_cw, -xi)
+        (lp, op), (lm, om) = loss_of(P, cp), loss_of(P, cm)
+        if np.any(op["sig"] != om["sig"]):
+            continue
+        fd = (lp - lm) / (2 * h)
+        assert fd == pytest.approx(g["pose"][0, k], rel=1e-5, abs=1e-7), ("pose", k)
+        checked += 1
+    assert checked >= 15
+    assert np.abs(g["means"]).max() > 0
