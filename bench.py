@@ -54,14 +54,21 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=640, help="crop width (px) per view for the oracle sample")
+    ap.add_argument("--depth-loss", default="l1", choices=list(DEPTH_LOSSES),
+                    help="depth term of the step: l1, kl (Eq. 7, fixed sigma_u) or kl-var (Eq. 7 with the "
+                         "rendered variance: forward and backward with the central depth moment)")
     return ap.parse_args()
+
+
+DEPTH_LOSSES = {"l1": "L1 rgb + L1 depth", "kl": "L1 rgb + KL depth (fixed sigma_u)",
+                "kl-var": "L1 rgb + KL depth (rendered variance)"}
 
 
 def workload_config(sc, args, tile=None, depth=None):
     W = sorted({(c.width, c.height) for c in sc.cameras})
     return {"workload": sc.name, "n_gaussians": sc.n, "views": len(sc.cameras),
             "resolutions": [f"{w}x{h}" for w, h in W], "n_pix": sc.n_pix, "sh_degree": sc.sh_degree,
-            "lidar_points": int(sc.lidar.shape[0]), "losses": "L1 rgb + L1 depth",
+            "lidar_points": int(sc.lidar.shape[0]), "losses": DEPTH_LOSSES[getattr(args, "depth_loss", "l1")],
             "tile": tile or args.tile, "batch_depth": depth or args.depth,
             "l2": "flushed (512 MiB write) before every timed step", "graph": True,
             "parallelism": "replicas", "seed": 0}
@@ -182,8 +189,9 @@ def job_throughput(pix_per_rank: int, ms: float, world: int) -> float:
 class Step:
     """All device buffers of one mapping step plus the calls that make it."""
 
-    def __init__(self, G, torch, sc, cfg, dev, inst_capacity=None):
+    def __init__(self, G, torch, sc, cfg, dev, inst_capacity=None, var=False):
         self.G, self.torch, self.sc, self.dev = G, torch, sc, dev
+        self.var = var
         t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
         self.P = [t(sc.means), t(sc.log_scales), t(sc.quats), t(sc.opacity_logits), t(sc.sh)]
         self.target = t(sc.target)
@@ -203,10 +211,15 @@ class Step:
                           densify_cnt=torch.zeros(sc.n, dtype=torch.int32, device=dev))
         self.loss_rgb = torch.zeros(1, device=dev)
         self.loss_depth = torch.zeros(1, device=dev)
+        # depth mean and variance and their adjoints (variance KL only)
+        self.dist = [torch.empty(npx, device=dev) for _ in range(2)] if var else []
+        self.g_var = [torch.zeros(npx, device=dev) for _ in range(2)] if var else []
 
     def zero(self):
         self.g_rgb.zero_()
         self.g_depth.zero_()
+        for v in self.g_var:
+            v.zero_()
         for v in self.grads.values():
             v.zero_()
 
@@ -223,20 +236,33 @@ class Step:
             G.gs_bin_sort(r.ws, G._stream())
 
         def fwd():
-            G.gs_render_fwd(r.ws, G._ptr(self.rgb), G._ptr(self.depth), G._ptr(self.alpha), G._stream())
+            if self.var:
+                G.gs_render_fwd_var(r.ws, G._ptr(self.rgb), G._ptr(self.depth), G._ptr(self.alpha),
+                                    G._ptr(self.dist[0]), G._ptr(self.dist[1]), G._stream())
+            else:
+                G.gs_render_fwd(r.ws, G._ptr(self.rgb), G._ptr(self.depth), G._ptr(self.alpha), G._stream())
 
         def losses():
             s = G._stream()
             G.gs_image_l1(r.ws, G._ptr(self.rgb), G._ptr(self.target), G._ptr(self.loss_rgb), G._ptr(self.g_rgb), s)
-            G.gs_depth_loss(r.ws, G._ptr(self.depth), G._ptr(self.alpha), G._ptr(self.lidar), self.lidar.shape[0],
-                            G._ptr(self.loss_depth), G._ptr(self.g_depth), s)
+            if self.var:
+                G.gs_depth_loss_var(r.ws, G._ptr(self.alpha), G._ptr(self.dist[0]), G._ptr(self.dist[1]),
+                                    G._ptr(self.lidar), self.lidar.shape[0], G._ptr(self.loss_depth),
+                                    *(G._ptr(x) for x in self.g_var), s)
+            else:
+                G.gs_depth_loss(r.ws, G._ptr(self.depth), G._ptr(self.alpha), G._ptr(self.lidar),
+                                self.lidar.shape[0], G._ptr(self.loss_depth), G._ptr(self.g_depth), s)
 
         def bwd():
             gg = self.grads
             grads = G.GsGrads(*(gg[k].data_ptr() for k in ("means", "log_scales", "quats", "opacity_logits", "sh",
                                                             "pose", "densify_acc", "densify_cnt")))
-            G.gs_render_bwd(r.ws, r.gaussians(*self.P), G._ptr(r.cams_dev), G._ptr(self.g_rgb),
-                            G._ptr(self.g_depth), None, grads, G._stream())
+            if self.var:
+                G.gs_render_bwd_var(r.ws, r.gaussians(*self.P), G._ptr(r.cams_dev), G._ptr(self.g_rgb),
+                                    None, None, *(G._ptr(x) for x in self.g_var), grads, G._stream())
+            else:
+                G.gs_render_bwd(r.ws, r.gaussians(*self.P), G._ptr(r.cams_dev), G._ptr(self.g_rgb),
+                                G._ptr(self.g_depth), None, grads, G._stream())
         return [("zero", self.zero), ("project", project), ("bin_sort", binsort), ("raster_fwd", fwd),
                 ("losses", losses), ("backward", bwd)]
 
@@ -323,16 +349,22 @@ def oracle_sample(sc, crop_w):
     return cams
 
 
-def run_oracle_step(O, P, cams, cfg, lidar_full, sc):
-    """project -> bin -> forward -> L1 image + L1 depth losses -> backward, in FP64."""
+def run_oracle_step(O, P, cams, cfg, lidar_full, sc, depth_loss="l1"):
+    """project -> bin -> forward -> L1 image + depth losses -> backward, in FP64."""
     rec = O.project(P, cams, cfg)
     keys, vals, ranges = O.bin(P, cams, cfg, rec)
     out = O.render_fwd(P, cams, cfg, rec, vals, ranges)
     npx = sum(c.width * c.height for c in cams)
     target = np.zeros(3 * npx)
     _, gC = O.image_l1(out["rgb"], target)
-    _, gD, _ = O.depth_loss(P, cams, cfg, out["depth"], out["alpha"], lidar_full, mode=0)
-    O.render_bwd(P, cams, cfg, rec, vals, ranges, gC, gD)
+    if depth_loss == "kl-var":
+        mean, var = O.render_depth_dist(P, cams, cfg, rec, vals, ranges)
+        _, gm, gv, _ = O.depth_loss_var(P, cams, cfg, out["alpha"], mean, var, lidar_full)
+        O.render_bwd(P, cams, cfg, rec, vals, ranges, gC, np.zeros(npx), None, gm, gv)
+    else:
+        _, gD, _ = O.depth_loss(P, cams, cfg, out["depth"], out["alpha"], lidar_full,
+                                mode=1 if depth_loss == "kl" else 0)
+        O.render_bwd(P, cams, cfg, rec, vals, ranges, gC, gD)
     return npx
 
 
@@ -351,10 +383,11 @@ def cpu_baseline(sc, args, reps=1):
     t0 = time.perf_counter()
     npx = 0
     for _ in range(reps):
-        npx += run_oracle_step(O, P, cams, cfg, lid, sc)
+        npx += run_oracle_step(O, P, cams, cfg, lid, sc, args.depth_loss)
     dt = time.perf_counter() - t0
     sample = (f"FP64 oracle, full step (project all {sc.n} Gaussians x {len(cams)} views, bin, forward, "
-              f"L1 rgb + L1 depth, backward) on centred {cams[0].width}x{cams[0].height} crops of every view, "
+              f"{DEPTH_LOSSES[args.depth_loss]}, backward) on centred {cams[0].width}x{cams[0].height} crops "
+              f"of every view, "
               f"{reps} step(s), {dt:.1f} s")
     return {"value": npx / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
             "seconds": dt, "pixels": npx}
@@ -414,13 +447,15 @@ def main():
 
     def build_step(tw, th, depth):
         """A Step whose instance capacity fits the scene (sized from a first run)."""
-        cfg = G.gs_config_default(tile_w=tw, tile_h=th, batch_depth=depth)
-        st_ = Step(G, torch, sc, cfg, dev)
+        cfg = G.gs_config_default(tile_w=tw, tile_h=th, batch_depth=depth,
+                                  depth_mode=1 if args.depth_loss == "kl" else 0)
+        mom = args.depth_loss == "kl-var"
+        st_ = Step(G, torch, sc, cfg, dev, var=mom)
         st_.run()
         code, need_, _ = st_.r.status()
         if code == G.GS_ERR_CAPACITY or need_ > st_.r.info["inst_capacity"]:
             st_.r.close()
-            st_ = Step(G, torch, sc, cfg, dev, inst_capacity=int(need_ * 1.25) + 1024)
+            st_ = Step(G, torch, sc, cfg, dev, inst_capacity=int(need_ * 1.25) + 1024, var=mom)
             st_.run()
         return st_
 
@@ -435,7 +470,8 @@ def main():
             st_.r.close()
             del g_
             return float(np.mean(t_))
-        key = autotune.signature(sc.cameras, sc.n, sc.sh_degree, sc.submap_offsets, extra="bench-step")
+        key = autotune.signature(sc.cameras, sc.n, sc.sh_degree, sc.submap_offsets,
+                                 extra="bench-step" + ("" if args.depth_loss == "l1" else "-" + args.depth_loss))
         tuned = autotune.tune(measure, key=key)
         tw, th, args.depth = tuned["tile_w"], tuned["tile_h"], tuned["batch_depth"]
     else:
@@ -490,7 +526,8 @@ def main():
             lid = sc.lidar[m].copy()
             lid[:, 3] = 0
             sub.lidar = lid
-            pv_steps.append(Step(G, torch, sub, G.gs_config_default(), dev, inst_capacity=need + 1024))
+            pv_steps.append(Step(G, torch, sub, G.gs_config_default(depth_mode=1 if args.depth_loss == "kl" else 0),
+                                 dev, inst_capacity=need + 1024, var=args.depth_loss == "kl-var"))
         run_all = lambda: [s.run() for s in pv_steps]
         pv_times = time_steps(torch, run_all, max(3, args.steps // 2), 3, flush)
         pv_ms = float(np.mean(pv_times))
@@ -536,11 +573,17 @@ def main():
     # algorithmic bytes of one raster-backward launch: instance pair ids (4 B),
     # visible records read once (48 B), per-pixel inputs (3 rgb + depth grads,
     # list count, final T = 24 B), tile ranges (8 B), image-space gradients of
-    # the visible pairs accumulated (40 B written)
-    alg_bytes = 4 * n_inst + 48 * nvis + 24 * npx + 8 * n_tiles + 40 * nvis
+    # the visible pairs accumulated (40 B written); the variance variant reads
+    # the (mean, var, 1/W) record and the two adjoints instead of the depth
+    # adjoint (44 B per pixel)
+    px_bytes = 44 if args.depth_loss == "kl-var" else 24
+    alg_bytes = 4 * n_inst + 48 * nvis + px_bytes * npx + 8 * n_tiles + 40 * nvis
     bwd_ms = kern["raster_bwd"]
     achieved = alg_bytes / (bwd_ms * 1e-3) / 1e9
-    traffic, traffic_note = measured_traffic("k_raster_bwd", sc.name, f"{tw}x{th}/{args.depth}")
+    if args.depth_loss == "kl-var":
+        traffic, traffic_note = None, "the ncu capture covers the kernel without the depth variance"
+    else:
+        traffic, traffic_note = measured_traffic("k_raster_bwd", sc.name, f"{tw}x{th}/{args.depth}")
     roofline = {"bound": "hbm", "kernel": "k_raster_bwd",
                 "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                 "traffic": traffic, "traffic_source": traffic_note,

@@ -138,6 +138,18 @@ gs_status gs_bin_sort(gs_workspace *ws, void *stream);
  * entries up to the last blended fragment and the final T for the backward. */
 gs_status gs_render_fwd(gs_workspace *ws, float *rgb, float *depth, float *alpha, void *stream);
 
+/* gs_render_fwd that also renders each pixel's depth distribution, the
+ * renderer's N(mu_u, sigma_u^2) of Eq. (7) (Sec. III-C): with the blending
+ * weights w = alpha T of the pixel's fragments and W = sum w,
+ * depth_mean (device, N_pix) = sum w z / W and depth_var (device, N_pix) =
+ * sum w (z - mean)^2 / W, both 0 where nothing blends.  They are accumulated
+ * front to back by a weighted Welford update in depths relative to the first
+ * blended fragment's, so that their rounding scales with the spread of the
+ * depths, not with the depth.  alpha is written as W (1 - T in exact
+ * arithmetic).  Keeps (mean, var, 1/W) per pixel for gs_render_bwd_var. */
+gs_status gs_render_fwd_var(gs_workspace *ws, float *rgb, float *depth, float *alpha, float *depth_mean,
+                            float *depth_var, void *stream);
+
 /* LiDAR depth consistency (Eq. 7).  lidar (device, [n_pts][4] float32 rows
  * u, v, z, view): pixel (floor u, floor v) of view `view`; a point is valid if
  * it lies inside the image, z > near_z and alpha > 0 there.  depth_mode 0:
@@ -146,6 +158,17 @@ gs_status gs_render_fwd(gs_workspace *ws, float *rgb, float *depth, float *alpha
  * N_pix, nullable) is accumulated with dL/dD.  Zero valid points give 0. */
 gs_status gs_depth_loss(gs_workspace *ws, const float *depth, const float *alpha, const float *lidar,
                         int64_t n_pts, float *loss, float *dL_ddepth, void *stream);
+
+/* Eq. (7) with the rendered distribution: the same valid points (alpha > 0)
+ * and lambda_L as gs_depth_loss, mean KL(N(z, sigma_L^2) || N(mu_u,
+ * sigma_u^2)) with mu_u = depth_mean and sigma_u^2 = max(depth_var, 0) +
+ * sigma_U^2 (sigma_U is the floor of the predicted spread); depth_mode is not
+ * used.  alpha, depth_mean, depth_var (device, N_pix) from gs_render_fwd_var;
+ * dL_dmean and dL_dvar (device, N_pix, each nullable) are accumulated (a
+ * clamped variance passes no gradient). */
+gs_status gs_depth_loss_var(gs_workspace *ws, const float *alpha, const float *depth_mean,
+                            const float *depth_var, const float *lidar, int64_t n_pts, float *loss,
+                            float *dL_dmean, float *dL_dvar, void *stream);
 
 /* L1 photometric term of Eq. (6) (with the SSIM weight lambda = 0):
  * loss = mean |rgb - target| over 3*N_pix values, dL_drgb += sign(rgb -
@@ -164,6 +187,14 @@ gs_status gs_render_bwd(gs_workspace *ws, const gs_gaussians *g, const gs_camera
                         const float *dL_drgb, const float *dL_ddepth, const float *dL_dalpha,
                         const gs_grads *out, void *stream);
 
+/* gs_render_bwd that also takes the adjoints of the depth mean and variance,
+ * dL_dmean and dL_dvar (device, N_pix, each nullable).  The last forward
+ * must have been gs_render_fwd_var (GS_ERR_STATE otherwise). */
+gs_status gs_render_bwd_var(gs_workspace *ws, const gs_gaussians *g, const gs_camera *cams_dev,
+                            const float *dL_drgb, const float *dL_ddepth, const float *dL_dalpha,
+                            const float *dL_dmean, const float *dL_dvar, const gs_grads *out,
+                            void *stream);
+
 /* Synchronise `stream` and report device-side conditions: returns
  * GS_ERR_CAPACITY if the last gs_bin_sort needed more instances than the
  * capacity. Any out pointer may be NULL. */
@@ -180,7 +211,8 @@ gs_status gs_workspace_info(gs_workspace *ws, int64_t *info, int32_t n_info);
  * 2 tile rectangles [n_pairs][4] i16, 3 sorted instance tile ids [capacity]
  * u32, 4 sorted instance pair ids [capacity] u32, 5 tile ranges [n_tiles][2]
  * u32, 6 per-pixel list count up to the last blended fragment [N_pix] u32,
- * 7 per-pixel final T [N_pix] f32, 8 image-space gradients [n_pairs][10] f32. */
+ * 7 per-pixel final T [N_pix] f32, 8 image-space gradients [n_pairs][10] f32,
+ * 9 per-pixel depth (mean, var, 1/W, 0) of gs_render_fwd_var [N_pix][4] f32. */
 gs_status gs_workspace_copy(gs_workspace *ws, int32_t which, void *dst, int64_t *bytes, void *stream);
 
 /* gs_image_l1 for callers that cannot allocate device memory (the paper has

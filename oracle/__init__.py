@@ -107,8 +107,8 @@ def lib():
         _lib.oracle_render_fwd_pixels.argtypes = [i32, P, P, P, P, P, P, i64, P, P, P, P, P, P, P]
         _lib.oracle_render_bwd.argtypes = [i64, P, P, P, P, P, i32, i32, P, P, P, P, P, P, P, P, P,
                                            P, P, P, P, P, P, P, P, P, P, P]
-        _lib.oracle_render_moments.argtypes = [i32, P, P, P, P, P, P, P, P]
-        _lib.oracle_depth_loss_var.argtypes = [i32, P, P, P, P, P, P, P, i64, P, d, d, d, P, P, P, P, P]
+        _lib.oracle_render_depth_dist.argtypes = [i32, P, P, P, P, P, P, P, P]
+        _lib.oracle_depth_loss_var.argtypes = [i32, P, P, P, P, P, P, i64, P, d, d, d, P, P, P]
         _lib.oracle_depth_loss_var.restype = d
         _lib.oracle_image_l1.argtypes = [i64, P, P, P]
         _lib.oracle_image_l1.restype = d
@@ -264,34 +264,32 @@ def render_brute(P: Params, cams, cfg: Config, rec) -> dict:
     return out
 
 
-def render_moments(P: Params, cams, cfg: Config, rec, vals, ranges):
-    """(m1, m2): first and second moments of the blended depths about each
-    pixel's first blended depth (reading R15 of the C file)."""
+def render_depth_dist(P: Params, cams, cfg: Config, rec, vals, ranges):
+    """(mean, var) per pixel: weighted mean and variance of the blended depths
+    under the weights w = alpha T (reading R15 of the C file)."""
     ca, cc = cameras(cams), cfg.c()
-    npx = _npix(cams)
-    m1, m2 = np.zeros(npx), np.zeros(npx)
-    lib().oracle_render_moments(len(cams), ca, _p(P.submap_offsets), ctypes.byref(cc),
-                                _p(np.ascontiguousarray(rec)), _p(np.ascontiguousarray(vals, np.int64)),
-                                _p(np.ascontiguousarray(ranges, np.int64)), _p(m1), _p(m2))
-    return m1, m2
+    mean, var = np.zeros(_npix(cams)), np.zeros(_npix(cams))
+    lib().oracle_render_depth_dist(len(cams), ca, _p(P.submap_offsets), ctypes.byref(cc),
+                                   _p(np.ascontiguousarray(rec)), _p(np.ascontiguousarray(vals, np.int64)),
+                                   _p(np.ascontiguousarray(ranges, np.int64)), _p(mean), _p(var))
+    return mean, var
 
 
-def depth_loss_var(P: Params, cams, cfg: Config, depth, alpha, m1, m2, lidar, sigma_L=0.05, sigma_U=0.05,
-                   lam=1.0):
-    """Eq. (7) with the rendered depth distribution. Returns (loss, gD, gA, gM1, gM2, n_valid)."""
+def depth_loss_var(P: Params, cams, cfg: Config, alpha, mean, var, lidar, sigma_L=0.05, sigma_U=0.05, lam=1.0):
+    """Eq. (7) with the rendered depth distribution. Returns (loss, g_mean, g_var, n_valid)."""
     ca, cc = cameras(cams), cfg.c()
-    depth, alpha, m1, m2 = _d(depth), _d(alpha), _d(m1), _d(m2)
+    alpha, mean, var = _d(alpha), _d(mean), _d(var)
     lid = _d(lidar).reshape(-1, 4)
-    g = [np.zeros_like(depth) for _ in range(4)]
+    g = [np.zeros_like(mean) for _ in range(2)]
     nv = ctypes.c_int64(0)
-    loss = lib().oracle_depth_loss_var(len(cams), ca, _p(P.submap_offsets), ctypes.byref(cc), _p(depth),
-                                       _p(alpha), _p(m1), _p(m2), lid.shape[0], _p(lid),
+    loss = lib().oracle_depth_loss_var(len(cams), ca, _p(P.submap_offsets), ctypes.byref(cc), _p(alpha),
+                                       _p(mean), _p(var), lid.shape[0], _p(lid),
                                        float(np.float32(sigma_L)), float(np.float32(sigma_U)),
                                        float(np.float32(lam)), *(_p(x) for x in g), ctypes.byref(nv))
     return (loss, *g, int(nv.value))
 
 
-def render_bwd(P: Params, cams, cfg: Config, rec, vals, ranges, dC, dD, dA=None, dM1=None, dM2=None) -> dict:
+def render_bwd(P: Params, cams, cfg: Config, rec, vals, ranges, dC, dD, dA=None, dmean=None, dvar=None) -> dict:
     ca, cc = cameras(cams), cfg.c()
     K = (P.sh_degree + 1) ** 2
     n_p = rec.shape[0]
@@ -300,13 +298,13 @@ def render_bwd(P: Params, cams, cfg: Config, rec, vals, ranges, dC, dD, dA=None,
              opacity_logits=np.zeros(P.n), sh=np.zeros((P.n, K, 3)),
              pose=np.zeros((len(cams), 6)), dens_acc=np.zeros(P.n), dens_cnt=np.zeros(P.n))
     dC, dD = _d(dC), _d(dD)
-    opt = [(_d(x) if x is not None else None) for x in (dA, dM1, dM2)]
-    dAp, dM1p, dM2p = (_p(x) if x is not None else None for x in opt)
+    opt = [(_d(x) if x is not None else None) for x in (dA, dmean, dvar)]
+    dAp, dmp, dvp = (_p(x) if x is not None else None for x in opt)
     lib().oracle_render_bwd(P.n, _p(P.means), _p(P.log_scales), _p(P.quats),
                             _p(P.opacity_logits), _p(P.sh), P.sh_degree, len(cams), ca,
                             _p(P.submap_offsets), ctypes.byref(cc), _p(np.ascontiguousarray(rec)),
                             _p(np.ascontiguousarray(vals, np.int64)),
-                            _p(np.ascontiguousarray(ranges, np.int64)), _p(dC), _p(dD), dAp, dM1p, dM2p,
+                            _p(np.ascontiguousarray(ranges, np.int64)), _p(dC), _p(dD), dAp, dmp, dvp,
                             _p(g["g2d"]), _p(g["means"]), _p(g["log_scales"]), _p(g["quats"]),
                             _p(g["opacity_logits"]), _p(g["sh"]), _p(g["pose"]),
                             _p(g["dens_acc"]), _p(g["dens_cnt"]))

@@ -44,11 +44,9 @@
  *       acc += ||(dL/du, dL/dv)|| in pixels and cnt += 1.
  *   R15 rendered depth distribution (for Eq. 7 with a predicted sigma_u):
  *       the weights w_k = alpha_k T_k of a pixel's blended fragments, of total
- *       A, spread over their depths z_k: mean mu = D/A, variance
- *       m2/A - (m1/A)^2 with m1 = sum w (z - c), m2 = sum w (z - c)^2 about
- *       c = the depth of the pixel's first blended fragment (the variance does
- *       not depend on c; the shift only avoids cancellation in float).
- *       sigma_u^2 = max(variance, 0) + sigma_U^2.
+ *       W = sum w (= A), spread over their depths z_k: mean mu_u = D/W and
+ *       variance var = sum w (z - mu_u)^2 / W (both 0 where nothing blends);
+ *       sigma_u^2 = max(var, 0) + sigma_U^2 (sigma_U is the floor).
  */
 #include <math.h>
 #include <stdint.h>
@@ -484,7 +482,7 @@ static double frag_alpha(const double *r, double px, double py, const oc_config 
 }
 
 typedef struct {
-    double C[3], D, T, M1, M2;
+    double C[3], D, T, mean, var;
     int64_t last;    /* list position of the last blended fragment, -1 if none */
     int64_t n_blend; /* number of blended fragments */
     double margin;   /* min log-distance of a discrete decision to its threshold */
@@ -496,7 +494,8 @@ typedef struct {
  * pixel centre (px, py).  pos[i] is the list position reported as `last`. */
 static void composite(const double *rec, const int64_t *cand, const int64_t *pos, int64_t n,
                       double px, double py, const oc_config *cfg, oc_pix *out) {
-    double T = 1.0, C[3] = {0, 0, 0}, D = 0.0, M1 = 0.0, M2 = 0.0, zc = 0.0, margin = 1e300, cm = 1e300;
+    double T = 1.0, C[3] = {0, 0, 0}, D = 0.0, margin = 1e300, cm = 1e300;
+    double *wz = (double *)malloc(sizeof(double) * 2 * (n > 0 ? n : 1)); /* blended (w, z) */
     int64_t last = -1, nb = 0;
     uint64_t sig = 1469598103934665603ull;
     double lmin = log(cfg->alpha_min), ltmin = log(cfg->t_min), lmax = log(cfg->alpha_max);
@@ -514,16 +513,22 @@ static void composite(const double *rec, const int64_t *cand, const int64_t *pos
         double w = al * T;
         for (int ch = 0; ch < 3; ++ch) C[ch] += w * r[C_R + ch];
         D += w * r[C_Z];
-        if (nb == 0) zc = r[C_Z];
-        M1 += w * (r[C_Z] - zc);
-        M2 += w * (r[C_Z] - zc) * (r[C_Z] - zc);
+        wz[2 * nb] = w;
+        wz[2 * nb + 1] = r[C_Z];
         T = Tn;
         last = pos[i];
         ++nb;
         sig = (sig ^ (uint64_t)cand[i]) * 1099511628211ull;
     }
+    /* R15: mean and variance of the blended depths, by definition */
+    double W = 0.0, M2 = 0.0;
+    for (int64_t k = 0; k < nb; ++k) W += wz[2 * k];
+    double mu = nb > 0 ? D / W : 0.0;
+    for (int64_t k = 0; k < nb; ++k) M2 += wz[2 * k] * (wz[2 * k + 1] - mu) * (wz[2 * k + 1] - mu);
+    free(wz);
     memcpy(out->C, C, sizeof C);
-    out->D = D; out->T = T; out->M1 = M1; out->M2 = M2; out->last = last; out->n_blend = nb;
+    out->D = D; out->T = T; out->mean = mu; out->var = nb > 0 ? M2 / W : 0.0;
+    out->last = last; out->n_blend = nb;
     out->margin = margin; out->clamp_margin = cm; out->sig = sig;
 }
 
@@ -570,11 +575,10 @@ int oracle_render_fwd(int n_views, const oc_camera *cams, const int64_t *submap_
     return 0;
 }
 
-/* Depth moments of the tiled forward (R15): m1, m2 per pixel about the
- * depth of the pixel's first blended fragment. */
-int oracle_render_moments(int n_views, const oc_camera *cams, const int64_t *submap_offsets,
-                          const oc_config *cfg, const double *rec, const int64_t *vals,
-                          const int64_t *ranges, double *m1, double *m2) {
+/* Mean and variance of the blended depths per pixel (R15). */
+int oracle_render_depth_dist(int n_views, const oc_camera *cams, const int64_t *submap_offsets,
+                             const oc_config *cfg, const double *rec, const int64_t *vals,
+                             const int64_t *ranges, double *mean, double *var) {
     oc_view *V = (oc_view *)malloc(sizeof(oc_view) * (n_views > 0 ? n_views : 1));
     make_views(n_views, cams, submap_offsets, cfg, V);
     for (int v = 0; v < n_views; ++v) {
@@ -589,9 +593,8 @@ int oracle_render_moments(int n_views, const oc_camera *cams, const int64_t *sub
                 oc_pix o;
                 composite(rec, vals + s, pos, n, x + 0.5, y + 0.5, cfg, &o);
                 free(pos);
-                int64_t pix = V[v].pix_off + y * W + x;
-                m1[pix] = o.M1;
-                m2[pix] = o.M2;
+                mean[V[v].pix_off + y * W + x] = o.mean;
+                var[V[v].pix_off + y * W + x] = o.var;
             }
     }
     free(V);
@@ -734,15 +737,15 @@ double oracle_depth_loss(int n_views, const oc_camera *cams, const int64_t *subm
     return nv > 0 ? lambda * s / (double)nv : 0.0;
 }
 
-/* Eq. (7) with the renderer's predicted distribution (R15): mu = D/A,
- * sigma_u^2 = max(m2/A - (m1/A)^2, 0) + sigma_U^2; mean over valid points of
- * KL(N(z, sigma_L^2) || N(mu, sigma_u^2)) times lambda.  Gradients (each
- * accumulated per pixel, nullable) w.r.t. D, A, m1 and m2. */
+/* Eq. (7) with the renderer's predicted distribution (R15):
+ * sigma_u^2 = max(var, 0) + sigma_U^2; mean over valid points (R12) of
+ * KL(N(z, sigma_L^2) || N(mean, sigma_u^2)) times lambda.  Gradients (each
+ * accumulated per pixel, nullable) w.r.t. mean and var. */
 double oracle_depth_loss_var(int n_views, const oc_camera *cams, const int64_t *submap_offsets,
-                             const oc_config *cfg, const double *depth, const double *alpha,
-                             const double *m1, const double *m2, int64_t n_pts, const double *lidar,
-                             double sigma_L, double sigma_U, double lambda, double *gD, double *gA,
-                             double *gM1, double *gM2, int64_t *n_valid) {
+                             const oc_config *cfg, const double *alpha, const double *mean,
+                             const double *var_in, int64_t n_pts, const double *lidar, double sigma_L,
+                             double sigma_U, double lambda, double *gmean, double *gvar,
+                             int64_t *n_valid) {
     oc_view *V = (oc_view *)malloc(sizeof(oc_view) * (n_views > 0 ? n_views : 1));
     make_views(n_views, cams, submap_offsets, cfg, V);
     double s = 0;
@@ -758,8 +761,8 @@ double oracle_depth_loss_var(int n_views, const oc_camera *cams, const int64_t *
             double A = alpha[pix];
             if (!(A > 0)) continue;
             double z = L[2];
-            double mu = depth[pix] / A, a1 = m1[pix] / A;
-            double var = m2[pix] / A - a1 * a1;
+            double mu = mean[pix];
+            double var = var_in[pix];
             int clamped = var < 0;
             double su2 = (clamped ? 0.0 : var) + sigma_U * sigma_U;
             double e = mu - z;
@@ -770,11 +773,8 @@ double oracle_depth_loss_var(int n_views, const oc_camera *cams, const int64_t *
                 double k = lambda / (double)nv;
                 double dmu = e / su2;                                                  /* dKL/dmu */
                 double dv = clamped ? 0.0 : 0.5 / su2 - (sigma_L * sigma_L + e * e) / (2.0 * su2 * su2);
-                /* mu = D/A; var = m2/A - (m1/A)^2 */
-                if (gD) gD[pix] += k * dmu / A;
-                if (gM1) gM1[pix] += k * dv * (-2.0 * a1 / A);
-                if (gM2) gM2[pix] += k * dv / A;
-                if (gA) gA[pix] += k * (dmu * (-mu / A) + dv * (-m2[pix] / (A * A) + 2.0 * a1 * a1 / A));
+                if (gmean) gmean[pix] += k * dmu;
+                if (gvar) gvar[pix] += k * dv;
             }
         }
         if (nv == 0) break;
@@ -795,7 +795,7 @@ double oracle_depth_loss_var(int n_views, const oc_camera *cams, const int64_t *
  * with w_k = alpha_k T_k and h_k = gC.c_k + gD z_k + gA (A = sum_k w_k). */
 static void pixel_adjoint(const double *rec, const int64_t *cand, int64_t n, double px, double py,
                           const oc_config *cfg, const double gC[3], double gD, double gA,
-                          double gM1, double gM2, double *g2d) {
+                          double gmean, double gvar, double *g2d) {
     int64_t *bl = (int64_t *)malloc(sizeof(int64_t) * (n > 0 ? n : 1));
     double *al = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
     double *raw = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
@@ -811,20 +811,37 @@ static void pixel_adjoint(const double *rec, const int64_t *cand, int64_t n, dou
         bl[m] = cand[i]; al[m] = a; raw[m] = rw; Tb[m] = T; ++m;
         T = Tn;
     }
-    /* the moments' reference depth is a constant of the adjoint (R15) */
-    double zc = m > 0 ? rec[bl[0] * OC_NCOL + C_Z] : 0.0;
+    /* R15: mu = sum w z / W, W = sum w, var = M2 / W, M2 = sum w (z - mu)^2.
+     * dmu/dw_k = (z_k - mu)/W, dmu/dz_k = w_k/W; with R = sum w (z - mu),
+     *   dM2/dw_k = (z_k - mu)^2 - 2 R dmu/dw_k,  dM2/dz_k = 2 w_k (z_k - mu) - 2 R dmu/dz_k,
+     *   dvar/dw_k = dM2/dw_k / W - M2/W^2,       dvar/dz_k = dM2/dz_k / W. */
+    double W = 0.0, Dz = 0.0, R = 0.0, M2 = 0.0;
+    for (int64_t j = 0; j < m; ++j) {
+        W += al[j] * Tb[j];
+        Dz += al[j] * Tb[j] * rec[bl[j] * OC_NCOL + C_Z];
+    }
+    double mu = m > 0 ? Dz / W : 0.0;
+    for (int64_t j = 0; j < m; ++j) {
+        double e = rec[bl[j] * OC_NCOL + C_Z] - mu;
+        R += al[j] * Tb[j] * e;
+        M2 += al[j] * Tb[j] * e * e;
+    }
     double suffix = 0.0;
     for (int64_t j = m - 1; j >= 0; --j) {
         const double *r = rec + bl[j] * OC_NCOL;
         double *g = g2d + bl[j] * OC_NGRAD;
         double w = al[j] * Tb[j];
-        double dz = r[C_Z] - zc;
+        double dz = r[C_Z] - mu;
+        double dmu_dw = dz / W, dmu_dz = w / W;
+        double dvar_dw = (dz * dz - 2.0 * R * dmu_dw) / W - M2 / (W * W);
+        double dvar_dz = (2.0 * w * dz - 2.0 * R * dmu_dz) / W;
+        /* h = dL/dw_j through C, D, A = sum w, mu and var */
         double h = gC[0] * r[C_R] + gC[1] * r[C_G] + gC[2] * r[C_B] + gD * r[C_Z] + gA +
-                   gM1 * dz + gM2 * dz * dz;
+                   gmean * dmu_dw + gvar * dvar_dw;
         double dal = Tb[j] * h - suffix / (1.0 - al[j]);
         suffix += w * h;
         g[G_R] += w * gC[0]; g[G_G] += w * gC[1]; g[G_B] += w * gC[2];
-        g[G_Z] += w * (gD + gM1 + 2.0 * gM2 * dz);
+        g[G_Z] += w * gD + gmean * dmu_dz + gvar * dvar_dz;
         if (raw[j] > cfg->alpha_max) continue; /* clamped: no dependence on o, pw */
         /* alpha = o exp(pw): dalpha/dln(o) = alpha, dalpha/dpw = alpha */
         double gpw = dal * al[j];
@@ -1022,7 +1039,7 @@ int oracle_render_bwd(int64_t n, const double *means, const double *log_scales, 
                       int n_views, const oc_camera *cams, const int64_t *submap_offsets,
                       const oc_config *cfg, const double *rec, const int64_t *vals,
                       const int64_t *ranges, const double *dC, const double *dD, const double *dA,
-                      const double *dM1, const double *dM2, double *g2d, double *g_means, double *g_ls, double *g_quats, double *g_om,
+                      const double *dmean, const double *dvar, double *g2d, double *g_means, double *g_ls, double *g_quats, double *g_om,
                       double *g_sh, double *g_pose, double *dens_acc, double *dens_cnt) {
     (void)n;
     oc_view *V = (oc_view *)malloc(sizeof(oc_view) * (n_views > 0 ? n_views : 1));
@@ -1035,12 +1052,12 @@ int oracle_render_bwd(int64_t n, const double *means, const double *log_scales, 
                 double gC[3];
                 for (int ch = 0; ch < 3; ++ch) gC[ch] = dC[3 * V[v].pix_off + ch * W * H + local];
                 double gD = dD ? dD[pix] : 0.0, gA = dA ? dA[pix] : 0.0;
-                double gM1 = dM1 ? dM1[pix] : 0.0, gM2 = dM2 ? dM2[pix] : 0.0;
-                if (gC[0] == 0 && gC[1] == 0 && gC[2] == 0 && gD == 0 && gA == 0 && gM1 == 0 && gM2 == 0)
+                double gmu = dmean ? dmean[pix] : 0.0, gv = dvar ? dvar[pix] : 0.0;
+                if (gC[0] == 0 && gC[1] == 0 && gC[2] == 0 && gD == 0 && gA == 0 && gmu == 0 && gv == 0)
                     continue;
                 int64_t t = V[v].tile_off + (y / cfg->tile_h) * V[v].ntx + x / cfg->tile_w;
                 int64_t s = ranges[2 * t], e = ranges[2 * t + 1];
-                pixel_adjoint(rec, vals + s, e - s, x + 0.5, y + 0.5, cfg, gC, gD, gA, gM1, gM2, g2d);
+                pixel_adjoint(rec, vals + s, e - s, x + 0.5, y + 0.5, cfg, gC, gD, gA, gmu, gv, g2d);
             }
     }
     int K = (sh_degree + 1) * (sh_degree + 1);

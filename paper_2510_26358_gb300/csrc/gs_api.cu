@@ -137,7 +137,7 @@ void gs_workspace_destroy(gs_workspace *ws) {
                     ws->vis_key, ws->vis_pair, ws->vis_key_alt, ws->vis_pair_alt, ws->ioff,
                     ws->inst_tile, ws->inst_val, ws->inst_tile_alt, ws->inst_val_alt, ws->ranges,
                     ws->tile_order, ws->tile_buckets,
-                    ws->last, ws->tfin, ws->hist, ws->part, ws->digit_tot, ws->pose_part, ws->red_part,
+                    ws->last, ws->tfin, ws->vstat, ws->hist, ws->part, ws->digit_tot, ws->pose_part, ws->red_part,
                     ws->st};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -277,6 +277,7 @@ gs_status gs_workspace_create(const gs_camera *cams, int32_t n_views, const int6
     GS_ALLOC(ws->tile_buckets, (size_t)2 * kOrderBuckets);
     GS_ALLOC(ws->last, (size_t)ws->n_pix);
     GS_ALLOC(ws->tfin, (size_t)ws->n_pix);
+    GS_ALLOC(ws->vstat, (size_t)ws->n_pix);
     GS_ALLOC(ws->hist, (size_t)256 * ws->sort_blocks);
     GS_ALLOC(ws->part, (size_t)ws->sort_blocks + 1);
     GS_ALLOC(ws->digit_tot, (size_t)256);
@@ -314,7 +315,7 @@ gs_status gs_project(gs_workspace *ws, const gs_gaussians *g, const gs_camera *c
     r = launch_project_fwd(ws, g, cams_dev, (cudaStream_t)stream);
     if (r == GS_OK) {
         ws->projected = true;
-        ws->binned = ws->rendered = false;
+        ws->binned = ws->rendered = ws->rendered_var = false;
     }
     return r;
 }
@@ -330,8 +331,21 @@ gs_status gs_bin_sort(gs_workspace *ws, void *stream) {
 gs_status gs_render_fwd(gs_workspace *ws, float *rgb, float *depth, float *alpha, void *stream) {
     if (!ws || !rgb || !depth || !alpha) return fail(GS_ERR_INVALID_ARG, "NULL argument");
     if (!ws->binned) return fail(GS_ERR_STATE, "gs_render_fwd before gs_bin_sort");
-    gs_status r = launch_raster_fwd(ws, rgb, depth, alpha, (cudaStream_t)stream);
-    if (r == GS_OK) ws->rendered = true;
+    gs_status r = launch_raster_fwd(ws, rgb, depth, alpha, nullptr, nullptr, (cudaStream_t)stream);
+    if (r == GS_OK) {
+        ws->rendered = true;
+        ws->rendered_var = false;
+    }
+    return r;
+}
+
+gs_status gs_render_fwd_var(gs_workspace *ws, float *rgb, float *depth, float *alpha, float *depth_mean,
+                            float *depth_var, void *stream) {
+    if (!ws || !rgb || !depth || !alpha || !depth_mean || !depth_var)
+        return fail(GS_ERR_INVALID_ARG, "NULL argument");
+    if (!ws->binned) return fail(GS_ERR_STATE, "gs_render_fwd_var before gs_bin_sort");
+    gs_status r = launch_raster_fwd(ws, rgb, depth, alpha, depth_mean, depth_var, (cudaStream_t)stream);
+    if (r == GS_OK) ws->rendered = ws->rendered_var = true;
     return r;
 }
 
@@ -340,7 +354,18 @@ gs_status gs_depth_loss(gs_workspace *ws, const float *depth, const float *alpha
     if (!ws || !depth || !alpha || !loss) return fail(GS_ERR_INVALID_ARG, "NULL argument");
     if (n_pts < 0 || (n_pts > 0 && !lidar)) return fail(GS_ERR_INVALID_ARG, "bad LiDAR array");
     if (lidar && !aligned(lidar, 16)) return fail(GS_ERR_INVALID_ARG, "lidar must be 16-byte aligned");
-    return launch_depth_loss(ws, depth, alpha, lidar, n_pts, loss, dL_ddepth, (cudaStream_t)stream);
+    return launch_depth_loss(ws, ws->cfg.depth_mode, depth, alpha, nullptr, lidar, n_pts, loss, dL_ddepth,
+                             nullptr, (cudaStream_t)stream);
+}
+
+gs_status gs_depth_loss_var(gs_workspace *ws, const float *alpha, const float *depth_mean, const float *depth_var,
+                            const float *lidar, int64_t n_pts, float *loss, float *dL_dmean, float *dL_dvar,
+                            void *stream) {
+    if (!ws || !alpha || !depth_mean || !depth_var || !loss) return fail(GS_ERR_INVALID_ARG, "NULL argument");
+    if (n_pts < 0 || (n_pts > 0 && !lidar)) return fail(GS_ERR_INVALID_ARG, "bad LiDAR array");
+    if (lidar && !aligned(lidar, 16)) return fail(GS_ERR_INVALID_ARG, "lidar must be 16-byte aligned");
+    return launch_depth_loss(ws, 2, depth_mean, alpha, depth_var, lidar, n_pts, loss, dL_dmean, dL_dvar,
+                             (cudaStream_t)stream);
 }
 
 gs_status gs_image_l1(gs_workspace *ws, const float *rgb, const float *target, float *loss, float *dL_drgb,
@@ -359,7 +384,23 @@ gs_status gs_render_bwd(gs_workspace *ws, const gs_gaussians *g, const gs_camera
         return fail(GS_ERR_INVALID_ARG, "a gradient pointer is NULL");
     if (!ws->rendered) return fail(GS_ERR_STATE, "gs_render_bwd before gs_render_fwd");
     cudaStream_t s = (cudaStream_t)stream;
-    r = launch_raster_bwd(ws, dL_drgb, dL_ddepth, dL_dalpha, s);
+    r = launch_raster_bwd(ws, dL_drgb, dL_ddepth, dL_dalpha, false, nullptr, nullptr, s);
+    if (r == GS_OK) r = launch_project_bwd(ws, g, cams_dev, out, s);
+    return r;
+}
+
+gs_status gs_render_bwd_var(gs_workspace *ws, const gs_gaussians *g, const gs_camera *cams_dev,
+                            const float *dL_drgb, const float *dL_ddepth, const float *dL_dalpha,
+                            const float *dL_dmean, const float *dL_dvar, const gs_grads *out, void *stream) {
+    if (!ws || !cams_dev || !dL_drgb || !out) return fail(GS_ERR_INVALID_ARG, "NULL argument");
+    gs_status r = check_gaussians(ws, g);
+    if (r != GS_OK) return r;
+    if (ws->n > 0 && (!out->means || !out->log_scales || !out->quats || !out->opacity_logits || !out->sh))
+        return fail(GS_ERR_INVALID_ARG, "a gradient pointer is NULL");
+    if (!ws->rendered_var)
+        return fail(GS_ERR_STATE, "gs_render_bwd_var needs gs_render_fwd_var as the last forward");
+    cudaStream_t s = (cudaStream_t)stream;
+    r = launch_raster_bwd(ws, dL_drgb, dL_ddepth, dL_dalpha, true, dL_dmean, dL_dvar, s);
     if (r == GS_OK) r = launch_project_bwd(ws, g, cams_dev, out, s);
     return r;
 }
@@ -397,6 +438,7 @@ gs_status gs_workspace_copy(gs_workspace *ws, int32_t which, void *dst, int64_t 
         case 6: src = ws->last; nb = ws->n_pix * 4; break;
         case 7: src = ws->tfin; nb = ws->n_pix * 4; break;
         case 8: src = ws->g2d; nb = ws->n_pairs * 40; break;
+        case 9: src = ws->vstat; nb = ws->n_pix * 16; break;
         default: return fail(GS_ERR_INVALID_ARG, "unknown buffer");
     }
     if (!dst) {

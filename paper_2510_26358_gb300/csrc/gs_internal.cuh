@@ -82,7 +82,7 @@ struct gs_workspace {
     gs::Consts consts{};
     int64_t n = 0, n_pairs = 0, n_tiles = 0, n_pix = 0, inst_cap = 0;
     int32_t tile_bits = 0, sort_blocks = 0, proj_blocks = 0, max_views_per_submap = 0;
-    int32_t raster_grid_fwd = 0, raster_grid_bwd = 0;
+    int32_t raster_grid_fwd = 0, raster_grid_bwd = 0, raster_grid_fwd_var = 0, raster_grid_bwd_var = 0;
     size_t bytes = 0;
     int64_t kernel_launches = 0;  // kernels enqueued by this workspace so far
     std::vector<gs::ViewInfo> views_h;
@@ -107,6 +107,7 @@ struct gs_workspace {
     uint32_t *tile_buckets = nullptr; // [2][kOrderBuckets] histogram and cursors for tile_order
     uint32_t *last = nullptr;      // [n_pix]
     float *tfin = nullptr;         // [n_pix]
+    float4 *vstat = nullptr;       // [n_pix] depth (mean, var, 1/W, 0) of the variance forward
     // scratch
     uint32_t *hist = nullptr;      // [256][sort_blocks]
     uint32_t *part = nullptr;      // [sort_blocks + 1]
@@ -115,7 +116,7 @@ struct gs_workspace {
     double *red_part = nullptr;    // [2][sort_blocks] loss partials
     gs::DevState *st = nullptr;
     // host-side order checks
-    bool projected = false, binned = false, rendered = false;
+    bool projected = false, binned = false, rendered = false, rendered_var = false;
     // optional per-stage timing (events recorded around each kernel group)
     bool profiling = false;
     cudaEvent_t ev[2 * GS_NUM_STAGES] = {};
@@ -156,13 +157,17 @@ gs_status launch_project_fwd(gs_workspace *ws, const gs_gaussians *g, const gs_c
 gs_status launch_project_bwd(gs_workspace *ws, const gs_gaussians *g, const gs_camera *cams,
                              const gs_grads *out, cudaStream_t s);
 gs_status launch_bin_sort(gs_workspace *ws, cudaStream_t s);
-gs_status launch_raster_fwd(gs_workspace *ws, float *rgb, float *depth, float *alpha,
-                            cudaStream_t s);
+// mean == nullptr: plain forward; otherwise also the depth mean and variance
+gs_status launch_raster_fwd(gs_workspace *ws, float *rgb, float *depth, float *alpha, float *mean,
+                            float *var, cudaStream_t s);
 gs_status launch_raster_bwd(gs_workspace *ws, const float *dL_drgb, const float *dL_ddepth,
-                            const float *dL_dalpha, cudaStream_t s);
-gs_status launch_depth_loss(gs_workspace *ws, const float *depth, const float *alpha,
-                            const float *lidar, int64_t n_pts, float *loss, float *dL_ddepth,
-                            cudaStream_t s);
+                            const float *dL_dalpha, bool var, const float *dL_dmean,
+                            const float *dL_dvar, cudaStream_t s);
+// mode 0, 1: gs_depth_loss on `depth`; mode 2: the rendered-variance KL on
+// (`depth` = mean, var), gradients to mean (dL_ddepth) and var
+gs_status launch_depth_loss(gs_workspace *ws, int mode, const float *depth, const float *alpha,
+                            const float *var, const float *lidar, int64_t n_pts, float *loss,
+                            float *dL_ddepth, float *dL_dvar, cudaStream_t s);
 gs_status launch_image_l1(gs_workspace *ws, const float *rgb, const float *target, float *loss,
                           float *dL_drgb, cudaStream_t s);
 // occupancy-derived persistent grid sizes for the rasterisers

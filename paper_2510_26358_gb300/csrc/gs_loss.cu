@@ -8,6 +8,12 @@
 // scaled by lambda_L.  The gradient dL/dD = lambda_L/|Omega| dl/dD is added to
 // the pixel (atomically: several returns may share a pixel).
 //
+// Mode 2 takes the renderer's own depth distribution as N(mu_u, sigma_u^2):
+// the rendered mean mu_u and sigma_u^2 = max(var, 0) + sigma_U^2 from the
+// rendered variance, and
+// KL = ln(sigma_u/sigma_L) + (sigma_L^2 + (z - mu_u)^2) / (2 sigma_u^2) - 1/2,
+// with gradients to mu_u and var.
+//
 // Photometric L1 (Eq. 6 with lambda = 0): mean |C - I| over every channel of
 // every pixel of every view, gradient sign(C - I)/n.
 //
@@ -37,13 +43,32 @@ struct DepthArgs {
     int32_t n_views, mode;
     float near_z, sigma_L, sigma_U, lambda;
     const float *depth, *alpha, *lidar;
+    const float *var;  // mode 2 (`depth` holds the mean)
     int64_t n_pts;
     double *part;  // [2][nb]
     int nb;
     float *loss;
-    float *grad;
+    float *grad;      // dL/dD (mode 2: dL/dmean)
+    float *grad_var;  // mode 2: dL/dvar
     DevState *st;
 };
+
+// Mode 2 at one pixel: the KL term and its partials w.r.t. (mean, var).
+struct VarTerm {
+    double kl, dmu, dvar;
+};
+__device__ __forceinline__ VarTerm var_term(double mu, double var, double z, double sl, double su) {
+    VarTerm t;
+    const bool clamped = var < 0.0;
+    const double v = (clamped ? 0.0 : var) + su * su;
+    const double e = mu - z;
+    t.kl = 0.5 * log(v) - log(sl) + (sl * sl + e * e) / (2.0 * v) - 0.5;
+    const double dmu = e / v;
+    const double dv = clamped ? 0.0 : 0.5 / v - (sl * sl + e * e) / (2.0 * v * v);
+    t.dmu = dmu;
+    t.dvar = dv;
+    return t;
+}
 
 // returns the pixel index or -1 if the return is not valid
 __device__ __forceinline__ int64_t lidar_pixel(const DepthArgs &A, int64_t i, float &z) {
@@ -68,6 +93,8 @@ __global__ void __launch_bounds__(LT) k_depth_partial(DepthArgs A) {
         double D = A.depth[pix], d = D - (double)z;
         if (A.mode == 0) {
             s += fabs(d);
+        } else if (A.mode == 2) {
+            s += var_term(D, A.var[pix], z, A.sigma_L, A.sigma_U).kl;
         } else {
             double sl = A.sigma_L, su = A.sigma_U;
             s += log(su / sl) + (sl * sl + d * d) / (2.0 * su * su) - 0.5;
@@ -108,6 +135,13 @@ __global__ void __launch_bounds__(LT) k_depth_grad(DepthArgs A) {
         float z;
         int64_t pix = lidar_pixel(A, i, z);
         if (pix < 0) continue;
+        if (A.mode == 2) {
+            const VarTerm t = var_term(A.depth[pix], A.var[pix], z, A.sigma_L, A.sigma_U);
+            const double k = scale;
+            if (A.grad) atomicAdd(A.grad + pix, (float)(k * t.dmu));
+            if (A.grad_var) atomicAdd(A.grad_var + pix, (float)(k * t.dvar));
+            continue;
+        }
         float d = A.depth[pix] - z;
         float g = A.mode == 0 ? (d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f)) : d * iv;
         atomicAdd(A.grad + pix, scale * g);
@@ -158,12 +192,15 @@ __global__ void __launch_bounds__(LT) k_l1_final(const double *part, int nb, int
 
 }  // namespace
 
-gs_status launch_depth_loss(gs_workspace *ws, const float *depth, const float *alpha, const float *lidar,
-                            int64_t n_pts, float *loss, float *dL_ddepth, cudaStream_t s) {
+gs_status launch_depth_loss(gs_workspace *ws, int mode, const float *depth, const float *alpha,
+                            const float *var, const float *lidar, int64_t n_pts, float *loss,
+                            float *dL_ddepth, float *dL_dvar, cudaStream_t s) {
     DepthArgs A{};
     A.views = ws->views;
     A.n_views = ws->n_views;
-    A.mode = ws->cfg.depth_mode;
+    A.mode = mode;
+    A.var = var;
+    A.grad_var = dL_dvar;
     A.near_z = ws->cfg.near_z;
     A.sigma_L = ws->cfg.sigma_L;
     A.sigma_U = ws->cfg.sigma_U;
@@ -180,7 +217,7 @@ gs_status launch_depth_loss(gs_workspace *ws, const float *depth, const float *a
     StageTimer timer(ws, GS_STAGE_DEPTH_LOSS, s);
     ++ws->kernel_launches; k_depth_partial<<<A.nb, LT, 0, s>>>(A);
     ++ws->kernel_launches; k_depth_final<<<1, LT, 0, s>>>(A);
-    if (dL_ddepth && n_pts > 0) {
+    if ((dL_ddepth || dL_dvar) && n_pts > 0) {
         ++ws->kernel_launches;
         k_depth_grad<<<A.nb, LT, 0, s>>>(A);
     }

@@ -22,6 +22,21 @@
 // In the backward each thread owns PPT vertically adjacent pixels of one
 // column: the shared memory loads, the loop overhead, the column part of the
 // exponent and the warp reduction are paid once per PPT pixels.
+//
+// The VAR variants also render each pixel's depth distribution under the
+// weights w: its mean mu = sum w z / W and variance var = sum w (z - mu)^2 / W,
+// W = sum w.  They are accumulated front to back by the weighted Welford
+// update, in depths relative to the first blended fragment's, c:
+//   W += w;  y = z - c;  d = y - m;  m += d w / W;  M2 += w d (y - m),
+// so that rounding scales with the spread of the depths, not with the depth
+// itself (mu = D / A in float loses ~sqrt(n) ulps of a 5 m depth, which a
+// centimetre-scale variance term magnifies).  mu = c + m and var = M2 / W are
+// kept per pixel (with 1/W) for the backward, and alpha is written as W
+// (1 - T in exact arithmetic).  With sum w (z - mu) = 0 the adjoints are
+//   dmu/dw_k = (z_k - mu) / W,                dmu/dz_k = w_k / W,
+//   dvar/dw_k = ((z_k - mu)^2 - var) / W,     dvar/dz_k = 2 w_k (z_k - mu) / W,
+// so with a = gmu / W and b = gvar / W, h gains a dz + b (dz^2 - var) and
+// dL/dz gains w (a + 2 b dz), dz = z - mu.
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -40,12 +55,15 @@ struct RasterArgs {
     float *tfin;
     // forward outputs
     float *rgb, *depth_out, *alpha_out;
+    float *mean_out, *var_out;  // VAR variants: depth mean and variance per pixel
+    float4 *vstat;              // VAR variants: (mean, var, 1/W, 0) per pixel, for the backward
     // backward inputs / outputs
     const float *dL_drgb, *dL_ddepth, *dL_dalpha;
+    const float *dL_dmean, *dL_dvar;  // VAR variant
     float *g2d;
 };
 
-template <int TW, int TH>
+template <int TW, int TH, bool VAR>
 __global__ void __launch_bounds__(TW * TH) k_raster_fwd(RasterArgs A) {
     constexpr int NT = TW * TH;
     static_assert(NT % 32 == 0, "the forward needs whole warps");
@@ -72,6 +90,7 @@ __global__ void __launch_bounds__(TW * TH) k_raster_fwd(RasterArgs A) {
         const float pxf = (float)px, pyf = (float)py;
         const uint2 rg = A.ranges[tile];
         float T = 1.f, Cr = 0.f, Cg = 0.f, Cb = 0.f, D = 0.f;
+        float Wsum = 0.f, zc = 0.f, mr = 0.f, M2 = 0.f;
         uint32_t cnt = 0;
         bool done = !inside;
         for (uint32_t b0 = rg.x; b0 < rg.y; b0 += A.depth) {
@@ -106,6 +125,14 @@ __global__ void __launch_bounds__(TW * TH) k_raster_fwd(RasterArgs A) {
                 Cg = __fmaf_rn(wgt, c.y, Cg);
                 Cb = __fmaf_rn(wgt, c.z, Cb);
                 D = __fmaf_rn(wgt, c.w, D);
+                if (VAR) {
+                    if (cnt == 0) zc = c.w;
+                    Wsum += wgt;
+                    const float y = c.w - zc;
+                    const float d = y - mr;
+                    mr = __fmaf_rn(d, __fdividef(wgt, Wsum), mr);
+                    M2 = __fmaf_rn(wgt * d, y - mr, M2);
+                }
                 T = Tn;
                 cnt = b0 + j - rg.x + 1;
             }
@@ -119,9 +146,20 @@ __global__ void __launch_bounds__(TW * TH) k_raster_fwd(RasterArgs A) {
             rgb[hw + pl] = Cg;
             rgb[2 * hw + pl] = Cb;
             A.depth_out[pix] = D;
-            A.alpha_out[pix] = 1.f - T;
+            // 1 - T loses the relative precision of a small alpha (T near 1);
+            // the variance variant has the direct sum of the weights at hand,
+            // which keeps it, as the normalised depth D / alpha needs
+            A.alpha_out[pix] = VAR ? Wsum : 1.f - T;
             A.last[pix] = cnt;
             A.tfin[pix] = T;
+            if (VAR) {
+                const float mean = zc + mr;
+                const float iw = Wsum > 0.f ? 1.f / Wsum : 0.f;
+                const float var = M2 * iw;
+                A.mean_out[pix] = mean;
+                A.var_out[pix] = var;
+                A.vstat[pix] = make_float4(mean, var, iw, 0.f);
+            }
         }
     }
 }
@@ -172,9 +210,10 @@ __device__ __forceinline__ int reduce10_component(int lane) {
 
 // At least 640 resident threads per SM (20 warps): measured best on the
 // 500k orchard (10 two-warp blocks: 0.54 ms; no bound: 0.60 ms; 14 or 16
-// blocks spill registers: 0.62 / 0.67 ms).
-template <int TW, int TH, int PPT>
-__global__ void __launch_bounds__(TW * TH / PPT, 640 / (TW * TH / PPT)) k_raster_bwd(RasterArgs A) {
+// blocks spill registers: 0.62 / 0.67 ms).  The VAR variant holds three more
+// values per pixel and takes 512 (16 warps) so that it does not spill.
+template <int TW, int TH, int PPT, bool VAR>
+__global__ void __launch_bounds__(TW * TH / PPT, (VAR ? 512 : 640) / (TW * TH / PPT)) k_raster_bwd(RasterArgs A) {
     constexpr int NT = TW * TH / PPT;
     static_assert(NT % 32 == 0, "the backward needs whole warps");
     constexpr int NW = (NT + 31) / 32;
@@ -215,12 +254,14 @@ __global__ void __launch_bounds__(TW * TH / PPT, 640 / (TW * TH / PPT)) k_raster
         const float *grgb = A.dL_drgb + 3 * (int64_t)vi.pix_off;
         uint32_t cnt[PPT], mycnt = 0;
         float T[PPT], gR[PPT], gG[PPT], gB[PPT], gD[PPT], gA[PPT], acc[PPT];
+        float zmu[PPT], ga[PPT], gb[PPT];
 #pragma unroll
         for (int i = 0; i < PPT; ++i) {
             const int py = py0 + i;
             cnt[i] = 0;
             T[i] = 1.f;
             gR[i] = gG[i] = gB[i] = gD[i] = gA[i] = acc[i] = 0.f;
+            zmu[i] = ga[i] = gb[i] = 0.f;
             if (px < vi.W && py < vi.H) {
                 const int64_t pl = (int64_t)py * vi.W + px;
                 const int64_t pix = vi.pix_off + pl;
@@ -231,6 +272,13 @@ __global__ void __launch_bounds__(TW * TH / PPT, 640 / (TW * TH / PPT)) k_raster
                 gB[i] = grgb[2 * hw + pl];
                 gD[i] = A.dL_ddepth ? A.dL_ddepth[pix] : 0.f;
                 gA[i] = A.dL_dalpha ? A.dL_dalpha[pix] : 0.f;
+                if (VAR) {
+                    const float4 vs = A.vstat[pix];
+                    zmu[i] = vs.x;
+                    ga[i] = A.dL_dmean ? A.dL_dmean[pix] * vs.z : 0.f;
+                    gb[i] = A.dL_dvar ? A.dL_dvar[pix] * vs.z : 0.f;
+                    gA[i] = __fmaf_rn(-gb[i], vs.y, gA[i]);  // the -b var part of every h
+                }
             }
             mycnt = max(mycnt, cnt[i]);
         }
@@ -280,13 +328,20 @@ __global__ void __launch_bounds__(TW * TH / PPT, 640 / (TW * TH / PPT)) k_raster
                     T[i] = T[i] * r1m;  // transmittance before this fragment
                     const float4 c = sC[j];
                     const float wgt = al * T[i];
-                    const float h = gR[i] * c.x + gG[i] * c.y + gB[i] * c.z + gD[i] * c.w + gA[i];
+                    float h = gR[i] * c.x + gG[i] * c.y + gB[i] * c.z + gD[i] * c.w + gA[i];
+                    float gz = gD[i];
+                    if (VAR) {
+                        const float dz = c.w - zmu[i];
+                        const float t = __fmaf_rn(gb[i], dz, ga[i]);  // a + b dz
+                        h = __fmaf_rn(t, dz, h);
+                        gz += __fmaf_rn(gb[i], dz, t);               // a + 2 b dz
+                    }
                     const float dLda = T[i] * h - acc[i] * r1m;
                     acc[i] = __fmaf_rn(wgt, h, acc[i]);
                     g[G_R] += wgt * gR[i];
                     g[G_G] += wgt * gG[i];
                     g[G_B] += wgt * gB[i];
-                    g[G_Z] += wgt * gD[i];
+                    g[G_Z] += wgt * gz;
                     if (araw <= amax) {
                         // gpw = dL/dpw with pw = -d^T Q d / 2 (natural log).  The warp sums
                         // the raw moments; the per-Gaussian factors are applied once after
@@ -339,28 +394,34 @@ size_t bwd_smem(int depth) {
     return (size_t)depth * (3 * sizeof(float4) + sizeof(float2) + sizeof(uint32_t));
 }
 
-template <int TW, int TH>
-gs_status configure_one(gs_workspace *ws) {
-    int depth = ws->cfg.batch_depth;
-    cudaError_t e;
-    e = cudaFuncSetAttribute(k_raster_fwd<TW, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)fwd_smem(256));
+template <int TW, int TH, bool VAR>
+cudaError_t configure_variant(gs_workspace *ws, int &grid_f, int &grid_b) {
+    constexpr int PPT = ppt_bwd<TW, TH>();
+    const int depth = ws->cfg.batch_depth;
+    cudaError_t e = cudaFuncSetAttribute(k_raster_fwd<TW, TH, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)fwd_smem(256));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_raster_bwd<TW, TH, ppt_bwd<TW, TH>()>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(k_raster_bwd<TW, TH, PPT, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)bwd_smem(256));
     int occ_f = 0, occ_b = 0;
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_f, k_raster_fwd<TW, TH>, TW * TH,
-                                                          fwd_smem(depth));
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_f, k_raster_fwd<TW, TH, VAR>, TW * TH, fwd_smem(depth));
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, k_raster_bwd<TW, TH, ppt_bwd<TW, TH>()>, TW * TH / ppt_bwd<TW, TH>(),
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, k_raster_bwd<TW, TH, PPT, VAR>, TW * TH / PPT,
                                                           bwd_smem(depth));
+    grid_f = std::max(1, occ_f) * ws->num_sms;
+    grid_b = std::max(1, occ_b) * ws->num_sms;
+    return e;
+}
+
+template <int TW, int TH>
+gs_status configure_one(gs_workspace *ws) {
+    cudaError_t e = configure_variant<TW, TH, false>(ws, ws->raster_grid_fwd, ws->raster_grid_bwd);
+    if (e == cudaSuccess) e = configure_variant<TW, TH, true>(ws, ws->raster_grid_fwd_var, ws->raster_grid_bwd_var);
     if (e != cudaSuccess) {
         set_last_error(std::string("raster_configure: ") + cudaGetErrorString(e));
         return GS_ERR_CUDA;
     }
-    ws->raster_grid_fwd = std::max(1, occ_f) * ws->num_sms;
-    ws->raster_grid_bwd = std::max(1, occ_b) * ws->num_sms;
     return GS_OK;
 }
 
@@ -384,14 +445,21 @@ template <int TW, int TH>
 gs_status run_fwd(gs_workspace *ws, RasterArgs A, cudaStream_t s) {
     StageTimer timer(ws, GS_STAGE_RASTER_FWD, s);
     ++ws->kernel_launches;
-    k_raster_fwd<TW, TH><<<ws->raster_grid_fwd, TW * TH, fwd_smem(A.depth), s>>>(A);
+    if (A.mean_out)
+        k_raster_fwd<TW, TH, true><<<ws->raster_grid_fwd_var, TW * TH, fwd_smem(A.depth), s>>>(A);
+    else
+        k_raster_fwd<TW, TH, false><<<ws->raster_grid_fwd, TW * TH, fwd_smem(A.depth), s>>>(A);
     return check_launch("raster_fwd");
 }
 template <int TW, int TH>
 gs_status run_bwd(gs_workspace *ws, RasterArgs A, cudaStream_t s) {
+    constexpr int PPT = ppt_bwd<TW, TH>();
     StageTimer timer(ws, GS_STAGE_RASTER_BWD, s);
     ++ws->kernel_launches;
-    k_raster_bwd<TW, TH, ppt_bwd<TW, TH>()><<<ws->raster_grid_bwd, TW * TH / ppt_bwd<TW, TH>(), bwd_smem(A.depth), s>>>(A);
+    if (A.vstat)
+        k_raster_bwd<TW, TH, PPT, true><<<ws->raster_grid_bwd_var, TW * TH / PPT, bwd_smem(A.depth), s>>>(A);
+    else
+        k_raster_bwd<TW, TH, PPT, false><<<ws->raster_grid_bwd, TW * TH / PPT, bwd_smem(A.depth), s>>>(A);
     return check_launch("raster_bwd");
 }
 
@@ -406,12 +474,18 @@ gs_status raster_configure(gs_workspace *ws) {
     return GS_ERR_INVALID_ARG;
 }
 
-gs_status launch_raster_fwd(gs_workspace *ws, float *rgb, float *depth, float *alpha, cudaStream_t s) {
+gs_status launch_raster_fwd(gs_workspace *ws, float *rgb, float *depth, float *alpha, float *mean,
+                            float *var, cudaStream_t s) {
     RasterArgs A = make_args(ws);
     A.counter = &ws->st->fwd_counter;
     A.rgb = rgb;
     A.depth_out = depth;
     A.alpha_out = alpha;
+    if (mean) {
+        A.mean_out = mean;
+        A.var_out = var;
+        A.vstat = ws->vstat;
+    }
     cudaMemsetAsync(A.counter, 0, sizeof(uint32_t), s);
     int tw = ws->cfg.tile_w, th = ws->cfg.tile_h;
     if (tw == 8 && th == 8) return run_fwd<8, 8>(ws, A, s);
@@ -421,12 +495,18 @@ gs_status launch_raster_fwd(gs_workspace *ws, float *rgb, float *depth, float *a
 }
 
 gs_status launch_raster_bwd(gs_workspace *ws, const float *dL_drgb, const float *dL_ddepth,
-                            const float *dL_dalpha, cudaStream_t s) {
+                            const float *dL_dalpha, bool var, const float *dL_dmean, const float *dL_dvar,
+                            cudaStream_t s) {
     RasterArgs A = make_args(ws);
     A.counter = &ws->st->bwd_counter;
     A.dL_drgb = dL_drgb;
     A.dL_ddepth = dL_ddepth;
     A.dL_dalpha = dL_dalpha;
+    if (var) {
+        A.vstat = ws->vstat;
+        A.dL_dmean = dL_dmean;
+        A.dL_dvar = dL_dvar;
+    }
     A.g2d = ws->g2d;
     {
         StageTimer timer(ws, GS_STAGE_ZERO_GRAD, s);

@@ -23,10 +23,12 @@ GS_OK, GS_ERR_INVALID_ARG, GS_ERR_CAPACITY, GS_ERR_CUDA, GS_ERR_STATE = range(5)
 GS_MAX_VIEWS = 64
 GS_MAX_SUBMAPS = 64
 # gs_workspace_copy buffer ids
-BUF_RECORDS, BUF_PAIR_KEYS, BUF_RECTS, BUF_INST_TILES, BUF_INST_PAIRS, BUF_RANGES, BUF_LAST, BUF_TFIN, BUF_G2D = range(9)
+(BUF_RECORDS, BUF_PAIR_KEYS, BUF_RECTS, BUF_INST_TILES, BUF_INST_PAIRS, BUF_RANGES, BUF_LAST, BUF_TFIN, BUF_G2D,
+ BUF_VSTAT) = range(10)
 
 EXPORTED = ("gs_config_default", "gs_workspace_create", "gs_workspace_destroy", "gs_project",
-            "gs_bin_sort", "gs_render_fwd", "gs_depth_loss", "gs_image_l1", "gs_render_bwd",
+            "gs_bin_sort", "gs_render_fwd", "gs_render_fwd_var", "gs_depth_loss", "gs_depth_loss_var",
+            "gs_image_l1", "gs_render_bwd", "gs_render_bwd_var",
             "gs_workspace_status", "gs_workspace_info", "gs_workspace_copy", "gs_workspace_set_profiling",
             "gs_workspace_stage_ms", "gs_image_l1_noalloc", "gs_status_string", "gs_last_error")
 IMAGE_L1_NOALLOC_MAX = 1024 * 65536  # GS_IMAGE_L1_NOALLOC_BLOCKS * GS_IMAGE_L1_NOALLOC_CHUNK
@@ -90,9 +92,12 @@ def lib() -> ctypes.CDLL:
     L.gs_project.argtypes = [P, ctypes.POINTER(GsGaussians), P, P]
     L.gs_bin_sort.argtypes = [P, P]
     L.gs_render_fwd.argtypes = [P, P, P, P, P]
+    L.gs_render_fwd_var.argtypes = [P, P, P, P, P, P, P]
     L.gs_depth_loss.argtypes = [P, P, P, P, i64, P, P, P]
+    L.gs_depth_loss_var.argtypes = [P, P, P, P, P, i64, P, P, P, P]
     L.gs_image_l1.argtypes = [P, P, P, P, P, P]
     L.gs_render_bwd.argtypes = [P, ctypes.POINTER(GsGaussians), P, P, P, P, ctypes.POINTER(GsGrads), P]
+    L.gs_render_bwd_var.argtypes = [P, ctypes.POINTER(GsGaussians), P, P, P, P, P, P, ctypes.POINTER(GsGrads), P]
     L.gs_workspace_status.argtypes = [P, P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
     L.gs_workspace_info.argtypes = [P, ctypes.POINTER(ctypes.c_int64), i32]
     L.gs_workspace_copy.argtypes = [P, i32, P, ctypes.POINTER(ctypes.c_int64), P]
@@ -103,8 +108,9 @@ def lib() -> ctypes.CDLL:
     L.gs_status_string.restype = ctypes.c_char_p
     L.gs_last_error.argtypes = []
     L.gs_last_error.restype = ctypes.c_char_p
-    for name in ("gs_workspace_create", "gs_project", "gs_bin_sort", "gs_render_fwd", "gs_depth_loss",
-                 "gs_image_l1", "gs_render_bwd", "gs_workspace_status", "gs_workspace_info",
+    for name in ("gs_workspace_create", "gs_project", "gs_bin_sort", "gs_render_fwd", "gs_render_fwd_var",
+                 "gs_depth_loss", "gs_depth_loss_var", "gs_image_l1", "gs_render_bwd", "gs_render_bwd_var",
+                 "gs_workspace_status", "gs_workspace_info",
                  "gs_workspace_copy", "gs_workspace_set_profiling", "gs_workspace_stage_ms",
                  "gs_image_l1_noalloc"):
         getattr(L, name).restype = i32
@@ -161,8 +167,17 @@ def gs_render_fwd(ws, rgb, depth, alpha, stream):
     _check(lib().gs_render_fwd(ws, rgb, depth, alpha, stream), "gs_render_fwd")
 
 
+def gs_render_fwd_var(ws, rgb, depth, alpha, depth_mean, depth_var, stream):
+    _check(lib().gs_render_fwd_var(ws, rgb, depth, alpha, depth_mean, depth_var, stream), "gs_render_fwd_var")
+
+
 def gs_depth_loss(ws, depth, alpha, lidar, n_pts, loss, dL_ddepth, stream):
     _check(lib().gs_depth_loss(ws, depth, alpha, lidar, int(n_pts), loss, dL_ddepth, stream), "gs_depth_loss")
+
+
+def gs_depth_loss_var(ws, alpha, depth_mean, depth_var, lidar, n_pts, loss, dL_dmean, dL_dvar, stream):
+    _check(lib().gs_depth_loss_var(ws, alpha, depth_mean, depth_var, lidar, int(n_pts), loss, dL_dmean, dL_dvar,
+                                   stream), "gs_depth_loss_var")
 
 
 def gs_image_l1(ws, rgb, target, loss, dL_drgb, stream):
@@ -177,6 +192,12 @@ def gs_image_l1_noalloc(rgb, target, n, loss, dL_drgb, stream):
 def gs_render_bwd(ws, g: GsGaussians, cams_dev, dL_drgb, dL_ddepth, dL_dalpha, grads: GsGrads, stream):
     _check(lib().gs_render_bwd(ws, ctypes.byref(g), cams_dev, dL_drgb, dL_ddepth, dL_dalpha,
                                ctypes.byref(grads), stream), "gs_render_bwd")
+
+
+def gs_render_bwd_var(ws, g: GsGaussians, cams_dev, dL_drgb, dL_ddepth, dL_dalpha, dL_dmean, dL_dvar,
+                      grads: GsGrads, stream):
+    _check(lib().gs_render_bwd_var(ws, ctypes.byref(g), cams_dev, dL_drgb, dL_ddepth, dL_dalpha, dL_dmean, dL_dvar,
+                                   ctypes.byref(grads), stream), "gs_render_bwd_var")
 
 
 def gs_workspace_status(ws, stream):
@@ -294,23 +315,29 @@ class Renderer:
         return GsGaussians(means.data_ptr(), log_scales.data_ptr(), quats.data_ptr(),
                            opacity_logits.data_ptr(), sh.data_ptr(), means.shape[0])
 
-    def forward(self, means, log_scales, quats, opacity_logits, sh, stream=None, outputs=None):
-        """project -> bin/sort -> rasterise. Returns (rgb [3*N_pix], depth [N_pix], alpha [N_pix])."""
+    def forward(self, means, log_scales, quats, opacity_logits, sh, stream=None, outputs=None, var=False):
+        """project -> bin/sort -> rasterise. Returns (rgb [3*N_pix], depth [N_pix], alpha [N_pix]), plus
+        the depth mean and variance [N_pix] each when ``var``."""
         torch = self.torch
         s = _stream(stream)
         g = self.gaussians(means, log_scales, quats, opacity_logits, sh)
         if outputs is None:
-            outputs = (torch.empty(3 * self.n_pix, device=self.device), torch.empty(self.n_pix, device=self.device),
-                       torch.empty(self.n_pix, device=self.device))
-        rgb, depth, alpha = outputs
+            outputs = tuple([torch.empty(3 * self.n_pix, device=self.device)] +
+                            [torch.empty(self.n_pix, device=self.device) for _ in range(4 if var else 2)])
         gs_project(self.ws, g, _ptr(self.cams_dev), s)
         gs_bin_sort(self.ws, s)
+        if var:
+            rgb, depth, alpha, mean, dvar = outputs
+            gs_render_fwd_var(self.ws, _ptr(rgb), _ptr(depth), _ptr(alpha), _ptr(mean), _ptr(dvar), s)
+            return rgb, depth, alpha, mean, dvar
+        rgb, depth, alpha = outputs
         gs_render_fwd(self.ws, _ptr(rgb), _ptr(depth), _ptr(alpha), s)
         return rgb, depth, alpha
 
     def backward(self, means, log_scales, quats, opacity_logits, sh, dL_drgb, dL_ddepth, dL_dalpha=None,
-                 grads=None, stream=None, pose=True, densify=True):
-        """Accumulates gradients into ``grads`` (dict of tensors; allocated zeroed if None)."""
+                 grads=None, stream=None, pose=True, densify=True, var=False, dL_dmean=None, dL_dvar=None):
+        """Accumulates gradients into ``grads`` (dict of tensors; allocated zeroed if None).  With ``var``
+        the adjoints of the depth mean and variance are taken too (after ``forward(var=True)``)."""
         torch = self.torch
         s = _stream(stream)
         g = self.gaussians(means, log_scales, quats, opacity_logits, sh)
@@ -328,13 +355,26 @@ class Renderer:
                      grads["pose"].data_ptr() if "pose" in grads else None,
                      grads["densify_acc"].data_ptr() if "densify_acc" in grads else None,
                      grads["densify_cnt"].data_ptr() if "densify_cnt" in grads else None)
-        gs_render_bwd(self.ws, g, _ptr(self.cams_dev), _ptr(dL_drgb), _ptr(dL_ddepth), _ptr(dL_dalpha), gg, s)
+        if var:
+            gs_render_bwd_var(self.ws, g, _ptr(self.cams_dev), _ptr(dL_drgb), _ptr(dL_ddepth), _ptr(dL_dalpha),
+                              _ptr(dL_dmean), _ptr(dL_dvar), gg, s)
+        else:
+            gs_render_bwd(self.ws, g, _ptr(self.cams_dev), _ptr(dL_drgb), _ptr(dL_ddepth), _ptr(dL_dalpha), gg, s)
         return grads
 
     def depth_loss(self, depth, alpha, lidar, dL_ddepth=None, stream=None):
         loss = self.torch.zeros(1, device=self.device)
         gs_depth_loss(self.ws, _ptr(depth), _ptr(alpha), _ptr(lidar), lidar.shape[0], _ptr(loss),
                       _ptr(dL_ddepth), _stream(stream))
+        return loss
+
+    def depth_loss_var(self, alpha, mean, var, lidar, grads=None, stream=None):
+        """Eq. (7) with the rendered variance; ``grads`` = (d_mean, d_var) tensors (each may be None)
+        accumulated in place."""
+        loss = self.torch.zeros(1, device=self.device)
+        gm, gv = grads if grads is not None else (None, None)
+        gs_depth_loss_var(self.ws, _ptr(alpha), _ptr(mean), _ptr(var), _ptr(lidar), lidar.shape[0],
+                          _ptr(loss), _ptr(gm), _ptr(gv), _stream(stream))
         return loss
 
     def image_l1(self, rgb, target, dL_drgb=None, stream=None):

@@ -33,19 +33,26 @@ def gpu_config(G, ocfg: O.Config, **kw):
                                ext_abs_pad=ocfg.ext_abs_pad, **kw)
 
 
-def run_gpu(sc, ocfg: O.Config, gC=None, gD=None, gA=None, depth=256, inst_capacity=None, **kw):
+def run_gpu(sc, ocfg: O.Config, gC=None, gD=None, gA=None, depth=256, inst_capacity=None, var=False,
+            gmean=None, gvar=None, **kw):
     """Forward (and backward when upstream gradients are given) on cuda:0.
-    Returns a dict of numpy arrays."""
+    With ``var`` the forward and backward with the depth mean and variance
+    are used (upstream gmean, gvar for the latter).  Returns a dict of numpy
+    arrays."""
     from paper_2510_26358_gb300 import gsraster as G
     torch, dev = torch_dev()
     cfg = gpu_config(G, ocfg, batch_depth=depth, **kw)
     r = G.Renderer(sc.cameras, sc.submap_offsets, sc.sh_degree, config=cfg,
                    inst_capacity=inst_capacity or (1 << 22))
     P = params_to_dev(sc)
-    rgb, dep, alp = r.forward(*P)
+    fw = r.forward(*P, var=var)
+    rgb, dep, alp = fw[:3]
     st, n_inst, n_vis = r.status()
     out = dict(status=st, n_inst=n_inst, n_vis=n_vis, rgb=rgb.cpu().numpy(), depth=dep.cpu().numpy(),
                alpha=alp.cpu().numpy())
+    if var:
+        out["mean"], out["var"] = fw[3].cpu().numpy(), fw[4].cpu().numpy()
+        out["vstat"] = r.buffer(G.BUF_VSTAT, torch.float32).cpu().numpy().reshape(-1, 4)
     out["rec"] = r.buffer(G.BUF_RECORDS, torch.float32).cpu().numpy().reshape(-1, 12)
     out["pkey"] = r.buffer(G.BUF_PAIR_KEYS, torch.int32).cpu().numpy().view(np.uint32)
     out["rect"] = r.buffer(G.BUF_RECTS, torch.int16).cpu().numpy().reshape(-1, 4)
@@ -57,7 +64,8 @@ def run_gpu(sc, ocfg: O.Config, gC=None, gD=None, gA=None, depth=256, inst_capac
     out["tfin"] = r.buffer(G.BUF_TFIN, torch.float32).cpu().numpy()
     if gC is not None:
         t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev)
-        grads = r.backward(*P, t(gC), t(gD), t(gA) if gA is not None else None)
+        o = lambda a: t(a) if a is not None else None
+        grads = r.backward(*P, t(gC), t(gD), o(gA), var=var, dL_dmean=o(gmean), dL_dvar=o(gvar))
         torch.cuda.synchronize()
         for k, v in grads.items():
             out["g_" + k] = v.cpu().numpy()

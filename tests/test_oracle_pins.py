@@ -14,8 +14,9 @@ sign, a transposed operand or a wrong index in the oracle fails at least one:
   backward                  central differences of every parameter type and
                             every pose twist; translation identity
   losses (Eqs. 6-7)         KL by numerical integration; FD of both losses
-  rendered depth variance   two-fragment closed form; zero for equal depths;
-                            Popoviciu bound; KL with the rendered variance by
+  rendered depth mean/var   two-fragment closed form; zero variance for equal
+                            depths; Popoviciu bound; invariance to a common
+                            depth shift; KL with the rendered variance by
                             quadrature, reduced to the fixed-sigma mode, and
                             FD through the whole render
 """
@@ -475,31 +476,30 @@ def test_image_l1_gradient():
 # rendered depth distribution: Eq. (7) with a predicted variance
 # ---------------------------------------------------------------------------
 
-def _moments(P, cams, cfg=CFG):
+def _dist(P, cams, cfg=CFG):
     rec, keys, vals, ranges, out = O.forward(P, cams, cfg)
-    m1, m2 = O.render_moments(P, cams, cfg, rec, vals, ranges)
-    return rec, vals, ranges, out, m1, m2
+    mean, var = O.render_depth_dist(P, cams, cfg, rec, vals, ranges)
+    return rec, vals, ranges, out, mean, var
 
 
 def test_two_fragment_variance_closed_form():
-    # two opaque-ish discs at z1 < z2: w1 = a1, w2 = a2 (1 - a1); the weighted
-    # variance of {z1, z2} is w1 w2 (z2 - z1)^2 / (w1 + w2)^2
+    # two discs at z1 < z2 with weights w1, w2: mean (w1 z1 + w2 z2) / A and
+    # variance w1 w2 (z2 - z1)^2 / A^2
     cam = _cam(16, 16, 20.0)
     a1, a2, z1, z2 = 0.6, 0.8, 1.3, 1.75
     P = _params([[0, 0, z1], [0, 0, z2]], [[math.log(0.5)] * 3] * 2, [[1, 0, 0, 0]] * 2,
                 [math.log(a1 / (1 - a1)), math.log(a2 / (1 - a2))], [[1.0, 1.0, 1.0]] * 2)
-    rec, vals, ranges, out, m1, m2 = _moments(P, [cam])
+    rec, vals, ranges, out, mean, var = _dist(P, [cam])
     pix = 8 * 16 + 8
-    A = out["alpha"][pix]
+    A, D = out["alpha"][pix], out["depth"][pix]
     # the two weights from alpha and depth: D = w1 z1 + w2 z2, A = w1 + w2
-    D = out["depth"][pix]
     w2 = (D - z1 * A) / (z2 - z1)
     w1 = A - w2
     assert w1 > 0.5 and w2 > 0.2
-    var = m2[pix] / A - (m1[pix] / A) ** 2
-    assert var == pytest.approx(w1 * w2 * (z2 - z1) ** 2 / A ** 2, rel=1e-12)
-    # the reference depth is the first fragment's: m1 = w2 (z2 - z1)
-    assert m1[pix] == pytest.approx(w2 * (z2 - z1), rel=1e-12)
+    # w1 is the disc's own alpha at the pixel centre; w2 = alpha_2 (1 - w1)
+    assert w1 == pytest.approx(a1 * math.exp(-0.5 * 0.5 / ((20 * 0.5 / z1) ** 2 + 0.3)), rel=1e-6)
+    assert mean[pix] == pytest.approx((w1 * z1 + w2 * z2) / A, rel=1e-13)
+    assert var[pix] == pytest.approx(w1 * w2 * (z2 - z1) ** 2 / A ** 2, rel=1e-12)
 
 
 def test_equal_depth_fragments_have_zero_variance():
@@ -507,44 +507,59 @@ def test_equal_depth_fragments_have_zero_variance():
     n = 4
     P = _params([[0.01 * i, -0.01 * i, 1.5] for i in range(n)], [[math.log(0.3)] * 3] * n,
                 [[1, 0, 0, 0]] * n, [0.5] * n, [[1.0, 1.0, 1.0]] * n)
-    rec, vals, ranges, out, m1, m2 = _moments(P, [cam])
+    rec, vals, ranges, out, mean, var = _dist(P, [cam])
     assert (out["nblend"] >= 3).any()
-    assert np.array_equal(m1, np.zeros_like(m1)) and np.array_equal(m2, np.zeros_like(m2))
+    assert np.abs(var).max() < 1e-28
+    m = out["alpha"] > 0
+    assert np.allclose(mean[m], 1.5, rtol=0, atol=1e-14) and np.all(mean[~m] == 0)
 
 
 def test_rendered_variance_bounds():
-    # 0 <= variance <= (z_max - z_min)^2 / 4 (Popoviciu), and m1 = D - c A with
-    # c inside the blended depth range
+    # 0 <= variance <= (z_max - z_min)^2 / 4 (Popoviciu); the mean lies in the
+    # blended depth range
     sc = S.random_box_scene(400, 48, 40, 45.0, seed=5)
     P = O.Params.from_scene(sc)
     cams = O.as_float32_cameras(sc.cameras)
-    rec, vals, ranges, out, m1, m2 = _moments(P, cams)
+    rec, vals, ranges, out, mean, var = _dist(P, cams)
     zs = rec[rec[:, O.C_VIS] > 0, O.C_Z]
     m = out["alpha"] > 0
-    A = out["alpha"][m]
-    var = m2[m] / A - (m1[m] / A) ** 2
-    assert var.min() >= -1e-12
-    assert var.max() <= (zs.max() - zs.min()) ** 2 / 4 + 1e-12
-    c = (out["depth"][m] - m1[m]) / A
-    assert c.min() >= zs.min() - 1e-9 and c.max() <= zs.max() + 1e-9
-    assert (var > 1e-4).sum() > 100
+    assert var[m].min() >= 0.0
+    assert var[m].max() <= (zs.max() - zs.min()) ** 2 / 4 + 1e-12
+    assert mean[m].min() >= zs.min() - 1e-12 and mean[m].max() <= zs.max() + 1e-12
+    assert np.allclose(mean[m], out["depth"][m] / out["alpha"][m], rtol=1e-12)
+    assert (var[m] > 1e-4).sum() > 100
+
+
+def test_variance_is_shift_free():
+    # moving every Gaussian and the camera by the same offset along the view
+    # axis moves the depths, not their spread: var is unchanged, the mean
+    # moves by the offset
+    sc = S.random_box_scene(300, 48, 40, 45.0, seed=6)
+    P = O.Params.from_scene(sc)
+    cams = O.as_float32_cameras(sc.cameras)
+    rec, vals, ranges, out, mean, var = _dist(P, cams)
+    P2 = P.copy()
+    P2.means[:, 2] += 3.0
+    cams2 = copy.deepcopy(cams)
+    cams2[0].T_cw = cams[0].T_cw.copy()
+    cams2[0].T_cw[2, 3] -= 3.0
+    rec2, vals2, ranges2, out2, mean2, var2 = _dist(P2, cams2)
+    assert np.array_equal(out["nblend"], out2["nblend"])
+    assert np.allclose(var2, var, rtol=1e-9, atol=1e-12)
+    assert np.allclose(mean2, mean, rtol=1e-12, atol=1e-12)
 
 
 def _var_loss_inputs(rng, n_pts=300):
-    # per-pixel (alpha, mean, spread) and LiDAR returns whose depth lies within
-    # a few decimetres of the rendered mean where they land, as in tracking
+    # per-pixel (alpha, mean, variance) and LiDAR returns whose depth lies
+    # within a few decimetres of the rendered mean where they land
     cams = [_cam(20, 16, 20.0), _cam(12, 10, 15.0)]
     P = O.Params(np.zeros((1, 3)), np.zeros((1, 3)), np.ones((1, 4)), np.zeros(1),
                  np.zeros((1, 1, 3)), 0, np.array([0, 1]))
     npx = 20 * 16 + 12 * 10
     alpha = rng.uniform(0.05, 1, npx)
     alpha[rng.random(npx) < 0.2] = 0.0
-    mu = rng.uniform(1, 5, npx)
-    depth = mu * alpha
-    c = mu + rng.uniform(-0.3, 0.1, npx)
-    sd = rng.uniform(0.0, 0.2, npx)
-    m1 = alpha * (mu - c)
-    m2 = alpha * (sd ** 2 + (mu - c) ** 2)
+    mean = np.where(alpha > 0, rng.uniform(1, 5, npx), 0.0)
+    var = np.where(alpha > 0, rng.uniform(0.0, 0.2, npx) ** 2, 0.0)
     vw = rng.integers(0, 2, n_pts)
     u, v = rng.uniform(-2, 22, n_pts), rng.uniform(-2, 18, n_pts)
     z = rng.uniform(0.1, 6, n_pts)
@@ -552,23 +567,20 @@ def _var_loss_inputs(rng, n_pts=300):
         cm = cams[vw[i]]
         if 0 <= u[i] < cm.width and 0 <= v[i] < cm.height:
             pix = (0 if vw[i] == 0 else 320) + int(v[i]) * cm.width + int(u[i])
-            z[i] = mu[pix] + rng.normal(0, 0.2)
+            z[i] = mean[pix] + rng.normal(0, 0.2)
     lid = np.stack([u, v, z, vw], 1)
-    return P, cams, depth, alpha, m1, m2, lid
+    return P, cams, alpha, mean, var, lid
 
 
 def test_variance_kl_reduces_to_fixed_sigma():
     # zero rendered variance: sigma_u = sigma_U, so the loss is the fixed-sigma
-    # KL mode evaluated on the normalised depth D / A
+    # KL mode evaluated on the mean depth
     rng = np.random.default_rng(4)
-    P, cams, depth, alpha, m1, m2, lid = _var_loss_inputs(rng)
-    z = np.zeros_like(depth)
-    lv = O.depth_loss_var(P, cams, CFG, depth, alpha, z, z, lid, 0.05, 0.08, 0.7)
-    dn = np.where(alpha > 0, depth / np.where(alpha > 0, alpha, 1), 0.0)
-    lk, gk, nk = O.depth_loss(P, cams, CFG, dn, alpha, lid, 1, 0.05, 0.08, 0.7)
-    assert lv[0] == pytest.approx(lk, rel=1e-13) and lv[5] == nk
-    m = alpha > 0
-    assert np.allclose(lv[1][m] * alpha[m], gk[m], rtol=1e-12, atol=1e-15)
+    P, cams, alpha, mean, var, lid = _var_loss_inputs(rng)
+    lv = O.depth_loss_var(P, cams, CFG, alpha, mean, np.zeros_like(var), lid, 0.05, 0.08, 0.7)
+    lk, gk, nk = O.depth_loss(P, cams, CFG, mean, alpha, lid, 1, 0.05, 0.08, 0.7)
+    assert lv[0] == pytest.approx(lk, rel=1e-13) and lv[3] == nk
+    assert np.allclose(lv[1], gk, rtol=1e-12, atol=1e-15)
 
 
 def test_variance_kl_matches_integration():
@@ -577,12 +589,12 @@ def test_variance_kl_matches_integration():
     cams = [_cam(4, 4, 5.0)]
     P = O.Params(np.zeros((1, 3)), np.zeros((1, 3)), np.ones((1, 4)), np.zeros(1),
                  np.zeros((1, 1, 3)), 0, np.array([0, 1]))
-    A, mu, c, sd, z = 0.7, 3.2, 3.05, 0.11, 3.3
+    A, mu, sd, z = 0.7, 3.2, 0.11, 3.3
     sL, sU = float(np.float32(0.05)), float(np.float32(0.04))
-    depth = np.full(16, 0.0); alpha = np.zeros(16); m1 = np.zeros(16); m2 = np.zeros(16)
-    depth[5], alpha[5], m1[5], m2[5] = A * mu, A, A * (mu - c), A * (sd ** 2 + (mu - c) ** 2)
+    alpha, mean, var = np.zeros(16), np.zeros(16), np.zeros(16)
+    alpha[5], mean[5], var[5] = A, mu, sd ** 2
     lid = np.array([[1.5, 1.5, z, 0]])
-    loss = O.depth_loss_var(P, cams, CFG, depth, alpha, m1, m2, lid, sL, sU, 1.0)[0]
+    loss = O.depth_loss_var(P, cams, CFG, alpha, mean, var, lid, sL, sU, 1.0)[0]
     s2 = math.sqrt(sd ** 2 + sU ** 2)
     p = lambda x: math.exp(-0.5 * ((x - z) / sL) ** 2) / (sL * math.sqrt(2 * math.pi))
     lq = lambda x: -0.5 * ((x - mu) / s2) ** 2 - math.log(s2 * math.sqrt(2 * math.pi))
@@ -593,48 +605,46 @@ def test_variance_kl_matches_integration():
 
 def test_variance_kl_gradient_fd():
     rng = np.random.default_rng(6)
-    P, cams, depth, alpha, m1, m2, lid = _var_loss_inputs(rng)
+    P, cams, alpha, mean, var, lid = _var_loss_inputs(rng)
     args = (0.05, 0.08, 0.7)
-    loss, gD, gA, gM1, gM2, nv = O.depth_loss_var(P, cams, CFG, depth, alpha, m1, m2, lid, *args)
+    loss, gm, gv, nv = O.depth_loss_var(P, cams, CFG, alpha, mean, var, lid, *args)
     assert nv > 50
     h = 1e-7
-    ins = [depth, alpha, m1, m2]
-    for k, g in enumerate((gD, gA, gM1, gM2)):
+    ins = [mean, var]
+    for k, g in enumerate((gm, gv)):
         for pix in rng.choice(np.nonzero(g)[0], 8, replace=False):
             xp = [x.copy() for x in ins]
             xm = [x.copy() for x in ins]
             xp[k][pix] += h
             xm[k][pix] -= h
-            fd = (O.depth_loss_var(P, cams, CFG, *xp, lid, *args)[0] -
-                  O.depth_loss_var(P, cams, CFG, *xm, lid, *args)[0]) / (2 * h)
+            fd = (O.depth_loss_var(P, cams, CFG, alpha, *xp, lid, *args)[0] -
+                  O.depth_loss_var(P, cams, CFG, alpha, *xm, lid, *args)[0]) / (2 * h)
             assert fd == pytest.approx(g[pix], rel=1e-5, abs=1e-8), (k, pix)
 
 
 def test_variance_kl_chain_fd():
-    # loss(render(params)) with the rendered variance: the adjoint through the
-    # depth moments against central differences of every parameter type and
-    # every pose twist
+    # loss(render(params)) with the rendered mean and variance: the adjoint
+    # against central differences of every parameter type and every pose twist
     sc = S.random_box_scene(250, 48, 40, 45.0, seed=12, sh_degree=1)
     P = O.Params.from_scene(sc)
     cams = O.as_float32_cameras(sc.cameras)
     rng = np.random.default_rng(8)
-    rec, vals, ranges, out, m1, m2 = _moments(P, cams)
+    rec, vals, ranges, out, mean, var = _dist(P, cams)
     hit = np.nonzero(out["alpha"] > 0.2)[0]
     pix = rng.choice(hit, 200, replace=False)
-    mu = out["depth"][pix] / out["alpha"][pix]
-    lid = np.stack([pix % 48 + 0.5, pix // 48 + 0.5, mu + rng.normal(0, 0.1, len(pix)),
+    lid = np.stack([pix % 48 + 0.5, pix // 48 + 0.5, mean[pix] + rng.normal(0, 0.1, len(pix)),
                     np.zeros(len(pix))], 1)
     args = (0.05, 0.03, 1.0)
 
     def loss_of(Pp, cc):
         r, k, v, rg, o = O.forward(Pp, cc, CFG)
-        a, b = O.render_moments(Pp, cc, CFG, r, v, rg)
-        return O.depth_loss_var(Pp, cc, CFG, o["depth"], o["alpha"], a, b, lid, *args)[0], o
+        a, b = O.render_depth_dist(Pp, cc, CFG, r, v, rg)
+        return O.depth_loss_var(Pp, cc, CFG, o["alpha"], a, b, lid, *args)[0], o
 
-    L0, gD, gA, gM1, gM2, nv = O.depth_loss_var(P, cams, CFG, out["depth"], out["alpha"], m1, m2, lid, *args)
+    L0, gm, gv, nv = O.depth_loss_var(P, cams, CFG, out["alpha"], mean, var, lid, *args)
     assert nv == len(pix)
     z = np.zeros(3 * 48 * 40)
-    g = O.render_bwd(P, cams, CFG, rec, vals, ranges, z, gD, gA, gM1, gM2)
+    g = O.render_bwd(P, cams, CFG, rec, vals, ranges, z, np.zeros(48 * 40), None, gm, gv)
     h = 1e-7
     checked = 0
     vis = np.unique(rec[rec[:, O.C_VIS] > 0, O.C_GAUSS].astype(int))
