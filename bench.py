@@ -177,6 +177,16 @@ def measured_traffic(kernel: str, workload: str, config: str):
     return int(rec["dram_bytes_per_launch"]), rec.get("command", "")
 
 
+# FP32 operations (an FMA counts 2) the backward needs per (pixel, fragment)
+# evaluation, from the adjoint's steps: offset to the mean 2, exponent through
+# the Cholesky factor 8, alpha clamp 1, T recovery 2, weight 1, h 8, dL/dalpha
+# 3, suffix sum 2, colour and depth gradients 8, dL/dpw 1, opacity gradient 1,
+# conic and mean moments 12 = 49 (plus two MUFU operations, ex2 and rcp).
+FLOPS_PER_FRAGMENT_BWD = 49
+# extra per evaluation for the depth mean and variance adjoints: dz 1, h 4, dL/dz 4
+FLOPS_PER_FRAGMENT_VAR = 9
+
+
 def job_throughput(pix_per_rank: int, ms: float, world: int) -> float:
     """Whole-job Mpix/s: every rank renders its own replica in `ms`."""
     return pix_per_rank * world / (ms * 1e-3) / 1e6
@@ -584,11 +594,28 @@ def main():
         traffic, traffic_note = None, "the ncu capture covers the kernel without the depth variance"
     else:
         traffic, traffic_note = measured_traffic("k_raster_bwd", sc.name, f"{tw}x{th}/{args.depth}")
-    roofline = {"bound": "hbm", "kernel": "k_raster_bwd",
-                "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                "traffic": traffic, "traffic_source": traffic_note,
-                "algorithmic_bytes": int(alg_bytes), "ms": bwd_ms,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6800 GB/s"}
+    roofline_hbm = {"bound": "hbm", "kernel": "k_raster_bwd",
+                    "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                    "traffic": traffic, "traffic_source": traffic_note,
+                    "algorithmic_bytes": int(alg_bytes), "ms": bwd_ms,
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6800 GB/s"}
+    # The raster backward is bound by FP32 arithmetic and issue, not DRAM (ncu:
+    # 77 % issue, ALU + FMA pipes busiest, DRAM 2 %): its roofline is the
+    # fragment rate.  Algorithmic work = (pixel, fragment) evaluations the
+    # adjoint needs, sum over pixels of the list count up to the last blended
+    # fragment, times FLOPS_PER_FRAGMENT_BWD; peak = SMs x 128 FP32 lanes x 2
+    # (FMA) x the sampled maximum SM clock.
+    n_frag = int(step.r.buffer(G.BUF_LAST, torch.int32).to(torch.int64).sum().item())
+    flops = n_frag * (FLOPS_PER_FRAGMENT_BWD + (FLOPS_PER_FRAGMENT_VAR if args.depth_loss == "kl-var" else 0))
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    f_max = (clocks or {}).get("sm_max_mhz") or 2070.0
+    alu_peak = n_sm * 128 * 2 * f_max * 1e6 / 1e12
+    alu_achieved = flops / (bwd_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": "k_raster_bwd", "achieved": alu_achieved, "peak": alu_peak,
+                "unit": "TFLOP/s", "frac": alu_achieved / alu_peak, "traffic": traffic,
+                "traffic_source": traffic_note, "fragments": n_frag,
+                "flops_per_fragment": flops / max(1, n_frag), "ms": bwd_ms,
+                "peak_source": f"derived: {n_sm} SMs x 128 FP32 lanes x 2 x {f_max:.0f} MHz (sampled max clock)"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -598,7 +625,7 @@ def main():
                                                                 "cached": tuned.get("cached"),
                                                                 "ms": tuned["timings"]}),
             "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches_per_step * args.steps),
-            "launches_per_step": int(launches_per_step), "roofline": roofline,
+            "launches_per_step": int(launches_per_step), "roofline": roofline, "roofline_hbm": roofline_hbm,
             "per_view": per_view, "breakdown_ms": breakdown, "kernel_ms": kern,
             "counts": {"visible_pairs": nvis, "instances": n_inst, "tiles": n_tiles}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

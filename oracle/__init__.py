@@ -266,7 +266,7 @@ def render_brute(P: Params, cams, cfg: Config, rec) -> dict:
 
 def render_depth_dist(P: Params, cams, cfg: Config, rec, vals, ranges):
     """(mean, var) per pixel: weighted mean and variance of the blended depths
-    under the weights w = alpha T (reading R15 of the C file)."""
+    under the weights w = alpha T (reading R16 of the C file)."""
     ca, cc = cameras(cams), cfg.c()
     mean, var = np.zeros(_npix(cams)), np.zeros(_npix(cams))
     lib().oracle_render_depth_dist(len(cams), ca, _p(P.submap_offsets), ctypes.byref(cc),

@@ -42,7 +42,7 @@
  *       pixels and views.
  *   R14 densification statistic: per view where the pair is visible,
  *       acc += ||(dL/du, dL/dv)|| in pixels and cnt += 1.
- *   R15 rendered depth distribution (for Eq. 7 with a predicted sigma_u):
+ *   R16 rendered depth distribution (for Eq. 7 with a predicted sigma_u):
  *       the weights w_k = alpha_k T_k of a pixel's blended fragments, of total
  *       W = sum w (= A), spread over their depths z_k: mean mu_u = D/W and
  *       variance var = sum w (z - mu_u)^2 / W (both 0 where nothing blends);
@@ -520,7 +520,7 @@ static void composite(const double *rec, const int64_t *cand, const int64_t *pos
         ++nb;
         sig = (sig ^ (uint64_t)cand[i]) * 1099511628211ull;
     }
-    /* R15: mean and variance of the blended depths, by definition */
+    /* R16: mean and variance of the blended depths, by definition */
     double W = 0.0, M2 = 0.0;
     for (int64_t k = 0; k < nb; ++k) W += wz[2 * k];
     double mu = nb > 0 ? D / W : 0.0;
@@ -575,7 +575,7 @@ int oracle_render_fwd(int n_views, const oc_camera *cams, const int64_t *submap_
     return 0;
 }
 
-/* Mean and variance of the blended depths per pixel (R15). */
+/* Mean and variance of the blended depths per pixel (R16). */
 int oracle_render_depth_dist(int n_views, const oc_camera *cams, const int64_t *submap_offsets,
                              const oc_config *cfg, const double *rec, const int64_t *vals,
                              const int64_t *ranges, double *mean, double *var) {
@@ -737,7 +737,7 @@ double oracle_depth_loss(int n_views, const oc_camera *cams, const int64_t *subm
     return nv > 0 ? lambda * s / (double)nv : 0.0;
 }
 
-/* Eq. (7) with the renderer's predicted distribution (R15):
+/* Eq. (7) with the renderer's predicted distribution (R16):
  * sigma_u^2 = max(var, 0) + sigma_U^2; mean over valid points (R12) of
  * KL(N(z, sigma_L^2) || N(mean, sigma_u^2)) times lambda.  Gradients (each
  * accumulated per pixel, nullable) w.r.t. mean and var. */
@@ -811,7 +811,7 @@ static void pixel_adjoint(const double *rec, const int64_t *cand, int64_t n, dou
         bl[m] = cand[i]; al[m] = a; raw[m] = rw; Tb[m] = T; ++m;
         T = Tn;
     }
-    /* R15: mu = sum w z / W, W = sum w, var = M2 / W, M2 = sum w (z - mu)^2.
+    /* R16: mu = sum w z / W, W = sum w, var = M2 / W, M2 = sum w (z - mu)^2.
      * dmu/dw_k = (z_k - mu)/W, dmu/dz_k = w_k/W; with R = sum w (z - mu),
      *   dM2/dw_k = (z_k - mu)^2 - 2 R dmu/dw_k,  dM2/dz_k = 2 w_k (z_k - mu) - 2 R dmu/dz_k,
      *   dvar/dw_k = dM2/dw_k / W - M2/W^2,       dvar/dz_k = dM2/dz_k / W. */
