@@ -112,6 +112,8 @@ def lib():
         _lib.oracle_depth_loss_var.restype = d
         _lib.oracle_image_l1.argtypes = [i64, P, P, P]
         _lib.oracle_image_l1.restype = d
+        _lib.oracle_ssim.argtypes = [i32, P, P, P, P]
+        _lib.oracle_ssim.restype = d
         _lib.oracle_kl_normal.argtypes = [d, d, d, d]
         _lib.oracle_kl_normal.restype = d
         _lib.oracle_depth_loss.argtypes = [i32, P, P, P, P, P, i64, P, i32, d, d, d, P, P]
@@ -317,6 +319,22 @@ def image_l1(C, I):
     grad = np.zeros_like(C)
     loss = lib().oracle_image_l1(C.size, _p(C), _p(I), _p(grad))
     return loss, grad
+
+
+def ssim(cams, C, I, grad=True):
+    """Mean SSIM (reading R17 of the C file) of planar images C against I laid
+    out like the renderer's RGB output; returns (mean SSIM, d mean / dC or None)."""
+    C, I = _d(C).ravel(), _d(I).ravel()
+    g = np.zeros_like(C) if grad else None
+    val = lib().oracle_ssim(len(cams), cameras(cams), _p(C), _p(I), _p(g) if grad else None)
+    return val, g
+
+
+def image_loss(cams, C, I, lam):
+    """Eq. (6): (1 - lam) mean|C - I| + lam (1 - mean SSIM); returns (loss, dL/dC)."""
+    l1, g1 = image_l1(C, I)
+    s, gs = ssim(cams, C, I)
+    return (1.0 - lam) * l1 + lam * (1.0 - s), (1.0 - lam) * g1 - lam * gs
 
 
 def kl_normal(m1, s1, m2, s2) -> float:

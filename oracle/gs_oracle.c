@@ -42,6 +42,11 @@
  *       pixels and views.
  *   R14 densification statistic: per view where the pair is visible,
  *       acc += ||(dL/du, dL/dv)|| in pixels and cnt += 1.
+ *   R17 SSIM term of Eq. (6): per channel of every view, the structural
+ *       similarity of Wang et al. (2004) with an 11x11 Gaussian window of
+ *       sigma 1.5 (weights normalised to sum 1), zero padding outside the
+ *       image ('same' output size), C1 = 0.01^2, C2 = 0.03^2 (unit dynamic
+ *       range), averaged over all channels, pixels and views.
  *   R16 rendered depth distribution (for Eq. 7 with a predicted sigma_u):
  *       the weights w_k = alpha_k T_k of a pixel's blended fragments, of total
  *       W = sum w (= A), spread over their depths z_k: mean mu_u = D/W and
@@ -693,6 +698,85 @@ double oracle_image_l1(int64_t n, const double *C, const double *I, double *grad
         if (grad) grad[i] = (d > 0 ? 1.0 : (d < 0 ? -1.0 : 0.0)) / (double)n;
     }
     return n > 0 ? s / (double)n : 0.0;
+}
+
+/* R17: the normalised 11-tap Gaussian window, sigma 1.5 */
+#define OC_SSIM_R 5
+static void ssim_window(double g[2 * OC_SSIM_R + 1]) {
+    double s = 0.0;
+    for (int i = -OC_SSIM_R; i <= OC_SSIM_R; ++i) {
+        g[i + OC_SSIM_R] = exp(-(double)(i * i) / (2.0 * 1.5 * 1.5));
+        s += g[i + OC_SSIM_R];
+    }
+    for (int i = 0; i < 2 * OC_SSIM_R + 1; ++i) g[i] /= s;
+}
+
+/* Mean SSIM (R17) of planar images rgb against target, views laid out as in
+ * the renderer's outputs.  grad (nullable) receives d(mean SSIM)/d rgb.
+ * Each pixel q takes window sums of x, y, x^2, y^2, xy over its 11x11
+ * neighbourhood (zero outside the image):
+ *   mu_x, mu_y, s_xx = E[x^2] - mu_x^2, s_yy, s_xy = E[xy] - mu_x mu_y,
+ *   S = (2 mu_x mu_y + C1)(2 s_xy + C2) / ((mu_x^2 + mu_y^2 + C1)(s_xx + s_yy + C2)).
+ * Adjoint: S depends on x only through m1 = E[x], m2 = E[x^2] and m12 = E[xy];
+ * with A = 2 mu_x mu_y + C1, B = 2 s_xy + C2, Cc = mu_x^2 + mu_y^2 + C1,
+ * D = s_xx + s_yy + C2:
+ *   dS/dmu_x (s fixed) = (B/D) (2 mu_y Cc - 2 mu_x A) / Cc^2,
+ *   dS/ds_xx = -A B / (Cc D^2),   dS/ds_xy = 2 A / (Cc D),
+ *   dS/dm1 = dS/dmu_x - 2 mu_x dS/ds_xx - mu_y dS/ds_xy,
+ *   dS/dm2 = dS/ds_xx,  dS/dm12 = dS/ds_xy,
+ * and x_p enters m1, m2, m12 of every q whose window holds p with weight
+ * g(p - q): d/dx_p = g (dS/dm1 + 2 x_p dS/dm2 + y_p dS/dm12). */
+double oracle_ssim(int n_views, const oc_camera *cams, const double *rgb, const double *target,
+                   double *grad) {
+    const double C1 = 0.01 * 0.01, C2 = 0.03 * 0.03;
+    double g[2 * OC_SSIM_R + 1];
+    ssim_window(g);
+    int64_t n_all = 0;
+    for (int v = 0; v < n_views; ++v) n_all += 3 * (int64_t)cams[v].width * cams[v].height;
+    if (grad)
+        for (int64_t i = 0; i < n_all; ++i) grad[i] = 0.0;
+    double total = 0.0;
+    int64_t off = 0;
+    for (int v = 0; v < n_views; ++v) {
+        const int W = cams[v].width, H = cams[v].height;
+        for (int ch = 0; ch < 3; ++ch, off += (int64_t)W * H) {
+            const double *x = rgb + off, *y = target + off;
+            for (int qy = 0; qy < H; ++qy)
+                for (int qx = 0; qx < W; ++qx) {
+                    double mx = 0, my = 0, exx = 0, eyy = 0, exy = 0;
+                    for (int j = -OC_SSIM_R; j <= OC_SSIM_R; ++j)
+                        for (int i = -OC_SSIM_R; i <= OC_SSIM_R; ++i) {
+                            int px = qx + i, py = qy + j;
+                            if (px < 0 || px >= W || py < 0 || py >= H) continue;
+                            double w = g[i + OC_SSIM_R] * g[j + OC_SSIM_R];
+                            double a = x[(int64_t)py * W + px], b = y[(int64_t)py * W + px];
+                            mx += w * a; my += w * b;
+                            exx += w * a * a; eyy += w * b * b; exy += w * a * b;
+                        }
+                    double sxx = exx - mx * mx, syy = eyy - my * my, sxy = exy - mx * my;
+                    double A = 2.0 * mx * my + C1, B = 2.0 * sxy + C2;
+                    double Cc = mx * mx + my * my + C1, D = sxx + syy + C2;
+                    total += A * B / (Cc * D);
+                    if (!grad) continue;
+                    double dmu = (B / D) * (2.0 * my * Cc - 2.0 * mx * A) / (Cc * Cc);
+                    double dsxx = -A * B / (Cc * D * D);
+                    double dsxy = 2.0 * A / (Cc * D);
+                    double d1 = dmu - 2.0 * mx * dsxx - my * dsxy, d2 = dsxx, d12 = dsxy;
+                    for (int j = -OC_SSIM_R; j <= OC_SSIM_R; ++j)
+                        for (int i = -OC_SSIM_R; i <= OC_SSIM_R; ++i) {
+                            int px = qx + i, py = qy + j;
+                            if (px < 0 || px >= W || py < 0 || py >= H) continue;
+                            double w = g[i + OC_SSIM_R] * g[j + OC_SSIM_R];
+                            int64_t p = (int64_t)py * W + px;
+                            grad[off + p] += w * (d1 + 2.0 * x[p] * d2 + y[p] * d12);
+                        }
+                }
+        }
+    }
+    if (n_all == 0) return 0.0;
+    if (grad)
+        for (int64_t i = 0; i < n_all; ++i) grad[i] /= (double)n_all;
+    return total / (double)n_all;
 }
 
 /* KL(N(m1, s1^2) || N(m2, s2^2)) */

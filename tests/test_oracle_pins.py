@@ -14,6 +14,9 @@ sign, a transposed operand or a wrong index in the oracle fails at least one:
   backward                  central differences of every parameter type and
                             every pose twist; translation identity
   losses (Eqs. 6-7)         KL by numerical integration; FD of both losses
+  SSIM (Eq. 6)              scipy's separable Gaussian filters; constant-image
+                            closed form; SSIM(x, x) = 1 with zero gradient;
+                            central differences; Eq. 6 composition
   rendered depth mean/var   two-fragment closed form; zero variance for equal
                             depths; Popoviciu bound; invariance to a common
                             depth shift; KL with the rendered variance by
@@ -675,3 +678,92 @@ def test_variance_kl_chain_fd():
         checked += 1
     assert checked >= 15
     assert np.abs(g["means"]).max() > 0
+
+
+# ---------------------------------------------------------------------------
+# SSIM term of Eq. (6)
+# ---------------------------------------------------------------------------
+
+def _ssim_by_scipy(x, y):
+    """SSIM map per Wang et al. with scipy's separable Gaussian filter: sigma
+    1.5 truncated at radius 5, zero padding (an implementation independent of
+    the oracle's direct window sums)."""
+    from scipy.ndimage import gaussian_filter
+    f = lambda a: gaussian_filter(a, sigma=1.5, truncate=5.0 / 1.5, mode="constant", cval=0.0)
+    C1, C2 = 0.01 ** 2, 0.03 ** 2
+    mx, my = f(x), f(y)
+    sxx, syy, sxy = f(x * x) - mx * mx, f(y * y) - my * my, f(x * y) - mx * my
+    return (2 * mx * my + C1) * (2 * sxy + C2) / ((mx * mx + my * my + C1) * (sxx + syy + C2))
+
+
+def _planes(rng, cams, smooth=False):
+    out = []
+    for c in cams:
+        a = rng.random((3, c.height, c.width))
+        if smooth:
+            from scipy.ndimage import gaussian_filter
+            a = np.stack([gaussian_filter(p, 2.0) for p in a])
+        out.append(a.ravel())
+    return np.concatenate(out)
+
+
+def test_ssim_matches_scipy_filters():
+    rng = np.random.default_rng(21)
+    cams = [_cam(37, 23), _cam(16, 40)]
+    x = _planes(rng, cams)
+    y = np.clip(x + 0.2 * rng.normal(size=x.size), 0, 1)
+    val, _ = O.ssim(cams, x, y, grad=False)
+    maps, off = [], 0
+    for c in cams:
+        for ch in range(3):
+            n = c.width * c.height
+            maps.append(_ssim_by_scipy(x[off:off + n].reshape(c.height, c.width),
+                                       y[off:off + n].reshape(c.height, c.width)).ravel())
+            off += n
+    ref = np.concatenate(maps).mean()
+    assert val == pytest.approx(ref, rel=1e-12, abs=1e-14)
+    assert 0.2 < val < 0.95
+
+
+def test_ssim_constant_images_closed_form():
+    # away from the border the windows see constants a, b: sigma terms vanish
+    # and SSIM = (2ab + C1) / (a^2 + b^2 + C1) (the border windows are cut by
+    # the zero padding, so compare a 5-pixel-wide interior through the map)
+    cams = [_cam(25, 21)]
+    a, b = 0.7, 0.4
+    C1 = 0.01 ** 2
+    x = np.full(3 * 25 * 21, a)
+    y = np.full(3 * 25 * 21, b)
+    val, g = O.ssim(cams, x, y)
+    m = _ssim_by_scipy(np.full((21, 25), a), np.full((21, 25), b))
+    assert m[5:-5, 5:-5] == pytest.approx((2 * a * b + C1) / (a * a + b * b + C1), rel=1e-12)
+    assert val == pytest.approx(m.mean(), rel=1e-12)
+
+
+def test_ssim_identity_is_maximum():
+    rng = np.random.default_rng(22)
+    cams = [_cam(30, 20)]
+    x = _planes(rng, cams)
+    val, g = O.ssim(cams, x, x)
+    assert val == pytest.approx(1.0, abs=1e-14)
+    assert np.abs(g).max() < 1e-14
+
+
+@pytest.mark.parametrize("smooth", [False, True])
+def test_ssim_gradient_fd(smooth):
+    rng = np.random.default_rng(23 + smooth)
+    cams = [_cam(19, 14), _cam(12, 17)]
+    x = _planes(rng, cams, smooth)
+    y = _planes(rng, cams, smooth)
+    val, g = O.ssim(cams, x, y)
+    h = 1e-6
+    for i in rng.choice(x.size, 25, replace=False):
+        xp, xm = x.copy(), x.copy()
+        xp[i] += h
+        xm[i] -= h
+        fd = (O.ssim(cams, xp, y, grad=False)[0] - O.ssim(cams, xm, y, grad=False)[0]) / (2 * h)
+        assert fd == pytest.approx(g[i], rel=1e-6, abs=2e-10), i  # FD rounding ~1e-16 / h
+    # Eq. (6) composes the two terms
+    lam = 0.2
+    L, gL = O.image_loss(cams, x, y, lam)
+    assert L == pytest.approx((1 - lam) * np.abs(x - y).mean() + lam * (1 - val), rel=1e-14)
