@@ -54,21 +54,28 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=640, help="crop width (px) per view for the oracle sample")
+    ap.add_argument("--ssim-lambda", type=float, default=0.0,
+                    help="weight lambda of the SSIM term of Eq. 6 (0: L1 image loss only)")
     ap.add_argument("--depth-loss", default="l1", choices=list(DEPTH_LOSSES),
                     help="depth term of the step: l1, kl (Eq. 7, fixed sigma_u) or kl-var (Eq. 7 with the "
                          "rendered variance: forward and backward with the central depth moment)")
     return ap.parse_args()
 
 
-DEPTH_LOSSES = {"l1": "L1 rgb + L1 depth", "kl": "L1 rgb + KL depth (fixed sigma_u)",
-                "kl-var": "L1 rgb + KL depth (rendered variance)"}
+DEPTH_LOSSES = {"l1": "L1 depth", "kl": "KL depth (fixed sigma_u)", "kl-var": "KL depth (rendered variance)"}
+
+
+def loss_label(args) -> str:
+    lam = getattr(args, "ssim_lambda", 0.0)
+    img = "L1 rgb" if lam == 0 else f"(1 - {lam:g}) L1 + {lam:g} (1 - SSIM) rgb"
+    return img + " + " + DEPTH_LOSSES[getattr(args, "depth_loss", "l1")]
 
 
 def workload_config(sc, args, tile=None, depth=None):
     W = sorted({(c.width, c.height) for c in sc.cameras})
     return {"workload": sc.name, "n_gaussians": sc.n, "views": len(sc.cameras),
             "resolutions": [f"{w}x{h}" for w, h in W], "n_pix": sc.n_pix, "sh_degree": sc.sh_degree,
-            "lidar_points": int(sc.lidar.shape[0]), "losses": DEPTH_LOSSES[getattr(args, "depth_loss", "l1")],
+            "lidar_points": int(sc.lidar.shape[0]), "losses": loss_label(args),
             "tile": tile or args.tile, "batch_depth": depth or args.depth,
             "l2": "flushed (512 MiB write) before every timed step", "graph": True,
             "parallelism": "replicas", "seed": 0}
@@ -147,7 +154,7 @@ def max_over_ranks(ms: float, device) -> float:
     return float(t.item())
 
 
-RASTER_SOURCES = ("paper_2510_26358_gb300/csrc/gs_raster.cu", "paper_2510_26358_gb300/csrc/gs_internal.cuh")
+RASTER_SOURCES = ("paper_2510_26358_gb300/csrc/gs_raster.cu", "paper_2510_26358_gb300/csrc/gs_frag.cuh")
 
 
 def raster_source_hash() -> str:
@@ -199,9 +206,10 @@ def job_throughput(pix_per_rank: int, ms: float, world: int) -> float:
 class Step:
     """All device buffers of one mapping step plus the calls that make it."""
 
-    def __init__(self, G, torch, sc, cfg, dev, inst_capacity=None, var=False):
+    def __init__(self, G, torch, sc, cfg, dev, inst_capacity=None, var=False, ssim_lambda=0.0):
         self.G, self.torch, self.sc, self.dev = G, torch, sc, dev
         self.var = var
+        self.ssim_lambda = ssim_lambda
         t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
         self.P = [t(sc.means), t(sc.log_scales), t(sc.quats), t(sc.opacity_logits), t(sc.sh)]
         self.target = t(sc.target)
@@ -219,7 +227,7 @@ class Step:
                           sh=torch.zeros_like(self.P[4]), pose=torch.zeros(len(sc.cameras), 6, device=dev),
                           densify_acc=torch.zeros(sc.n, device=dev),
                           densify_cnt=torch.zeros(sc.n, dtype=torch.int32, device=dev))
-        self.loss_rgb = torch.zeros(1, device=dev)
+        self.loss_rgb = torch.zeros(3, device=dev)
         self.loss_depth = torch.zeros(1, device=dev)
         # depth mean and variance and their adjoints (variance KL only)
         self.dist = [torch.empty(npx, device=dev) for _ in range(2)] if var else []
@@ -254,7 +262,12 @@ class Step:
 
         def losses():
             s = G._stream()
-            G.gs_image_l1(r.ws, G._ptr(self.rgb), G._ptr(self.target), G._ptr(self.loss_rgb), G._ptr(self.g_rgb), s)
+            if self.ssim_lambda > 0:
+                G.gs_image_loss(r.ws, G._ptr(self.rgb), G._ptr(self.target), self.ssim_lambda, G._ptr(self.loss_rgb),
+                                G._ptr(self.g_rgb), s)
+            else:
+                G.gs_image_l1(r.ws, G._ptr(self.rgb), G._ptr(self.target), G._ptr(self.loss_rgb), G._ptr(self.g_rgb),
+                              s)
             if self.var:
                 G.gs_depth_loss_var(r.ws, G._ptr(self.alpha), G._ptr(self.dist[0]), G._ptr(self.dist[1]),
                                     G._ptr(self.lidar), self.lidar.shape[0], G._ptr(self.loss_depth),
@@ -359,14 +372,17 @@ def oracle_sample(sc, crop_w):
     return cams
 
 
-def run_oracle_step(O, P, cams, cfg, lidar_full, sc, depth_loss="l1"):
-    """project -> bin -> forward -> L1 image + depth losses -> backward, in FP64."""
+def run_oracle_step(O, P, cams, cfg, lidar_full, sc, depth_loss="l1", ssim_lambda=0.0):
+    """project -> bin -> forward -> image + depth losses -> backward, in FP64."""
     rec = O.project(P, cams, cfg)
     keys, vals, ranges = O.bin(P, cams, cfg, rec)
     out = O.render_fwd(P, cams, cfg, rec, vals, ranges)
     npx = sum(c.width * c.height for c in cams)
     target = np.zeros(3 * npx)
-    _, gC = O.image_l1(out["rgb"], target)
+    if ssim_lambda > 0:
+        _, gC = O.image_loss(cams, out["rgb"], target, ssim_lambda)
+    else:
+        _, gC = O.image_l1(out["rgb"], target)
     if depth_loss == "kl-var":
         mean, var = O.render_depth_dist(P, cams, cfg, rec, vals, ranges)
         _, gm, gv, _ = O.depth_loss_var(P, cams, cfg, out["alpha"], mean, var, lidar_full)
@@ -393,10 +409,10 @@ def cpu_baseline(sc, args, reps=1):
     t0 = time.perf_counter()
     npx = 0
     for _ in range(reps):
-        npx += run_oracle_step(O, P, cams, cfg, lid, sc, args.depth_loss)
+        npx += run_oracle_step(O, P, cams, cfg, lid, sc, args.depth_loss, args.ssim_lambda)
     dt = time.perf_counter() - t0
     sample = (f"FP64 oracle, full step (project all {sc.n} Gaussians x {len(cams)} views, bin, forward, "
-              f"{DEPTH_LOSSES[args.depth_loss]}, backward) on centred {cams[0].width}x{cams[0].height} crops "
+              f"{loss_label(args)}, backward) on centred {cams[0].width}x{cams[0].height} crops "
               f"of every view, "
               f"{reps} step(s), {dt:.1f} s")
     return {"value": npx / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
@@ -460,12 +476,13 @@ def main():
         cfg = G.gs_config_default(tile_w=tw, tile_h=th, batch_depth=depth,
                                   depth_mode=1 if args.depth_loss == "kl" else 0)
         mom = args.depth_loss == "kl-var"
-        st_ = Step(G, torch, sc, cfg, dev, var=mom)
+        st_ = Step(G, torch, sc, cfg, dev, var=mom, ssim_lambda=args.ssim_lambda)
         st_.run()
         code, need_, _ = st_.r.status()
         if code == G.GS_ERR_CAPACITY or need_ > st_.r.info["inst_capacity"]:
             st_.r.close()
-            st_ = Step(G, torch, sc, cfg, dev, inst_capacity=int(need_ * 1.25) + 1024, var=mom)
+            st_ = Step(G, torch, sc, cfg, dev, inst_capacity=int(need_ * 1.25) + 1024, var=mom,
+                       ssim_lambda=args.ssim_lambda)
             st_.run()
         return st_
 
@@ -481,7 +498,8 @@ def main():
             del g_
             return float(np.mean(t_))
         key = autotune.signature(sc.cameras, sc.n, sc.sh_degree, sc.submap_offsets,
-                                 extra="bench-step" + ("" if args.depth_loss == "l1" else "-" + args.depth_loss))
+                                 extra="bench-step" + ("" if args.depth_loss == "l1" else "-" + args.depth_loss)
+                                 + ("" if args.ssim_lambda == 0 else "-ssim"))
         tuned = autotune.tune(measure, key=key)
         tw, th, args.depth = tuned["tile_w"], tuned["tile_h"], tuned["batch_depth"]
     else:
@@ -537,7 +555,8 @@ def main():
             lid[:, 3] = 0
             sub.lidar = lid
             pv_steps.append(Step(G, torch, sub, G.gs_config_default(depth_mode=1 if args.depth_loss == "kl" else 0),
-                                 dev, inst_capacity=need + 1024, var=args.depth_loss == "kl-var"))
+                                 dev, inst_capacity=need + 1024, var=args.depth_loss == "kl-var",
+                                 ssim_lambda=args.ssim_lambda))
         run_all = lambda: [s.run() for s in pv_steps]
         pv_times = time_steps(torch, run_all, max(3, args.steps // 2), 3, flush)
         pv_ms = float(np.mean(pv_times))
@@ -563,7 +582,7 @@ def main():
             for h, d in zip(host, dst):
                 d.copy_(h, non_blocking=True)
             graph.replay()
-            loss_h[0:1].copy_(step.loss_rgb, non_blocking=True)
+            loss_h[0:1].copy_(step.loss_rgb[0:1], non_blocking=True)
             loss_h[1:2].copy_(step.loss_depth, non_blocking=True)
         e_times = time_steps(torch, e2e_step, max(3, args.steps // 2), 3, flush)
         e_ms = float(np.mean(e_times))

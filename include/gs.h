@@ -176,6 +176,17 @@ gs_status gs_depth_loss_var(gs_workspace *ws, const float *alpha, const float *d
 gs_status gs_image_l1(gs_workspace *ws, const float *rgb, const float *target, float *loss,
                       float *dL_drgb, void *stream);
 
+/* The photometric loss of Eq. (6) (Sec. III-C):
+ * (1 - lambda) mean |rgb - target| + lambda (1 - mean SSIM).  SSIM per channel
+ * plane of every view, 11x11 Gaussian window of sigma 1.5 (normalised), zero
+ * padding outside the image, C1 = 0.01^2, C2 = 0.03^2 (unit dynamic range),
+ * averaged over the 3*N_pix values.  rgb, target, dL_drgb: (device) planar as
+ * the renderer's output; loss (device, 3 floats) receives the total, the L1
+ * term and 1 - SSIM; dL_drgb (nullable) is accumulated.  lambda in [0, 1]
+ * (the paper leaves it open; 3DGS uses 0.2), GS_ERR_INVALID_ARG otherwise. */
+gs_status gs_image_loss(gs_workspace *ws, const float *rgb, const float *target, float lambda, float *loss,
+                        float *dL_drgb, void *stream);
+
 /* Backward of gs_render_fwd and gs_project: walks each tile's list back to
  * front from the last blended fragment, recomputing alpha, reduces each
  * Gaussian's contributions across the warp before one atomic per component,
@@ -254,7 +265,8 @@ enum {
     GS_STAGE_ZERO_GRAD = 9,  /* clearing the image-space gradients */
     GS_STAGE_RASTER_BWD = 10, /* backward compositing */
     GS_STAGE_PROJECT_BWD = 11, /* projection adjoint and pose reduction */
-    GS_NUM_STAGES = 12
+    GS_STAGE_IMAGE_SSIM = 12, /* SSIM forward and backward of gs_image_loss */
+    GS_NUM_STAGES = 13
 };
 gs_status gs_workspace_set_profiling(gs_workspace *ws, int32_t on);
 gs_status gs_workspace_stage_ms(gs_workspace *ws, float *ms, int32_t n);

@@ -137,7 +137,7 @@ void gs_workspace_destroy(gs_workspace *ws) {
                     ws->vis_key, ws->vis_pair, ws->vis_key_alt, ws->vis_pair_alt, ws->ioff,
                     ws->inst_tile, ws->inst_val, ws->inst_tile_alt, ws->inst_val_alt, ws->ranges,
                     ws->tile_order, ws->tile_buckets,
-                    ws->last, ws->tfin, ws->vstat, ws->hist, ws->part, ws->digit_tot, ws->pose_part, ws->red_part,
+                    ws->last, ws->tfin, ws->vstat, ws->hist, ws->part, ws->digit_tot, ws->pose_part, ws->red_part, ws->ssim_d, ws->ssim_part,
                     ws->st};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -283,6 +283,9 @@ gs_status gs_workspace_create(const gs_camera *cams, int32_t n_views, const int6
     GS_ALLOC(ws->digit_tot, (size_t)256);
     GS_ALLOC(ws->pose_part, (size_t)std::max(1, blocks) * maxv * 6);
     GS_ALLOC(ws->red_part, (size_t)2 * ws->sort_blocks);
+    ws->n_ssim_tiles = ssim_tiles(ws->views_h);
+    GS_ALLOC(ws->ssim_d, (size_t)9 * ws->n_pix);
+    GS_ALLOC(ws->ssim_part, (size_t)std::max<int64_t>(1, ws->n_ssim_tiles));
     GS_ALLOC(ws->st, 1);
 #undef GS_ALLOC
     if (r == GS_OK) {
@@ -372,6 +375,13 @@ gs_status gs_image_l1(gs_workspace *ws, const float *rgb, const float *target, f
                       void *stream) {
     if (!ws || !rgb || !target || !loss) return fail(GS_ERR_INVALID_ARG, "NULL argument");
     return launch_image_l1(ws, rgb, target, loss, dL_drgb, (cudaStream_t)stream);
+}
+
+gs_status gs_image_loss(gs_workspace *ws, const float *rgb, const float *target, float lambda, float *loss,
+                        float *dL_drgb, void *stream) {
+    if (!ws || !rgb || !target || !loss) return fail(GS_ERR_INVALID_ARG, "NULL argument");
+    if (!(lambda >= 0.f && lambda <= 1.f)) return fail(GS_ERR_INVALID_ARG, "lambda must lie in [0, 1]");
+    return launch_image_loss(ws, rgb, target, lambda, loss, dL_drgb, (cudaStream_t)stream);
 }
 
 gs_status gs_render_bwd(gs_workspace *ws, const gs_gaussians *g, const gs_camera *cams_dev,

@@ -1,6 +1,6 @@
-// Internal declarations of libgsraster: workspace layout, per-view tables,
-// launch helpers and the per-fragment arithmetic that the forward and the
-// backward rasteriser must evaluate bit-identically.
+// Internal declarations of libgsraster: workspace layout, device state and
+// the stage launchers.  The types and per-fragment arithmetic the kernels are
+// built from live in gs_frag.cuh.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -10,40 +10,9 @@
 #include <vector>
 
 #include "../../include/gs.h"
+#include "gs_frag.cuh"
 
 namespace gs {
-
-// ---------------------------------------------------------------------------
-// constants
-// ---------------------------------------------------------------------------
-
-constexpr uint32_t kInvalidKey = 0xFFFFFFFFu;  // pair depth key of an invisible pair
-constexpr int kRecF4 = 3;                     // float4 per projected record
-constexpr int kGrad = 10;                     // floats per image-space gradient record
-// image-space gradient components (same order as the oracle's)
-enum { G_U = 0, G_V, G_QA, G_QB, G_QC, G_LNO, G_R, G_G, G_B, G_Z };
-
-// sqrt(log2(e)/2): scales the Cholesky factor of Sigma'^-1 so that
-// log2(alpha) = log2(o) - (t1^2 + t2^2)
-constexpr float kCholScale = 0.84932180028801904272f;
-// 2 ln 2 = 1/kCholScale^2: converts scaled factors back to natural units
-constexpr float kTwoLn2 = 1.38629436111989061883f;
-constexpr float kLog2e = 1.44269504088896340736f;
-
-constexpr int kSortThreads = 256;
-constexpr int kProjThreads = 256;
-constexpr int kOrderBuckets = 64;     // list-length buckets of the raster work order
-constexpr int kOrderShift = 5;        // bucket = min(63, length >> 5)
-
-// ---------------------------------------------------------------------------
-// tables
-// ---------------------------------------------------------------------------
-
-struct ViewInfo {
-    int32_t W, H, ntx, nty;
-    int32_t pix_off, tile_off, pair_off, g0;
-    int32_t ng, submap, k_in_submap, pad;
-};
 
 struct SubmapInfo {
     int32_t g0, ng, nviews, block0;  // block0: first projection-backward block
@@ -63,15 +32,6 @@ struct DevState {
     uint32_t pad[7];
 };
 constexpr uint32_t kFlagCapacity = 1u;
-
-// Constants every kernel needs, passed by value.
-struct Consts {
-    float near_z, dilation, alpha_min, alpha_max, t_min, jac_clamp;
-    float ext_rel_pad, ext_abs_pad;
-    float log2_alpha_min;   // log2(alpha_min)
-    float ln_alpha_min;     // ln(alpha_min)
-    int32_t tile_w, tile_h;
-};
 
 }  // namespace gs
 
@@ -114,6 +74,9 @@ struct gs_workspace {
     uint32_t *digit_tot = nullptr; // [256] digit totals of the current radix pass
     float *pose_part = nullptr;    // [proj_blocks][max_views_per_submap][6]
     double *red_part = nullptr;    // [2][sort_blocks] loss partials
+    int64_t n_ssim_tiles = 0;      // 32x16 SSIM tiles over all channel planes
+    float *ssim_d = nullptr;       // [3][3 n_pix] SSIM partials for the backward
+    double *ssim_part = nullptr;   // [n_ssim_tiles] per-tile sums of the SSIM map
     gs::DevState *st = nullptr;
     // host-side order checks
     bool projected = false, binned = false, rendered = false, rendered_var = false;
@@ -170,81 +133,15 @@ gs_status launch_depth_loss(gs_workspace *ws, int mode, const float *depth, cons
                             float *dL_ddepth, float *dL_dvar, cudaStream_t s);
 gs_status launch_image_l1(gs_workspace *ws, const float *rgb, const float *target, float *loss,
                           float *dL_drgb, cudaStream_t s);
+// Eq. (6): (1 - lambda) L1 + lambda (1 - SSIM); loss[0..2] = total, L1, 1 - SSIM
+gs_status launch_image_loss(gs_workspace *ws, const float *rgb, const float *target, float lambda,
+                            float *loss, float *dL_drgb, cudaStream_t s);
+// SSIM map sums into ws->ssim_part; with dL_drgb, adds grad_scale * dSSIM/dx
+gs_status launch_ssim(gs_workspace *ws, const float *rgb, const float *target, float grad_scale,
+                      float *dL_drgb, cudaStream_t s);
+int64_t ssim_tiles(const std::vector<ViewInfo> &views);
 // occupancy-derived persistent grid sizes for the rasterisers
 gs_status raster_configure(gs_workspace *ws);
 gs_status sort_configure();
-
-// ---------------------------------------------------------------------------
-// device helpers
-// ---------------------------------------------------------------------------
-
-__device__ __forceinline__ float rcp_approx(float x) {
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-__device__ __forceinline__ float ex2_approx(float x) {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-// Staged copy of one projected record, as the rasterisers keep it in shared
-// memory: a = (U, V, k1, k2) with U, V the integer pixel of the mean and
-// k1 = l11 hx + l12 hy, k2 = l22 hy; b = (l11, l12, l22, log2 o) the scaled
-// Cholesky factor of Sigma'^-1; c = (r, g, b, z).
-__device__ __forceinline__ void stage_record(const float4 r0, const float4 r1, float4 &a, float4 &b) {
-    // r0 = (U, V, hx, hy), r1 = (l11, l12, l22, log2o)
-    a.x = r0.x;
-    a.y = r0.y;
-    a.z = __fmaf_rn(r1.x, r0.z, __fmul_rn(r1.y, r0.w));
-    a.w = __fmul_rn(r1.z, r0.w);
-    b = r1;
-}
-
-// log2 of the unclamped alpha of a staged Gaussian at integer pixel (px, py):
-// d = (px - U + hx, py - V + hy), t1 = l11 dx + l12 dy, t2 = l22 dy,
-// e = log2 o - t1^2 - t2^2, evaluated as
-//   column part (shared by the pixels of one column):  dxi = px - U,
-//                                                      u1 = l11 dxi + k1
-//   pixel part:   dyi = py - V,  t1 = l12 dyi + u1,  t2 = l22 dyi + k2,
-//                 e = log2 o - t1^2 - t2^2
-// with exact integer offsets dxi, dyi.  Both passes call these functions, so
-// the backward recomputes exactly the forward's alpha and decisions, for any
-// tile size and any number of pixels per thread.
-__device__ __forceinline__ void frag_column(const float4 a, const float4 b, float pxf, float &dxi, float &u1) {
-    dxi = __fsub_rn(pxf, a.x);
-    u1 = __fmaf_rn(b.x, dxi, a.z);
-}
-
-__device__ __forceinline__ float frag_pixel(const float4 a, const float4 b, float u1, float pyf, float &t1,
-                                            float &t2, float &dyi) {
-    dyi = __fsub_rn(pyf, a.y);
-    t1 = __fmaf_rn(b.y, dyi, u1);
-    t2 = __fmaf_rn(b.z, dyi, a.w);
-    return __fmaf_rn(-t1, t1, __fmaf_rn(-t2, t2, b.w));
-}
-
-__device__ __forceinline__ int view_of_tile(const ViewInfo *views, int n_views, int tile) {
-    int lo = 0, hi = n_views - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (views[mid].tile_off <= tile) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
-__host__ __device__ inline void chunk_range(uint64_t n, int b, int nblocks, int tile, uint32_t &lo,
-                                            uint32_t &hi) {
-    uint64_t per = (n + nblocks - 1) / nblocks;
-    per = (per + tile - 1) / tile * tile;
-    uint64_t l = (uint64_t)b * per;
-    if (l > n) l = n;
-    uint64_t h = l + per;
-    if (h > n) h = n;
-    lo = (uint32_t)l;
-    hi = (uint32_t)h;
-}
 
 }  // namespace gs

@@ -15,7 +15,8 @@
 // with gradients to mu_u and var.
 //
 // Photometric L1 (Eq. 6 with lambda = 0): mean |C - I| over every channel of
-// every pixel of every view, gradient sign(C - I)/n.
+// every pixel of every view, gradient sign(C - I)/n.  The full Eq. 6 adds
+// lambda (1 - SSIM) (gs_ssim.cu) and scales the L1 gradient by (1 - lambda).
 //
 // Sums are deterministic: per-block partials in double, then one block adds
 // them in block order.
@@ -157,10 +158,9 @@ __device__ __forceinline__ float l1_term(float c, float t, float inv, float &g) 
 // Four terms are added in float, each group of four into a double; the
 // block and grid sums are in double and in a fixed order.
 __global__ void __launch_bounds__(LT) k_l1_partial(const float *rgb, const float *target, int64_t n,
-                                                  float *grad, double *part) {
+                                                  float *grad, double *part, float inv) {
     __shared__ double sm[32];
     double s = 0.0;
-    const float inv = (float)(1.0 / (double)n);
     const bool vec = ((((uintptr_t)rgb) | ((uintptr_t)target) | ((uintptr_t)grad)) & 15) == 0;
     const int64_t n4 = vec ? n / 4 : 0;
     const int64_t stride = (int64_t)gridDim.x * LT;
@@ -188,6 +188,22 @@ __global__ void __launch_bounds__(LT) k_l1_final(const double *part, int nb, int
     for (int i = threadIdx.x; i < nb; i += LT) s += part[i];
     double t = block_sum_d(s, sm);
     if (threadIdx.x == 0) *loss = (float)(t / (double)n);
+}
+
+// loss[0] = (1 - lambda) L1 + lambda (1 - SSIM), loss[1] = L1, loss[2] = 1 - SSIM
+__global__ void __launch_bounds__(LT) k_image_loss_final(const double *l1part, int nb, const double *spart,
+                                                        int64_t ns, int64_t n, float lambda, float *loss) {
+    __shared__ double sm[32];
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < nb; i += LT) a += l1part[i];
+    for (int64_t i = threadIdx.x; i < ns; i += LT) b += spart[i];
+    const double l1 = block_sum_d(a, sm) / (double)n;
+    const double dssim = 1.0 - block_sum_d(b, sm) / (double)n;
+    if (threadIdx.x == 0) {
+        loss[0] = (float)((1.0 - (double)lambda) * l1 + (double)lambda * dssim);
+        loss[1] = (float)l1;
+        loss[2] = (float)dssim;
+    }
 }
 
 }  // namespace
@@ -229,9 +245,29 @@ gs_status launch_image_l1(gs_workspace *ws, const float *rgb, const float *targe
     int64_t n = 3 * ws->n_pix;
     int nb = ws->sort_blocks;
     StageTimer timer(ws, GS_STAGE_IMAGE_L1, s);
-    ++ws->kernel_launches; k_l1_partial<<<nb, LT, 0, s>>>(rgb, target, n, dL_drgb, ws->red_part);
+    ++ws->kernel_launches;
+    k_l1_partial<<<nb, LT, 0, s>>>(rgb, target, n, dL_drgb, ws->red_part, (float)(1.0 / (double)n));
     ++ws->kernel_launches; k_l1_final<<<1, LT, 0, s>>>(ws->red_part, nb, n, loss);
     return check_launch("image_l1");
+}
+
+gs_status launch_image_loss(gs_workspace *ws, const float *rgb, const float *target, float lambda, float *loss,
+                            float *dL_drgb, cudaStream_t s) {
+    const int64_t n = 3 * ws->n_pix;
+    const int nb = ws->sort_blocks;
+    {
+        StageTimer timer(ws, GS_STAGE_IMAGE_L1, s);
+        ++ws->kernel_launches;
+        k_l1_partial<<<nb, LT, 0, s>>>(rgb, target, n, dL_drgb, ws->red_part,
+                                       (float)((1.0 - (double)lambda) / (double)n));
+    }
+    gs_status r = check_launch("image_loss");
+    if (r != GS_OK) return r;
+    r = launch_ssim(ws, rgb, target, (float)(-(double)lambda / (double)n), dL_drgb, s);
+    if (r != GS_OK) return r;
+    ++ws->kernel_launches;
+    k_image_loss_final<<<1, LT, 0, s>>>(ws->red_part, nb, ws->ssim_part, ws->n_ssim_tiles, n, lambda, loss);
+    return check_launch("image_loss");
 }
 
 }  // namespace gs

@@ -28,12 +28,12 @@ GS_MAX_SUBMAPS = 64
 
 EXPORTED = ("gs_config_default", "gs_workspace_create", "gs_workspace_destroy", "gs_project",
             "gs_bin_sort", "gs_render_fwd", "gs_render_fwd_var", "gs_depth_loss", "gs_depth_loss_var",
-            "gs_image_l1", "gs_render_bwd", "gs_render_bwd_var",
+            "gs_image_l1", "gs_image_loss", "gs_render_bwd", "gs_render_bwd_var",
             "gs_workspace_status", "gs_workspace_info", "gs_workspace_copy", "gs_workspace_set_profiling",
             "gs_workspace_stage_ms", "gs_image_l1_noalloc", "gs_status_string", "gs_last_error")
 IMAGE_L1_NOALLOC_MAX = 1024 * 65536  # GS_IMAGE_L1_NOALLOC_BLOCKS * GS_IMAGE_L1_NOALLOC_CHUNK
 STAGES = ("project", "compact", "depth_sort", "emit", "tile_sort", "ranges", "raster_fwd", "image_l1",
-          "depth_loss", "zero_grad", "raster_bwd", "project_bwd")
+          "depth_loss", "zero_grad", "raster_bwd", "project_bwd", "image_ssim")
 
 
 class GsError(RuntimeError):
@@ -96,6 +96,7 @@ def lib() -> ctypes.CDLL:
     L.gs_depth_loss.argtypes = [P, P, P, P, i64, P, P, P]
     L.gs_depth_loss_var.argtypes = [P, P, P, P, P, i64, P, P, P, P]
     L.gs_image_l1.argtypes = [P, P, P, P, P, P]
+    L.gs_image_loss.argtypes = [P, P, P, ctypes.c_float, P, P, P]
     L.gs_render_bwd.argtypes = [P, ctypes.POINTER(GsGaussians), P, P, P, P, ctypes.POINTER(GsGrads), P]
     L.gs_render_bwd_var.argtypes = [P, ctypes.POINTER(GsGaussians), P, P, P, P, P, P, ctypes.POINTER(GsGrads), P]
     L.gs_workspace_status.argtypes = [P, P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
@@ -109,7 +110,8 @@ def lib() -> ctypes.CDLL:
     L.gs_last_error.argtypes = []
     L.gs_last_error.restype = ctypes.c_char_p
     for name in ("gs_workspace_create", "gs_project", "gs_bin_sort", "gs_render_fwd", "gs_render_fwd_var",
-                 "gs_depth_loss", "gs_depth_loss_var", "gs_image_l1", "gs_render_bwd", "gs_render_bwd_var",
+                 "gs_depth_loss", "gs_depth_loss_var", "gs_image_l1", "gs_image_loss", "gs_render_bwd",
+                 "gs_render_bwd_var",
                  "gs_workspace_status", "gs_workspace_info",
                  "gs_workspace_copy", "gs_workspace_set_profiling", "gs_workspace_stage_ms",
                  "gs_image_l1_noalloc"):
@@ -182,6 +184,10 @@ def gs_depth_loss_var(ws, alpha, depth_mean, depth_var, lidar, n_pts, loss, dL_d
 
 def gs_image_l1(ws, rgb, target, loss, dL_drgb, stream):
     _check(lib().gs_image_l1(ws, rgb, target, loss, dL_drgb, stream), "gs_image_l1")
+
+
+def gs_image_loss(ws, rgb, target, lam, loss, dL_drgb, stream):
+    _check(lib().gs_image_loss(ws, rgb, target, float(lam), loss, dL_drgb, stream), "gs_image_loss")
 
 
 def gs_image_l1_noalloc(rgb, target, n, loss, dL_drgb, stream):
@@ -380,6 +386,12 @@ class Renderer:
     def image_l1(self, rgb, target, dL_drgb=None, stream=None):
         loss = self.torch.zeros(1, device=self.device)
         gs_image_l1(self.ws, _ptr(rgb), _ptr(target), _ptr(loss), _ptr(dL_drgb), _stream(stream))
+        return loss
+
+    def image_loss(self, rgb, target, lam=0.2, dL_drgb=None, stream=None):
+        """Eq. (6): returns a [3] tensor (total, L1, 1 - SSIM); accumulates dL/drgb when given."""
+        loss = self.torch.zeros(3, device=self.device)
+        gs_image_loss(self.ws, _ptr(rgb), _ptr(target), lam, _ptr(loss), _ptr(dL_drgb), _stream(stream))
         return loss
 
     def status(self, stream=None):
