@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(LT) k_image_loss_final(const double *l1part, i
     for (int i = threadIdx.x; i < nb; i += LT) a += l1part[i];
     for (int64_t i = threadIdx.x; i < ns; i += LT) b += spart[i];
     const double l1 = block_sum_d(a, sm) / (double)n;
-    const double dssim = 1.0 - block_sum_d(b, sm) / (double)n;
+    const double dssim = block_sum_d(b, sm) / (double)n;  // the SSIM partials hold sums of 1 - S
     if (threadIdx.x == 0) {
         loss[0] = (float)((1.0 - (double)lambda) * l1 + (double)lambda * dssim);
         loss[1] = (float)l1;

@@ -11,7 +11,7 @@
 // horizontally, then vertically, and writes S's partial derivatives w.r.t.
 // the three window sums that depend on x,
 //   d1 = dS/dE[x],  d2 = dS/dE[x^2],  d12 = dS/dE[xy],
-// plus a per-CTA sum of S (double).  Backward: the same tiling filters
+// plus a per-CTA sum of 1 - S (double).  Backward: the same tiling filters
 // (d1, d2, d12) with the same window (the adjoint of a zero-padded symmetric
 // filter is itself) and adds scale * (G*d1 + 2 x G*d2 + y G*d12) to dL/dx.
 //
@@ -35,7 +35,14 @@ namespace {
 
 constexpr int TX = 32, TY = 16, R = 5, K = 2 * R + 1;
 constexpr int IW = TX + 2 * R, IH = TY + 2 * R;
-constexpr int NT = 256, ROWS = NT / TX;  // 8 output rows per pass, 2 passes
+constexpr int SW = IW + 1;  // staged row stride: odd, so the blocked row reads hit distinct banks
+constexpr int HW = TX + 1;  // filtered row stride
+constexpr int NT = 256;
+constexpr int HB = 4;                     // horizontal outputs per thread
+constexpr int HITEMS = IH * (TX / HB);    // 208 row segments per tile
+constexpr int VB = 2;                     // vertical outputs per thread (consecutive rows)
+static_assert(TY == VB * (NT / TX), "one vertical pass covers the tile");
+static_assert(HITEMS <= NT, "one horizontal pass covers the tile");
 constexpr float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
 
 struct SsimArgs {
@@ -44,9 +51,10 @@ struct SsimArgs {
     const float *x, *y;  // planar images (rendered, target)
     float *dmap;         // [3][n_elem] partials, nullptr: no backward
     float *grad;         // dL/dx, accumulated
-    double *part;        // [grid] per-CTA sums of S
+    double *part;        // [grid] per-CTA sums of 1 - S
     int64_t n_elem;
     float scale;         // gradient scale of S (backward)
+    float gsum;          // sum of the 11 weights (the in-image weight of an interior axis)
     float g[K];          // window weights
 };
 
@@ -77,87 +85,129 @@ __device__ __forceinline__ PlaneTile locate(const SsimArgs &A, int b) {
     return p;
 }
 
-__device__ __forceinline__ double block_sum(double v, double *sm) {
+// Sum of the window weights whose tap lands inside [0, n) for an output at i.
+__device__ __forceinline__ float inside_weight(const SsimArgs &A, int i, int n) {
+    if (i >= R && i < n - R) return A.gsum;
+    float w = 0.f;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (lane == 0) sm[w] = v;
-    __syncthreads();
-    double t = 0.0;
-    for (int i = 0; i < NT / 32; ++i) t += sm[i];
-    return t;
+    for (int k = 0; k < K; ++k) {
+        const int t = i - R + k;
+        w += t >= 0 && t < n ? A.g[k] : 0.f;
+    }
+    return w;
 }
 
-__global__ void __launch_bounds__(NT) k_ssim_fwd(SsimArgs A) {
-    __shared__ float sx[IH][IW], sy[IH][IW];
-    __shared__ float sh[5][IH][TX];
-    __shared__ double red[NT / 32];
-    const PlaneTile P = locate(A, blockIdx.x);
-    const float *x = A.x + P.base, *y = A.y + P.base;
-    const int tid = threadIdx.x;
-    // shift: the tile's first pixel, always inside the image
-    const float cx = x[(int64_t)P.y0 * P.W + P.x0], cy = y[(int64_t)P.y0 * P.W + P.x0];
-    for (int i = tid; i < IH * IW; i += NT) {
-        const int r = i / IW, c = i % IW;
-        const int gx = P.x0 - R + c, gy = P.y0 - R + r;
-        const bool in = gx >= 0 && gx < P.W && gy >= 0 && gy < P.H;
-        const int64_t o = (int64_t)gy * P.W + gx;
-        sx[r][c] = in ? x[o] - cx : 0.f;
-        sy[r][c] = in ? y[o] - cy : 0.f;
+// Horizontal pass of the forward: row segment `item` (row r, columns
+// c0..c0+HB-1) of x', y', x'^2, y'^2 and x'y' from HB + 2R staged x', y'.
+__device__ __forceinline__ void horizontal_fwd(const SsimArgs &A, const float (*src)[IH][SW],
+                                               float (*dst)[IH][HW], int item) {
+    const int r = item / (TX / HB), c0 = (item % (TX / HB)) * HB;
+    float u[HB + 2 * R], w[HB + 2 * R];
+#pragma unroll
+    for (int j = 0; j < HB + 2 * R; ++j) {
+        u[j] = src[0][r][c0 + j];
+        w[j] = src[1][r][c0 + j];
     }
-    __syncthreads();
-    for (int i = tid; i < IH * TX; i += NT) {
-        const int r = i / TX, c = i % TX;
+#pragma unroll
+    for (int o = 0; o < HB; ++o) {
         float a = 0.f, b = 0.f, aa = 0.f, bb = 0.f, ab = 0.f;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            const float u = sx[r][c + k], w = sy[r][c + k];
-            const float gu = A.g[k] * u, gw = A.g[k] * w;
+            const float gu = A.g[k] * u[o + k], gw = A.g[k] * w[o + k];
             a += gu;
             b += gw;
-            aa = __fmaf_rn(gu, u, aa);
-            bb = __fmaf_rn(gw, w, bb);
-            ab = __fmaf_rn(gu, w, ab);
+            aa = __fmaf_rn(gu, u[o + k], aa);
+            bb = __fmaf_rn(gw, w[o + k], bb);
+            ab = __fmaf_rn(gu, w[o + k], ab);
         }
-        sh[0][r][c] = a;
-        sh[1][r][c] = b;
-        sh[2][r][c] = aa;
-        sh[3][r][c] = bb;
-        sh[4][r][c] = ab;
+        dst[0][r][c0 + o] = a;
+        dst[1][r][c0 + o] = b;
+        dst[2][r][c0 + o] = aa;
+        dst[3][r][c0 + o] = bb;
+        dst[4][r][c0 + o] = ab;
+    }
+}
+
+// Horizontal pass of the backward over NQ staged maps.
+template <int NQ>
+__device__ __forceinline__ void horizontal(const SsimArgs &A, const float (*src)[IH][SW], float (*dst)[IH][HW],
+                                           int item) {
+    const int r = item / (TX / HB), c0 = (item % (TX / HB)) * HB;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        float v[HB + 2 * R];
+#pragma unroll
+        for (int j = 0; j < HB + 2 * R; ++j) v[j] = src[q][r][c0 + j];
+#pragma unroll
+        for (int o = 0; o < HB; ++o) {
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k < K; ++k) acc = __fmaf_rn(A.g[k], v[o + k], acc);
+            dst[q][r][c0 + o] = acc;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(NT) k_ssim_fwd(SsimArgs A) {
+    __shared__ float st[2][IH][SW];  // staged x', y'
+    __shared__ float sh[5][IH][HW];
+    __shared__ double red[NT / 32];
+    const PlaneTile P = locate(A, blockIdx.x);
+    const float *x = A.x + P.base, *y = A.y + P.base;
+    const int tid = threadIdx.x, lx = tid & 31, ly = tid >> 5;
+    // shift: the tile's first pixel, always inside the image
+    const float cx = x[(int64_t)P.y0 * P.W + P.x0], cy = y[(int64_t)P.y0 * P.W + P.x0];
+    for (int r = ly; r < IH; r += NT / 32) {
+        const int gy = P.y0 - R + r;
+        for (int c = lx; c < IW; c += 32) {
+            const int gx = P.x0 - R + c;
+            const bool in = gx >= 0 && gx < P.W && gy >= 0 && gy < P.H;
+            const int64_t o = (int64_t)gy * P.W + gx;
+            st[0][r][c] = in ? x[o] - cx : 0.f;
+            st[1][r][c] = in ? y[o] - cy : 0.f;
+        }
     }
     __syncthreads();
-    const int tx = tid % TX, ty = tid / TX;
-    double acc = 0.0;
+    if (tid < HITEMS) horizontal_fwd(A, st, sh, tid);
+    __syncthreads();
+    const int gx = P.x0 + lx, oy0 = VB * ly;
+    float m[VB][5];
 #pragma unroll
-    for (int pass = 0; pass < TY / ROWS; ++pass) {
-        const int oy = ty + pass * ROWS;
-        const int gx = P.x0 + tx, gy = P.y0 + oy;
+    for (int b = 0; b < VB; ++b)
+#pragma unroll
+        for (int q = 0; q < 5; ++q) m[b][q] = 0.f;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        float v[K + VB - 1];
+#pragma unroll
+        for (int j = 0; j < K + VB - 1; ++j) v[j] = sh[q][oy0 + j][lx];
+#pragma unroll
+        for (int b = 0; b < VB; ++b)
+#pragma unroll
+            for (int k = 0; k < K; ++k) m[b][q] = __fmaf_rn(A.g[k], v[b + k], m[b][q]);
+    }
+    float dsum = 0.f;  // sum of 1 - S over this thread's pixels
+    const float wx = inside_weight(A, gx, P.W);
+#pragma unroll
+    for (int b = 0; b < VB; ++b) {
+        const int gy = P.y0 + oy0 + b;
         if (gx >= P.W || gy >= P.H) continue;
-        float m[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-        float wx = 0.f, wy = 0.f;  // window weight inside the image, per axis
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-#pragma unroll
-            for (int q = 0; q < 5; ++q) m[q] = __fmaf_rn(A.g[j], sh[q][oy + j][tx], m[q]);
-            const int ix = gx - R + j, iy = gy - R + j;
-            wx += ix >= 0 && ix < P.W ? A.g[j] : 0.f;
-            wy += iy >= 0 && iy < P.H ? A.g[j] : 0.f;
-        }
-        const float W = wx * wy, cw = 1.f - W;
-        const float px = m[0], py = m[1];  // E[x'], E[y']
+        const float W = wx * inside_weight(A, gy, P.H), cw = 1.f - W;
+        const float px = m[b][0], py = m[b][1];  // E[x'], E[y']
         const float mx = __fmaf_rn(cx, W, px), my = __fmaf_rn(cy, W, py);
-        const float sxx = (m[2] - px * px) + cw * cx * (2.f * px + cx * W);
-        const float syy = (m[3] - py * py) + cw * cy * (2.f * py + cy * W);
-        const float sxy = (m[4] - px * py) + cw * (cy * px + cx * py + cx * cy * W);
+        const float sxx = (m[b][2] - px * px) + cw * cx * (2.f * px + cx * W);
+        const float syy = (m[b][3] - py * py) + cw * cy * (2.f * py + cy * W);
+        const float sxy = (m[b][4] - px * py) + cw * (cy * px + cx * py + cx * cy * W);
         const float Aa = 2.f * mx * my + C1, B = 2.f * sxy + C2;
         const float Cc = mx * mx + my * my + C1, D = sxx + syy + C2;
         const float iC = 1.f / Cc, iD = 1.f / D;
         const float S = Aa * B * iC * iD;
-        acc += (double)S;
+        // 1 - S as (Cc D - A B) / (Cc D): keeps its relative precision near S = 1
+        dsum += __fmaf_rn(Cc, D, -Aa * B) * iC * iD;
         if (A.dmap) {
-            const float dsxx = -S * iD;                                       // -A B / (Cc D^2)
-            const float dsxy = 2.f * Aa * iC * iD;                            // 2 A / (Cc D)
-            const float dmu = 2.f * B * iD * (my * Cc - mx * Aa) * iC * iC;   // dS/dmu_x, s fixed
+            const float dsxx = -S * iD;                                      // -A B / (Cc D^2)
+            const float dsxy = 2.f * Aa * iC * iD;                           // 2 A / (Cc D)
+            const float dmu = 2.f * B * iD * (my * Cc - mx * Aa) * iC * iC;  // dS/dmu_x, s fixed
             const float d1 = dmu - 2.f * mx * dsxx - my * dsxy;
             const int64_t e = P.base + (int64_t)gy * P.W + gx;
             A.dmap[e] = d1;
@@ -165,49 +215,59 @@ __global__ void __launch_bounds__(NT) k_ssim_fwd(SsimArgs A) {
             A.dmap[2 * A.n_elem + e] = dsxy;
         }
     }
-    const double t = block_sum(acc, red);
-    if (tid == 0) A.part[blockIdx.x] = t;
+    // warp sum in float (at most 64 terms), then the 8 warps in double
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+    if (lx == 0) red[ly] = (double)dsum;
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0.0;
+        for (int i = 0; i < NT / 32; ++i) t += red[i];
+        A.part[blockIdx.x] = t;
+    }
 }
 
 __global__ void __launch_bounds__(NT) k_ssim_bwd(SsimArgs A) {
-    __shared__ float sd[3][IH][IW];
-    __shared__ float sh[3][IH][TX];
+    __shared__ float st[3][IH][SW];
+    __shared__ float sh[3][IH][HW];
     const PlaneTile P = locate(A, blockIdx.x);
-    const int tid = threadIdx.x;
-    for (int i = tid; i < IH * IW; i += NT) {
-        const int r = i / IW, c = i % IW;
-        const int gx = P.x0 - R + c, gy = P.y0 - R + r;
-        const bool in = gx >= 0 && gx < P.W && gy >= 0 && gy < P.H;
-        const int64_t e = P.base + (int64_t)gy * P.W + gx;
+    const int tid = threadIdx.x, lx = tid & 31, ly = tid >> 5;
+    for (int r = ly; r < IH; r += NT / 32) {
+        const int gy = P.y0 - R + r;
+        for (int c = lx; c < IW; c += 32) {
+            const int gx = P.x0 - R + c;
+            const bool in = gx >= 0 && gx < P.W && gy >= 0 && gy < P.H;
+            const int64_t e = P.base + (int64_t)gy * P.W + gx;
 #pragma unroll
-        for (int q = 0; q < 3; ++q) sd[q][r][c] = in ? A.dmap[q * A.n_elem + e] : 0.f;
+            for (int q = 0; q < 3; ++q) st[q][r][c] = in ? A.dmap[q * A.n_elem + e] : 0.f;
+        }
     }
     __syncthreads();
-    for (int i = tid; i < IH * TX; i += NT) {
-        const int r = i / TX, c = i % TX;
-        float s[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-        for (int k = 0; k < K; ++k)
-#pragma unroll
-            for (int q = 0; q < 3; ++q) s[q] = __fmaf_rn(A.g[k], sd[q][r][c + k], s[q]);
-#pragma unroll
-        for (int q = 0; q < 3; ++q) sh[q][r][c] = s[q];
-    }
+    if (tid < HITEMS) horizontal<3>(A, st, sh, tid);
     __syncthreads();
-    const int tx = tid % TX, ty = tid / TX;
+    const int gx = P.x0 + lx, oy0 = VB * ly;
+    float f[VB][3];
 #pragma unroll
-    for (int pass = 0; pass < TY / ROWS; ++pass) {
-        const int oy = ty + pass * ROWS;
-        const int gx = P.x0 + tx, gy = P.y0 + oy;
+    for (int b = 0; b < VB; ++b)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) f[b][q] = 0.f;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        float v[K + VB - 1];
+#pragma unroll
+        for (int j = 0; j < K + VB - 1; ++j) v[j] = sh[q][oy0 + j][lx];
+#pragma unroll
+        for (int b = 0; b < VB; ++b)
+#pragma unroll
+            for (int k = 0; k < K; ++k) f[b][q] = __fmaf_rn(A.g[k], v[b + k], f[b][q]);
+    }
+#pragma unroll
+    for (int b = 0; b < VB; ++b) {
+        const int gy = P.y0 + oy0 + b;
         if (gx >= P.W || gy >= P.H) continue;
-        float f[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-        for (int j = 0; j < K; ++j)
-#pragma unroll
-            for (int q = 0; q < 3; ++q) f[q] = __fmaf_rn(A.g[j], sh[q][oy + j][tx], f[q]);
         const int64_t e = P.base + (int64_t)gy * P.W + gx;
         const float xv = A.x[e], yv = A.y[e];
-        A.grad[e] += A.scale * (f[0] + 2.f * xv * f[1] + yv * f[2]);
+        A.grad[e] += A.scale * (f[b][0] + 2.f * xv * f[b][1] + yv * f[b][2]);
     }
 }
 
@@ -236,7 +296,11 @@ gs_status launch_ssim(gs_workspace *ws, const float *rgb, const float *target, f
         g[i] = std::exp(-(double)((i - R) * (i - R)) / (2.0 * 1.5 * 1.5));
         sum += g[i];
     }
-    for (int i = 0; i < K; ++i) A.g[i] = (float)(g[i] / sum);
+    A.gsum = 0.f;
+    for (int i = 0; i < K; ++i) {
+        A.g[i] = (float)(g[i] / sum);
+        A.gsum += A.g[i];
+    }
     const int grid = (int)ws->n_ssim_tiles;
     if (grid == 0) return GS_OK;
     StageTimer timer(ws, GS_STAGE_IMAGE_SSIM, s);
