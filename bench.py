@@ -24,6 +24,7 @@ value = pixels of all ranks / max time over ranks.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import math
 import os
@@ -56,6 +57,10 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=640, help="crop width (px) per view for the oracle sample")
     ap.add_argument("--ssim-lambda", type=float, default=0.0,
                     help="weight lambda of the SSIM term of Eq. 6 (0: L1 image loss only)")
+    ap.add_argument("--adam", action="store_true",
+                    help="end the step with an Adam update of every Gaussian parameter (inside the timed graph)")
+    ap.add_argument("--lifecycle", action="store_true",
+                    help="also time one map-lifecycle pass (prune, reset, split / clone) on the workload")
     ap.add_argument("--depth-loss", default="l1", choices=list(DEPTH_LOSSES),
                     help="depth term of the step: l1, kl (Eq. 7, fixed sigma_u) or kl-var (Eq. 7 with the "
                          "rendered variance: forward and backward with the central depth moment)")
@@ -68,7 +73,13 @@ DEPTH_LOSSES = {"l1": "L1 depth", "kl": "KL depth (fixed sigma_u)", "kl-var": "K
 def loss_label(args) -> str:
     lam = getattr(args, "ssim_lambda", 0.0)
     img = "L1 rgb" if lam == 0 else f"(1 - {lam:g}) L1 + {lam:g} (1 - SSIM) rgb"
-    return img + " + " + DEPTH_LOSSES[getattr(args, "depth_loss", "l1")]
+    return img + " + " + DEPTH_LOSSES[getattr(args, "depth_loss", "l1")] + (" + Adam" if getattr(args, "adam", False)
+                                                                           else "")
+
+
+# per-array learning rates of the Adam option (means, log-scales, quaternions,
+# opacity logits, SH): the usual 3DGS values
+ADAM_LR = (1.6e-4, 5e-3, 1e-3, 5e-2, 2.5e-3)
 
 
 def workload_config(sc, args, tile=None, depth=None):
@@ -194,6 +205,51 @@ FLOPS_PER_FRAGMENT_BWD = 49
 FLOPS_PER_FRAGMENT_VAR = 9
 
 
+def lifecycle_timing(torch, G, step, sc, dev, reps=5):
+    """One lifecycle pass (prune, opacity reset, split / clone) over the
+    workload's Gaussians with the densification statistic of the last step;
+    gamma_g is set to the 90th percentile of the mean image-space gradient so
+    that about a tenth of the visible splats densify.  CUDA events, mean of
+    `reps` passes after one warm-up."""
+    keys = ("means", "log_scales", "quats", "opacity_logits", "sh")
+    params = dict(zip(keys, step.P))
+    acc, cnt = step.grads["densify_acc"], step.grads["densify_cnt"]
+    g = acc[cnt > 0] / cnt[cnt > 0].float()
+    gamma = float(torch.quantile(g[:1 << 20].float(), 0.9)) if g.numel() else 1.0
+    ls_max = step.P[1].max(1).values
+    kappa = float(torch.quantile(ls_max[:1 << 20], 0.5).exp())
+    lp = G.lifecycle_params(G.GS_LC_PRUNE | G.GS_LC_DENSIFY | G.GS_LC_RESET, densify_grad=gamma,
+                            split_scale=kappa, clone_scale=kappa)
+    normals = torch.randn(sc.n, 2, 3, device=dev, generator=torch.Generator(device=dev).manual_seed(0))
+    lc = G.Lifecycle(sc.n, len(sc.submap_offsets) - 1)
+    cap = 2 * sc.n
+    out = {k: torch.empty((cap,) + tuple(v.shape[1:]), device=dev) for k, v in params.items()}
+    offs = torch.as_tensor(sc.submap_offsets, dtype=torch.int64, device=dev)
+    offs_out = torch.empty_like(offs)
+    s = G._stream()
+
+    def run():
+        G.gs_lifecycle_run(lc.lc, lp, sc.sh_degree, sc.n, offs.numel() - 1, G._ptr(offs), G.param_arrays(params),
+                           None, None, G._ptr(acc), G._ptr(cnt), G._ptr(normals), G.param_arrays(out), None, None,
+                           cap, G._ptr(offs_out), None, s)
+    run()
+    st, n_out = G.gs_lifecycle_status(lc.lc, s)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    ev[0].record()
+    for _ in range(reps):
+        run()
+    ev[1].record()
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1]) / reps
+    lc.close()
+    nsh = 3 * (sc.sh_degree + 1) ** 2
+    bytes_moved = sc.n * (4 * 11 + 8) + n_out * 4 * (11 + nsh)
+    return {"ms": ms, "n_in": sc.n, "n_out": n_out, "status": int(st), "gamma_g": gamma, "kappa": kappa,
+            "algorithmic_bytes": int(bytes_moved + sc.n * 4 * nsh),
+            "gbs": (bytes_moved + sc.n * 4 * nsh) / (ms * 1e-3) / 1e9}
+
+
 def job_throughput(pix_per_rank: int, ms: float, world: int) -> float:
     """Whole-job Mpix/s: every rank renders its own replica in `ms`."""
     return pix_per_rank * world / (ms * 1e-3) / 1e6
@@ -206,7 +262,7 @@ def job_throughput(pix_per_rank: int, ms: float, world: int) -> float:
 class Step:
     """All device buffers of one mapping step plus the calls that make it."""
 
-    def __init__(self, G, torch, sc, cfg, dev, inst_capacity=None, var=False, ssim_lambda=0.0):
+    def __init__(self, G, torch, sc, cfg, dev, inst_capacity=None, var=False, ssim_lambda=0.0, adam=False):
         self.G, self.torch, self.sc, self.dev = G, torch, sc, dev
         self.var = var
         self.ssim_lambda = ssim_lambda
@@ -232,6 +288,11 @@ class Step:
         # depth mean and variance and their adjoints (variance KL only)
         self.dist = [torch.empty(npx, device=dev) for _ in range(2)] if var else []
         self.g_var = [torch.zeros(npx, device=dev) for _ in range(2)] if var else []
+        # Adam moments (the bias-correction step is a constant of the captured graph)
+        self.adam = adam
+        if adam:
+            self.adam_m = [torch.zeros_like(p) for p in self.P]
+            self.adam_v = [torch.zeros_like(p) for p in self.P]
 
     def zero(self):
         self.g_rgb.zero_()
@@ -286,8 +347,15 @@ class Step:
             else:
                 G.gs_render_bwd(r.ws, r.gaussians(*self.P), G._ptr(r.cams_dev), G._ptr(self.g_rgb),
                                 G._ptr(self.g_depth), None, grads, G._stream())
-        return [("zero", self.zero), ("project", project), ("bin_sort", binsort), ("raster_fwd", fwd),
-                ("losses", losses), ("backward", bwd)]
+        def adam():
+            keys = ("means", "log_scales", "quats", "opacity_logits", "sh")
+            pa = lambda ts: G.GsParamArrays(*(t.data_ptr() for t in ts))
+            ap = G.GsAdamParams((ctypes.c_float * 5)(*ADAM_LR), 0.9, 0.999, 1e-15, 10)
+            G.gs_adam_step(pa(self.P), pa([self.grads[k] for k in keys]), pa(self.adam_m), pa(self.adam_v),
+                           self.P[0].shape[0], self.sc.sh_degree, ap, G._stream())
+        st = [("zero", self.zero), ("project", project), ("bin_sort", binsort), ("raster_fwd", fwd),
+              ("losses", losses), ("backward", bwd)]
+        return st + ([("adam", adam)] if self.adam else [])
 
     def run(self):
         for _, f in self.stages():
@@ -372,8 +440,8 @@ def oracle_sample(sc, crop_w):
     return cams
 
 
-def run_oracle_step(O, P, cams, cfg, lidar_full, sc, depth_loss="l1", ssim_lambda=0.0):
-    """project -> bin -> forward -> image + depth losses -> backward, in FP64."""
+def run_oracle_step(O, P, cams, cfg, lidar_full, sc, depth_loss="l1", ssim_lambda=0.0, adam=False):
+    """project -> bin -> forward -> image + depth losses -> backward (-> Adam), in FP64."""
     rec = O.project(P, cams, cfg)
     keys, vals, ranges = O.bin(P, cams, cfg, rec)
     out = O.render_fwd(P, cams, cfg, rec, vals, ranges)
@@ -386,11 +454,16 @@ def run_oracle_step(O, P, cams, cfg, lidar_full, sc, depth_loss="l1", ssim_lambd
     if depth_loss == "kl-var":
         mean, var = O.render_depth_dist(P, cams, cfg, rec, vals, ranges)
         _, gm, gv, _ = O.depth_loss_var(P, cams, cfg, out["alpha"], mean, var, lidar_full)
-        O.render_bwd(P, cams, cfg, rec, vals, ranges, gC, np.zeros(npx), None, gm, gv)
+        g = O.render_bwd(P, cams, cfg, rec, vals, ranges, gC, np.zeros(npx), None, gm, gv)
     else:
         _, gD, _ = O.depth_loss(P, cams, cfg, out["depth"], out["alpha"], lidar_full,
                                 mode=1 if depth_loss == "kl" else 0)
-        O.render_bwd(P, cams, cfg, rec, vals, ranges, gC, gD)
+        g = O.render_bwd(P, cams, cfg, rec, vals, ranges, gC, gD)
+    if adam:
+        from oracle import lifecycle as OL
+        for i, k in enumerate(OL.FIELDS):
+            a = getattr(P, k)
+            OL.adam(a, g[k], np.zeros_like(a), np.zeros_like(a), 10, ADAM_LR[i])
     return npx
 
 
@@ -409,7 +482,7 @@ def cpu_baseline(sc, args, reps=1):
     t0 = time.perf_counter()
     npx = 0
     for _ in range(reps):
-        npx += run_oracle_step(O, P, cams, cfg, lid, sc, args.depth_loss, args.ssim_lambda)
+        npx += run_oracle_step(O, P, cams, cfg, lid, sc, args.depth_loss, args.ssim_lambda, args.adam)
     dt = time.perf_counter() - t0
     sample = (f"FP64 oracle, full step (project all {sc.n} Gaussians x {len(cams)} views, bin, forward, "
               f"{loss_label(args)}, backward) on centred {cams[0].width}x{cams[0].height} crops "
@@ -476,13 +549,13 @@ def main():
         cfg = G.gs_config_default(tile_w=tw, tile_h=th, batch_depth=depth,
                                   depth_mode=1 if args.depth_loss == "kl" else 0)
         mom = args.depth_loss == "kl-var"
-        st_ = Step(G, torch, sc, cfg, dev, var=mom, ssim_lambda=args.ssim_lambda)
+        st_ = Step(G, torch, sc, cfg, dev, var=mom, ssim_lambda=args.ssim_lambda, adam=args.adam)
         st_.run()
         code, need_, _ = st_.r.status()
         if code == G.GS_ERR_CAPACITY or need_ > st_.r.info["inst_capacity"]:
             st_.r.close()
             st_ = Step(G, torch, sc, cfg, dev, inst_capacity=int(need_ * 1.25) + 1024, var=mom,
-                       ssim_lambda=args.ssim_lambda)
+                       ssim_lambda=args.ssim_lambda, adam=args.adam)
             st_.run()
         return st_
 
@@ -499,7 +572,7 @@ def main():
             return float(np.mean(t_))
         key = autotune.signature(sc.cameras, sc.n, sc.sh_degree, sc.submap_offsets,
                                  extra="bench-step" + ("" if args.depth_loss == "l1" else "-" + args.depth_loss)
-                                 + ("" if args.ssim_lambda == 0 else "-ssim"))
+                                 + ("" if args.ssim_lambda == 0 else "-ssim") + ("-adam" if args.adam else ""))
         tuned = autotune.tune(measure, key=key)
         tw, th, args.depth = tuned["tile_w"], tuned["tile_h"], tuned["batch_depth"]
     else:
@@ -532,6 +605,7 @@ def main():
 
     breakdown = stage_breakdown(torch, step, max(3, args.steps // 2), flush)
     kern = kernel_breakdown(torch, G, step, max(3, args.steps // 2), flush)
+    lifecycle = lifecycle_timing(torch, G, step, sc, dev) if args.lifecycle else None
 
     # per-view plain version: one workspace per camera, no graph
     per_view = None
@@ -556,7 +630,7 @@ def main():
             sub.lidar = lid
             pv_steps.append(Step(G, torch, sub, G.gs_config_default(depth_mode=1 if args.depth_loss == "kl" else 0),
                                  dev, inst_capacity=need + 1024, var=args.depth_loss == "kl-var",
-                                 ssim_lambda=args.ssim_lambda))
+                                 ssim_lambda=args.ssim_lambda, adam=args.adam))
         run_all = lambda: [s.run() for s in pv_steps]
         pv_times = time_steps(torch, run_all, max(3, args.steps // 2), 3, flush)
         pv_ms = float(np.mean(pv_times))
@@ -645,7 +719,7 @@ def main():
                                                                 "ms": tuned["timings"]}),
             "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches_per_step * args.steps),
             "launches_per_step": int(launches_per_step), "roofline": roofline, "roofline_hbm": roofline_hbm,
-            "per_view": per_view, "breakdown_ms": breakdown, "kernel_ms": kern,
+            "per_view": per_view, "breakdown_ms": breakdown, "kernel_ms": kern, "lifecycle": lifecycle,
             "counts": {"visible_pairs": nvis, "instances": n_inst, "tiles": n_tiles}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = {k: v for k, v in cpu_baseline(sc, args, reps=2).items()

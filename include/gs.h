@@ -247,6 +247,79 @@ gs_status gs_workspace_copy(gs_workspace *ws, int32_t which, void *dst, int64_t 
 gs_status gs_image_l1_noalloc(const float *rgb, const float *target, int64_t n, float *loss,
                               float *dL_drgb, void *stream);
 
+/* ------------------------------------------------------------------------ */
+/* Map lifecycle and optimiser step (Sec. III-B, "Gaussian Splats Lifecycle */
+/* Operations"; the paper names no optimiser, Adam is this library's).       */
+/* ------------------------------------------------------------------------ */
+
+/* Mutable Gaussian parameter arrays (device, float32, the layouts of
+ * gs_gaussians).  Also used for gradients and optimiser moments. */
+typedef struct {
+    float *means, *log_scales, *quats, *opacity_logits, *sh;
+} gs_param_arrays;
+
+#define GS_LC_PRUNE 1   /* drop splats with o < prune_opacity, s > prune_scale_max or s < prune_scale_min */
+#define GS_LC_DENSIFY 2 /* mean image-space gradient > densify_grad: split if s > split_scale, clone if s <= clone_scale */
+#define GS_LC_RESET 4   /* prune_opacity < o < reset_opacity and reset_scale_min < s < reset_scale_max: o = reset_opacity */
+
+/* Lifecycle thresholds.  s is the largest axis scale exp(log_scale); o the
+ * opacity sigmoid(logit).  Every comparison is made on the stored logit or
+ * log-scale against the threshold moved to that domain (float32).  The paper
+ * gives prune_opacity 0.01, prune_scale_max 0.3 m, prune_scale_min 5e-5 m;
+ * densify_grad (gamma_g), split_scale (kappa), clone_scale (2 s_init),
+ * reset_opacity, reset_scale_min/max (s_min, s_max) are left to the caller. */
+typedef struct {
+    int32_t ops;          /* GS_LC_* bits */
+    float prune_opacity, prune_scale_max, prune_scale_min;
+    float densify_grad;   /* on the mean of ||dL/d(u,v)|| (pixels) over the counted views */
+    float split_scale, clone_scale;
+    float split_shrink;   /* children's scales = parent's / split_shrink (1.6) */
+    float reset_opacity, reset_scale_min, reset_scale_max;
+} gs_lifecycle_params;
+
+typedef struct gs_lifecycle gs_lifecycle;
+
+/* Scratch for up to max_in input splats and max_submaps submaps (allocates). */
+gs_status gs_lifecycle_create(int64_t max_in, int32_t max_submaps, gs_lifecycle **out);
+void gs_lifecycle_destroy(gs_lifecycle *lc);
+
+/* One lifecycle pass over n_in splats in order.  Per splat: prune drops it;
+ * otherwise the opacity reset applies, then densification: a split writes two
+ * children mu + R(q) diag(exp(log_scale)) z_k (z_k = split_normals[j][k][0..2],
+ * standard-normal samples the caller draws) with log_scale - ln(split_shrink)
+ * and the parent's quaternion, opacity and SH; a clone writes the splat and an
+ * exact copy after it.  The outputs keep the input order, so each submap stays
+ * contiguous: submap_offsets_out (device, n_submaps+1) receives the new
+ * partition and n_out (device, 1, nullable) the number of output splats.
+ * in_m/in_v/out_m/out_v (all or none): Adam moments, carried for surviving
+ * splats and zero for copies and children.  densify_acc/densify_cnt (device,
+ * n_in; the gs_grads statistic) and split_normals (device, [n_in][2][3]) are
+ * needed with GS_LC_DENSIFY.  submap_offsets_in (device, n_submaps+1).
+ * Outputs must not alias inputs.  If the outputs need more than out_capacity
+ * rows nothing is written and gs_lifecycle_status returns GS_ERR_CAPACITY. */
+gs_status gs_lifecycle_run(gs_lifecycle *lc, const gs_lifecycle_params *p, int32_t sh_degree, int64_t n_in,
+                           int32_t n_submaps, const int64_t *submap_offsets_in, const gs_param_arrays *in,
+                           const gs_param_arrays *in_m, const gs_param_arrays *in_v, const float *densify_acc,
+                           const int32_t *densify_cnt, const float *split_normals, const gs_param_arrays *out,
+                           const gs_param_arrays *out_m, const gs_param_arrays *out_v, int64_t out_capacity,
+                           int64_t *submap_offsets_out, int64_t *n_out, void *stream);
+
+/* Synchronise `stream`; *n_needed (nullable) = outputs the last run needed;
+ * GS_ERR_CAPACITY if they exceeded its capacity. */
+gs_status gs_lifecycle_status(gs_lifecycle *lc, void *stream, int64_t *n_needed);
+
+/* Adam step on n splats: m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
+ * p -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps), with one
+ * learning rate per array (means, log_scales, quats, opacity_logits, sh). */
+typedef struct {
+    float lr[5];
+    float beta1, beta2, eps;
+    int32_t step; /* 1-based */
+} gs_adam_params;
+gs_status gs_adam_step(const gs_param_arrays *param, const gs_param_arrays *grad, const gs_param_arrays *m,
+                       const gs_param_arrays *v, int64_t n, int32_t sh_degree, const gs_adam_params *p,
+                       void *stream);
+
 /* Optional per-stage timing. With profiling on, each call records CUDA
  * events on its stream around every stage below (do not enable it while
  * capturing a CUDA graph); gs_workspace_stage_ms synchronises on the events

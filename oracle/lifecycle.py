@@ -49,7 +49,9 @@ def _f32(x) -> np.float32:
 
 
 def thresholds(p: dict) -> dict:
-    """The paper's thresholds moved to the logit / log domain, as float32 (R18)."""
+    """The paper's thresholds moved to the logit / log domain, as float32 (R18).
+    The parameters themselves are float32 values (as the C ABI holds them)."""
+    p = {k: float(np.float32(v)) for k, v in p.items()}
     logit = lambda t: _f32(math.log(t / (1.0 - t)))
     return dict(opa=logit(p["prune_opacity"]), smax=_f32(math.log(p["prune_scale_max"])),
                 smin=_f32(math.log(p["prune_scale_min"])), grad=_f32(p["densify_grad"]),

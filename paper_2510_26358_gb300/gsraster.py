@@ -30,7 +30,10 @@ EXPORTED = ("gs_config_default", "gs_workspace_create", "gs_workspace_destroy", 
             "gs_bin_sort", "gs_render_fwd", "gs_render_fwd_var", "gs_depth_loss", "gs_depth_loss_var",
             "gs_image_l1", "gs_image_loss", "gs_render_bwd", "gs_render_bwd_var",
             "gs_workspace_status", "gs_workspace_info", "gs_workspace_copy", "gs_workspace_set_profiling",
-            "gs_workspace_stage_ms", "gs_image_l1_noalloc", "gs_status_string", "gs_last_error")
+            "gs_workspace_stage_ms", "gs_image_l1_noalloc", "gs_status_string", "gs_last_error",
+            "gs_lifecycle_create", "gs_lifecycle_destroy", "gs_lifecycle_run", "gs_lifecycle_status", "gs_adam_step")
+GS_LC_PRUNE, GS_LC_DENSIFY, GS_LC_RESET = 1, 2, 4
+PARAM_FIELDS = ("means", "log_scales", "quats", "opacity_logits", "sh")
 IMAGE_L1_NOALLOC_MAX = 1024 * 65536  # GS_IMAGE_L1_NOALLOC_BLOCKS * GS_IMAGE_L1_NOALLOC_CHUNK
 STAGES = ("project", "compact", "depth_sort", "emit", "tile_sort", "ranges", "raster_fwd", "image_l1",
           "depth_loss", "zero_grad", "raster_bwd", "project_bwd", "image_ssim")
@@ -66,6 +69,21 @@ class GsGrads(ctypes.Structure):
     _fields_ = [("means", ctypes.c_void_p), ("log_scales", ctypes.c_void_p), ("quats", ctypes.c_void_p),
                 ("opacity_logits", ctypes.c_void_p), ("sh", ctypes.c_void_p), ("pose", ctypes.c_void_p),
                 ("densify_acc", ctypes.c_void_p), ("densify_cnt", ctypes.c_void_p)]
+
+
+class GsParamArrays(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_void_p) for k in ("means", "log_scales", "quats", "opacity_logits", "sh")]
+
+
+class GsLifecycleParams(ctypes.Structure):
+    _fields_ = [("ops", ctypes.c_int32)] + [(k, ctypes.c_float) for k in (
+        "prune_opacity", "prune_scale_max", "prune_scale_min", "densify_grad", "split_scale", "clone_scale",
+        "split_shrink", "reset_opacity", "reset_scale_min", "reset_scale_max")]
+
+
+class GsAdamParams(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float * 5), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float), ("step", ctypes.c_int32)]
 
 
 assert ctypes.sizeof(GsCamera) == 80 and ctypes.sizeof(GsConfig) == 64
@@ -105,6 +123,14 @@ def lib() -> ctypes.CDLL:
     L.gs_image_l1_noalloc.argtypes = [P, P, i64, P, P, P]
     L.gs_workspace_set_profiling.argtypes = [P, i32]
     L.gs_workspace_stage_ms.argtypes = [P, ctypes.POINTER(ctypes.c_float), i32]
+    PA = ctypes.POINTER(GsParamArrays)
+    L.gs_lifecycle_create.argtypes = [i64, i32, ctypes.POINTER(ctypes.c_void_p)]
+    L.gs_lifecycle_destroy.argtypes = [P]
+    L.gs_lifecycle_destroy.restype = None
+    L.gs_lifecycle_run.argtypes = [P, ctypes.POINTER(GsLifecycleParams), i32, i64, i32, P, PA, PA, PA, P, P, P, PA,
+                                   PA, PA, i64, P, P, P]
+    L.gs_lifecycle_status.argtypes = [P, P, ctypes.POINTER(ctypes.c_int64)]
+    L.gs_adam_step.argtypes = [PA, PA, PA, PA, i64, i32, ctypes.POINTER(GsAdamParams), P]
     L.gs_status_string.argtypes = [i32]
     L.gs_status_string.restype = ctypes.c_char_p
     L.gs_last_error.argtypes = []
@@ -114,10 +140,120 @@ def lib() -> ctypes.CDLL:
                  "gs_render_bwd_var",
                  "gs_workspace_status", "gs_workspace_info",
                  "gs_workspace_copy", "gs_workspace_set_profiling", "gs_workspace_stage_ms",
-                 "gs_image_l1_noalloc"):
+                 "gs_image_l1_noalloc", "gs_lifecycle_create", "gs_lifecycle_run", "gs_lifecycle_status",
+                 "gs_adam_step"):
         getattr(L, name).restype = i32
     _lib = L
     return L
+
+
+def param_arrays(d) -> GsParamArrays | None:
+    """GsParamArrays from a dict of tensors keyed by PARAM_FIELDS (None stays None)."""
+    if d is None:
+        return None
+    return GsParamArrays(*(d[k].data_ptr() for k in PARAM_FIELDS))
+
+
+def _pa(x):
+    return ctypes.byref(x) if x is not None else None
+
+
+def gs_lifecycle_create(max_in, max_submaps):
+    out = ctypes.c_void_p()
+    _check(lib().gs_lifecycle_create(int(max_in), int(max_submaps), ctypes.byref(out)), "gs_lifecycle_create")
+    return out
+
+
+def gs_lifecycle_destroy(lc):
+    lib().gs_lifecycle_destroy(lc)
+
+
+def gs_lifecycle_run(lc, params: GsLifecycleParams, sh_degree, n_in, n_submaps, offs_in, pin, pin_m, pin_v, acc, cnt,
+                     normals, pout, pout_m, pout_v, out_capacity, offs_out, n_out, stream):
+    _check(lib().gs_lifecycle_run(lc, ctypes.byref(params), int(sh_degree), int(n_in), int(n_submaps), offs_in,
+                                  _pa(pin), _pa(pin_m), _pa(pin_v), acc, cnt, normals, _pa(pout), _pa(pout_m),
+                                  _pa(pout_v), int(out_capacity), offs_out, n_out, stream), "gs_lifecycle_run")
+
+
+def gs_lifecycle_status(lc, stream):
+    """Returns (status, outputs needed); does not raise on capacity."""
+    n = ctypes.c_int64(0)
+    st = lib().gs_lifecycle_status(lc, stream, ctypes.byref(n))
+    if st not in (GS_OK, GS_ERR_CAPACITY):
+        _check(st, "gs_lifecycle_status")
+    return st, int(n.value)
+
+
+def gs_adam_step(param, grad, m, v, n, sh_degree, params: GsAdamParams, stream):
+    _check(lib().gs_adam_step(_pa(param), _pa(grad), _pa(m), _pa(v), int(n), int(sh_degree), ctypes.byref(params),
+                              stream), "gs_adam_step")
+
+
+def lifecycle_params(ops, **kw) -> GsLifecycleParams:
+    """GsLifecycleParams with the paper's pruning thresholds and the given rest."""
+    d = dict(prune_opacity=0.01, prune_scale_max=0.3, prune_scale_min=5e-5, densify_grad=2e-4, split_scale=0.02,
+             clone_scale=0.01, split_shrink=1.6, reset_opacity=0.1, reset_scale_min=1e-4, reset_scale_max=0.25)
+    d.update(kw)
+    return GsLifecycleParams(int(ops), *(float(d[k]) for k in (
+        "prune_opacity", "prune_scale_max", "prune_scale_min", "densify_grad", "split_scale", "clone_scale",
+        "split_shrink", "reset_opacity", "reset_scale_min", "reset_scale_max")))
+
+
+class Lifecycle:
+    """Lifecycle scratch plus the torch marshalling of one pass."""
+
+    def __init__(self, max_in, max_submaps, device=None):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device or "cuda")
+        with torch.cuda.device(self.device):
+            self.lc = gs_lifecycle_create(max_in, max_submaps)
+
+    def close(self):
+        if getattr(self, "lc", None):
+            gs_lifecycle_destroy(self.lc)
+            self.lc = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, params: dict, submap_offsets, sh_degree, lc_params: GsLifecycleParams, densify_acc=None,
+            densify_cnt=None, split_normals=None, moments=None, capacity=None, stream=None):
+        """One pass; returns (params_out, moments_out or None, submap_offsets_out [S+1] int64, n_out).
+        Raises GsError(GS_ERR_CAPACITY) if the outputs exceed ``capacity`` (default 2 n)."""
+        torch = self.torch
+        n = params["means"].shape[0]
+        cap = 2 * n if capacity is None else int(capacity)
+        offs = torch.as_tensor(submap_offsets, dtype=torch.int64, device=self.device)
+        alloc = lambda: {k: torch.empty((max(cap, 1),) + tuple(params[k].shape[1:]), device=self.device)
+                         for k in PARAM_FIELDS}
+        out = alloc()
+        mom_out = (alloc(), alloc()) if moments is not None else None
+        offs_out = torch.empty(offs.numel(), dtype=torch.int64, device=self.device)
+        n_out = torch.empty(1, dtype=torch.int64, device=self.device)
+        s = _stream(stream)
+        gs_lifecycle_run(self.lc, lc_params, sh_degree, n, offs.numel() - 1, _ptr(offs), param_arrays(params),
+                         param_arrays(moments[0]) if moments else None, param_arrays(moments[1]) if moments else None,
+                         _ptr(densify_acc), _ptr(densify_cnt), _ptr(split_normals), param_arrays(out),
+                         param_arrays(mom_out[0]) if moments else None, param_arrays(mom_out[1]) if moments else None,
+                         cap, _ptr(offs_out), _ptr(n_out), s)
+        st, need = gs_lifecycle_status(self.lc, s)
+        if st == GS_ERR_CAPACITY:
+            raise GsError(st, "gs_lifecycle_run", f"{need} outputs needed, capacity {cap}")
+        trim = lambda d: {k: v[:need] for k, v in d.items()}
+        return trim(out), (tuple(trim(d) for d in mom_out) if moments else None), offs_out, need
+
+
+def adam_step(params: dict, grads: dict, m: dict, v: dict, sh_degree, step, lr, beta1=0.9, beta2=0.999, eps=1e-15,
+              stream=None):
+    """Adam on the five parameter tensors in place; ``lr`` a float or five floats."""
+    lrs = [float(lr)] * 5 if isinstance(lr, (int, float)) else [float(x) for x in lr]
+    p = GsAdamParams((ctypes.c_float * 5)(*lrs), float(beta1), float(beta2), float(eps), int(step))
+    gs_adam_step(param_arrays(params), param_arrays(grads), param_arrays(m), param_arrays(v),
+                 params["means"].shape[0], sh_degree, p, _stream(stream))
 
 
 def status_string(s: int) -> str:

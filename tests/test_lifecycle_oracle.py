@@ -102,7 +102,7 @@ def test_split_children_are_covariance_samples():
                 d = out["means"][pos + k] - params["means"][j]
                 zz = z[j, k].astype(np.float64)
                 assert d @ Si @ d == pytest.approx(float(zz @ zz), rel=1e-9)
-                assert np.allclose(np.exp(out["log_scales"][pos + k]) * 1.6,
+                assert np.allclose(np.exp(out["log_scales"][pos + k]) * float(np.float32(1.6)),
                                    np.exp(params["log_scales"][j].astype(np.float64)), rtol=1e-12)
                 assert np.array_equal(out["quats"][pos + k], params["quats"][j].astype(np.float64))
             checked += 1
