@@ -61,6 +61,8 @@ def parse():
                     help="end the step with an Adam update of every Gaussian parameter (inside the timed graph)")
     ap.add_argument("--lifecycle", action="store_true",
                     help="also time one map-lifecycle pass (prune, reset, split / clone) on the workload")
+    ap.add_argument("--active-set", action="store_true",
+                    help="also time voxel-hash insertion of a point batch, LRU selection and an offload to host memory")
     ap.add_argument("--depth-loss", default="l1", choices=list(DEPTH_LOSSES),
                     help="depth term of the step: l1, kl (Eq. 7, fixed sigma_u) or kl-var (Eq. 7 with the "
                          "rendered variance: forward and backward with the central depth moment)")
@@ -248,6 +250,74 @@ def lifecycle_timing(torch, G, step, sc, dev, reps=5):
     return {"ms": ms, "n_in": sc.n, "n_out": n_out, "status": int(st), "gamma_g": gamma, "kappa": kappa,
             "algorithmic_bytes": int(bytes_moved + sc.n * 4 * nsh),
             "gbs": (bytes_moved + sc.n * 4 * nsh) / (ms * 1e-3) / 1e9}
+
+
+def active_set_timing(torch, G, step, sc, dev, reps=5):
+    """Voxel-hash insertion (Eq. 5) of a keyframe's fused points into the
+    workload's map, LRU selection over its splats and the offload of the
+    selected ones to pinned host memory, each timed with CUDA events (mean of
+    `reps` after one warm-up).  Points: 300k, a fifth on existing splats
+    (jittered by 1 mm), the rest uniform in the map's bounding box, with
+    colours; host store: 100k keys of random voxels; v = 0.05 m; last_used
+    frames uniform in [0, 30); tau = 80 % of the splats."""
+    gen = torch.Generator(device=dev).manual_seed(0)
+    means = step.P[0]
+    n = means.shape[0]
+    lo, hi = means.min(0).values, means.max(0).values
+    n_pts = 300_000
+    on = means[torch.randint(0, n, (n_pts // 5,), device=dev, generator=gen)]
+    on = on + 1e-3 * torch.rand(on.shape, device=dev, generator=gen)
+    off = lo + (hi - lo) * torch.rand(n_pts - on.shape[0], 3, device=dev, generator=gen)
+    pts = torch.cat([torch.cat([on, off]), torch.rand(n_pts, 3, device=dev, generator=gen)], 1).contiguous()
+    vm = G.VoxelMap(n_pts, n)
+    v = 0.05
+    keys = vm.keys(means, v)
+    host_keys = torch.randint(0, 2 ** 62, (100_000,), device=dev, generator=gen)
+    lu = torch.randint(0, 30, (n,), dtype=torch.int32, device=dev, generator=gen)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        ev[0].record()
+        for _ in range(reps):
+            fn()
+        ev[1].record()
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1]) / reps
+
+    K = (sc.sh_degree + 1) ** 2
+    new = dict(means=torch.empty(n_pts, 3, device=dev), log_scales=torch.empty(n_pts, 3, device=dev),
+               quats=torch.empty(n_pts, 4, device=dev), opacity_logits=torch.empty(n_pts, device=dev),
+               sh=torch.empty(n_pts, K, 3, device=dev))
+    new_keys = torch.empty(n_pts, dtype=torch.int64, device=dev)
+    reload = torch.empty(host_keys.shape[0], dtype=torch.int32, device=dev)
+    ip = G.GsInsertParams(v, 0.02, 0.1, 31)
+    s = G._stream()
+
+    def insert():
+        G.lib().gs_voxel_insert(vm.vx, ctypes.byref(ip), G._ptr(pts), n_pts, G._ptr(keys), G._ptr(lu), n,
+                                G._ptr(host_keys), G._ptr(reload), host_keys.shape[0], sc.sh_degree,
+                                ctypes.byref(G.param_arrays(new)), G._ptr(new_keys), n_pts, None, s)
+    t_insert = timed(insert)
+    n_new = ctypes.c_int64(0)
+    G.lib().gs_voxel_status(vm.vx, s, ctypes.byref(n_new))
+    tau = int(0.8 * n)
+    flags = torch.empty(n, dtype=torch.int32, device=dev)
+    t_select = timed(lambda: G.lib().gs_active_select(vm.vx, G._ptr(lu), n, tau, G._ptr(flags), s))
+    params = dict(zip(("means", "log_scales", "quats", "opacity_logits", "sh"), step.P))
+    kept = {k: torch.empty_like(t) for k, t in params.items()}
+    moved = {k: torch.empty(t.shape, dtype=t.dtype).pin_memory() for k, t in params.items()}
+    pk, pm = G.param_arrays(kept), G.param_arrays(moved)
+    pin = G.param_arrays(params)
+    t_part = timed(lambda: G.lib().gs_partition(vm.vx, G._ptr(flags), n, sc.sh_degree, ctypes.byref(pin), None, None,
+                                                ctypes.byref(pk), None, None, ctypes.byref(pm), None, None, None, s))
+    vm.close()
+    row = 4 * (3 + 3 + 4 + 1 + 3 * K)
+    moved_bytes = (n - tau) * row
+    return {"points": n_pts, "splats": n, "host_keys": int(host_keys.shape[0]), "voxel": v,
+            "new_splats": int(n_new.value), "insert_ms": t_insert, "select_ms": t_select, "tau": tau,
+            "partition_ms": t_part, "offloaded": n - tau, "offload_gbs_to_host": moved_bytes / (t_part * 1e-3) / 1e9}
 
 
 def job_throughput(pix_per_rank: int, ms: float, world: int) -> float:
@@ -606,6 +676,7 @@ def main():
     breakdown = stage_breakdown(torch, step, max(3, args.steps // 2), flush)
     kern = kernel_breakdown(torch, G, step, max(3, args.steps // 2), flush)
     lifecycle = lifecycle_timing(torch, G, step, sc, dev) if args.lifecycle else None
+    active_set = active_set_timing(torch, G, step, sc, dev) if args.active_set else None
 
     # per-view plain version: one workspace per camera, no graph
     per_view = None
@@ -720,6 +791,7 @@ def main():
             "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches_per_step * args.steps),
             "launches_per_step": int(launches_per_step), "roofline": roofline, "roofline_hbm": roofline_hbm,
             "per_view": per_view, "breakdown_ms": breakdown, "kernel_ms": kern, "lifecycle": lifecycle,
+            "active_set": active_set,
             "counts": {"visible_pairs": nvis, "instances": n_inst, "tiles": n_tiles}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = {k: v for k, v in cpu_baseline(sc, args, reps=2).items()

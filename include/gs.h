@@ -320,6 +320,68 @@ gs_status gs_adam_step(const gs_param_arrays *param, const gs_param_arrays *grad
                        const gs_param_arrays *v, int64_t n, int32_t sh_degree, const gs_adam_params *p,
                        void *stream);
 
+/* ------------------------------------------------------------------------ */
+/* Voxel-hash insertion (Sec. III-B, Eq. 5) and the LRU active set          */
+/* ("Memory Management").                                                    */
+/* ------------------------------------------------------------------------ */
+
+/* Eq. (5) keys: k = floor(x/v) P1 + floor(y/v) P2 + floor(z/v) P3 in unsigned
+ * 64-bit arithmetic (wrap-around), P1..P3 = 73856093, 19349663, 83492791
+ * (Teschner et al.; the paper gives none), x/v divided in float32 before the
+ * floor; the all-ones key is folded onto its predecessor.  xyz (device,
+ * n rows of `stride` floats, x y z first), keys (device, n). */
+gs_status gs_voxel_keys(const float *xyz, int64_t n, int32_t stride, float voxel, uint64_t *keys, void *stream);
+
+typedef struct gs_voxel gs_voxel;
+
+/* Scratch for batches of up to max_points points and for LRU selection and
+ * partitions of up to max_items splats (allocates). */
+gs_status gs_voxel_create(int64_t max_points, int64_t max_items, gs_voxel **out);
+void gs_voxel_destroy(gs_voxel *vx);
+
+typedef struct {
+    float voxel;   /* v of Eq. (5), metres */
+    float s_init;  /* scale of a new splat (isotropic), metres */
+    float o_init;  /* opacity of a new splat, (0, 1) */
+    int32_t frame; /* written to last_used of the splats the batch touches */
+} gs_insert_params;
+
+/* Inserts a batch of fused points (device, [n_points][6]: x y z r g b).
+ * Device splats whose key (splat_keys, device, n_splats) equals a point's key
+ * get last_used (device, n_splats) = frame; host-resident splats whose key
+ * (host_keys, device, n_host) equals a point's key get reload[h] = 1 (0
+ * otherwise); every voxel of the batch known to neither creates one splat from
+ * its first point in input order: mean = the point, log-scales ln(s_init),
+ * quaternion (1,0,0,0), opacity o_init, SH DC = (rgb - 1/2) / Y00, other SH
+ * coefficients 0.  New splats are written in point order to new_splats and
+ * their keys to new_keys (device, new_capacity rows); *n_new (device,
+ * nullable) receives their number.  More than new_capacity writes none of
+ * them: gs_voxel_status reports GS_ERR_CAPACITY. */
+gs_status gs_voxel_insert(gs_voxel *vx, const gs_insert_params *p, const float *points, int64_t n_points,
+                          const uint64_t *splat_keys, int32_t *last_used, int64_t n_splats,
+                          const uint64_t *host_keys, int32_t *reload, int64_t n_host, int32_t sh_degree,
+                          const gs_param_arrays *new_splats, uint64_t *new_keys, int64_t new_capacity,
+                          int64_t *n_new, void *stream);
+
+/* Synchronise; *n_new (nullable) = splats the last insert created or needed. */
+gs_status gs_voxel_status(gs_voxel *vx, void *stream, int64_t *n_new);
+
+/* LRU offload selection: with n > tau splats, flags (device, n) = 1 for the
+ * n - tau smallest (last_used, index) pairs, 0 for the others. */
+gs_status gs_active_select(gs_voxel *vx, const int32_t *last_used, int64_t n, int64_t tau, int32_t *flags,
+                           void *stream);
+
+/* Stable partition of n splat rows by flags (device, n): rows with flag 0 go
+ * in order to `kept`, rows with flag 1 in order to `moved`, with their keys and
+ * last_used (each pair nullable).  Any output may be host memory that the
+ * device can address (pinned, mapped): offloading to the CPU store and
+ * reloading from it are partitions.  counts (device, 2, nullable) receives
+ * (kept, moved). */
+gs_status gs_partition(gs_voxel *vx, const int32_t *flags, int64_t n, int32_t sh_degree, const gs_param_arrays *in,
+                       const uint64_t *in_keys, const int32_t *in_last_used, const gs_param_arrays *kept,
+                       uint64_t *kept_keys, int32_t *kept_last_used, const gs_param_arrays *moved,
+                       uint64_t *moved_keys, int32_t *moved_last_used, int64_t *counts, void *stream);
+
 /* Optional per-stage timing. With profiling on, each call records CUDA
  * events on its stream around every stage below (do not enable it while
  * capturing a CUDA graph); gs_workspace_stage_ms synchronises on the events

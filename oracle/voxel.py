@@ -10,6 +10,8 @@ Eq. 5 gives the key, the paper gives neither the primes nor v):
        with Teschner et al.'s primes P1 = 73856093, P2 = 19349663,
        P3 = 83492791; x/v is divided in float32 (the stored precision) before
        the floor, on both implementations.  A splat's key is that of its mean.
+       The all-ones key (which marks empty hash slots) is folded onto
+       all-ones minus one.
   R24  inserting a batch of points (x, y, z, r, g, b) at frame f: every
        device splat whose key equals some point's key gets last_used = f;
        every host-resident splat whose key equals some point's key is flagged
@@ -44,7 +46,10 @@ def cell(x, v) -> int:
 
 
 def key(p, v) -> int:
-    return (cell(p[0], v) * P1 + cell(p[1], v) * P2 + cell(p[2], v) * P3) & MASK
+    """Eq. (5) (R23); the all-ones key is folded onto its predecessor, which
+    the GPU table reserves for empty slots."""
+    k = (cell(p[0], v) * P1 + cell(p[1], v) * P2 + cell(p[2], v) * P3) & MASK
+    return k if k != MASK else MASK - 1
 
 
 def keys(xyz, v) -> np.ndarray:

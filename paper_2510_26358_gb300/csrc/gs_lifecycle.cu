@@ -18,6 +18,7 @@
 // writes coalesce).  A total above the output capacity writes nothing and
 // sets the flag gs_lifecycle_status reports.
 #include "gs_internal.cuh"
+#include "gs_scan.cuh"
 
 #include <cmath>
 
@@ -65,38 +66,9 @@ __device__ __forceinline__ uint8_t classify(const Thresholds &t, const float *ls
     return A_KEEP;
 }
 
-__device__ __forceinline__ uint32_t block_sum_u32(uint32_t v, uint32_t *sm) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) sm[w] = v;
-    __syncthreads();
-    uint32_t t = 0;
-    for (int i = 0; i < LT / 32; ++i) t += sm[i];
-    return t;
-}
-
-// block-wide exclusive scan of one value per thread; returns the exclusive
-// prefix and the block total
+__device__ __forceinline__ uint32_t block_sum_u32(uint32_t v, uint32_t *sm) { return gs::block_sum_u32<LT>(v, sm); }
 __device__ __forceinline__ uint32_t block_scan_u32(uint32_t v, uint32_t *sm, uint32_t &total) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    uint32_t x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    __syncthreads();
-    if (lane == 31) sm[w] = x;
-    __syncthreads();
-    uint32_t wpre = 0;
-    total = 0;
-    for (int i = 0; i < LT / 32; ++i) {
-        if (i < w) wpre += sm[i];
-        total += sm[i];
-    }
-    return wpre + x - v;
+    return gs::block_scan_u32<LT>(v, sm, total);
 }
 
 __global__ void __launch_bounds__(LT) k_lc_classify(Thresholds t, Arrays in, const float *acc, const int32_t *cnt,

@@ -31,7 +31,9 @@ EXPORTED = ("gs_config_default", "gs_workspace_create", "gs_workspace_destroy", 
             "gs_image_l1", "gs_image_loss", "gs_render_bwd", "gs_render_bwd_var",
             "gs_workspace_status", "gs_workspace_info", "gs_workspace_copy", "gs_workspace_set_profiling",
             "gs_workspace_stage_ms", "gs_image_l1_noalloc", "gs_status_string", "gs_last_error",
-            "gs_lifecycle_create", "gs_lifecycle_destroy", "gs_lifecycle_run", "gs_lifecycle_status", "gs_adam_step")
+            "gs_lifecycle_create", "gs_lifecycle_destroy", "gs_lifecycle_run", "gs_lifecycle_status", "gs_adam_step",
+            "gs_voxel_keys", "gs_voxel_create", "gs_voxel_destroy", "gs_voxel_insert", "gs_voxel_status",
+            "gs_active_select", "gs_partition")
 GS_LC_PRUNE, GS_LC_DENSIFY, GS_LC_RESET = 1, 2, 4
 PARAM_FIELDS = ("means", "log_scales", "quats", "opacity_logits", "sh")
 IMAGE_L1_NOALLOC_MAX = 1024 * 65536  # GS_IMAGE_L1_NOALLOC_BLOCKS * GS_IMAGE_L1_NOALLOC_CHUNK
@@ -86,6 +88,11 @@ class GsAdamParams(ctypes.Structure):
                 ("eps", ctypes.c_float), ("step", ctypes.c_int32)]
 
 
+class GsInsertParams(ctypes.Structure):
+    _fields_ = [("voxel", ctypes.c_float), ("s_init", ctypes.c_float), ("o_init", ctypes.c_float),
+                ("frame", ctypes.c_int32)]
+
+
 assert ctypes.sizeof(GsCamera) == 80 and ctypes.sizeof(GsConfig) == 64
 
 _lib = None
@@ -131,6 +138,15 @@ def lib() -> ctypes.CDLL:
                                    PA, PA, i64, P, P, P]
     L.gs_lifecycle_status.argtypes = [P, P, ctypes.POINTER(ctypes.c_int64)]
     L.gs_adam_step.argtypes = [PA, PA, PA, PA, i64, i32, ctypes.POINTER(GsAdamParams), P]
+    L.gs_voxel_keys.argtypes = [P, i64, i32, ctypes.c_float, P, P]
+    L.gs_voxel_create.argtypes = [i64, i64, ctypes.POINTER(ctypes.c_void_p)]
+    L.gs_voxel_destroy.argtypes = [P]
+    L.gs_voxel_destroy.restype = None
+    L.gs_voxel_insert.argtypes = [P, ctypes.POINTER(GsInsertParams), P, i64, P, P, i64, P, P, i64, i32, PA, P, i64,
+                                  P, P]
+    L.gs_voxel_status.argtypes = [P, P, ctypes.POINTER(ctypes.c_int64)]
+    L.gs_active_select.argtypes = [P, P, i64, i64, P, P]
+    L.gs_partition.argtypes = [P, P, i64, i32, PA, P, P, PA, P, P, PA, P, P, P, P]
     L.gs_status_string.argtypes = [i32]
     L.gs_status_string.restype = ctypes.c_char_p
     L.gs_last_error.argtypes = []
@@ -141,7 +157,8 @@ def lib() -> ctypes.CDLL:
                  "gs_workspace_status", "gs_workspace_info",
                  "gs_workspace_copy", "gs_workspace_set_profiling", "gs_workspace_stage_ms",
                  "gs_image_l1_noalloc", "gs_lifecycle_create", "gs_lifecycle_run", "gs_lifecycle_status",
-                 "gs_adam_step"):
+                 "gs_adam_step", "gs_voxel_keys", "gs_voxel_create", "gs_voxel_insert", "gs_voxel_status",
+                 "gs_active_select", "gs_partition"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -254,6 +271,86 @@ def adam_step(params: dict, grads: dict, m: dict, v: dict, sh_degree, step, lr, 
     p = GsAdamParams((ctypes.c_float * 5)(*lrs), float(beta1), float(beta2), float(eps), int(step))
     gs_adam_step(param_arrays(params), param_arrays(grads), param_arrays(m), param_arrays(v),
                  params["means"].shape[0], sh_degree, p, _stream(stream))
+
+
+def gs_voxel_keys(xyz, n, stride, voxel, keys, stream):
+    _check(lib().gs_voxel_keys(xyz, int(n), int(stride), float(voxel), keys, stream), "gs_voxel_keys")
+
+
+class VoxelMap:
+    """Scratch of the voxel-hash insertion and the active-set operations, with
+    torch marshalling.  Keys are int64 tensors holding the unsigned 64-bit keys'
+    bits; last_used, reload and flags are int32 tensors."""
+
+    def __init__(self, max_points, max_items, device=None):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device or "cuda")
+        out = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(lib().gs_voxel_create(int(max_points), int(max_items), ctypes.byref(out)), "gs_voxel_create")
+        self.vx = out
+
+    def close(self):
+        if getattr(self, "vx", None):
+            lib().gs_voxel_destroy(self.vx)
+            self.vx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def keys(self, xyz, voxel, stream=None):
+        """Eq. (5) keys of the rows of xyz ([n, >= 3] float32)."""
+        keys = self.torch.empty(xyz.shape[0], dtype=self.torch.int64, device=self.device)
+        gs_voxel_keys(_ptr(xyz), xyz.shape[0], xyz.stride(0), voxel, _ptr(keys), _stream(stream))
+        return keys
+
+    def insert(self, points, splat_keys, last_used, host_keys, sh_degree, voxel, s_init, o_init, frame,
+               capacity=None, stream=None):
+        """Returns (reload int32 [n_host], new params dict, new keys, n_new); updates last_used in place."""
+        torch = self.torch
+        n_pts = points.shape[0]
+        cap = n_pts if capacity is None else int(capacity)
+        K = (sh_degree + 1) ** 2
+        new = dict(means=torch.empty(max(cap, 1), 3, device=self.device),
+                   log_scales=torch.empty(max(cap, 1), 3, device=self.device),
+                   quats=torch.empty(max(cap, 1), 4, device=self.device),
+                   opacity_logits=torch.empty(max(cap, 1), device=self.device),
+                   sh=torch.empty(max(cap, 1), K, 3, device=self.device))
+        new_keys = torch.empty(max(cap, 1), dtype=torch.int64, device=self.device)
+        reload = torch.empty(host_keys.shape[0], dtype=torch.int32, device=self.device)
+        p = GsInsertParams(float(voxel), float(s_init), float(o_init), int(frame))
+        s = _stream(stream)
+        _check(lib().gs_voxel_insert(self.vx, ctypes.byref(p), _ptr(points), n_pts, _ptr(splat_keys),
+                                     _ptr(last_used), splat_keys.shape[0], _ptr(host_keys), _ptr(reload),
+                                     host_keys.shape[0], int(sh_degree), ctypes.byref(param_arrays(new)),
+                                     _ptr(new_keys), cap, None, s), "gs_voxel_insert")
+        n = ctypes.c_int64(0)
+        st = lib().gs_voxel_status(self.vx, s, ctypes.byref(n))
+        if st != GS_OK:
+            raise GsError(st, "gs_voxel_insert", f"{n.value} new splats, capacity {cap}")
+        n = int(n.value)
+        return reload, {k: v[:n] for k, v in new.items()}, new_keys[:n], n
+
+    def select(self, last_used, tau, stream=None):
+        flags = self.torch.empty(last_used.shape[0], dtype=self.torch.int32, device=self.device)
+        _check(lib().gs_active_select(self.vx, _ptr(last_used), last_used.shape[0], int(tau), _ptr(flags),
+                                      _stream(stream)), "gs_active_select")
+        return flags
+
+    def partition(self, flags, sh_degree, params, keys, last_used, kept, kept_keys, kept_lu, moved, moved_keys,
+                  moved_lu, stream=None):
+        """Stable partition into caller-allocated outputs (device or pinned host tensors)."""
+        counts = self.torch.empty(2, dtype=self.torch.int64, device=self.device)
+        _check(lib().gs_partition(self.vx, _ptr(flags), flags.shape[0], int(sh_degree),
+                                  ctypes.byref(param_arrays(params)), _ptr(keys), _ptr(last_used),
+                                  ctypes.byref(param_arrays(kept)), _ptr(kept_keys), _ptr(kept_lu),
+                                  ctypes.byref(param_arrays(moved)), _ptr(moved_keys), _ptr(moved_lu),
+                                  _ptr(counts), _stream(stream)), "gs_partition")
+        return counts
 
 
 def status_string(s: int) -> str:
