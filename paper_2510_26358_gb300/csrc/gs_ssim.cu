@@ -33,16 +33,17 @@
 namespace gs {
 namespace {
 
-constexpr int TX = 32, TY = 16, R = 5, K = 2 * R + 1;
+constexpr int TX = 32, TY = 32, R = 5, K = 2 * R + 1;
 constexpr int IW = TX + 2 * R, IH = TY + 2 * R;
 constexpr int SW = IW + 1;  // staged row stride: odd, so the blocked row reads hit distinct banks
 constexpr int HW = TX + 1;  // filtered row stride
 constexpr int NT = 256;
 constexpr int HB = 4;                     // horizontal outputs per thread
 constexpr int HITEMS = IH * (TX / HB);    // 208 row segments per tile
-constexpr int VB = 2;                     // vertical outputs per thread (consecutive rows)
+constexpr int VB = 4;                     // vertical outputs per thread (consecutive rows)
+constexpr int SLOADS = (IH * IW + NT - 1) / NT;  // staged values per thread and map
 static_assert(TY == VB * (NT / TX), "one vertical pass covers the tile");
-static_assert(HITEMS <= NT, "one horizontal pass covers the tile");
+static_assert(HITEMS <= 2 * NT, "two horizontal passes cover the tile");
 constexpr float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
 
 struct SsimArgs {
@@ -102,23 +103,25 @@ __device__ __forceinline__ float inside_weight(const SsimArgs &A, int i, int n) 
 __device__ __forceinline__ void horizontal_fwd(const SsimArgs &A, const float (*src)[IH][SW],
                                                float (*dst)[IH][HW], int item) {
     const int r = item / (TX / HB), c0 = (item % (TX / HB)) * HB;
-    float u[HB + 2 * R], w[HB + 2 * R];
+    float u[HB + 2 * R], w[HB + 2 * R], uu[HB + 2 * R], ww[HB + 2 * R], uw[HB + 2 * R];
 #pragma unroll
     for (int j = 0; j < HB + 2 * R; ++j) {
         u[j] = src[0][r][c0 + j];
         w[j] = src[1][r][c0 + j];
+        uu[j] = u[j] * u[j];
+        ww[j] = w[j] * w[j];
+        uw[j] = u[j] * w[j];
     }
 #pragma unroll
     for (int o = 0; o < HB; ++o) {
         float a = 0.f, b = 0.f, aa = 0.f, bb = 0.f, ab = 0.f;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            const float gu = A.g[k] * u[o + k], gw = A.g[k] * w[o + k];
-            a += gu;
-            b += gw;
-            aa = __fmaf_rn(gu, u[o + k], aa);
-            bb = __fmaf_rn(gw, w[o + k], bb);
-            ab = __fmaf_rn(gu, w[o + k], ab);
+            a = __fmaf_rn(A.g[k], u[o + k], a);
+            b = __fmaf_rn(A.g[k], w[o + k], b);
+            aa = __fmaf_rn(A.g[k], uu[o + k], aa);
+            bb = __fmaf_rn(A.g[k], ww[o + k], bb);
+            ab = __fmaf_rn(A.g[k], uw[o + k], ab);
         }
         dst[0][r][c0 + o] = a;
         dst[1][r][c0 + o] = b;
@@ -157,18 +160,29 @@ __global__ void __launch_bounds__(NT) k_ssim_fwd(SsimArgs A) {
     const int tid = threadIdx.x, lx = tid & 31, ly = tid >> 5;
     // shift: the tile's first pixel, always inside the image
     const float cx = x[(int64_t)P.y0 * P.W + P.x0], cy = y[(int64_t)P.y0 * P.W + P.x0];
-    for (int r = ly; r < IH; r += NT / 32) {
-        const int gy = P.y0 - R + r;
-        for (int c = lx; c < IW; c += 32) {
-            const int gx = P.x0 - R + c;
-            const bool in = gx >= 0 && gx < P.W && gy >= 0 && gy < P.H;
+    {
+        // every load of the thread is issued before the first shared store
+        float vx[SLOADS], vy[SLOADS];
+#pragma unroll
+        for (int k = 0; k < SLOADS; ++k) {
+            const int i = tid + k * NT, r = i / IW, c = i % IW;
+            const int gx = P.x0 - R + c, gy = P.y0 - R + r;
+            const bool in = i < IH * IW && gx >= 0 && gx < P.W && gy >= 0 && gy < P.H;
             const int64_t o = (int64_t)gy * P.W + gx;
-            st[0][r][c] = in ? x[o] - cx : 0.f;
-            st[1][r][c] = in ? y[o] - cy : 0.f;
+            vx[k] = in ? x[o] - cx : 0.f;
+            vy[k] = in ? y[o] - cy : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < SLOADS; ++k) {
+            const int i = tid + k * NT;
+            if (i < IH * IW) {
+                st[0][i / IW][i % IW] = vx[k];
+                st[1][i / IW][i % IW] = vy[k];
+            }
         }
     }
     __syncthreads();
-    if (tid < HITEMS) horizontal_fwd(A, st, sh, tid);
+    for (int item = tid; item < HITEMS; item += NT) horizontal_fwd(A, st, sh, item);
     __syncthreads();
     const int gx = P.x0 + lx, oy0 = VB * ly;
     float m[VB][5];
@@ -232,18 +246,28 @@ __global__ void __launch_bounds__(NT) k_ssim_bwd(SsimArgs A) {
     __shared__ float sh[3][IH][HW];
     const PlaneTile P = locate(A, blockIdx.x);
     const int tid = threadIdx.x, lx = tid & 31, ly = tid >> 5;
-    for (int r = ly; r < IH; r += NT / 32) {
-        const int gy = P.y0 - R + r;
-        for (int c = lx; c < IW; c += 32) {
-            const int gx = P.x0 - R + c;
-            const bool in = gx >= 0 && gx < P.W && gy >= 0 && gy < P.H;
+    {
+        float v[3][SLOADS];
+#pragma unroll
+        for (int k = 0; k < SLOADS; ++k) {
+            const int i = tid + k * NT, r = i / IW, c = i % IW;
+            const int gx = P.x0 - R + c, gy = P.y0 - R + r;
+            const bool in = i < IH * IW && gx >= 0 && gx < P.W && gy >= 0 && gy < P.H;
             const int64_t e = P.base + (int64_t)gy * P.W + gx;
 #pragma unroll
-            for (int q = 0; q < 3; ++q) st[q][r][c] = in ? A.dmap[q * A.n_elem + e] : 0.f;
+            for (int q = 0; q < 3; ++q) v[q][k] = in ? A.dmap[q * A.n_elem + e] : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < SLOADS; ++k) {
+            const int i = tid + k * NT;
+            if (i < IH * IW) {
+#pragma unroll
+                for (int q = 0; q < 3; ++q) st[q][i / IW][i % IW] = v[q][k];
+            }
         }
     }
     __syncthreads();
-    if (tid < HITEMS) horizontal<3>(A, st, sh, tid);
+    for (int item = tid; item < HITEMS; item += NT) horizontal<3>(A, st, sh, item);
     __syncthreads();
     const int gx = P.x0 + lx, oy0 = VB * ly;
     float f[VB][3];
