@@ -32,6 +32,7 @@ struct DevState {
     uint32_t pad[7];
 };
 constexpr uint32_t kFlagCapacity = 1u;
+constexpr uint32_t kFlagTimeout = 2u;  // a bounded device wait (TMA) gave up
 
 }  // namespace gs
 

@@ -26,9 +26,21 @@
 //   s_xy = E[x'y'] - M'_x M'_y + (1 - W)(c_y M'_x + c_x M'_y + c_x c_y W),
 // identities of the zero-padded sums whose correction vanishes in the
 // interior (W = 1).
+//
+// Views whose width is a multiple of 4 (at most kTmaViews of them) stage the
+// halo tiles with TMA: one thread issues cp.async.bulk.tensor loads of a
+// 48 x 42 box starting at (x0 - 8, y0 - 5) (x a multiple of 4 floats, as the
+// copy requires) that complete on an mbarrier; the copy's out-of-bounds zero
+// fill is the zero padding.  The wait is bounded: on time-out the kernel sets
+// a flag of the workspace state and leaves the tile.  Other layouts use the
+// same kernels with per-thread staging loads.
 #include "gs_internal.cuh"
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <cmath>
+#include <mutex>
 
 namespace gs {
 namespace {
@@ -57,17 +69,29 @@ struct SsimArgs {
     float scale;         // gradient scale of S (backward)
     float gsum;          // sum of the 11 weights (the in-image weight of an interior axis)
     float g[K];          // window weights
+    uint32_t *flags;     // workspace state flags (TMA wait time-out)
 };
 
 struct PlaneTile {
     int64_t base;  // element offset of the channel plane
     int W, H, x0, y0;
+    int v, ch;
 };
+
+// TMA path: per view, 3-D maps (x, y, channel) of the two images and a 4-D map
+// (x, y, channel, partial) of the backward's three partial maps.
+constexpr int kTmaViews = 8;
+constexpr int BW = IW + 6;    // box width: columns x0 - 8 .. x0 + 39
+constexpr int BOFF = 3;       // halo column c lives at box column c + BOFF
+struct SsimTma {
+    CUtensorMap x[kTmaViews], y[kTmaViews], d[kTmaViews];
+};
+constexpr uint32_t kTmaWaitLimit = 1u << 22;
 
 // CTA b -> (view, channel, tile); views in order, channels in order, tiles
 // row-major.  The grid holds exactly sum_v 3 ntx(v) nty(v) CTAs.
 __device__ __forceinline__ PlaneTile locate(const SsimArgs &A, int b) {
-    PlaneTile p{0, 0, 0, 0, 0};
+    PlaneTile p{0, 0, 0, 0, 0, 0, 0};
     for (int v = 0; v < A.n_views; ++v) {
         const ViewInfo vi = A.views[v];
         const int ntx = (vi.W + TX - 1) / TX, nty = (vi.H + TY - 1) / TY;
@@ -79,6 +103,8 @@ __device__ __forceinline__ PlaneTile locate(const SsimArgs &A, int b) {
             p.H = vi.H;
             p.x0 = (t % ntx) * TX;
             p.y0 = (t / ntx) * TY;
+            p.v = v;
+            p.ch = ch;
             return p;
         }
         b -= 3 * per_plane;
@@ -151,39 +177,10 @@ __device__ __forceinline__ void horizontal(const SsimArgs &A, const float (*src)
     }
 }
 
-__global__ void __launch_bounds__(NT) k_ssim_fwd(SsimArgs A) {
-    __shared__ float st[2][IH][SW];  // staged x', y'
-    __shared__ float sh[5][IH][HW];
-    __shared__ double red[NT / 32];
-    const PlaneTile P = locate(A, blockIdx.x);
-    const float *x = A.x + P.base, *y = A.y + P.base;
-    const int tid = threadIdx.x, lx = tid & 31, ly = tid >> 5;
-    // shift: the tile's first pixel, always inside the image
-    const float cx = x[(int64_t)P.y0 * P.W + P.x0], cy = y[(int64_t)P.y0 * P.W + P.x0];
-    {
-        // every load of the thread is issued before the first shared store
-        float vx[SLOADS], vy[SLOADS];
-#pragma unroll
-        for (int k = 0; k < SLOADS; ++k) {
-            const int i = tid + k * NT, r = i / IW, c = i % IW;
-            const int gx = P.x0 - R + c, gy = P.y0 - R + r;
-            const bool in = i < IH * IW && gx >= 0 && gx < P.W && gy >= 0 && gy < P.H;
-            const int64_t o = (int64_t)gy * P.W + gx;
-            vx[k] = in ? x[o] - cx : 0.f;
-            vy[k] = in ? y[o] - cy : 0.f;
-        }
-#pragma unroll
-        for (int k = 0; k < SLOADS; ++k) {
-            const int i = tid + k * NT;
-            if (i < IH * IW) {
-                st[0][i / IW][i % IW] = vx[k];
-                st[1][i / IW][i % IW] = vy[k];
-            }
-        }
-    }
-    __syncthreads();
-    for (int item = tid; item < HITEMS; item += NT) horizontal_fwd(A, st, sh, item);
-    __syncthreads();
+// Vertical pass, SSIM, its partials and the tile's sum of 1 - S (shared by
+// both staging paths).
+__device__ __forceinline__ void ssim_epilogue(const SsimArgs &A, const PlaneTile &P, const float (*sh)[IH][HW],
+                                              float cx, float cy, int lx, int ly, double *red) {
     const int gx = P.x0 + lx, oy0 = VB * ly;
     float m[VB][5];
 #pragma unroll
@@ -234,11 +231,76 @@ __global__ void __launch_bounds__(NT) k_ssim_fwd(SsimArgs A) {
     for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
     if (lx == 0) red[ly] = (double)dsum;
     __syncthreads();
-    if (tid == 0) {
+    if (threadIdx.x == 0) {
         double t = 0.0;
         for (int i = 0; i < NT / 32; ++i) t += red[i];
         A.part[blockIdx.x] = t;
     }
+}
+
+// Vertical pass of the backward and the gradient (shared by both staging paths).
+__device__ __forceinline__ void ssim_bwd_epilogue(const SsimArgs &A, const PlaneTile &P, const float (*sh)[IH][HW],
+                                                  int lx, int ly) {
+    const int gx = P.x0 + lx, oy0 = VB * ly;
+    float f[VB][3];
+#pragma unroll
+    for (int b = 0; b < VB; ++b)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) f[b][q] = 0.f;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        float v[K + VB - 1];
+#pragma unroll
+        for (int j = 0; j < K + VB - 1; ++j) v[j] = sh[q][oy0 + j][lx];
+#pragma unroll
+        for (int b = 0; b < VB; ++b)
+#pragma unroll
+            for (int k = 0; k < K; ++k) f[b][q] = __fmaf_rn(A.g[k], v[b + k], f[b][q]);
+    }
+#pragma unroll
+    for (int b = 0; b < VB; ++b) {
+        const int gy = P.y0 + oy0 + b;
+        if (gx >= P.W || gy >= P.H) continue;
+        const int64_t e = P.base + (int64_t)gy * P.W + gx;
+        const float xv = A.x[e], yv = A.y[e];
+        A.grad[e] += A.scale * (f[b][0] + 2.f * xv * f[b][1] + yv * f[b][2]);
+    }
+}
+
+__global__ void __launch_bounds__(NT) k_ssim_fwd(SsimArgs A) {
+    __shared__ float st[2][IH][SW];  // staged x', y'
+    __shared__ float sh[5][IH][HW];
+    __shared__ double red[NT / 32];
+    const PlaneTile P = locate(A, blockIdx.x);
+    const float *x = A.x + P.base, *y = A.y + P.base;
+    const int tid = threadIdx.x, lx = tid & 31, ly = tid >> 5;
+    // shift: the tile's first pixel, always inside the image
+    const float cx = x[(int64_t)P.y0 * P.W + P.x0], cy = y[(int64_t)P.y0 * P.W + P.x0];
+    {
+        // every load of the thread is issued before the first shared store
+        float vx[SLOADS], vy[SLOADS];
+#pragma unroll
+        for (int k = 0; k < SLOADS; ++k) {
+            const int i = tid + k * NT, r = i / IW, c = i % IW;
+            const int gx = P.x0 - R + c, gy = P.y0 - R + r;
+            const bool in = i < IH * IW && gx >= 0 && gx < P.W && gy >= 0 && gy < P.H;
+            const int64_t o = (int64_t)gy * P.W + gx;
+            vx[k] = in ? x[o] - cx : 0.f;
+            vy[k] = in ? y[o] - cy : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < SLOADS; ++k) {
+            const int i = tid + k * NT;
+            if (i < IH * IW) {
+                st[0][i / IW][i % IW] = vx[k];
+                st[1][i / IW][i % IW] = vy[k];
+            }
+        }
+    }
+    __syncthreads();
+    for (int item = tid; item < HITEMS; item += NT) horizontal_fwd(A, st, sh, item);
+    __syncthreads();
+    ssim_epilogue(A, P, sh, cx, cy, lx, ly, red);
 }
 
 __global__ void __launch_bounds__(NT) k_ssim_bwd(SsimArgs A) {
@@ -269,30 +331,196 @@ __global__ void __launch_bounds__(NT) k_ssim_bwd(SsimArgs A) {
     __syncthreads();
     for (int item = tid; item < HITEMS; item += NT) horizontal<3>(A, st, sh, item);
     __syncthreads();
-    const int gx = P.x0 + lx, oy0 = VB * ly;
-    float f[VB][3];
-#pragma unroll
-    for (int b = 0; b < VB; ++b)
-#pragma unroll
-        for (int q = 0; q < 3; ++q) f[b][q] = 0.f;
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        float v[K + VB - 1];
-#pragma unroll
-        for (int j = 0; j < K + VB - 1; ++j) v[j] = sh[q][oy0 + j][lx];
-#pragma unroll
-        for (int b = 0; b < VB; ++b)
-#pragma unroll
-            for (int k = 0; k < K; ++k) f[b][q] = __fmaf_rn(A.g[k], v[b + k], f[b][q]);
+    ssim_bwd_epilogue(A, P, sh, lx, ly);
+}
+
+
+// ---------------------------------------------------------------------------
+// TMA staging
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];"
+        ::"r"(smem_u32(dst)), "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Waits for the tile's copies (phase 0).  Returns false after the bounded
+// wait, having set the time-out flag (a second bounded wait lets copies still
+// in flight land before the CTA leaves).
+__device__ __forceinline__ bool tma_wait(uint64_t *bar, uint32_t *flags) {
+    for (uint32_t it = 0; it < kTmaWaitLimit; ++it)
+        if (mbar_try_wait(bar, 0)) return true;
+    if (threadIdx.x == 0) atomicOr(flags, kFlagTimeout);
+    for (uint32_t it = 0; it < kTmaWaitLimit; ++it)
+        if (mbar_try_wait(bar, 0)) break;
+    return false;
+}
+
+__global__ void __launch_bounds__(NT) k_ssim_fwd_tma(SsimArgs A, const __grid_constant__ SsimTma T) {
+    __shared__ __align__(128) float tx_[IH][BW];
+    __shared__ __align__(128) float ty_[IH][BW];
+    __shared__ float sh[5][IH][HW];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ double red[NT / 32];
+    const PlaneTile P = locate(A, blockIdx.x);
+    const int tid = threadIdx.x, lx = tid & 31, ly = tid >> 5;
+    if (tid == 0) {
+        mbar_init(&bar);
+        mbar_expect_tx(&bar, 2u * IH * BW * sizeof(float));
+        tma_load_3d(&tx_[0][0], &T.x[P.v], P.x0 - R - BOFF, P.y0 - R, P.ch, &bar);
+        tma_load_3d(&ty_[0][0], &T.y[P.v], P.x0 - R - BOFF, P.y0 - R, P.ch, &bar);
     }
+    __syncthreads();
+    if (!tma_wait(&bar, A.flags)) return;
+    // shift: the tile's first pixel (halo row R, column R)
+    const float cx = tx_[R][R + BOFF], cy = ty_[R][R + BOFF];
+    for (int item = tid; item < HITEMS; item += NT) {
+        const int r = item / (TX / HB), c0 = (item % (TX / HB)) * HB;
+        const int gy = P.y0 - R + r;
+        const bool row_in = gy >= 0 && gy < P.H;
+        float u[HB + 2 * R], w[HB + 2 * R], uu[HB + 2 * R], ww[HB + 2 * R], uw[HB + 2 * R];
 #pragma unroll
-    for (int b = 0; b < VB; ++b) {
-        const int gy = P.y0 + oy0 + b;
-        if (gx >= P.W || gy >= P.H) continue;
-        const int64_t e = P.base + (int64_t)gy * P.W + gx;
-        const float xv = A.x[e], yv = A.y[e];
-        A.grad[e] += A.scale * (f[b][0] + 2.f * xv * f[b][1] + yv * f[b][2]);
+        for (int j = 0; j < HB + 2 * R; ++j) {
+            const int gx = P.x0 - R + c0 + j;
+            const bool in = row_in && gx >= 0 && gx < P.W;
+            u[j] = in ? tx_[r][c0 + j + BOFF] - cx : 0.f;
+            w[j] = in ? ty_[r][c0 + j + BOFF] - cy : 0.f;
+            uu[j] = u[j] * u[j];
+            ww[j] = w[j] * w[j];
+            uw[j] = u[j] * w[j];
+        }
+#pragma unroll
+        for (int o = 0; o < HB; ++o) {
+            float a = 0.f, b = 0.f, aa = 0.f, bb = 0.f, ab = 0.f;
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                a = __fmaf_rn(A.g[k], u[o + k], a);
+                b = __fmaf_rn(A.g[k], w[o + k], b);
+                aa = __fmaf_rn(A.g[k], uu[o + k], aa);
+                bb = __fmaf_rn(A.g[k], ww[o + k], bb);
+                ab = __fmaf_rn(A.g[k], uw[o + k], ab);
+            }
+            sh[0][r][c0 + o] = a;
+            sh[1][r][c0 + o] = b;
+            sh[2][r][c0 + o] = aa;
+            sh[3][r][c0 + o] = bb;
+            sh[4][r][c0 + o] = ab;
+        }
     }
+    __syncthreads();
+    ssim_epilogue(A, P, sh, cx, cy, lx, ly, red);
+}
+
+__global__ void __launch_bounds__(NT) k_ssim_bwd_tma(SsimArgs A, const __grid_constant__ SsimTma T) {
+    __shared__ __align__(128) float sd[3][IH][BW];
+    __shared__ float sh[3][IH][HW];
+    __shared__ __align__(8) uint64_t bar;
+    const PlaneTile P = locate(A, blockIdx.x);
+    const int tid = threadIdx.x, lx = tid & 31, ly = tid >> 5;
+    if (tid == 0) {
+        mbar_init(&bar);
+        mbar_expect_tx(&bar, 3u * IH * BW * sizeof(float));
+#pragma unroll
+        for (int q = 0; q < 3; ++q) tma_load_4d(&sd[q][0][0], &T.d[P.v], P.x0 - R - BOFF, P.y0 - R, P.ch, q, &bar);
+    }
+    __syncthreads();
+    if (!tma_wait(&bar, A.flags)) return;
+    for (int item = tid; item < HITEMS; item += NT) {
+        const int r = item / (TX / HB), c0 = (item % (TX / HB)) * HB;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            float v[HB + 2 * R];
+#pragma unroll
+            for (int j = 0; j < HB + 2 * R; ++j) v[j] = sd[q][r][c0 + j + BOFF];
+#pragma unroll
+            for (int o = 0; o < HB; ++o) {
+                float acc = 0.f;
+#pragma unroll
+                for (int k = 0; k < K; ++k) acc = __fmaf_rn(A.g[k], v[o + k], acc);
+                sh[q][r][c0 + o] = acc;
+            }
+        }
+    }
+    __syncthreads();
+    ssim_bwd_epilogue(A, P, sh, lx, ly);
+}
+
+std::once_flag g_encode_once;
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    std::call_once(g_encode_once, [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    });
+    return g_encode;
+}
+
+// The maps of every view, or false if a view or a buffer does not suit TMA.
+bool encode_maps(gs_workspace *ws, const float *rgb, const float *target, SsimTma &T) {
+    if (ws->n_views > kTmaViews) return false;
+    auto enc = encode_fn();
+    if (!enc) return false;
+    if (((uintptr_t)rgb | (uintptr_t)target | (uintptr_t)ws->ssim_d) & 15) return false;
+    const uint64_t n_elem = 3 * (uint64_t)ws->n_pix;
+    for (int v = 0; v < ws->n_views; ++v) {
+        const ViewInfo &vi = ws->views_h[v];
+        if (vi.W % 4 != 0) return false;
+        const uint64_t W = vi.W, H = vi.H, off = 3 * (uint64_t)vi.pix_off;
+        const cuuint64_t dim3[3] = {W, H, 3}, str3[2] = {W * 4, W * H * 4};
+        const cuuint64_t dim4[4] = {W, H, 3, 3}, str4[3] = {W * 4, W * H * 4, n_elem * 4};
+        const cuuint32_t box3[3] = {(cuuint32_t)BW, (cuuint32_t)IH, 1}, box4[4] = {(cuuint32_t)BW, (cuuint32_t)IH, 1, 1};
+        const cuuint32_t one[4] = {1, 1, 1, 1};
+        CUresult r = enc(&T.x[v], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)(rgb + off), dim3, str3, box3, one,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r == CUDA_SUCCESS)
+            r = enc(&T.y[v], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)(target + off), dim3, str3, box3, one,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r == CUDA_SUCCESS)
+            r = enc(&T.d[v], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void *)(ws->ssim_d + off), dim4, str4, box4, one,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return false;
+    }
+    return true;
 }
 
 }  // namespace
@@ -315,6 +543,7 @@ gs_status launch_ssim(gs_workspace *ws, const float *rgb, const float *target, f
     A.part = ws->ssim_part;
     A.n_elem = 3 * ws->n_pix;
     A.scale = grad_scale;
+    A.flags = &ws->st->flags;
     double g[K], sum = 0.0;
     for (int i = 0; i < K; ++i) {
         g[i] = std::exp(-(double)((i - R) * (i - R)) / (2.0 * 1.5 * 1.5));
@@ -327,13 +556,17 @@ gs_status launch_ssim(gs_workspace *ws, const float *rgb, const float *target, f
     }
     const int grid = (int)ws->n_ssim_tiles;
     if (grid == 0) return GS_OK;
+    SsimTma T;
+    const bool tma = encode_maps(ws, rgb, target, T);
     StageTimer timer(ws, GS_STAGE_IMAGE_SSIM, s);
     ++ws->kernel_launches;
-    k_ssim_fwd<<<grid, NT, 0, s>>>(A);
+    if (tma) k_ssim_fwd_tma<<<grid, NT, 0, s>>>(A, T);
+    else k_ssim_fwd<<<grid, NT, 0, s>>>(A);
     gs_status r = check_launch("ssim_fwd");
     if (r != GS_OK || !dL_drgb || grad_scale == 0.f) return r;
     ++ws->kernel_launches;
-    k_ssim_bwd<<<grid, NT, 0, s>>>(A);
+    if (tma) k_ssim_bwd_tma<<<grid, NT, 0, s>>>(A, T);
+    else k_ssim_bwd<<<grid, NT, 0, s>>>(A);
     return check_launch("ssim_bwd");
 }
 
