@@ -29,10 +29,11 @@
  *    of W*H over the views before v.
  *  - Gradients are accumulated (+=) into the caller's buffers.
  *  - Errors: argument errors return at once and enqueue nothing. Conditions
- *    found on the device (instance capacity exceeded) set a flag in the
- *    workspace that lasts until the next gs_bin_sort; the kernels that follow
- *    then work on empty lists (blank images, zero gradients) and
- *    gs_workspace_status reports the flag. Nothing traps or aborts.
+ *    found on the device (instance capacity exceeded, a bounded device wait
+ *    that ran out) set a flag in the workspace that lasts until the next
+ *    gs_bin_sort; after a capacity overflow the kernels that follow work on
+ *    empty lists (blank images, zero gradients).  gs_workspace_status reports
+ *    the flags.  Nothing traps or aborts.
  */
 #ifndef GS_H
 #define GS_H
@@ -381,6 +382,13 @@ gs_status gs_partition(gs_voxel *vx, const int32_t *flags, int64_t n, int32_t sh
                        const uint64_t *in_keys, const int32_t *in_last_used, const gs_param_arrays *kept,
                        uint64_t *kept_keys, int32_t *kept_last_used, const gs_param_arrays *moved,
                        uint64_t *moved_keys, int32_t *moved_last_used, int64_t *counts, void *stream);
+
+/* Self-test of the bound on device-side waits (the TMA staging of the SSIM
+ * kernels waits on an mbarrier for at most a second): one block waits on a
+ * barrier that no copy will ever complete for limit_ns (1 .. 2e9), then sets
+ * the workspace's time-out flag and writes *result (device int32) = 1.
+ * gs_workspace_status then reports GS_ERR_CUDA until the next gs_bin_sort. */
+gs_status gs_selftest_wait_timeout(gs_workspace *ws, int64_t limit_ns, int32_t *result, void *stream);
 
 /* Optional per-stage timing. With profiling on, each call records CUDA
  * events on its stream around every stage below (do not enable it while

@@ -101,10 +101,13 @@ __global__ void k_scan_parts(uint32_t *part, int nb, uint32_t *total, DevState *
             *total = (uint32_t)t;
         } else {
             st->n_inst_needed = t;
+            // every binning starts the flags afresh: capacity for this one,
+            // no device-wait time-out yet
             if (t > cap) {
-                st->flags |= kFlagCapacity;
+                st->flags = kFlagCapacity;
                 st->n_inst = 0;
             } else {
+                st->flags = 0u;
                 st->n_inst = (uint32_t)t;
             }
         }

@@ -70,6 +70,7 @@ struct SsimArgs {
     float gsum;          // sum of the 11 weights (the in-image weight of an interior axis)
     float g[K];          // window weights
     uint32_t *flags;     // workspace state flags (TMA wait time-out)
+    uint64_t wait_ns;    // limit of a TMA wait
 };
 
 struct PlaneTile {
@@ -86,7 +87,7 @@ constexpr int BOFF = 3;       // halo column c lives at box column c + BOFF
 struct SsimTma {
     CUtensorMap x[kTmaViews], y[kTmaViews], d[kTmaViews];
 };
-constexpr uint32_t kTmaWaitLimit = 1u << 22;
+constexpr uint64_t kTmaWaitNs = 1000000000ull;  // 1 s for a tile's copies
 
 // CTA b -> (view, channel, tile); views in order, channels in order, tiles
 // row-major.  The grid holds exactly sum_v 3 ntx(v) nty(v) CTAs.
@@ -376,16 +377,40 @@ __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
-// Waits for the tile's copies (phase 0).  Returns false after the bounded
-// wait, having set the time-out flag (a second bounded wait lets copies still
-// in flight land before the CTA leaves).
-__device__ __forceinline__ bool tma_wait(uint64_t *bar, uint32_t *flags) {
-    for (uint32_t it = 0; it < kTmaWaitLimit; ++it)
-        if (mbar_try_wait(bar, 0)) return true;
-    if (threadIdx.x == 0) atomicOr(flags, kFlagTimeout);
-    for (uint32_t it = 0; it < kTmaWaitLimit; ++it)
-        if (mbar_try_wait(bar, 0)) break;
-    return false;
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits for the tile's copies (phase 0) for at most limit_ns.  On time-out it
+// sets the flag, waits a tenth of that again so that copies still in flight
+// land before the CTA leaves, and returns false.
+__device__ __forceinline__ bool tma_wait(uint64_t *bar, uint32_t *flags, uint64_t limit_ns) {
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, 0))
+        if (global_ns() - t0 > limit_ns) {
+            if (threadIdx.x == 0) atomicOr(flags, kFlagTimeout);
+            const uint64_t t1 = global_ns();
+            while (!mbar_try_wait(bar, 0))
+                if (global_ns() - t1 > limit_ns / 10) break;
+            return false;
+        }
+    return true;
+}
+
+// Self-test of the bounded wait: a barrier that expects bytes no copy will
+// ever deliver (none is issued), so the wait must run out and set the flag.
+__global__ void k_wait_selftest(uint32_t *flags, uint64_t limit_ns, int32_t *result) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar);
+        mbar_expect_tx(&bar, 16u);
+    }
+    __syncthreads();
+    const bool done = tma_wait(&bar, flags, limit_ns);
+    __syncthreads();
+    if (threadIdx.x == 0) *result = done ? 0 : 1;
 }
 
 __global__ void __launch_bounds__(NT) k_ssim_fwd_tma(SsimArgs A, const __grid_constant__ SsimTma T) {
@@ -403,7 +428,7 @@ __global__ void __launch_bounds__(NT) k_ssim_fwd_tma(SsimArgs A, const __grid_co
         tma_load_3d(&ty_[0][0], &T.y[P.v], P.x0 - R - BOFF, P.y0 - R, P.ch, &bar);
     }
     __syncthreads();
-    if (!tma_wait(&bar, A.flags)) return;
+    if (!tma_wait(&bar, A.flags, A.wait_ns)) return;
     // shift: the tile's first pixel (halo row R, column R)
     const float cx = tx_[R][R + BOFF], cy = ty_[R][R + BOFF];
     for (int item = tid; item < HITEMS; item += NT) {
@@ -456,7 +481,7 @@ __global__ void __launch_bounds__(NT) k_ssim_bwd_tma(SsimArgs A, const __grid_co
         for (int q = 0; q < 3; ++q) tma_load_4d(&sd[q][0][0], &T.d[P.v], P.x0 - R - BOFF, P.y0 - R, P.ch, q, &bar);
     }
     __syncthreads();
-    if (!tma_wait(&bar, A.flags)) return;
+    if (!tma_wait(&bar, A.flags, A.wait_ns)) return;
     for (int item = tid; item < HITEMS; item += NT) {
         const int r = item / (TX / HB), c0 = (item % (TX / HB)) * HB;
 #pragma unroll
@@ -544,6 +569,7 @@ gs_status launch_ssim(gs_workspace *ws, const float *rgb, const float *target, f
     A.n_elem = 3 * ws->n_pix;
     A.scale = grad_scale;
     A.flags = &ws->st->flags;
+    A.wait_ns = kTmaWaitNs;
     double g[K], sum = 0.0;
     for (int i = 0; i < K; ++i) {
         g[i] = std::exp(-(double)((i - R) * (i - R)) / (2.0 * 1.5 * 1.5));
@@ -571,3 +597,13 @@ gs_status launch_ssim(gs_workspace *ws, const float *rgb, const float *target, f
 }
 
 }  // namespace gs
+
+extern "C" gs_status gs_selftest_wait_timeout(gs_workspace *ws, int64_t limit_ns, int32_t *result, void *stream) {
+    if (!ws || !result || limit_ns <= 0 || limit_ns > 2000000000ll) {
+        gs::set_last_error("gs_selftest_wait_timeout: bad arguments");
+        return GS_ERR_INVALID_ARG;
+    }
+    ++ws->kernel_launches;
+    gs::k_wait_selftest<<<1, 64, 0, (cudaStream_t)stream>>>(&ws->st->flags, (uint64_t)limit_ns, result);
+    return gs::check_launch("wait_selftest");
+}

@@ -278,3 +278,51 @@ def test_invalid_arguments_and_call_order():
     assert L.gs_depth_loss(ws, p, p, mis, 1, p, None, s) == G.GS_ERR_INVALID_ARG
     assert "aligned" in G.last_error()
     L.gs_workspace_destroy(ws)
+
+
+def test_capacity_flag_clears_on_the_next_binning():
+    # an overflow blanks that frame only: the next gs_bin_sort that fits renders
+    # normally on the same workspace, identical to a fresh one
+    torch, dev = torch_dev()
+    G = _G()
+    from tests.gpu_helpers import params_to_dev
+    sc = S.random_box_scene(2000, 96, 64, 90.0, seed=2)
+    P = params_to_dev(sc)
+    r = G.Renderer(sc.cameras, sc.submap_offsets, 0, inst_capacity=600)
+    r.forward(*P)
+    st, need, _ = r.status()
+    assert st == G.GS_ERR_CAPACITY and need > 600
+    P_small = [p.clone() for p in P]
+    P_small[0][100:, 2] = -5.0  # all but 100 Gaussians behind the camera
+    rgb, dep, alp = [t.clone() for t in r.forward(*P_small)]
+    st, need2, _ = r.status()
+    assert st == G.GS_OK and need2 <= 600 and bool(alp.any())
+    fresh = G.Renderer(sc.cameras, sc.submap_offsets, 0, inst_capacity=600)
+    rgb2, dep2, alp2 = fresh.forward(*P_small)
+    torch.cuda.synchronize()
+    assert torch.equal(rgb, rgb2) and torch.equal(alp, alp2)
+    r.close()
+    fresh.close()
+
+
+def test_device_wait_timeout_is_reported():
+    # the bounded wait of the TMA staging, run out on purpose on a barrier no
+    # copy completes: a status, not a hang or a fault; cleared by the next binning
+    torch, dev = torch_dev()
+    G = _G()
+    from tests.gpu_helpers import params_to_dev
+    sc = S.random_box_scene(500, 64, 48, 60.0, seed=3)
+    P = params_to_dev(sc)
+    r = G.Renderer(sc.cameras, sc.submap_offsets, 0, inst_capacity=1 << 16)
+    r.forward(*P)
+    assert r.status()[0] == G.GS_OK
+    res = torch.zeros(1, dtype=torch.int32, device=dev)
+    assert G.lib().gs_selftest_wait_timeout(r.ws, 50_000_000, G._ptr(res), G._stream()) == G.GS_OK
+    torch.cuda.synchronize()
+    assert int(res.item()) == 1
+    with pytest.raises(G.GsError) as ei:
+        st = r.status()
+    assert ei.value.status == G.GS_ERR_CUDA
+    r.forward(*P)
+    assert r.status()[0] == G.GS_OK
+    r.close()
