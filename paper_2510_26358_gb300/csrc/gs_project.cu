@@ -10,8 +10,11 @@
 // Precision: the view-space depth is the double-precision dot product
 // ((R0 mu0 + R1 mu1) + R2 mu2) + t (exact products of float inputs), rounded to
 // float for the sort key, so keys are reproducible bit for bit.  The pixel
-// mean is formed in double and kept as an integer pixel plus a small float
-// offset, so that per-fragment offsets are exact integers plus that offset.
+// mean is formed in float-float arithmetic (error-free products and sums,
+// about 48 bits) and kept as an integer pixel plus a small float offset, so
+// that per-fragment offsets are exact integers plus that offset.  Only the
+// depth key uses double: GB300's FP64 rate is a small fraction of its FP32
+// rate, and the visible pairs are a sparse subset of every warp.
 // The image covariance is built from the rows of J W R S, its determinant
 // through the Lagrange identity (a sum of squares), so no step cancels.
 //
@@ -129,6 +132,65 @@ __device__ __forceinline__ double view_coord(const float *Ti, float m0, float m1
     return s + (double)Ti[3];
 }
 
+// float-float arithmetic: (hi, lo) with |lo| <= ulp(hi) / 2.  The rounded
+// operations are explicit so that no multiply-add contraction changes them.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ float2 renorm(float s, float e) {
+    const float hi = __fadd_rn(s, e);
+    return make_float2(hi, __fsub_rn(e, __fsub_rn(hi, s)));
+}
+
+// W_i . mu + t_i: exact products (fma residuals), compensated sums
+__device__ __forceinline__ float2 view_coord_ff(const float *Ti, float m0, float m1, float m2) {
+    const float p0 = __fmul_rn(Ti[0], m0), p1 = __fmul_rn(Ti[1], m1), p2 = __fmul_rn(Ti[2], m2);
+    float err = __fadd_rn(__fadd_rn(__fmaf_rn(Ti[0], m0, -p0), __fmaf_rn(Ti[1], m1, -p1)),
+                          __fmaf_rn(Ti[2], m2, -p2));
+    float s, t;
+    two_sum(p0, p1, s, t);
+    err = __fadd_rn(err, t);
+    two_sum(s, p2, s, t);
+    err = __fadd_rn(err, t);
+    two_sum(s, Ti[3], s, t);
+    err = __fadd_rn(err, t);
+    return renorm(s, err);
+}
+
+// f x / z + c for float-float x, z
+__device__ __forceinline__ float2 ff_pinhole(float f, float2 x, float2 z, float c) {
+    const float q0 = __fdiv_rn(x.x, z.x);
+    // remainder x - q0 z: the hi part exactly (fma), plus the small terms
+    const float r = __fadd_rn(__fmaf_rn(-q0, z.x, x.x), __fmaf_rn(-q0, z.y, x.y));
+    const float q1 = __fdiv_rn(r, z.x);
+    const float a = __fmul_rn(f, q0);
+    const float ea = __fmaf_rn(f, q0, -a);
+    float s, es;
+    two_sum(a, c, s, es);
+    return renorm(s, __fadd_rn(__fadd_rn(ea, es), __fmul_rn(f, q1)));
+}
+
+// floor / ceil of hi + lo (|lo| <= ulp(hi) / 2, |hi| < 2^23): a non-integer
+// hi keeps its floor / ceil; an integer hi moves by one if lo points away
+__device__ __forceinline__ float floor_ff(float2 v) {
+    const float f = floorf(v.x);
+    return (f == v.x && v.y < 0.f) ? f - 1.f : f;
+}
+__device__ __forceinline__ float ceil_ff(float2 v) {
+    const float c = ceilf(v.x);
+    return (c == v.x && v.y > 0.f) ? c + 1.f : c;
+}
+
+// v - d for float-float v and a float d
+__device__ __forceinline__ float2 ff_sub(float2 v, float d) {
+    float s, e;
+    two_sum(v.x, -d, s, e);
+    return renorm(s, __fadd_rn(e, v.y));
+}
+
 __device__ __forceinline__ int submap_of(const SubmapInfo *subs, int n_submaps, int64_t g) {
     int lo = 0, hi = n_submaps - 1;
     while (lo < hi) {
@@ -172,7 +234,7 @@ struct ProjArgs {
 // Projection of one pair in float after the exact depth: Jacobian, image
 // covariance rows T2 = J W R S, and the derived quantities.
 struct PairGeom {
-    float pxf, pyf, pzf;          // view-space mean (rounded from double)
+    float pxf, pyf, pzf;          // view-space mean (rounded)
     float J00, J02, J11, J12;     // projection Jacobian
     bool clx, cly;                // tangent clamped
     float txc, tyc;               // clamped tangent times z
@@ -181,11 +243,11 @@ struct PairGeom {
     float a, b, c, det;           // Sigma' and its determinant
 };
 
-__device__ __forceinline__ void pair_geom(const Cam &cam, int W, int H, const Consts &k, double px,
-                                          double py, double pz, const float M[9], PairGeom &G) {
-    G.pxf = (float)px;
-    G.pyf = (float)py;
-    G.pzf = (float)pz;
+__device__ __forceinline__ void pair_geom(const Cam &cam, int W, int H, const Consts &k, float px, float py,
+                                          float pz, const float M[9], PairGeom &G) {
+    G.pxf = px;
+    G.pyf = py;
+    G.pzf = pz;
     float limx = k.jac_clamp * fmaxf(cam.cx, (float)W - cam.cx) / cam.fx;
     float limy = k.jac_clamp * fmaxf(cam.cy, (float)H - cam.cy) / cam.fy;
     float xr = G.pxf / G.pzf, yr = G.pyf / G.pzf;
@@ -284,12 +346,16 @@ __global__ void __launch_bounds__(kProjThreads) k_project_fwd(ProjArgs A) {
         // skip the exact double-precision depth (the margin dwarfs the float error)
         const float z_est = __fmaf_rn(cam.T[10], mu[2], __fmaf_rn(cam.T[9], mu[1], __fmaf_rn(cam.T[8], mu[0], cam.T[11])));
         bool vis = qn > 0.f && E > 0.f && z_est > k.near_z - 1e-5f * (mabs + fabsf(cam.T[11]) + 1.f);
-        double px = 0.0, py = 0.0, pz = 0.0;
+        double pz = 0.0;
+        float2 pxx = make_float2(0.f, 0.f), pyy = pxx, pzz = pxx;
         if (vis) {
-            px = view_coord(cam.T, mu[0], mu[1], mu[2]);
-            py = view_coord(cam.T + 4, mu[0], mu[1], mu[2]);
-            pz = view_coord(cam.T + 8, mu[0], mu[1], mu[2]);
+            pz = view_coord(cam.T + 8, mu[0], mu[1], mu[2]);  // the exact depth, for the key
             vis = pz > (double)k.near_z;
+        }
+        if (vis) {
+            pxx = view_coord_ff(cam.T, mu[0], mu[1], mu[2]);
+            pyy = view_coord_ff(cam.T + 4, mu[0], mu[1], mu[2]);
+            pzz = view_coord_ff(cam.T + 8, mu[0], mu[1], mu[2]);
         }
         PairGeom G;
         float4 r0 = make_float4(0, 0, 0, 0), r1 = r0, r2 = r0;
@@ -298,7 +364,7 @@ __global__ void __launch_bounds__(kProjThreads) k_project_fwd(ProjArgs A) {
             // The rows of W R S have norm <= smax, so Sigma'_xx <= (|J00| + |J02|)^2 smax^2 + dil:
             // a pair whose mean lies farther outside the image than that bound on the
             // support's half-extent (plus a margin for this float estimate) has no pixel.
-            float zf = (float)pz, xf = (float)px, yf = (float)py;
+            float zf = pzz.x, xf = pxx.x, yf = pyy.x;
             float iz = 1.f / zf;
             float limx = k.jac_clamp * fmaxf(cam.cx, (float)vi.W - cam.cx) / cam.fx;
             float limy = k.jac_clamp * fmaxf(cam.cy, (float)vi.H - cam.cy) / cam.fy;
@@ -315,26 +381,25 @@ __global__ void __launch_bounds__(kProjThreads) k_project_fwd(ProjArgs A) {
                 vis = false;
         }
         if (vis) {
-            pair_geom(cam, vi.W, vi.H, k, px, py, pz, M, G);
+            pair_geom(cam, vi.W, vi.H, k, pxx.x, pyy.x, pzz.x, M, G);
             vis = G.det > 0.f;
         }
         if (vis) {
-            // pixel mean in double, split into integer pixel + offset
-            double iz = 1.0 / pz;
-            double u = (double)cam.fx * px * iz + (double)cam.cx;
-            double vv = (double)cam.fy * py * iz + (double)cam.cy;
-            double Uf = floor(u), Vf = floor(vv);
-            float hx = (float)(0.5 - (u - Uf));
-            float hy = (float)(0.5 - (vv - Vf));
+            // pixel mean (float-float), split into integer pixel + offset
+            const float2 u = ff_pinhole(cam.fx, pxx, pzz, cam.cx);
+            const float2 vv = ff_pinhole(cam.fy, pyy, pzz, cam.cy);
+            const float Uf = floor_ff(u), Vf = floor_ff(vv);
+            float hx = __fsub_rn(0.5f, __fadd_rn(__fsub_rn(u.x, Uf), u.y));
+            float hy = __fsub_rn(0.5f, __fadd_rn(__fsub_rn(vv.x, Vf), vv.y));
             // padded axis-aligned extent of {d : d^T Sigma'^-1 d <= E}
             float ex = sqrtf(E * G.a) * (1.f + k.ext_rel_pad) + k.ext_abs_pad;
             float ey = sqrtf(E * G.c) * (1.f + k.ext_rel_pad) + k.ext_abs_pad;
-            double xlo = ceil(u - (double)ex - 0.5), xhi = floor(u + (double)ex - 0.5);
-            double ylo = ceil(vv - (double)ey - 0.5), yhi = floor(vv + (double)ey - 0.5);
-            xlo = fmax(xlo, 0.0);
-            ylo = fmax(ylo, 0.0);
-            xhi = fmin(xhi, (double)(vi.W - 1));
-            yhi = fmin(yhi, (double)(vi.H - 1));
+            float xlo = ceil_ff(ff_sub(u, ex + 0.5f)), xhi = floor_ff(ff_sub(u, 0.5f - ex));
+            float ylo = ceil_ff(ff_sub(vv, ey + 0.5f)), yhi = floor_ff(ff_sub(vv, 0.5f - ey));
+            xlo = fmaxf(xlo, 0.f);
+            ylo = fmaxf(ylo, 0.f);
+            xhi = fminf(xhi, (float)(vi.W - 1));
+            yhi = fminf(yhi, (float)(vi.H - 1));
             vis = xlo <= xhi && ylo <= yhi;
             if (vis) {
                 rc = make_short4((short)((int)xlo / k.tile_w), (short)((int)ylo / k.tile_h),
@@ -357,7 +422,7 @@ __global__ void __launch_bounds__(kProjThreads) k_project_fwd(ProjArgs A) {
                     for (int ch = 0; ch < 3; ++ch) acc[ch] = __fmaf_rn(__ldg(shg + 3 * kk + ch), Y[kk], acc[ch]);
 #pragma unroll
                 for (int ch = 0; ch < 3; ++ch) rgb[ch] = fmaxf(acc[ch], 0.f);
-                r0 = make_float4((float)Uf, (float)Vf, hx, hy);
+                r0 = make_float4(Uf, Vf, hx, hy);
                 r1 = make_float4(l11, l12, l22, log2o);
                 r2 = make_float4(rgb[0], rgb[1], rgb[2], __double2float_rn(pz));
             }
@@ -441,11 +506,10 @@ __global__ void __launch_bounds__(kProjThreads, 2) k_project_bwd(ProjArgs A) {
             float glno = gg[G_LNO], gz = gg[G_Z];
             float grgb[3] = {gg[G_R], gg[G_G], gg[G_B]};
             Cam cam = load_cam(A.cams, v);
-            double pxd = view_coord(cam.T, mu[0], mu[1], mu[2]);
-            double pyd = view_coord(cam.T + 4, mu[0], mu[1], mu[2]);
-            double pzd = view_coord(cam.T + 8, mu[0], mu[1], mu[2]);
             PairGeom G;
-            pair_geom(cam, vi.W, vi.H, k, pxd, pyd, pzd, M, G);
+            pair_geom(cam, vi.W, vi.H, k, view_coord_ff(cam.T, mu[0], mu[1], mu[2]).x,
+                      view_coord_ff(cam.T + 4, mu[0], mu[1], mu[2]).x, view_coord_ff(cam.T + 8, mu[0], mu[1], mu[2]).x,
+                      M, G);
             const float p[3] = {G.pxf, G.pyf, G.pzf};
             const float *T = cam.T;
             float gp[3] = {0.f, 0.f, gz};
