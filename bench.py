@@ -365,12 +365,8 @@ class Step:
             self.adam_v = [torch.zeros_like(p) for p in self.P]
 
     def zero(self):
-        self.g_rgb.zero_()
-        self.g_depth.zero_()
-        for v in self.g_var:
-            v.zero_()
-        for v in self.grads.values():
-            v.zero_()
+        # one library launch for every gradient buffer the step accumulates into
+        self.G.gs_zero_buffers([self.g_rgb, self.g_depth, *self.g_var, *self.grads.values()])
 
     # stage-by-stage so that the breakdown can put events between them
     def stages(self):
@@ -655,6 +651,8 @@ def main():
     k0 = G.gs_workspace_info(step.r.ws)["kernel_launches"]
     step.run()
     launches_per_step = G.gs_workspace_info(step.r.ws)["kernel_launches"] - k0
+    # the gradient zeroing and the Adam step are library kernels outside the workspace
+    launches_per_step += 1 + (1 if args.adam else 0)
 
     graph = make_graph(torch, step)
     # timed region: graph replays, clocks sampled meanwhile

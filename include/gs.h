@@ -390,6 +390,11 @@ gs_status gs_partition(gs_voxel *vx, const int32_t *flags, int64_t n, int32_t sh
  * gs_workspace_status then reports GS_ERR_CUDA until the next gs_bin_sort. */
 gs_status gs_selftest_wait_timeout(gs_workspace *ws, int64_t limit_ns, int32_t *result, void *stream);
 
+/* Sets count (0..16) device buffers to zero in one launch: ptrs[i] (device)
+ * of bytes[i] bytes (host arrays).  For the gradient buffers, which the
+ * backward accumulates into. */
+gs_status gs_zero_buffers(void *const *ptrs, const int64_t *bytes, int32_t count, void *stream);
+
 /* Optional per-stage timing. With profiling on, each call records CUDA
  * events on its stream around every stage below (do not enable it while
  * capturing a CUDA graph); gs_workspace_stage_ms synchronises on the events

@@ -307,6 +307,36 @@ __global__ void __launch_bounds__(LT) k_adam(AdamArgs A) {
     }
 }
 
+// Zeroing of up to kZeroMax device buffers in one launch: blocks are given to
+// the buffers in proportion to their sizes, 16 bytes per store where aligned.
+constexpr int kZeroMax = 16;
+constexpr int kZeroChunk = 16 * 4 * LT;  // bytes per block
+struct ZeroArgs {
+    unsigned char *p[kZeroMax];
+    int64_t bytes[kZeroMax];
+    int32_t b0[kZeroMax + 1];  // first block of each buffer
+    int32_t n;
+};
+
+__global__ void __launch_bounds__(LT) k_zero(ZeroArgs A) {
+    const int b = blockIdx.x;
+    int s = 0;
+#pragma unroll 1
+    while (s + 1 < A.n && b >= A.b0[s + 1]) ++s;
+    unsigned char *p = A.p[s];
+    const int64_t lo = (int64_t)(b - A.b0[s]) * kZeroChunk;
+    const int64_t hi = min(A.bytes[s], lo + (int64_t)kZeroChunk);
+    if ((((uintptr_t)p) & 15) == 0) {
+        const int64_t v_lo = (lo + 15) / 16, v_hi = hi / 16;
+        for (int64_t i = v_lo + threadIdx.x; i < v_hi; i += LT)
+            reinterpret_cast<float4 *>(p)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int64_t i = lo + threadIdx.x; i < min(hi, v_lo * 16); i += LT) p[i] = 0;
+        for (int64_t i = max(lo, v_hi * 16) + threadIdx.x; i < hi; i += LT) p[i] = 0;
+    } else {
+        for (int64_t i = lo + threadIdx.x; i < hi; i += LT) p[i] = 0;
+    }
+}
+
 Thresholds thresholds(const gs_lifecycle_params &p) {
     auto logit = [](double t) { return (float)std::log(t / (1.0 - t)); };
     Thresholds t{};
@@ -453,6 +483,35 @@ gs_status gs_lifecycle_status(gs_lifecycle *lc, void *stream, int64_t *n_needed)
     }
     if (n_needed) *n_needed = h[0];
     return h[1] ? GS_ERR_CAPACITY : GS_OK;
+}
+
+gs_status gs_zero_buffers(void *const *ptrs, const int64_t *bytes, int32_t count, void *stream) {
+    if (count < 0 || count > kZeroMax || (count > 0 && (!ptrs || !bytes))) {
+        set_last_error("gs_zero_buffers: bad arguments");
+        return GS_ERR_INVALID_ARG;
+    }
+    ZeroArgs A{};
+    int64_t blocks = 0;
+    for (int i = 0; i < count; ++i) {
+        if (bytes[i] < 0 || (bytes[i] > 0 && !ptrs[i])) {
+            set_last_error("gs_zero_buffers: bad buffer");
+            return GS_ERR_INVALID_ARG;
+        }
+        if (bytes[i] == 0) continue;
+        A.p[A.n] = static_cast<unsigned char *>(ptrs[i]);
+        A.bytes[A.n] = bytes[i];
+        A.b0[A.n] = (int32_t)blocks;
+        blocks += (bytes[i] + kZeroChunk - 1) / kZeroChunk;
+        ++A.n;
+    }
+    if (A.n == 0) return GS_OK;
+    if (blocks > 0x7FFFFFFF) {
+        set_last_error("gs_zero_buffers: too large");
+        return GS_ERR_INVALID_ARG;
+    }
+    A.b0[A.n] = (int32_t)blocks;
+    k_zero<<<(unsigned)blocks, LT, 0, (cudaStream_t)stream>>>(A);
+    return check_launch("zero_buffers");
 }
 
 gs_status gs_adam_step(const gs_param_arrays *param, const gs_param_arrays *grad, const gs_param_arrays *m,

@@ -33,7 +33,7 @@ EXPORTED = ("gs_config_default", "gs_workspace_create", "gs_workspace_destroy", 
             "gs_workspace_stage_ms", "gs_image_l1_noalloc", "gs_status_string", "gs_last_error",
             "gs_lifecycle_create", "gs_lifecycle_destroy", "gs_lifecycle_run", "gs_lifecycle_status", "gs_adam_step",
             "gs_voxel_keys", "gs_voxel_create", "gs_voxel_destroy", "gs_voxel_insert", "gs_voxel_status",
-            "gs_active_select", "gs_partition", "gs_selftest_wait_timeout")
+            "gs_active_select", "gs_partition", "gs_selftest_wait_timeout", "gs_zero_buffers")
 GS_LC_PRUNE, GS_LC_DENSIFY, GS_LC_RESET = 1, 2, 4
 PARAM_FIELDS = ("means", "log_scales", "quats", "opacity_logits", "sh")
 IMAGE_L1_NOALLOC_MAX = 1024 * 65536  # GS_IMAGE_L1_NOALLOC_BLOCKS * GS_IMAGE_L1_NOALLOC_CHUNK
@@ -148,6 +148,7 @@ def lib() -> ctypes.CDLL:
     L.gs_active_select.argtypes = [P, P, i64, i64, P, P]
     L.gs_partition.argtypes = [P, P, i64, i32, PA, P, P, PA, P, P, PA, P, P, P, P]
     L.gs_selftest_wait_timeout.argtypes = [P, i64, P, P]
+    L.gs_zero_buffers.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int64), i32, P]
     L.gs_status_string.argtypes = [i32]
     L.gs_status_string.restype = ctypes.c_char_p
     L.gs_last_error.argtypes = []
@@ -159,7 +160,7 @@ def lib() -> ctypes.CDLL:
                  "gs_workspace_copy", "gs_workspace_set_profiling", "gs_workspace_stage_ms",
                  "gs_image_l1_noalloc", "gs_lifecycle_create", "gs_lifecycle_run", "gs_lifecycle_status",
                  "gs_adam_step", "gs_voxel_keys", "gs_voxel_create", "gs_voxel_insert", "gs_voxel_status",
-                 "gs_active_select", "gs_partition", "gs_selftest_wait_timeout"):
+                 "gs_active_select", "gs_partition", "gs_selftest_wait_timeout", "gs_zero_buffers"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -352,6 +353,14 @@ class VoxelMap:
                                   ctypes.byref(param_arrays(moved)), _ptr(moved_keys), _ptr(moved_lu),
                                   _ptr(counts), _stream(stream)), "gs_partition")
         return counts
+
+
+def gs_zero_buffers(tensors, stream=None):
+    """Zero up to 16 device tensors in one library launch."""
+    ts = [t for t in tensors if t is not None and t.numel() > 0]
+    ptrs = (ctypes.c_void_p * max(1, len(ts)))(*[t.data_ptr() for t in ts])
+    sizes = (ctypes.c_int64 * max(1, len(ts)))(*[t.numel() * t.element_size() for t in ts])
+    _check(lib().gs_zero_buffers(ptrs, sizes, len(ts), _stream(stream)), "gs_zero_buffers")
 
 
 def status_string(s: int) -> str:

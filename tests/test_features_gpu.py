@@ -326,3 +326,23 @@ def test_device_wait_timeout_is_reported():
     r.forward(*P)
     assert r.status()[0] == G.GS_OK
     r.close()
+
+
+def test_zero_buffers():
+    # many buffers, odd sizes, unaligned starts, empty ones: exactly the given bytes become 0
+    torch, dev = torch_dev()
+    G = _G()
+    base = torch.full((1 << 20,), 7, dtype=torch.uint8, device=dev)
+    views = [base[3:3 + 1001], base[5000:5000 + 64 * 1024 + 5], base[200000:200000], base[300001:300001 + 7],
+             base[400000:400000 + 900000 - 400000]]
+    G.gs_zero_buffers(views)
+    torch.cuda.synchronize()
+    ref = torch.full_like(base, 7)
+    for a, b in ((3, 1004), (5000, 5000 + 64 * 1024 + 5), (300001, 300008), (400000, 900000)):
+        ref[a:b] = 0
+    assert torch.equal(base, ref)
+    f = torch.ones(12345, 7, device=dev)
+    G.gs_zero_buffers([f])
+    assert int(torch.count_nonzero(f)) == 0
+    with pytest.raises(G.GsError):
+        G.gs_zero_buffers([torch.ones(4, device=dev)] * 17)
