@@ -134,7 +134,7 @@ const char *gs_last_error(void) { return g_last_error.c_str(); }
 void gs_workspace_destroy(gs_workspace *ws) {
     if (!ws) return;
     void *ptrs[] = {ws->views, ws->subs, ws->sub_views, ws->rec, ws->pkey, ws->rect, ws->g2d,
-                    ws->vis_key, ws->vis_pair, ws->vis_key_alt, ws->vis_pair_alt, ws->ioff,
+                    ws->vis_key, ws->vis_pair, ws->vis_key_alt, ws->vis_pair_alt, ws->ioff, ws->win_pair,
                     ws->inst_tile, ws->inst_val, ws->inst_tile_alt, ws->inst_val_alt, ws->ranges,
                     ws->tile_order, ws->tile_buckets,
                     ws->last, ws->tfin, ws->vstat, ws->hist, ws->part, ws->digit_tot, ws->pose_part, ws->red_part, ws->ssim_d, ws->ssim_part,
@@ -268,6 +268,7 @@ gs_status gs_workspace_create(const gs_camera *cams, int32_t n_views, const int6
     GS_ALLOC(ws->vis_key_alt, P);
     GS_ALLOC(ws->vis_pair_alt, P);
     GS_ALLOC(ws->ioff, P);
+    GS_ALLOC(ws->win_pair, I / kEmitWindow + 2);
     GS_ALLOC(ws->inst_tile, I);
     GS_ALLOC(ws->inst_val, I);
     GS_ALLOC(ws->inst_tile_alt, I);

@@ -32,6 +32,7 @@ struct DevState {
     uint32_t pad[7];
 };
 constexpr uint32_t kFlagCapacity = 1u;
+constexpr int kEmitWindow = 1024;      // output slots per emission window
 constexpr uint32_t kFlagTimeout = 2u;  // a bounded device wait (TMA) gave up
 
 }  // namespace gs
@@ -60,6 +61,7 @@ struct gs_workspace {
     float *g2d = nullptr;          // [n_pairs][10]
     uint32_t *vis_key = nullptr, *vis_pair = nullptr, *vis_key_alt = nullptr, *vis_pair_alt = nullptr;
     uint32_t *ioff = nullptr;      // [n_pairs]
+    uint32_t *win_pair = nullptr;  // [inst_cap / kEmitWindow + 1] owner of each emission window's first slot
     // per-instance buffers
     uint32_t *inst_tile = nullptr, *inst_val = nullptr, *inst_tile_alt = nullptr, *inst_val_alt = nullptr;
     // per-tile / per-pixel

@@ -302,10 +302,15 @@ __global__ void __launch_bounds__(T) k_count_instances(const uint32_t *vis_pair,
     if (threadIdx.x == 0) part[blockIdx.x] = tot;
 }
 
-// ioff[i] <- first output slot of sorted pair i (exclusive scan of the counts)
+// ioff[i] <- first output slot of sorted pair i (exclusive scan of the counts);
+// win_pair[w] <- the pair that owns slot w * kEmitWindow (every slot belongs to
+// exactly one pair, so each window start is written once)
 __global__ void __launch_bounds__(T) k_instance_offsets(const DevState *st, const uint32_t *part, int nb,
-                                                       uint32_t *ioff) {
+                                                       uint32_t *ioff, uint32_t *win_pair, uint32_t n_win) {
     __shared__ uint32_t sm[32];
+    // over capacity the offsets are not used (emission writes nothing) and
+    // would index past the window table
+    if (st->flags & kFlagCapacity) return;
     uint32_t n = st->n_vis;
     uint32_t lo, hi;
     chunk_range(n, blockIdx.x, nb, T, lo, hi);
@@ -315,7 +320,13 @@ __global__ void __launch_bounds__(T) k_instance_offsets(const DevState *st, cons
         uint32_t c = i < hi ? ioff[i] : 0u;
         uint32_t tot;
         uint32_t ex = block_exclusive_scan(c, sm, &tot);
-        if (i < hi) ioff[i] = base + ex;
+        if (i < hi) {
+            const uint32_t start = base + ex;
+            ioff[i] = start;
+            for (uint32_t w = (start + kEmitWindow - 1) / kEmitWindow;
+                 c > 0 && w < n_win && w * (uint64_t)kEmitWindow < (uint64_t)start + c; ++w)
+                win_pair[w] = i;
+        }
         base += tot;
     }
 }
@@ -323,10 +334,10 @@ __global__ void __launch_bounds__(T) k_instance_offsets(const DevState *st, cons
 // Instances of the depth-sorted visible pairs, in that order, each pair's
 // tiles row-major.  The work is split by output slot, not by pair (pairs in
 // depth order have very uneven rectangles): a block takes a window of
-// kEmitWindow consecutive slots, finds the pairs that cover it by binary
-// search in ioff, stages them in shared memory, and every thread writes one
-// instance per step, locating its pair by binary search in the stage.
-constexpr int kEmitWindow = 1024;
+// kEmitWindow consecutive slots, takes the pairs that cover it from the
+// window-start table (the pairs owning its first slot and the next window's),
+// stages them in shared memory, and every thread writes one instance per
+// step, locating its pair by binary search in the stage.
 
 __device__ __forceinline__ uint32_t last_le(const uint32_t *a, uint32_t n, uint32_t x) {
     // largest i < n with a[i] <= x (a nondecreasing, a[0] <= x)
@@ -341,7 +352,8 @@ __device__ __forceinline__ uint32_t last_le(const uint32_t *a, uint32_t n, uint3
 __global__ void __launch_bounds__(T) k_emit_instances(const uint32_t *vis_pair, const short4 *rect,
                                                      const ViewInfo *views, int n_views,
                                                      const DevState *st, const uint32_t *ioff,
-                                                     uint32_t *inst_tile, uint32_t *inst_val) {
+                                                     const uint32_t *win_pair, uint32_t *inst_tile,
+                                                     uint32_t *inst_val) {
     __shared__ uint32_t s_off[kEmitWindow];
     __shared__ uint32_t s_pair[kEmitWindow];
     __shared__ short4 s_rect[kEmitWindow];
@@ -354,8 +366,18 @@ __global__ void __launch_bounds__(T) k_emit_instances(const uint32_t *vis_pair, 
     for (uint32_t wdw = blockIdx.x; wdw < windows; wdw += gridDim.x) {
         const uint32_t o0 = wdw * kEmitWindow;
         const uint32_t o1 = min(o0 + kEmitWindow, total);
-        if (t == 0) s_range[0] = last_le(ioff, n, o0);
-        if (t == 1) s_range[1] = last_le(ioff, n, o1 - 1);
+        if (t == 0) s_range[0] = win_pair[wdw];
+        if (t == 1) {
+            // the pair owning slot o1 - 1: the last pair if this is the last
+            // window, else the owner of the next window's first slot, or the
+            // pair before it when that one starts exactly at o1
+            uint32_t p1 = n - 1;
+            if (wdw + 1 < windows) {
+                p1 = win_pair[wdw + 1];
+                if (ioff[p1] == o1) --p1;
+            }
+            s_range[1] = p1;
+        }
         __syncthreads();
         const uint32_t s0 = s_range[0], np = s_range[1] - s0 + 1;  // np <= window: every pair has >= 1 slot
         for (uint32_t k = t; k < np; k += T) {
@@ -496,9 +518,11 @@ gs_status launch_bin_sort(gs_workspace *ws, cudaStream_t s) {
     StageTimer timer(ws, GS_STAGE_EMIT, s);
     ++ws->kernel_launches; k_count_instances<<<nb, T, 0, s>>>(v, ws->rect, st, ws->ioff, ws->part, nb);
     ++ws->kernel_launches; k_scan_parts<<<1, T, 0, s>>>(ws->part, nb, nullptr, st, (uint64_t)ws->inst_cap, 1);
-    ++ws->kernel_launches; k_instance_offsets<<<nb, T, 0, s>>>(st, ws->part, nb, ws->ioff);
+    ++ws->kernel_launches; k_instance_offsets<<<nb, T, 0, s>>>(st, ws->part, nb, ws->ioff, ws->win_pair,
+                                                                  (uint32_t)(ws->inst_cap / kEmitWindow + 2));
     ++ws->kernel_launches;
-    k_emit_instances<<<4 * ws->num_sms, T, 0, s>>>(v, ws->rect, ws->views, ws->n_views, st, ws->ioff, tk, tv);
+    k_emit_instances<<<4 * ws->num_sms, T, 0, s>>>(v, ws->rect, ws->views, ws->n_views, st, ws->ioff, ws->win_pair,
+                                                   tk, tv);
     if ((r = check_launch("emit")) != GS_OK) return r;
     }
     // 4. stable sort of the instances by tile id
