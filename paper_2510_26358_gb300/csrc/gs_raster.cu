@@ -208,12 +208,11 @@ __device__ __forceinline__ int reduce10_component(int lane) {
     return ok ? 5 * b4 + 3 * b3 + 2 * b2 + b1 : -1;
 }
 
-// At least 640 resident threads per SM (20 warps): measured best on the
-// 500k orchard (10 two-warp blocks: 0.54 ms; no bound: 0.60 ms; 14 or 16
-// blocks spill registers: 0.62 / 0.67 ms).  The VAR variant holds three more
-// values per pixel and takes 512 (16 warps) so that it does not spill.
+// At least 512 resident threads per SM (16 warps, 128 registers a thread):
+// with eight pixels a thread, measured best on the 500k orchard (16 one-warp
+// blocks: 0.435 ms; 14: 0.441 ms).
 template <int TW, int TH, int PPT, bool VAR>
-__global__ void __launch_bounds__(TW * TH / PPT, (VAR ? 512 : 640) / (TW * TH / PPT)) k_raster_bwd(RasterArgs A) {
+__global__ void __launch_bounds__(TW * TH / PPT, 512 / (TW * TH / PPT)) k_raster_bwd(RasterArgs A) {
     constexpr int NT = TW * TH / PPT;
     static_assert(NT % 32 == 0, "the backward needs whole warps");
     constexpr int NW = (NT + 31) / 32;
@@ -312,21 +311,39 @@ __global__ void __launch_bounds__(TW * TH / PPT, (VAR ? 512 : 640) / (TW * TH / 
                 const float4 a = sA[j], b = sB[j];
                 float dxi, u1;
                 frag_column(a, b, pxf, dxi, u1);
-                float g[kGrad];
-#pragma unroll
-                for (int q = 0; q < kGrad; ++q) g[q] = 0.f;
+                // the forward's alpha decision for each of the thread's pixels:
+                // ar = the unclamped alpha of a pixel the fragment reaches, else 0
+                float ar[PPT], t1_0 = 0.f, t2_0 = 0.f, dyi_0 = 0.f;
                 bool any = false;
 #pragma unroll
                 for (int i = 0; i < PPT; ++i) {
                     float t1, t2, dyi;
                     const float e = frag_pixel(a, b, u1, (float)(py0 + i), t1, t2, dyi);
-                    if (!(rel < cnt[i] && e >= l2amin)) continue;
-                    any = true;
-                    const float araw = ex2_approx(e);
-                    const float al = fminf(amax, araw);
-                    const float r1m = rcp_approx(1.f - al);
+                    if (i == 0) {
+                        t1_0 = t1;
+                        t2_0 = t2;
+                        dyi_0 = dyi;
+                    }
+                    const bool in = rel < cnt[i] && e >= l2amin;
+                    ar[i] = in ? ex2_approx(e) : 0.f;
+                    any |= in;
+                }
+                if (!__any_sync(0xffffffffu, any)) continue;
+                // Every pixel runs the same instructions: a pixel this fragment
+                // does not reach takes alpha = 0, for which each update below is
+                // exactly the identity (T * 1, acc + 0 * h, sums + 0).
+                const float4 c = sC[j];
+                float sR = 0.f, sG = 0.f, sB_ = 0.f, sZ = 0.f;  // sum wgt dL/dc
+                // sums of gpw = dL/dpw over the column's pixels i = 0..PPT-1,
+                // weighted by 1, i and i^2: the pixel offsets are dx (one per
+                // column) and dy_i = dy_0 + i, and t1, t2 are affine in i, so
+                // these three give every second-order moment the gradient needs
+                float S0 = 0.f, S1 = 0.f, S2 = 0.f;
+#pragma unroll
+                for (int i = 0; i < PPT; ++i) {
+                    const float al = fminf(amax, ar[i]);
+                    const float r1m = ar[i] > 0.f ? rcp_approx(1.f - al) : 1.f;
                     T[i] = T[i] * r1m;  // transmittance before this fragment
-                    const float4 c = sC[j];
                     const float wgt = al * T[i];
                     float h = gR[i] * c.x + gG[i] * c.y + gB[i] * c.z + gD[i] * c.w + gA[i];
                     float gz = gD[i];
@@ -338,36 +355,43 @@ __global__ void __launch_bounds__(TW * TH / PPT, (VAR ? 512 : 640) / (TW * TH / 
                     }
                     const float dLda = T[i] * h - acc[i] * r1m;
                     acc[i] = __fmaf_rn(wgt, h, acc[i]);
-                    g[G_R] += wgt * gR[i];
-                    g[G_G] += wgt * gG[i];
-                    g[G_B] += wgt * gB[i];
-                    g[G_Z] += wgt * gz;
-                    if (araw <= amax) {
-                        // gpw = dL/dpw with pw = -d^T Q d / 2 (natural log).  The warp sums
-                        // the raw moments; the per-Gaussian factors are applied once after
-                        // the reduction (see below).
-                        const float gpw = dLda * al;
-                        const float2 hh = sH[j];
-                        const float dx = dxi + hh.x, dy = dyi + hh.y;
-                        g[G_LNO] += gpw;
-                        g[G_U] = __fmaf_rn(gpw, t1, g[G_U]);  // sum gpw t1
-                        g[G_V] = __fmaf_rn(gpw, t2, g[G_V]);  // sum gpw t2
-                        const float gx = gpw * dx, gy = gpw * dy;
-                        g[G_QA] = __fmaf_rn(gx, dx, g[G_QA]);  // sum gpw dx^2
-                        g[G_QB] = __fmaf_rn(gx, dy, g[G_QB]);  // sum gpw dx dy
-                        g[G_QC] = __fmaf_rn(gy, dy, g[G_QC]);  // sum gpw dy^2
+                    sR = __fmaf_rn(wgt, gR[i], sR);
+                    sG = __fmaf_rn(wgt, gG[i], sG);
+                    sB_ = __fmaf_rn(wgt, gB[i], sB_);
+                    sZ = __fmaf_rn(wgt, gz, sZ);
+                    // gpw with pw = -d^T Q d / 2 (natural log); a clamped alpha
+                    // has no gradient through pw
+                    const float gpw = ar[i] > 0.f && ar[i] <= amax ? dLda * al : 0.f;
+                    S0 += gpw;
+                    if (i > 0) {
+                        S1 = __fmaf_rn(gpw, (float)i, S1);
+                        S2 = __fmaf_rn(gpw, (float)(i * i), S2);
                     }
                 }
-                if (__any_sync(0xffffffffu, any)) {
-                    const float tot = warp_reduce_scatter10(g, lane);
-                    if (my_comp >= 0) {
-                        // dL/dQ = -1/2 sum gpw d d^T; dpw/du = (Q d)_x = l11 t1 / s^2,
-                        // dpw/dv = (l12 t1 + l22 t2) / s^2 with 1/s^2 = 2 ln 2: each lane
-                        // scales its sum by c0 + c11 l11 + c22 l22 (constants per lane)
-                        float *gp = A.g2d + (size_t)sP[j] * kGrad;
-                        atomicAdd(gp + my_comp, tot * __fmaf_rn(sc11, b.x, __fmaf_rn(sc22, b.z, sc0)));
-                        if (my_comp == G_U) atomicAdd(gp + G_V, kTwoLn2 * b.y * tot);
-                    }
+                // per-lane raw moments; the per-Gaussian factors are applied
+                // once after the warp reduction (see below)
+                const float2 hh = sH[j];
+                const float dx = dxi + hh.x, dy0 = dyi_0 + hh.y;
+                const float sy = __fmaf_rn(dy0, S0, S1);  // sum gpw dy
+                float g[kGrad];
+                g[G_LNO] = S0;
+                g[G_U] = __fmaf_rn(t1_0, S0, b.y * S1);  // sum gpw t1, t1_i = t1_0 + l12 i
+                g[G_V] = __fmaf_rn(t2_0, S0, b.z * S1);  // sum gpw t2, t2_i = t2_0 + l22 i
+                g[G_QA] = dx * dx * S0;                     // sum gpw dx^2
+                g[G_QB] = dx * sy;                          // sum gpw dx dy
+                g[G_QC] = __fmaf_rn(dy0, sy, __fmaf_rn(dy0, S1, S2));  // sum gpw dy^2
+                g[G_R] = sR;
+                g[G_G] = sG;
+                g[G_B] = sB_;
+                g[G_Z] = sZ;
+                const float tot = warp_reduce_scatter10(g, lane);
+                if (my_comp >= 0) {
+                    // dL/dQ = -1/2 sum gpw d d^T; dpw/du = (Q d)_x = l11 t1 / s^2,
+                    // dpw/dv = (l12 t1 + l22 t2) / s^2 with 1/s^2 = 2 ln 2: each lane
+                    // scales its sum by c0 + c11 l11 + c22 l22 (constants per lane)
+                    float *gp = A.g2d + (size_t)sP[j] * kGrad;
+                    atomicAdd(gp + my_comp, tot * __fmaf_rn(sc11, b.x, __fmaf_rn(sc22, b.z, sc0)));
+                    if (my_comp == G_U) atomicAdd(gp + G_V, kTwoLn2 * b.y * tot);
                 }
             }
         }
@@ -382,12 +406,14 @@ __global__ void k_zero_g2d(const uint32_t *vis_pair, const DevState *st, float *
 }
 
 // Pixels per thread of the backward (the forward uses one, so that a pixel
-// leaves the list as soon as it saturates).  Four amortise the warp reduction
-// best on 16x16 and larger tiles (measured: 2 -> 0.66 ms, 4 -> 0.54 ms, 8 ->
-// 0.56 ms on the 500k orchard); an 8x8 tile keeps 2 so that its CTA is still
-// a whole warp, which the full-mask shuffles and votes require.
-template <int TW, int TH>
-constexpr int ppt_bwd() { return TW * TH / 4 >= 64 ? 4 : 2; }
+// leaves the list as soon as it saturates).  More pixels a thread amortise the
+// per-fragment warp reduction and the shared-memory reads over more pixels:
+// on the 500k orchard with 16x16 tiles, 4 -> 0.467 ms and 8 (one warp a tile)
+// -> 0.435 ms.  The VAR variant holds three more values a pixel and keeps 4
+// (8 spills).  An 8x8 tile keeps 2 so that its CTA is still a whole warp,
+// which the full-mask shuffles and votes require.
+template <int TW, int TH, bool VAR>
+constexpr int ppt_bwd() { return TW * TH >= 256 ? (VAR ? 4 : 8) : 2; }
 
 size_t fwd_smem(int depth) { return (size_t)depth * 3 * sizeof(float4); }
 size_t bwd_smem(int depth) {
@@ -396,7 +422,7 @@ size_t bwd_smem(int depth) {
 
 template <int TW, int TH, bool VAR>
 cudaError_t configure_variant(gs_workspace *ws, int &grid_f, int &grid_b) {
-    constexpr int PPT = ppt_bwd<TW, TH>();
+    constexpr int PPT = ppt_bwd<TW, TH, VAR>();
     const int depth = ws->cfg.batch_depth;
     cudaError_t e = cudaFuncSetAttribute(k_raster_fwd<TW, TH, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)fwd_smem(256));
@@ -453,13 +479,13 @@ gs_status run_fwd(gs_workspace *ws, RasterArgs A, cudaStream_t s) {
 }
 template <int TW, int TH>
 gs_status run_bwd(gs_workspace *ws, RasterArgs A, cudaStream_t s) {
-    constexpr int PPT = ppt_bwd<TW, TH>();
+    constexpr int PV = ppt_bwd<TW, TH, true>(), P = ppt_bwd<TW, TH, false>();
     StageTimer timer(ws, GS_STAGE_RASTER_BWD, s);
     ++ws->kernel_launches;
     if (A.vstat)
-        k_raster_bwd<TW, TH, PPT, true><<<ws->raster_grid_bwd_var, TW * TH / PPT, bwd_smem(A.depth), s>>>(A);
+        k_raster_bwd<TW, TH, PV, true><<<ws->raster_grid_bwd_var, TW * TH / PV, bwd_smem(A.depth), s>>>(A);
     else
-        k_raster_bwd<TW, TH, PPT, false><<<ws->raster_grid_bwd, TW * TH / PPT, bwd_smem(A.depth), s>>>(A);
+        k_raster_bwd<TW, TH, P, false><<<ws->raster_grid_bwd, TW * TH / P, bwd_smem(A.depth), s>>>(A);
     return check_launch("raster_bwd");
 }
 
