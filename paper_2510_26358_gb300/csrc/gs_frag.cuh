@@ -66,6 +66,55 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
+// Two floats in one 64-bit register, for the packed single-precision
+// arithmetic of sm_100 and later: one add / sub / mul / fma instruction works
+// both halves, each rounded exactly as the scalar instruction rounds it (no
+// flush to zero, like the scalar code built without -ftz).
+struct f2 {
+    unsigned long long v;
+};
+
+__device__ __forceinline__ f2 f2_pack(float lo, float hi) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ f2 f2_bcast(float x) { return f2_pack(x, x); }
+__device__ __forceinline__ void f2_unpack(f2 a, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a.v));
+}
+__device__ __forceinline__ float f2_lo(f2 a) {
+    float lo, hi;
+    f2_unpack(a, lo, hi);
+    return lo;
+}
+__device__ __forceinline__ float f2_hi(f2 a) {
+    float lo, hi;
+    f2_unpack(a, lo, hi);
+    return hi;
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+    return d;
+}
+__device__ __forceinline__ f2 f2_sub(f2 a, f2 b) {
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+    return d;
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+    return d;
+}
+// a * b + c with one rounding per half
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return d;
+}
+
 // Staged copy of one projected record, as the rasterisers keep it in shared
 // memory: a = (U, V, k1, k2) with U, V the integer pixel of the mean and
 // k1 = l11 hx + l12 hy, k2 = l22 hy; b = (l11, l12, l22, log2 o) the scaled

@@ -235,11 +235,20 @@ __device__ __forceinline__ int reduce10_component(int lane) {
 // At least 512 resident threads per SM (16 warps, 128 registers a thread):
 // with eight pixels a thread, measured best on the 500k orchard (16 one-warp
 // blocks: 0.435 ms; 14: 0.441 ms).
+//
+// A thread's PPT pixels are worked in Q = PPT/2 packed pairs (pixel p in the
+// low half, pixel p + Q in the high half), so that one f32x2 instruction does
+// the arithmetic of two pixels.  The alpha decision is taken on
+// -e = fma(t1, t1, fma(t2, t2, -log2 o)), which is exactly the negation of
+// the forward's e = fma(-t1, t1, fma(-t2, t2, log2 o)) (round to nearest is
+// symmetric), so both passes take the same decisions bit for bit.
 template <int TW, int TH, int PPT, bool VAR>
 __global__ void __launch_bounds__(TW * TH / PPT, 512 / (TW * TH / PPT)) k_raster_bwd(RasterArgs A) {
     constexpr int NT = TW * TH / PPT;
     static_assert(NT % 32 == 0, "the backward needs whole warps");
+    static_assert(PPT % 2 == 0, "the backward works pixels in pairs");
     constexpr int NW = (NT + 31) / 32;
+    constexpr int Q = PPT / 2;
     extern __shared__ float4 smem[];
     float4 *sA = smem, *sB = smem + A.depth, *sC = smem + 2 * A.depth;
     float2 *sH = reinterpret_cast<float2 *>(smem + 3 * A.depth);
@@ -247,14 +256,17 @@ __global__ void __launch_bounds__(TW * TH / PPT, 512 / (TW * TH / PPT)) k_raster
     __shared__ int s_tile;
     __shared__ uint32_t s_max[NW];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const float amax = A.c.alpha_max, l2amin = A.c.log2_alpha_min;
+    const float amax = A.c.alpha_max, nl2amin = -A.c.log2_alpha_min;
+    const f2 ONE = f2_bcast(1.f);
     // component this lane adds after the reduction (even lanes only), and the
     // factors c0 + c11 l11 + c22 l22 that turn its raw sum into the gradient
+    // (the colour and depth sums come out negated, see below)
     const int my_comp = (lane & 1) ? -1 : reduce10_component(lane);
     const float sc0 = my_comp == G_QA || my_comp == G_QC ? -0.5f
                       : my_comp == G_QB                  ? -1.f
                       : my_comp == G_U || my_comp == G_V ? 0.f
-                                                         : 1.f;
+                      : my_comp == G_LNO                 ? 1.f
+                                                         : -1.f;
     const float sc11 = my_comp == G_U ? kTwoLn2 : 0.f;
     const float sc22 = my_comp == G_V ? kTwoLn2 : 0.f;
     for (;;) {
@@ -272,38 +284,54 @@ __global__ void __launch_bounds__(TW * TH / PPT, 512 / (TW * TH / PPT)) k_raster
         const int px = (lt % vi.ntx) * TW + tid % TW;
         const int py0 = (lt / vi.ntx) * TH + (tid / TW) * PPT;
         const float pxf = (float)px;
+        const f2 PY0 = f2_pack((float)py0, (float)(py0 + Q));
         const uint2 rg = A.ranges[tile];
         const int64_t hw = (int64_t)vi.W * vi.H;
         const float *grgb = A.dL_drgb + 3 * (int64_t)vi.pix_off;
         uint32_t cnt[PPT], mycnt = 0;
-        float T[PPT], gR[PPT], gG[PPT], gB[PPT], gD[PPT], gA[PPT], acc[PPT];
-        float zmu[PPT], ga[PPT], gb[PPT];
+        f2 T[Q], gR[Q], gG[Q], gB[Q], gD[Q], gA[Q], nacc[Q];  // nacc = -acc
+        f2 zmu[Q], ga[Q], gb[Q];
 #pragma unroll
-        for (int i = 0; i < PPT; ++i) {
-            const int py = py0 + i;
-            cnt[i] = 0;
-            T[i] = 1.f;
-            gR[i] = gG[i] = gB[i] = gD[i] = gA[i] = acc[i] = 0.f;
-            zmu[i] = ga[i] = gb[i] = 0.f;
-            if (px < vi.W && py < vi.H) {
-                const int64_t pl = (int64_t)py * vi.W + px;
-                const int64_t pix = vi.pix_off + pl;
-                cnt[i] = A.last[pix];
-                T[i] = A.tfin[pix];
-                gR[i] = grgb[pl];
-                gG[i] = grgb[hw + pl];
-                gB[i] = grgb[2 * hw + pl];
-                gD[i] = A.dL_ddepth ? A.dL_ddepth[pix] : 0.f;
-                gA[i] = A.dL_dalpha ? A.dL_dalpha[pix] : 0.f;
-                if (VAR) {
-                    const float4 vs = A.vstat[pix];
-                    zmu[i] = vs.x;
-                    ga[i] = A.dL_dmean ? A.dL_dmean[pix] * vs.z : 0.f;
-                    gb[i] = A.dL_dvar ? A.dL_dvar[pix] * vs.z : 0.f;
-                    gA[i] = __fmaf_rn(-gb[i], vs.y, gA[i]);  // the -b var part of every h
+        for (int p = 0; p < Q; ++p) {
+            float t_[2], r_[2], g_[2], b_[2], d_[2], a_[2], z_[2], ma_[2], mb_[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int i = p + h * Q, py = py0 + i;
+                cnt[i] = 0;
+                t_[h] = 1.f;
+                r_[h] = g_[h] = b_[h] = d_[h] = a_[h] = z_[h] = ma_[h] = mb_[h] = 0.f;
+                if (px < vi.W && py < vi.H) {
+                    const int64_t pl = (int64_t)py * vi.W + px;
+                    const int64_t pix = vi.pix_off + pl;
+                    cnt[i] = A.last[pix];
+                    t_[h] = A.tfin[pix];
+                    r_[h] = grgb[pl];
+                    g_[h] = grgb[hw + pl];
+                    b_[h] = grgb[2 * hw + pl];
+                    d_[h] = A.dL_ddepth ? A.dL_ddepth[pix] : 0.f;
+                    a_[h] = A.dL_dalpha ? A.dL_dalpha[pix] : 0.f;
+                    if (VAR) {
+                        const float4 vs = A.vstat[pix];
+                        z_[h] = vs.x;
+                        ma_[h] = A.dL_dmean ? A.dL_dmean[pix] * vs.z : 0.f;
+                        mb_[h] = A.dL_dvar ? A.dL_dvar[pix] * vs.z : 0.f;
+                        a_[h] = __fmaf_rn(-mb_[h], vs.y, a_[h]);  // the -b var part of every h
+                    }
                 }
+                mycnt = max(mycnt, cnt[i]);
             }
-            mycnt = max(mycnt, cnt[i]);
+            T[p] = f2_pack(t_[0], t_[1]);
+            gR[p] = f2_pack(r_[0], r_[1]);
+            gG[p] = f2_pack(g_[0], g_[1]);
+            gB[p] = f2_pack(b_[0], b_[1]);
+            gD[p] = f2_pack(d_[0], d_[1]);
+            gA[p] = f2_pack(a_[0], a_[1]);
+            nacc[p] = f2_bcast(0.f);
+            if (VAR) {
+                zmu[p] = f2_pack(z_[0], z_[1]);
+                ga[p] = f2_pack(ma_[0], ma_[1]);
+                gb[p] = f2_pack(mb_[0], mb_[1]);
+            }
         }
         uint32_t wmax = mycnt;
 #pragma unroll
@@ -339,61 +367,103 @@ __global__ void __launch_bounds__(TW * TH / PPT, 512 / (TW * TH / PPT)) k_raster
                 // ar = the unclamped alpha of a pixel the fragment reaches, else 0
                 float ar[PPT], t1_0 = 0.f, t2_0 = 0.f, dyi_0 = 0.f;
                 bool any = false;
+                {
+                    const f2 AY = f2_bcast(a.y), L12 = f2_bcast(b.y), L22 = f2_bcast(b.z);
+                    const f2 U1 = f2_bcast(u1), K2 = f2_bcast(a.w), NBW = f2_bcast(-b.w);
+                    f2 PY = PY0;
 #pragma unroll
-                for (int i = 0; i < PPT; ++i) {
-                    float t1, t2, dyi;
-                    const float e = frag_pixel(a, b, u1, (float)(py0 + i), t1, t2, dyi);
-                    if (i == 0) {
-                        t1_0 = t1;
-                        t2_0 = t2;
-                        dyi_0 = dyi;
+                    for (int p = 0; p < Q; ++p) {
+                        const f2 dy = f2_sub(PY, AY);  // dyi = py - V, exact as in the forward
+                        if (p + 1 < Q) PY = f2_add(PY, ONE);
+                        const f2 t1 = f2_fma(L12, dy, U1);
+                        const f2 t2 = f2_fma(L22, dy, K2);
+                        const f2 ne = f2_fma(t1, t1, f2_fma(t2, t2, NBW));  // -e
+                        if (p == 0) {
+                            t1_0 = f2_lo(t1);
+                            t2_0 = f2_lo(t2);
+                            dyi_0 = f2_lo(dy);
+                        }
+                        float n_[2];
+                        f2_unpack(ne, n_[0], n_[1]);
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int i = p + h * Q;
+                            const bool in = rel < cnt[i] && n_[h] <= nl2amin;
+                            ar[i] = in ? ex2_approx(-n_[h]) : 0.f;
+                            any |= in;
+                        }
                     }
-                    const bool in = rel < cnt[i] && e >= l2amin;
-                    ar[i] = in ? ex2_approx(e) : 0.f;
-                    any |= in;
                 }
                 if (!__any_sync(0xffffffffu, any)) continue;
                 // Every pixel runs the same instructions: a pixel this fragment
                 // does not reach takes alpha = 0, for which each update below is
-                // exactly the identity (T * 1, acc + 0 * h, sums + 0).
+                // exactly the identity (T * 1, acc + 0 * h, sums + 0; the
+                // reciprocal approximation returns 1 for 1 on sm_103, measured).
+                // The blended sums are carried negated (nwgt = -wgt), which
+                // saves the negations the packed instructions cannot fold.
                 const float4 c = sC[j];
-                float sR = 0.f, sG = 0.f, sB_ = 0.f, sZ = 0.f;  // sum wgt dL/dc
-                // sums of gpw = dL/dpw over the column's pixels i = 0..PPT-1,
-                // weighted by 1, i and i^2: the pixel offsets are dx (one per
-                // column) and dy_i = dy_0 + i, and t1, t2 are affine in i, so
-                // these three give every second-order moment the gradient needs
-                float S0 = 0.f, S1 = 0.f, S2 = 0.f;
+                const f2 CX = f2_bcast(c.x), CY = f2_bcast(c.y), CZ = f2_bcast(c.z), CW = f2_bcast(c.w);
+                f2 sR, sG, sB_, sZ;  // sums of -wgt dL/dc
+                // R_k = sum over pairs p of p^k gpw (k = 0, 1, 2), gpw = dL/dpw
+                f2 R0, R1, R2;
 #pragma unroll
-                for (int i = 0; i < PPT; ++i) {
-                    const float al = fminf(amax, ar[i]);
-                    const float r1m = ar[i] > 0.f ? rcp_approx(1.f - al) : 1.f;
-                    T[i] = T[i] * r1m;  // transmittance before this fragment
-                    const float wgt = al * T[i];
-                    float h = gR[i] * c.x + gG[i] * c.y + gB[i] * c.z + gD[i] * c.w + gA[i];
-                    float gz = gD[i];
+                for (int p = 0; p < Q; ++p) {
+                    const float a0 = ar[p], a1 = ar[p + Q];
+                    const f2 nal = f2_pack(fmaxf(-amax, -a0), fmaxf(-amax, -a1));  // -alpha
+                    // alpha of an unclamped pixel, else 0: a clamped alpha has no
+                    // gradient through pw
+                    const f2 ag = f2_pack(a0 <= amax ? a0 : 0.f, a1 <= amax ? a1 : 0.f);
+                    float o_[2];
+                    f2_unpack(f2_add(ONE, nal), o_[0], o_[1]);
+                    const f2 r1m = f2_pack(rcp_approx(o_[0]), rcp_approx(o_[1]));  // 1 / (1 - alpha)
+                    T[p] = f2_mul(T[p], r1m);  // transmittance before this fragment
+                    const f2 nwgt = f2_mul(nal, T[p]);
+                    f2 h = f2_fma(gR[p], CX, f2_fma(gG[p], CY, f2_fma(gB[p], CZ, f2_fma(gD[p], CW, gA[p]))));
+                    f2 gz = gD[p];
                     if (VAR) {
-                        const float dz = c.w - zmu[i];
-                        const float t = __fmaf_rn(gb[i], dz, ga[i]);  // a + b dz
-                        h = __fmaf_rn(t, dz, h);
-                        gz += __fmaf_rn(gb[i], dz, t);               // a + 2 b dz
+                        const f2 dz = f2_sub(CW, zmu[p]);
+                        const f2 t = f2_fma(gb[p], dz, ga[p]);  // a + b dz
+                        h = f2_fma(t, dz, h);
+                        gz = f2_add(gz, f2_fma(gb[p], dz, t));  // a + 2 b dz
                     }
-                    const float dLda = T[i] * h - acc[i] * r1m;
-                    acc[i] = __fmaf_rn(wgt, h, acc[i]);
-                    sR = __fmaf_rn(wgt, gR[i], sR);
-                    sG = __fmaf_rn(wgt, gG[i], sG);
-                    sB_ = __fmaf_rn(wgt, gB[i], sB_);
-                    sZ = __fmaf_rn(wgt, gz, sZ);
-                    // gpw with pw = -d^T Q d / 2 (natural log); a clamped alpha
-                    // has no gradient through pw
-                    const float gpw = ar[i] > 0.f && ar[i] <= amax ? dLda * al : 0.f;
-                    S0 += gpw;
-                    if (i > 0) {
-                        S1 = __fmaf_rn(gpw, (float)i, S1);
-                        S2 = __fmaf_rn(gpw, (float)(i * i), S2);
+                    // dL/dalpha = T h - acc / (1 - alpha)
+                    const f2 dLda = f2_fma(T[p], h, f2_mul(nacc[p], r1m));
+                    nacc[p] = f2_fma(nwgt, h, nacc[p]);
+                    const f2 gpw = f2_mul(dLda, ag);
+                    if (p == 0) {
+                        sR = f2_mul(nwgt, gR[p]);
+                        sG = f2_mul(nwgt, gG[p]);
+                        sB_ = f2_mul(nwgt, gB[p]);
+                        sZ = f2_mul(nwgt, gz);
+                        R0 = gpw;
+                    } else {
+                        sR = f2_fma(nwgt, gR[p], sR);
+                        sG = f2_fma(nwgt, gG[p], sG);
+                        sB_ = f2_fma(nwgt, gB[p], sB_);
+                        sZ = f2_fma(nwgt, gz, sZ);
+                        R0 = f2_add(R0, gpw);
+                    }
+                    if (p == 1) {
+                        R1 = gpw;
+                        R2 = gpw;
+                    } else if (p > 1) {
+                        R1 = f2_fma(gpw, f2_bcast((float)p), R1);
+                        R2 = f2_fma(gpw, f2_bcast((float)(p * p)), R2);
                     }
                 }
-                // per-lane raw moments; the per-Gaussian factors are applied
-                // once after the warp reduction (see below)
+                if (Q == 1) R1 = R2 = f2_bcast(0.f);
+                // S_k = sum over the column's pixels i of i^k gpw: pixel p + Q
+                // sits in the high half of pair p
+                float r0l, r0h, r1l, r1h, r2l, r2h;
+                f2_unpack(R0, r0l, r0h);
+                f2_unpack(R1, r1l, r1h);
+                f2_unpack(R2, r2l, r2h);
+                const float S0 = r0l + r0h;
+                const float S1 = __fmaf_rn((float)Q, r0h, r1l + r1h);
+                const float S2 = __fmaf_rn((float)(Q * Q), r0h, __fmaf_rn((float)(2 * Q), r1h, r2l + r2h));
+                // per-lane raw moments: the pixel offsets are dx (one per column)
+                // and dy_i = dy_0 + i, and t1, t2 are affine in i; the
+                // per-Gaussian factors are applied once after the warp reduction
                 const float2 hh = sH[j];
                 const float dx = dxi + hh.x, dy0 = dyi_0 + hh.y;
                 const float sy = __fmaf_rn(dy0, S0, S1);  // sum gpw dy
@@ -404,15 +474,16 @@ __global__ void __launch_bounds__(TW * TH / PPT, 512 / (TW * TH / PPT)) k_raster
                 g[G_QA] = dx * dx * S0;                     // sum gpw dx^2
                 g[G_QB] = dx * sy;                          // sum gpw dx dy
                 g[G_QC] = __fmaf_rn(dy0, sy, __fmaf_rn(dy0, S1, S2));  // sum gpw dy^2
-                g[G_R] = sR;
-                g[G_G] = sG;
-                g[G_B] = sB_;
-                g[G_Z] = sZ;
+                g[G_R] = f2_lo(sR) + f2_hi(sR);
+                g[G_G] = f2_lo(sG) + f2_hi(sG);
+                g[G_B] = f2_lo(sB_) + f2_hi(sB_);
+                g[G_Z] = f2_lo(sZ) + f2_hi(sZ);
                 const float tot = warp_reduce_scatter10(g, lane);
                 if (my_comp >= 0) {
                     // dL/dQ = -1/2 sum gpw d d^T; dpw/du = (Q d)_x = l11 t1 / s^2,
                     // dpw/dv = (l12 t1 + l22 t2) / s^2 with 1/s^2 = 2 ln 2: each lane
-                    // scales its sum by c0 + c11 l11 + c22 l22 (constants per lane)
+                    // scales its sum by c0 + c11 l11 + c22 l22 (constants per lane;
+                    // c0 = -1 undoes the negation of the colour and depth sums)
                     float *gp = A.g2d + (size_t)sP[j] * kGrad;
                     atomicAdd(gp + my_comp, tot * __fmaf_rn(sc11, b.x, __fmaf_rn(sc22, b.z, sc0)));
                     if (my_comp == G_U) atomicAdd(gp + G_V, kTwoLn2 * b.y * tot);
