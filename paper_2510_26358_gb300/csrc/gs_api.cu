@@ -133,7 +133,7 @@ const char *gs_last_error(void) { return g_last_error.c_str(); }
 
 void gs_workspace_destroy(gs_workspace *ws) {
     if (!ws) return;
-    void *ptrs[] = {ws->views, ws->subs, ws->sub_views, ws->rec, ws->pkey, ws->rect, ws->g2d,
+    void *ptrs[] = {ws->views, ws->subs, ws->sub_views, ws->rec, ws->pkey, ws->rect, ws->g2d, ws->gdir,
                     ws->vis_key, ws->vis_pair, ws->vis_key_alt, ws->vis_pair_alt, ws->ioff, ws->win_pair,
                     ws->inst_tile, ws->inst_val, ws->inst_tile_alt, ws->inst_val_alt, ws->ranges,
                     ws->tile_order, ws->tile_buckets,
@@ -229,7 +229,7 @@ gs_status gs_workspace_create(const gs_camera *cams, int32_t n_views, const int6
         si.ng = (int32_t)(submap_offsets[s + 1] - submap_offsets[s]);
         si.nviews = nviews[s];
         si.block0 = blocks;
-        si.nblocks = (si.ng + kProjThreads - 1) / kProjThreads;
+        si.nblocks = (si.ng + kProjBwdChunk - 1) / kProjBwdChunk;
         blocks += si.nblocks;
         ws->subs_h.push_back(si);
     }
@@ -263,6 +263,7 @@ gs_status gs_workspace_create(const gs_camera *cams, int32_t n_views, const int6
     GS_ALLOC(ws->pkey, P);
     GS_ALLOC(ws->rect, P);
     GS_ALLOC(ws->g2d, P * kGrad);
+    GS_ALLOC(ws->gdir, P);
     GS_ALLOC(ws->vis_key, P);
     GS_ALLOC(ws->vis_pair, P);
     GS_ALLOC(ws->vis_key_alt, P);

@@ -18,11 +18,18 @@
 // The image covariance is built from the rows of J W R S, its determinant
 // through the Lagrange identity (a sum of squares), so no step cancels.
 //
-// Backward (chain rule through the same steps): one thread per Gaussian
-// accumulates the parameter gradients of all its views in registers and
-// writes them once; the pose twist of each view is reduced over the block
-// (blocks never straddle a submap) and summed per view by a second kernel in
-// a fixed order.
+// Backward (chain rule through the same steps), over chunks of one submap:
+// each block first packs the chunk's Gaussians that some view sees (most are
+// outside every frustum), then
+//   k_sh_bwd       three lanes (one per colour channel) per Gaussian: SH
+//                  coefficient gradients, written once per Gaussian, and the
+//                  colour's gradient w.r.t. the view direction per pair;
+//   k_project_bwd  one lane per Gaussian walks its views and accumulates the
+//                  geometric gradients in registers, written once; the pose
+//                  twist of each view is reduced over the block and summed
+//                  per view by k_pose_reduce in a fixed order.
+// The forward stores a clamped colour channel as -0, so the backward reads
+// the clamp decision from the record instead of recomputing the colour.
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -228,6 +235,7 @@ struct ProjArgs {
     // backward
     const float *g2d;
     float *gm, *gls, *gq, *gom, *gsh, *pose_part, *dens_acc;
+    float4 *gdir;     // [pairs] dL/d(view direction) of the colour (x, y, z, unused)
     int32_t *dens_cnt;
 };
 
@@ -421,7 +429,9 @@ __global__ void __launch_bounds__(kProjThreads) k_project_fwd(ProjArgs A) {
 #pragma unroll
                     for (int ch = 0; ch < 3; ++ch) acc[ch] = __fmaf_rn(__ldg(shg + 3 * kk + ch), Y[kk], acc[ch]);
 #pragma unroll
-                for (int ch = 0; ch < 3; ++ch) rgb[ch] = fmaxf(acc[ch], 0.f);
+                // a clamped channel is stored as -0: it renders as 0, and its
+                // sign bit hands the clamp decision to the backward
+                for (int ch = 0; ch < 3; ++ch) rgb[ch] = acc[ch] < 0.f ? -0.f : acc[ch];
                 r0 = make_float4(Uf, Vf, hx, hy);
                 r1 = make_float4(l11, l12, l22, log2o);
                 r2 = make_float4(rgb[0], rgb[1], rgb[2], __double2float_rn(pz));
@@ -437,251 +447,376 @@ __global__ void __launch_bounds__(kProjThreads) k_project_fwd(ProjArgs A) {
     }
 }
 
-template <int DEG>
-__global__ void __launch_bounds__(kProjThreads, 2) k_project_bwd(ProjArgs A) {
-    extern __shared__ float red[];  // [views of the submap][warps][6]
-    const Consts &k = A.c;
-    // blocks are laid out per submap
-    int b = blockIdx.x;
-    int s = 0;
-    {
-        int lo = 0, hi = A.n_submaps - 1;
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (A.subs[mid].block0 <= b) lo = mid; else hi = mid - 1;
-        }
-        s = lo;
+// submap of projection-backward block b (blocks never straddle a submap)
+__device__ __forceinline__ int submap_of_block(const ProjArgs &A, int b) {
+    int lo = 0, hi = A.n_submaps - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (A.subs[mid].block0 <= b) lo = mid; else hi = mid - 1;
     }
-    const SubmapInfo sub = A.subs[s];
-    int64_t local = (int64_t)(b - sub.block0) * blockDim.x + threadIdx.x;
-    bool live = local < sub.ng;
-    int64_t g = sub.g0 + (live ? local : 0);
-    constexpr int K = (DEG + 1) * (DEG + 1);
+    return lo;
+}
 
-    // which of the submap's views see this Gaussian
-    uint32_t vis_mask = 0;
-    for (int kv = 0; kv < sub.nviews; ++kv) {
-        const ViewInfo vi = A.views[A.sub_views[s * A.maxv + kv]];
-        if (live && A.pkey[(int64_t)vi.pair_off + (g - vi.g0)] != kInvalidKey) vis_mask |= 1u << kv;
-    }
-    const bool any_vis = vis_mask != 0;
-
-    float mu[3] = {0, 0, 0}, ls[3] = {0, 0, 0}, q[4] = {1, 0, 0, 0}, om = 0.f;
-    if (any_vis) {
-        mu[0] = __ldg(A.means + 3 * g); mu[1] = __ldg(A.means + 3 * g + 1); mu[2] = __ldg(A.means + 3 * g + 2);
-        ls[0] = __ldg(A.log_scales + 3 * g); ls[1] = __ldg(A.log_scales + 3 * g + 1);
-        ls[2] = __ldg(A.log_scales + 3 * g + 2);
-        q[0] = __ldg(A.quats + 4 * g); q[1] = __ldg(A.quats + 4 * g + 1);
-        q[2] = __ldg(A.quats + 4 * g + 2); q[3] = __ldg(A.quats + 4 * g + 3);
-        om = __ldg(A.opac + g);
-    }
-    // SH coefficients are read from cache where needed and their gradients
-    // accumulated in place (this thread is the only writer of Gaussian g)
-    const float *shg = A.sh + g * (3 * K);
-    float *gsh = A.gsh + g * (3 * K);
-    float qh[4], R[9];
-    float qn = quat_rot(q, qh, R);
-    float S[3] = {expf(ls[0]), expf(ls[1]), expf(ls[2])};
-    float M[9];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) M[3 * i + j] = R[3 * i + j] * S[j];
-    float o = 1.f / (1.f + expf(-om));
-
-    float gmu[3] = {0, 0, 0}, gM[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, gom = 0.f;
-    float dacc = 0.f;
-    int dcnt = 0;
-
+// The Gaussians of chunk c0 of submap s that at least one of the submap's
+// views sees, in index order: s_item gets the chunk index, s_mask the views.
+// Most Gaussians lie outside every frustum; packing the visible ones keeps
+// the lanes of the backward busy.  All visibility loads are issued before
+// the one barrier; positions come from per-warp ballots.  Returns the count
+// (the same in every thread); the whole block must call it.  s_cnt holds
+// kProjBwdChunk / 32 counters.
+__device__ int chunk_visible(const ProjArgs &A, int s, const SubmapInfo &sub, int64_t c0, int *s_item,
+                             unsigned long long *s_mask, uint32_t *s_cnt) {
+    constexpr int F = kProjBwdChunk / kProjBwdThreads, NW = kProjBwdThreads / 32;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned long long m[F];
+#pragma unroll
+    for (int f = 0; f < F; ++f) m[f] = 0ull;
     for (int kv = 0; kv < sub.nviews; ++kv) {
-        int v = A.sub_views[s * A.maxv + kv];
-        const ViewInfo vi = A.views[v];
-        int64_t pair = (int64_t)vi.pair_off + (g - vi.g0);
-        float gpose[6] = {0, 0, 0, 0, 0, 0};
-        bool vis = (vis_mask >> kv) & 1u;
-        if (vis) {
-            const float *gg = A.g2d + pair * kGrad;
-            float gu = gg[G_U], gv = gg[G_V], gqa = gg[G_QA], gqb = gg[G_QB], gqc = gg[G_QC];
-            float glno = gg[G_LNO], gz = gg[G_Z];
-            float grgb[3] = {gg[G_R], gg[G_G], gg[G_B]};
-            Cam cam = load_cam(A.cams, v);
-            PairGeom G;
-            pair_geom(cam, vi.W, vi.H, k, view_coord_ff(cam.T, mu[0], mu[1], mu[2]).x,
-                      view_coord_ff(cam.T + 4, mu[0], mu[1], mu[2]).x, view_coord_ff(cam.T + 8, mu[0], mu[1], mu[2]).x,
-                      M, G);
-            const float p[3] = {G.pxf, G.pyf, G.pzf};
-            const float *T = cam.T;
-            float gp[3] = {0.f, 0.f, gz};
-            // pixel mean
-            float iz = 1.f / p[2], iz2 = iz * iz;
-            gp[0] += gu * cam.fx * iz;
-            gp[1] += gv * cam.fy * iz;
-            gp[2] -= (gu * cam.fx * p[0] + gv * cam.fy * p[1]) * iz2;
-            // colour
-            float w[3], wn;
-            view_dir(cam, mu, w, wn);
-            float iw = 1.f / wn;
-            float d[3] = {w[0] * iw, w[1] * iw, w[2] * iw};
-            float Y[16], dY[16][3];
-            sh_basis<DEG>(d[0], d[1], d[2], Y);
-            sh_basis_grad<DEG>(d[0], d[1], d[2], dY);
-            float gdir[3] = {0, 0, 0};
-            // colour of the forward, same FMA order, to take the same clamp decision
-            float acc[3] = {0.5f, 0.5f, 0.5f};
+        const ViewInfo &vi = A.views[A.sub_views[s * A.maxv + kv]];
+        const uint32_t *pk = A.pkey + (int64_t)vi.pair_off + (sub.g0 + c0 - vi.g0);
 #pragma unroll
-            for (int kk = 0; kk < K; ++kk)
-#pragma unroll
-                for (int ch = 0; ch < 3; ++ch) acc[ch] = __fmaf_rn(__ldg(shg + 3 * kk + ch), Y[kk], acc[ch]);
-            float gcol[3];
-#pragma unroll
-            for (int ch = 0; ch < 3; ++ch) gcol[ch] = acc[ch] < 0.f ? 0.f : grgb[ch];  // clamped: no gradient
-#pragma unroll
-            for (int kk = 0; kk < K; ++kk) {
-                float t = 0.f;
-#pragma unroll
-                for (int ch = 0; ch < 3; ++ch) {
-                    gsh[3 * kk + ch] += gcol[ch] * Y[kk];
-                    t = __fmaf_rn(gcol[ch], __ldg(shg + 3 * kk + ch), t);
-                }
-                gdir[0] += t * dY[kk][0];
-                gdir[1] += t * dY[kk][1];
-                gdir[2] += t * dY[kk][2];
-            }
-            float dd = d[0] * gdir[0] + d[1] * gdir[1] + d[2] * gdir[2];
-            float gw[3] = {(gdir[0] - d[0] * dd) * iw, (gdir[1] - d[1] * dd) * iw, (gdir[2] - d[2] * dd) * iw};
-            // dL/dSigma' = -Q G Q with Q = Sigma'^-1, G = [[gqa, gqb/2], [gqb/2, gqc]]
-            float idet = 1.f / G.det;
-            float Qa = G.c * idet, Qb = -G.b * idet, Qc = G.a * idet;
-            float hb = 0.5f * gqb;
-            float QG00 = Qa * gqa + Qb * hb, QG01 = Qa * hb + Qb * gqc;
-            float QG10 = Qb * gqa + Qc * hb, QG11 = Qb * hb + Qc * gqc;
-            float Ma = -(QG00 * Qa + QG01 * Qb);
-            float Mb = -(QG00 * Qb + QG01 * Qc);
-            float Mc = -(QG10 * Qb + QG11 * Qc);
-            // Sigma' = T2 T2^T + dil I with T2 = J W M (rows r0, r1):
-            // dL/dT2 = 2 Msym T2 (Msym = [[Ma, Mb], [Mb, Mc]])
-            float gr0[3], gr1[3];
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                gr0[j] = 2.f * (Ma * G.r0[j] + Mb * G.r1[j]);
-                gr1[j] = 2.f * (Mb * G.r0[j] + Mc * G.r1[j]);
-            }
-            // T2 = J WM: rows r0 = J00 WM0 + J02 WM2, r1 = J11 WM1 + J12 WM2
-            float gJ00 = gr0[0] * G.WM[0] + gr0[1] * G.WM[1] + gr0[2] * G.WM[2];
-            float gJ02 = gr0[0] * G.WM[6] + gr0[1] * G.WM[7] + gr0[2] * G.WM[8];
-            float gJ11 = gr1[0] * G.WM[3] + gr1[1] * G.WM[4] + gr1[2] * G.WM[5];
-            float gJ12 = gr1[0] * G.WM[6] + gr1[1] * G.WM[7] + gr1[2] * G.WM[8];
-            float gWM[9];
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                gWM[j] = G.J00 * gr0[j];
-                gWM[3 + j] = G.J11 * gr1[j];
-                gWM[6 + j] = G.J02 * gr0[j] + G.J12 * gr1[j];
-            }
-            // J as a function of p (clamped tangent: J02 = -fx c / z)
-            gp[2] += -(gJ00 * cam.fx + gJ11 * cam.fy) * iz2;
-            if (!G.clx) {
-                gp[0] += -gJ02 * cam.fx * iz2;
-                gp[2] += 2.f * gJ02 * cam.fx * p[0] * iz2 * iz;
-            } else {
-                gp[2] += gJ02 * cam.fx * (G.txc * iz) * iz2;
-            }
-            if (!G.cly) {
-                gp[1] += -gJ12 * cam.fy * iz2;
-                gp[2] += 2.f * gJ12 * cam.fy * p[1] * iz2 * iz;
-            } else {
-                gp[2] += gJ12 * cam.fy * (G.tyc * iz) * iz2;
-            }
-            // WM = Rb M: dL/dM += Rb^T gWM ; pose rotation: Rb -> (I + [phi]x) Rb
-#pragma unroll
-            for (int i = 0; i < 3; ++i)
-#pragma unroll
-                for (int j = 0; j < 3; ++j)
-                    gM[3 * i + j] += T[i] * gWM[j] + T[4 + i] * gWM[3 + j] + T[8 + i] * gWM[6 + j];
-            // dL/dphi from WM: delta WM = [phi]x WM -> dL/dphi = sum_j WM_j x gWM_j (columns)
-            float A_[9];  // A = gWM WM^T
-#pragma unroll
-            for (int i = 0; i < 3; ++i)
-#pragma unroll
-                for (int j = 0; j < 3; ++j)
-                    A_[3 * i + j] = gWM[3 * i] * G.WM[3 * j] + gWM[3 * i + 1] * G.WM[3 * j + 1] +
-                                    gWM[3 * i + 2] * G.WM[3 * j + 2];
-            // tr(A^T [phi]x WM...) : dL = sum_ij gWM_ij ([phi]x WM)_ij = tr(gWM^T [phi]x WM)
-            //   = tr([phi]x WM gWM^T) = tr([phi]x A^T); axial part
-            gpose[3] += A_[7] - A_[5];
-            gpose[4] += A_[2] - A_[6];
-            gpose[5] += A_[3] - A_[1];
-            // mean and pose translation: p = Rb mu + t
-            gmu[0] += T[0] * gp[0] + T[4] * gp[1] + T[8] * gp[2] + gw[0];
-            gmu[1] += T[1] * gp[0] + T[5] * gp[1] + T[9] * gp[2] + gw[1];
-            gmu[2] += T[2] * gp[0] + T[6] * gp[1] + T[10] * gp[2] + gw[2];
-            float gwc[3] = {T[0] * gw[0] + T[1] * gw[1] + T[2] * gw[2],
-                            T[4] * gw[0] + T[5] * gw[1] + T[6] * gw[2],
-                            T[8] * gw[0] + T[9] * gw[1] + T[10] * gw[2]};
-            gpose[0] += gp[0] + gwc[0];
-            gpose[1] += gp[1] + gwc[1];
-            gpose[2] += gp[2] + gwc[2];
-            gpose[3] += p[1] * gp[2] - p[2] * gp[1];
-            gpose[4] += p[2] * gp[0] - p[0] * gp[2];
-            gpose[5] += p[0] * gp[1] - p[1] * gp[0];
-            // opacity: d ln o / d omega = 1 - o
-            gom += glno * (1.f - o);
-            dacc += sqrtf(gu * gu + gv * gv);
-            dcnt += 1;
+        for (int f = 0; f < F; ++f) {
+            const int loc = f * kProjBwdThreads + threadIdx.x;
+            if (c0 + loc < sub.ng && pk[loc] != kInvalidKey) m[f] |= 1ull << kv;
         }
-        // pose twist of this view: warp sums into shared memory, one slot per
-        // (view, warp); the block sums them after the loop
-        if (__any_sync(0xffffffffu, vis)) {
+    }
+    uint32_t bal[F];
 #pragma unroll
-            for (int i = 0; i < 6; ++i)
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) gpose[i] += __shfl_xor_sync(0xffffffffu, gpose[i], o);
-        }
-        if (lane == 0)
-#pragma unroll
-            for (int i = 0; i < 6; ++i) red[(kv * (kProjThreads / 32) + wid) * 6 + i] = gpose[i];
+    for (int f = 0; f < F; ++f) {
+        bal[f] = __ballot_sync(0xffffffffu, m[f] != 0ull);
+        if (lane == 0) s_cnt[f * NW + wid] = __popc(bal[f]);
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < sub.nviews * 6; idx += blockDim.x) {
-        int kv = idx / 6, i = idx % 6;
-        float t = 0.f;
-        for (int w = 0; w < kProjThreads / 32; ++w) t += red[(kv * (kProjThreads / 32) + w) * 6 + i];
-        A.pose_part[((int64_t)b * A.maxv + kv) * 6 + i] = t;
-    }
-    if (!any_vis) return;
-    // M = R diag(S): dL/dS_k = sum_i gM_ik R_ik, dL/dls_k = dL/dS_k S_k; dL/dR_ik = gM_ik S_k
-    float gR[9];
-    float gls[3];
+    // exclusive prefix in (f, warp) order, which is chunk index order
+    uint32_t run = 0, base[F];
 #pragma unroll
-    for (int kk = 0; kk < 3; ++kk) {
-        gls[kk] = (gM[kk] * R[kk] + gM[3 + kk] * R[3 + kk] + gM[6 + kk] * R[6 + kk]) * S[kk];
-        gR[kk] = gM[kk] * S[kk];
-        gR[3 + kk] = gM[3 + kk] * S[kk];
-        gR[6 + kk] = gM[6 + kk] * S[kk];
+    for (int f = 0; f < F; ++f) {
+        for (int w = 0; w < NW; ++w) {
+            if (w == wid) base[f] = run;
+            run += s_cnt[f * NW + w];
+        }
     }
-    // rotation of the normalised quaternion, then the normalisation
-    float w = qh[0], x = qh[1], y = qh[2], z = qh[3];
-    float gw_ = 2.f * (-z * gR[1] + y * gR[2] + z * gR[3] - x * gR[5] - y * gR[6] + x * gR[7]);
-    float gx_ = 2.f * (y * gR[1] + z * gR[2] + y * gR[3] - 2.f * x * gR[4] - w * gR[5] + z * gR[6] +
-                       w * gR[7] - 2.f * x * gR[8]);
-    float gy_ = 2.f * (-2.f * y * gR[0] + x * gR[1] + w * gR[2] + x * gR[3] + z * gR[5] - w * gR[6] +
-                       z * gR[7] - 2.f * y * gR[8]);
-    float gz_ = 2.f * (-2.f * z * gR[0] - w * gR[1] + x * gR[2] + w * gR[3] - 2.f * z * gR[4] +
-                       y * gR[5] + x * gR[6] + y * gR[7]);
-    float dq = w * gw_ + x * gx_ + y * gy_ + z * gz_;
-    float iq = qn > 0.f ? 1.f / qn : 0.f;
-    float gq[4] = {(gw_ - w * dq) * iq, (gx_ - x * dq) * iq, (gy_ - y * dq) * iq, (gz_ - z * dq) * iq};
+    const uint32_t below = (1u << lane) - 1u;
+#pragma unroll
+    for (int f = 0; f < F; ++f)
+        if (m[f]) {
+            const uint32_t pos = base[f] + __popc(bal[f] & below);
+            s_item[pos] = f * kProjBwdThreads + threadIdx.x;
+            s_mask[pos] = m[f];
+        }
+    __syncthreads();
+    return (int)run;
+}
+
+// Adjoint of the SH colour, c_ch = max(0, 1/2 + sum_k sh_(k, ch) Y_k(d)) with
+// d the unit direction from the camera centre to the mean: dL/dsh_(k, ch) =
+// gc_ch Y_k and dL/dd = sum_(k, ch) gc_ch sh_(k, ch) grad Y_k, where gc is the
+// pixel-space colour gradient of the pair, zero on a clamped channel.  Three
+// lanes (one per channel) work one visible Gaussian: they read its SH row
+// together (consecutive floats), keep their channel's coefficients and
+// gradient sums in registers across the Gaussian's views, and write the row
+// once; dL/dd of each pair goes to gdir for the geometric adjoint.
+template <int DEG>
+__global__ void __launch_bounds__(kProjBwdThreads) k_sh_bwd(ProjArgs A) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    constexpr int NWARP = kProjBwdThreads / 32, GPW = 10;  // ten groups of three lanes a warp
+    __shared__ int s_item[kProjBwdChunk];
+    __shared__ unsigned long long s_mask[kProjBwdChunk];
+    __shared__ uint32_t s_scan[kProjBwdChunk / 32];
+    const int b = blockIdx.x, s = submap_of_block(A, b);
+    const SubmapInfo sub = A.subs[s];
+    const int64_t c0 = (int64_t)(b - sub.block0) * kProjBwdChunk;
+    const int n_items = chunk_visible(A, s, sub, c0, s_item, s_mask, s_scan);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int grp = lane / 3, ch = lane - 3 * grp, lead = 3 * grp;  // lanes 30, 31 idle
+    for (int base = wid * GPW; base < n_items; base += NWARP * GPW) {
+        const int it = base + grp;
+        const bool live = grp < GPW && it < n_items;
+        unsigned long long mask = live ? s_mask[it] : 0ull;
+        const int64_t g = sub.g0 + c0 + (live ? s_item[it] : 0);
+        float mu[3] = {0.f, 0.f, 0.f}, shc[K], gacc[K];
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) {
+            shc[kk] = live ? __ldg(A.sh + g * (3 * K) + 3 * kk + ch) : 0.f;
+            gacc[kk] = 0.f;
+        }
+        if (live) {
+            mu[0] = __ldg(A.means + 3 * g);
+            mu[1] = __ldg(A.means + 3 * g + 1);
+            mu[2] = __ldg(A.means + 3 * g + 2);
+        }
+        for (;;) {
+            const bool act = mask != 0ull;
+            if (!__any_sync(0xffffffffu, act)) break;
+            float gd[3] = {0.f, 0.f, 0.f};
+            int64_t pair = 0;
+            if (act) {
+                const int kv = __ffsll((long long)mask) - 1;
+                mask &= mask - 1ull;
+                const int v = A.sub_views[s * A.maxv + kv];
+                const ViewInfo vi = A.views[v];
+                pair = (int64_t)vi.pair_off + (g - vi.g0);
+                const Cam cam = load_cam(A.cams, v);
+                float w[3], wn;
+                view_dir(cam, mu, w, wn);
+                const float iw = 1.f / wn;
+                const float d[3] = {w[0] * iw, w[1] * iw, w[2] * iw};
+                // the forward marked a clamped channel by the sign of its colour
+                const float cf = reinterpret_cast<const float *>(A.rec + 3 * pair + 2)[ch];
+                const float gc = signbit(cf) ? 0.f : A.g2d[pair * kGrad + G_R + ch];
+                float Y[16], dY[16][3];
+                sh_basis<DEG>(d[0], d[1], d[2], Y);
+                sh_basis_grad<DEG>(d[0], d[1], d[2], dY);
+#pragma unroll
+                for (int kk = 0; kk < K; ++kk) {
+                    gacc[kk] = __fmaf_rn(gc, Y[kk], gacc[kk]);
+                    const float t = gc * shc[kk];
+                    gd[0] = __fmaf_rn(t, dY[kk][0], gd[0]);
+                    gd[1] = __fmaf_rn(t, dY[kk][1], gd[1]);
+                    gd[2] = __fmaf_rn(t, dY[kk][2], gd[2]);
+                }
+            }
+            // sum over the three channels of the group, in channel order
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const float a1 = __shfl_sync(0xffffffffu, gd[i], min(lead + 1, 31));
+                const float a2 = __shfl_sync(0xffffffffu, gd[i], min(lead + 2, 31));
+                gd[i] = (gd[i] + a1) + a2;
+            }
+            if (act && ch == 0) A.gdir[pair] = make_float4(gd[0], gd[1], gd[2], 0.f);
+        }
+        if (live) {
+            float *gsh = A.gsh + g * (3 * K) + ch;
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) gsh[3 * kk] += gacc[kk];
+        }
+    }
+}
+
+template <int DEG>
+__global__ void __launch_bounds__(kProjBwdThreads, 512 / kProjBwdThreads) k_project_bwd(ProjArgs A) {
+    constexpr int NWARP = kProjBwdThreads / 32;
+    extern __shared__ float red[];  // [views of the submap][warps][6] pose twist sums
+    __shared__ int s_item[kProjBwdChunk];                  // chunk index of a visible Gaussian
+    __shared__ unsigned long long s_mask[kProjBwdChunk];  // the views that see it
+    __shared__ uint32_t s_scan[kProjBwdChunk / 32];
+    const Consts &k = A.c;
+    // blocks are laid out per submap, kProjBwdChunk Gaussians each
+    const int b = blockIdx.x, s = submap_of_block(A, b);
+    const SubmapInfo sub = A.subs[s];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int64_t c0 = (int64_t)(b - sub.block0) * kProjBwdChunk;
+    for (int i = tid; i < sub.nviews * NWARP * 6; i += kProjBwdThreads) red[i] = 0.f;
+
+    // 1. the chunk's Gaussians that some view sees
+    const int n_items = chunk_visible(A, s, sub, c0, s_item, s_mask, s_scan);
+
+    // 2. each warp takes 32 of them at a time; a lane walks the views of its
+    //    Gaussian in order and is the only writer of its gradients
+    for (int base = wid * 32; base < n_items; base += kProjBwdThreads) {
+        const int it = base + lane;
+        const bool live = it < n_items;
+        unsigned long long mask = live ? s_mask[it] : 0ull;
+        const int64_t g = sub.g0 + c0 + (live ? s_item[it] : 0);
+        float mu[3] = {0, 0, 0}, ls[3] = {0, 0, 0}, q[4] = {1, 0, 0, 0}, om = 0.f;
+        if (live) {
+            mu[0] = __ldg(A.means + 3 * g); mu[1] = __ldg(A.means + 3 * g + 1); mu[2] = __ldg(A.means + 3 * g + 2);
+            ls[0] = __ldg(A.log_scales + 3 * g); ls[1] = __ldg(A.log_scales + 3 * g + 1);
+            ls[2] = __ldg(A.log_scales + 3 * g + 2);
+            q[0] = __ldg(A.quats + 4 * g); q[1] = __ldg(A.quats + 4 * g + 1);
+            q[2] = __ldg(A.quats + 4 * g + 2); q[3] = __ldg(A.quats + 4 * g + 3);
+            om = __ldg(A.opac + g);
+        }
+        float qh[4], R[9];
+        float qn = quat_rot(q, qh, R);
+        float S[3] = {expf(ls[0]), expf(ls[1]), expf(ls[2])};
+        float M[9];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) M[3 * i + j] = R[3 * i + j] * S[j];
+        float o = 1.f / (1.f + expf(-om));
+
+        float gmu[3] = {0, 0, 0}, gM[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, gom = 0.f;
+        float dacc = 0.f;
+        int dcnt = 0;
+        for (;;) {
+            const bool act = mask != 0ull;
+            if (!__any_sync(0xffffffffu, act)) break;
+            const int kv = act ? __ffsll((long long)mask) - 1 : -1;
+            if (act) mask &= mask - 1ull;
+            float gpose[6] = {0, 0, 0, 0, 0, 0};
+            if (act) {
+                int v = A.sub_views[s * A.maxv + kv];
+                const ViewInfo vi = A.views[v];
+                int64_t pair = (int64_t)vi.pair_off + (g - vi.g0);
+                    const float *gg = A.g2d + pair * kGrad;
+                    float gu = gg[G_U], gv = gg[G_V], gqa = gg[G_QA], gqb = gg[G_QB], gqc = gg[G_QC];
+                    float glno = gg[G_LNO], gz = gg[G_Z];
+                    Cam cam = load_cam(A.cams, v);
+                    PairGeom G;
+                    pair_geom(cam, vi.W, vi.H, k, view_coord_ff(cam.T, mu[0], mu[1], mu[2]).x,
+                              view_coord_ff(cam.T + 4, mu[0], mu[1], mu[2]).x, view_coord_ff(cam.T + 8, mu[0], mu[1], mu[2]).x,
+                              M, G);
+                    const float p[3] = {G.pxf, G.pyf, G.pzf};
+                    const float *T = cam.T;
+                    float gp[3] = {0.f, 0.f, gz};
+                    // pixel mean
+                    float iz = 1.f / p[2], iz2 = iz * iz;
+                    gp[0] += gu * cam.fx * iz;
+                    gp[1] += gv * cam.fy * iz;
+                    gp[2] -= (gu * cam.fx * p[0] + gv * cam.fy * p[1]) * iz2;
+                    // colour
+                    float w[3], wn;
+                    view_dir(cam, mu, w, wn);
+                    float iw = 1.f / wn;
+                    float d[3] = {w[0] * iw, w[1] * iw, w[2] * iw};
+                    // view-direction gradient of the colour, from the SH adjoint
+                    const float4 gd4 = A.gdir[pair];
+                    const float gdir[3] = {gd4.x, gd4.y, gd4.z};
+                    float dd = d[0] * gdir[0] + d[1] * gdir[1] + d[2] * gdir[2];
+                    float gw[3] = {(gdir[0] - d[0] * dd) * iw, (gdir[1] - d[1] * dd) * iw, (gdir[2] - d[2] * dd) * iw};
+                    // dL/dSigma' = -Q G Q with Q = Sigma'^-1, G = [[gqa, gqb/2], [gqb/2, gqc]]
+                    float idet = 1.f / G.det;
+                    float Qa = G.c * idet, Qb = -G.b * idet, Qc = G.a * idet;
+                    float hb = 0.5f * gqb;
+                    float QG00 = Qa * gqa + Qb * hb, QG01 = Qa * hb + Qb * gqc;
+                    float QG10 = Qb * gqa + Qc * hb, QG11 = Qb * hb + Qc * gqc;
+                    float Ma = -(QG00 * Qa + QG01 * Qb);
+                    float Mb = -(QG00 * Qb + QG01 * Qc);
+                    float Mc = -(QG10 * Qb + QG11 * Qc);
+                    // Sigma' = T2 T2^T + dil I with T2 = J W M (rows r0, r1):
+                    // dL/dT2 = 2 Msym T2 (Msym = [[Ma, Mb], [Mb, Mc]])
+                    float gr0[3], gr1[3];
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        gr0[j] = 2.f * (Ma * G.r0[j] + Mb * G.r1[j]);
+                        gr1[j] = 2.f * (Mb * G.r0[j] + Mc * G.r1[j]);
+                    }
+                    // T2 = J WM: rows r0 = J00 WM0 + J02 WM2, r1 = J11 WM1 + J12 WM2
+                    float gJ00 = gr0[0] * G.WM[0] + gr0[1] * G.WM[1] + gr0[2] * G.WM[2];
+                    float gJ02 = gr0[0] * G.WM[6] + gr0[1] * G.WM[7] + gr0[2] * G.WM[8];
+                    float gJ11 = gr1[0] * G.WM[3] + gr1[1] * G.WM[4] + gr1[2] * G.WM[5];
+                    float gJ12 = gr1[0] * G.WM[6] + gr1[1] * G.WM[7] + gr1[2] * G.WM[8];
+                    float gWM[9];
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        gWM[j] = G.J00 * gr0[j];
+                        gWM[3 + j] = G.J11 * gr1[j];
+                        gWM[6 + j] = G.J02 * gr0[j] + G.J12 * gr1[j];
+                    }
+                    // J as a function of p (clamped tangent: J02 = -fx c / z)
+                    gp[2] += -(gJ00 * cam.fx + gJ11 * cam.fy) * iz2;
+                    if (!G.clx) {
+                        gp[0] += -gJ02 * cam.fx * iz2;
+                        gp[2] += 2.f * gJ02 * cam.fx * p[0] * iz2 * iz;
+                    } else {
+                        gp[2] += gJ02 * cam.fx * (G.txc * iz) * iz2;
+                    }
+                    if (!G.cly) {
+                        gp[1] += -gJ12 * cam.fy * iz2;
+                        gp[2] += 2.f * gJ12 * cam.fy * p[1] * iz2 * iz;
+                    } else {
+                        gp[2] += gJ12 * cam.fy * (G.tyc * iz) * iz2;
+                    }
+                    // WM = Rb M: dL/dM += Rb^T gWM ; pose rotation: Rb -> (I + [phi]x) Rb
+#pragma unroll
+                    for (int i = 0; i < 3; ++i)
+#pragma unroll
+                        for (int j = 0; j < 3; ++j)
+                            gM[3 * i + j] += T[i] * gWM[j] + T[4 + i] * gWM[3 + j] + T[8 + i] * gWM[6 + j];
+                    // dL/dphi from WM: delta WM = [phi]x WM -> dL/dphi = sum_j WM_j x gWM_j (columns)
+                    float A_[9];  // A = gWM WM^T
+#pragma unroll
+                    for (int i = 0; i < 3; ++i)
+#pragma unroll
+                        for (int j = 0; j < 3; ++j)
+                            A_[3 * i + j] = gWM[3 * i] * G.WM[3 * j] + gWM[3 * i + 1] * G.WM[3 * j + 1] +
+                                            gWM[3 * i + 2] * G.WM[3 * j + 2];
+                    // tr(A^T [phi]x WM...) : dL = sum_ij gWM_ij ([phi]x WM)_ij = tr(gWM^T [phi]x WM)
+                    //   = tr([phi]x WM gWM^T) = tr([phi]x A^T); axial part
+                    gpose[3] += A_[7] - A_[5];
+                    gpose[4] += A_[2] - A_[6];
+                    gpose[5] += A_[3] - A_[1];
+                    // mean and pose translation: p = Rb mu + t
+                    gmu[0] += T[0] * gp[0] + T[4] * gp[1] + T[8] * gp[2] + gw[0];
+                    gmu[1] += T[1] * gp[0] + T[5] * gp[1] + T[9] * gp[2] + gw[1];
+                    gmu[2] += T[2] * gp[0] + T[6] * gp[1] + T[10] * gp[2] + gw[2];
+                    float gwc[3] = {T[0] * gw[0] + T[1] * gw[1] + T[2] * gw[2],
+                                    T[4] * gw[0] + T[5] * gw[1] + T[6] * gw[2],
+                                    T[8] * gw[0] + T[9] * gw[1] + T[10] * gw[2]};
+                    gpose[0] += gp[0] + gwc[0];
+                    gpose[1] += gp[1] + gwc[1];
+                    gpose[2] += gp[2] + gwc[2];
+                    gpose[3] += p[1] * gp[2] - p[2] * gp[1];
+                    gpose[4] += p[2] * gp[0] - p[0] * gp[2];
+                    gpose[5] += p[0] * gp[1] - p[1] * gp[0];
+                    // opacity: d ln o / d omega = 1 - o
+                    gom += glno * (1.f - o);
+                    dacc += sqrtf(gu * gu + gv * gv);
+                    dcnt += 1;
+            }
+            // pose twist: one warp sum per view that some lane worked in this
+            // step, added to the warp's slot of that view (fixed order)
+            unsigned pend = __ballot_sync(0xffffffffu, act);
+            while (pend) {
+                const int kv0 = __shfl_sync(0xffffffffu, kv, __ffs(pend) - 1);
+                const bool mine = kv == kv0;
+                pend &= ~__ballot_sync(0xffffffffu, mine);
+                float t[6];
+#pragma unroll
+                for (int i = 0; i < 6; ++i) {
+                    t[i] = mine ? gpose[i] : 0.f;
+#pragma unroll
+                    for (int o2 = 16; o2 > 0; o2 >>= 1) t[i] += __shfl_xor_sync(0xffffffffu, t[i], o2);
+                }
+                if (lane == 0)
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) red[(kv0 * NWARP + wid) * 6 + i] += t[i];
+            }
+        }
+        if (live) {
+            // M = R diag(S): dL/dS_k = sum_i gM_ik R_ik, dL/dls_k = dL/dS_k S_k; dL/dR_ik = gM_ik S_k
+            float gR[9];
+            float gls[3];
+#pragma unroll
+            for (int kk = 0; kk < 3; ++kk) {
+                gls[kk] = (gM[kk] * R[kk] + gM[3 + kk] * R[3 + kk] + gM[6 + kk] * R[6 + kk]) * S[kk];
+                gR[kk] = gM[kk] * S[kk];
+                gR[3 + kk] = gM[3 + kk] * S[kk];
+                gR[6 + kk] = gM[6 + kk] * S[kk];
+            }
+            // rotation of the normalised quaternion, then the normalisation
+            float w = qh[0], x = qh[1], y = qh[2], z = qh[3];
+            float gw_ = 2.f * (-z * gR[1] + y * gR[2] + z * gR[3] - x * gR[5] - y * gR[6] + x * gR[7]);
+            float gx_ = 2.f * (y * gR[1] + z * gR[2] + y * gR[3] - 2.f * x * gR[4] - w * gR[5] + z * gR[6] +
+                               w * gR[7] - 2.f * x * gR[8]);
+            float gy_ = 2.f * (-2.f * y * gR[0] + x * gR[1] + w * gR[2] + x * gR[3] + z * gR[5] - w * gR[6] +
+                               z * gR[7] - 2.f * y * gR[8]);
+            float gz_ = 2.f * (-2.f * z * gR[0] - w * gR[1] + x * gR[2] + w * gR[3] - 2.f * z * gR[4] +
+                               y * gR[5] + x * gR[6] + y * gR[7]);
+            float dq = w * gw_ + x * gx_ + y * gy_ + z * gz_;
+            float iq = qn > 0.f ? 1.f / qn : 0.f;
+            float gq[4] = {(gw_ - w * dq) * iq, (gx_ - x * dq) * iq, (gy_ - y * dq) * iq, (gz_ - z * dq) * iq};
 
 #pragma unroll
-    for (int i = 0; i < 3; ++i) A.gm[3 * g + i] += gmu[i];
+            for (int i = 0; i < 3; ++i) A.gm[3 * g + i] += gmu[i];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) A.gls[3 * g + i] += gls[i];
+            for (int i = 0; i < 3; ++i) A.gls[3 * g + i] += gls[i];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) A.gq[4 * g + i] += gq[i];
-    A.gom[g] += gom;
-    if (A.dens_acc) A.dens_acc[g] += dacc;
-    if (A.dens_cnt) A.dens_cnt[g] += dcnt;
+            for (int i = 0; i < 4; ++i) A.gq[4 * g + i] += gq[i];
+            A.gom[g] += gom;
+            if (A.dens_acc) A.dens_acc[g] += dacc;
+            if (A.dens_cnt) A.dens_cnt[g] += dcnt;
+        }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < sub.nviews * 6; idx += kProjBwdThreads) {
+        int kv = idx / 6, i = idx % 6;
+        float t = 0.f;
+        for (int w = 0; w < NWARP; ++w) t += red[(kv * NWARP + w) * 6 + i];
+        A.pose_part[((int64_t)b * A.maxv + kv) * 6 + i] = t;
+    }
 }
 
 // pose[v][i] += sum over the blocks of v's submap of the partials of v's slot;
@@ -756,14 +891,21 @@ gs_status launch_project_bwd(gs_workspace *ws, const gs_gaussians *g, const gs_c
     A.pose_part = ws->pose_part;
     A.dens_acc = out->densify_acc;
     A.dens_cnt = out->densify_cnt;
+    A.gdir = ws->gdir;
     StageTimer timer(ws, GS_STAGE_PROJECT_BWD, s);
     if (ws->proj_blocks > 0) {
-        size_t smem = sizeof(float) * ws->max_views_per_submap * (kProjThreads / 32) * 6;
+        size_t smem = sizeof(float) * ws->max_views_per_submap * (kProjBwdThreads / 32) * 6;
         switch (ws->sh_degree) {
-            case 0: ++ws->kernel_launches; k_project_bwd<0><<<ws->proj_blocks, kProjThreads, smem, s>>>(A); break;
-            case 1: ++ws->kernel_launches; k_project_bwd<1><<<ws->proj_blocks, kProjThreads, smem, s>>>(A); break;
-            case 2: ++ws->kernel_launches; k_project_bwd<2><<<ws->proj_blocks, kProjThreads, smem, s>>>(A); break;
-            default: ++ws->kernel_launches; k_project_bwd<3><<<ws->proj_blocks, kProjThreads, smem, s>>>(A); break;
+            case 0: ++ws->kernel_launches; k_sh_bwd<0><<<ws->proj_blocks, kProjBwdThreads, 0, s>>>(A); break;
+            case 1: ++ws->kernel_launches; k_sh_bwd<1><<<ws->proj_blocks, kProjBwdThreads, 0, s>>>(A); break;
+            case 2: ++ws->kernel_launches; k_sh_bwd<2><<<ws->proj_blocks, kProjBwdThreads, 0, s>>>(A); break;
+            default: ++ws->kernel_launches; k_sh_bwd<3><<<ws->proj_blocks, kProjBwdThreads, 0, s>>>(A); break;
+        }
+        switch (ws->sh_degree) {
+            case 0: ++ws->kernel_launches; k_project_bwd<0><<<ws->proj_blocks, kProjBwdThreads, smem, s>>>(A); break;
+            case 1: ++ws->kernel_launches; k_project_bwd<1><<<ws->proj_blocks, kProjBwdThreads, smem, s>>>(A); break;
+            case 2: ++ws->kernel_launches; k_project_bwd<2><<<ws->proj_blocks, kProjBwdThreads, smem, s>>>(A); break;
+            default: ++ws->kernel_launches; k_project_bwd<3><<<ws->proj_blocks, kProjBwdThreads, smem, s>>>(A); break;
         }
         gs_status st = check_launch("project_bwd");
         if (st != GS_OK) return st;
