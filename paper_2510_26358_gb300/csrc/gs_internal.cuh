@@ -37,7 +37,8 @@ struct DevState {
     uint32_t bwd_counter;
     float depth_scale;          // lambda_L / |Omega| of the last gs_depth_loss
     uint32_t depth_valid;
-    uint32_t pad[7];
+    uint32_t done_l1, done_depth;  // finished blocks of the loss reductions (the last one finishes)
+    uint32_t pad[5];
 };
 constexpr uint32_t kFlagCapacity = 1u;
 constexpr int kEmitWindow = 1024;      // output slots per emission window

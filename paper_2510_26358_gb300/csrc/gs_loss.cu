@@ -39,6 +39,20 @@ __device__ __forceinline__ double block_sum_d(double v, double *sm) {
     return t;
 }
 
+// Called by every thread after thread 0 has written the block's partial:
+// true in the one block that finishes last (it then sees every partial, and
+// puts the counter back to 0 for the next launch when it is done with it).
+__device__ __forceinline__ bool last_block(uint32_t *counter) {
+    __shared__ bool s_last;
+    if (threadIdx.x == 0) {
+        __threadfence();  // this block's partial before the count
+        s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last) __threadfence();  // every other partial before the reads below
+    return s_last;
+}
+
 struct DepthArgs {
     const ViewInfo *views;
     int32_t n_views, mode;
@@ -108,23 +122,23 @@ __global__ void __launch_bounds__(LT) k_depth_partial(DepthArgs A) {
         A.part[blockIdx.x] = ts;
         A.part[A.nb + blockIdx.x] = tc;
     }
-}
-
-__global__ void __launch_bounds__(LT) k_depth_final(DepthArgs A) {
-    __shared__ double sm[32];
-    double s = 0.0, c = 0.0;
-    // fixed order: each thread a fixed strided set, then a fixed tree
+    if (!last_block(&A.st->done_depth)) return;
+    // the last block: grid sums in a fixed order (each thread a fixed strided
+    // set, then a fixed tree), the loss and the gradient scale
+    s = 0.0;
+    c = 0.0;
     for (int i = threadIdx.x; i < A.nb; i += LT) {
         s += A.part[i];
         c += A.part[A.nb + i];
     }
-    double ts = block_sum_d(s, sm);
-    double tc = block_sum_d(c, sm);
+    ts = block_sum_d(s, sm);
+    tc = block_sum_d(c, sm);
     if (threadIdx.x == 0) {
         double scale = tc > 0.0 ? (double)A.lambda / tc : 0.0;
         *A.loss = (float)(ts * scale);
         A.st->depth_scale = (float)scale;
         A.st->depth_valid = (uint32_t)tc;
+        A.st->done_depth = 0u;
     }
 }
 
@@ -156,22 +170,39 @@ __device__ __forceinline__ float l1_term(float c, float t, float inv, float &g) 
 }
 
 // Four terms are added in float, each group of four into a double; the
-// block and grid sums are in double and in a fixed order.
+// block and grid sums are in double and in a fixed order.  A thread works
+// four grid strides at once (more loads in flight), in the same order.  With
+// `done` set, the last block also writes the mean to *loss (else a separate
+// kernel combines the partials).
 __global__ void __launch_bounds__(LT) k_l1_partial(const float *rgb, const float *target, int64_t n,
-                                                  float *grad, double *part, float inv) {
+                                                  float *grad, double *part, float inv, uint32_t *done,
+                                                  float *loss) {
+    constexpr int U = 4;
     __shared__ double sm[32];
     double s = 0.0;
     const bool vec = ((((uintptr_t)rgb) | ((uintptr_t)target) | ((uintptr_t)grad)) & 15) == 0;
     const int64_t n4 = vec ? n / 4 : 0;
     const int64_t stride = (int64_t)gridDim.x * LT;
-    for (int64_t i = (int64_t)blockIdx.x * LT + threadIdx.x; i < n4; i += stride) {
-        const float4 c = reinterpret_cast<const float4 *>(rgb)[i];
-        const float4 t = reinterpret_cast<const float4 *>(target)[i];
-        float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (grad) g = reinterpret_cast<float4 *>(grad)[i];
-        s += (double)(l1_term(c.x, t.x, inv, g.x) + l1_term(c.y, t.y, inv, g.y) +
-                      l1_term(c.z, t.z, inv, g.z) + l1_term(c.w, t.w, inv, g.w));
-        if (grad) reinterpret_cast<float4 *>(grad)[i] = g;
+    for (int64_t i0 = (int64_t)blockIdx.x * LT + threadIdx.x; i0 < n4; i0 += U * stride) {
+        float4 c[U], t[U], g[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = i0 + u * stride;
+            c[u] = t[u] = g[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (i < n4) {
+                c[u] = reinterpret_cast<const float4 *>(rgb)[i];
+                t[u] = reinterpret_cast<const float4 *>(target)[i];
+                if (grad) g[u] = reinterpret_cast<float4 *>(grad)[i];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = i0 + u * stride;
+            if (i >= n4) break;
+            s += (double)(l1_term(c[u].x, t[u].x, inv, g[u].x) + l1_term(c[u].y, t[u].y, inv, g[u].y) +
+                          l1_term(c[u].z, t[u].z, inv, g[u].z) + l1_term(c[u].w, t[u].w, inv, g[u].w));
+            if (grad) reinterpret_cast<float4 *>(grad)[i] = g[u];
+        }
     }
     for (int64_t i = 4 * n4 + (int64_t)blockIdx.x * LT + threadIdx.x; i < n; i += stride) {
         float g = grad ? grad[i] : 0.f;
@@ -180,14 +211,14 @@ __global__ void __launch_bounds__(LT) k_l1_partial(const float *rgb, const float
     }
     double t = block_sum_d(s, sm);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
-}
-
-__global__ void __launch_bounds__(LT) k_l1_final(const double *part, int nb, int64_t n, float *loss) {
-    __shared__ double sm[32];
-    double s = 0.0;
-    for (int i = threadIdx.x; i < nb; i += LT) s += part[i];
-    double t = block_sum_d(s, sm);
-    if (threadIdx.x == 0) *loss = (float)(t / (double)n);
+    if (!done || !last_block(done)) return;
+    s = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += LT) s += part[i];
+    t = block_sum_d(s, sm);
+    if (threadIdx.x == 0) {
+        *loss = (float)(t / (double)n);
+        *done = 0u;
+    }
 }
 
 // loss[0] = (1 - lambda) L1 + lambda (1 - SSIM), loss[1] = L1, loss[2] = 1 - SSIM
@@ -232,7 +263,6 @@ gs_status launch_depth_loss(gs_workspace *ws, int mode, const float *depth, cons
     A.st = ws->st;
     StageTimer timer(ws, GS_STAGE_DEPTH_LOSS, s);
     ++ws->kernel_launches; k_depth_partial<<<A.nb, LT, 0, s>>>(A);
-    ++ws->kernel_launches; k_depth_final<<<1, LT, 0, s>>>(A);
     if ((dL_ddepth || dL_dvar) && n_pts > 0) {
         ++ws->kernel_launches;
         k_depth_grad<<<A.nb, LT, 0, s>>>(A);
@@ -246,8 +276,8 @@ gs_status launch_image_l1(gs_workspace *ws, const float *rgb, const float *targe
     int nb = ws->sort_blocks;
     StageTimer timer(ws, GS_STAGE_IMAGE_L1, s);
     ++ws->kernel_launches;
-    k_l1_partial<<<nb, LT, 0, s>>>(rgb, target, n, dL_drgb, ws->red_part, (float)(1.0 / (double)n));
-    ++ws->kernel_launches; k_l1_final<<<1, LT, 0, s>>>(ws->red_part, nb, n, loss);
+    k_l1_partial<<<nb, LT, 0, s>>>(rgb, target, n, dL_drgb, ws->red_part, (float)(1.0 / (double)n),
+                                   &ws->st->done_l1, loss);
     return check_launch("image_l1");
 }
 
@@ -259,7 +289,7 @@ gs_status launch_image_loss(gs_workspace *ws, const float *rgb, const float *tar
         StageTimer timer(ws, GS_STAGE_IMAGE_L1, s);
         ++ws->kernel_launches;
         k_l1_partial<<<nb, LT, 0, s>>>(rgb, target, n, dL_drgb, ws->red_part,
-                                       (float)((1.0 - (double)lambda) / (double)n));
+                                       (float)((1.0 - (double)lambda) / (double)n), nullptr, nullptr);
     }
     gs_status r = check_launch("image_loss");
     if (r != GS_OK) return r;
