@@ -24,8 +24,22 @@ GRAD_TOL = 1e-4
 MARGIN = 1e-4
 
 
+def _overlap_scene():
+    """Degree-3 box scene seen by three cameras with overlapping frusta (the
+    first camera and two seeded perturbations of it), so that many Gaussians
+    are seen by several views."""
+    sc = S.random_box_scene(8_000, 160, 120, 150.0, seed=3, sh_degree=3)
+    rng = np.random.default_rng(3)
+    cam0 = sc.cameras[0]
+    sc.cameras = [cam0] + [S.perturb_pose(cam0, rng, sigma_t=0.15, sigma_deg=4.0) for _ in range(2)]
+    sc.target = rng.random(3 * sum(c.width * c.height for c in sc.cameras)).astype(np.float32)
+    sc.name = "box_overlap"
+    return sc
+
+
 def _scenes():
     return {
+        "box_overlap": _overlap_scene(),
         "box10k": S.random_box_scene(10_000, 320, 240, 300.0, seed=0),
         "orchard_rig": S.orchard_scene(40_000, 3, 4, 200, 120, rear=True, pose_noise=True,
                                        lidar_per_view=3000, seed=1, name="orchard_rig"),
@@ -141,3 +155,19 @@ def test_gradients(case):
     assert np.array_equal(cnt, go["dens_cnt"]) or case["rec"][:, O.C_RECT_AMBIG].any()
     for k, v in res.items():
         assert v <= GRAD_TOL, (k, v)
+
+
+def test_scenes_reach_the_colour_clamp_and_shared_gaussians():
+    """The gradient parity above covers two paths of the projection adjoint:
+    colour channels clamped at 0 (the forward marks them, the SH adjoint must
+    give them no gradient) and Gaussians seen by several views (one lane walks
+    their views and accumulates their gradients).  Both occur in the scenes."""
+    clamped = shared = 0
+    for sc in SCENES.values():
+        P = O.Params.from_scene(sc)
+        rec = O.project(P, O.as_float32_cameras(sc.cameras), O.Config())
+        r = rec[rec[:, O.C_VIS] > 0]
+        clamped += int((r[:, O.C_CLR:O.C_CLB + 1] > 0).sum())
+        shared += int((np.bincount(r[:, O.C_GAUSS].astype(np.int64)) > 1).sum())
+    print(f"clamped channels {clamped}, Gaussians seen by several views {shared}")
+    assert clamped > 0 and shared > 0
