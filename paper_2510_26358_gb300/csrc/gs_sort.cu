@@ -65,11 +65,16 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s
 // visible-pair compaction
 // ---------------------------------------------------------------------------
 
+// Both compaction kernels split the pairs into the same per-block chunks,
+// whole multiples of kCompactStep keys (8 a thread, read as two 16-byte
+// loads), so that the compaction takes few block-wide scans.
+constexpr int kCompactStep = 8 * T;
+
 __global__ void __launch_bounds__(T) k_count_visible(const uint32_t *pkey, uint32_t n, uint32_t *part,
                                                     int nb) {
     __shared__ uint32_t sm[32];
     uint32_t lo, hi;
-    chunk_range(n, blockIdx.x, nb, T, lo, hi);
+    chunk_range(n, blockIdx.x, nb, kCompactStep, lo, hi);
     uint32_t c = 0;
     for (uint32_t i = lo + threadIdx.x; i < hi; i += T) c += pkey[i] != kInvalidKey;
     uint32_t tot;
@@ -118,18 +123,33 @@ __global__ void __launch_bounds__(T) k_compact_visible(const uint32_t *pkey, uin
                                                       int nb, uint32_t *vis_key, uint32_t *vis_pair) {
     __shared__ uint32_t sm[32];
     uint32_t lo, hi;
-    chunk_range(n, blockIdx.x, nb, T, lo, hi);
+    chunk_range(n, blockIdx.x, nb, kCompactStep, lo, hi);
     uint32_t base = part[blockIdx.x];
-    for (uint32_t t0 = lo; t0 < hi; t0 += T) {
-        uint32_t i = t0 + threadIdx.x;
-        uint32_t k = i < hi ? pkey[i] : kInvalidKey;
-        uint32_t f = k != kInvalidKey;
-        uint32_t tot;
-        uint32_t ex = block_exclusive_scan(f, sm, &tot);
-        if (f) {
-            vis_key[base + ex] = k;
-            vis_pair[base + ex] = i;
+    for (uint32_t t0 = lo; t0 < hi; t0 += kCompactStep) {
+        // this thread's 8 consecutive keys, in pair order
+        const uint32_t i0 = t0 + 8 * threadIdx.x;
+        uint32_t k[8];
+        if (i0 + 8 <= hi) {
+            const uint4 a = reinterpret_cast<const uint4 *>(pkey + i0)[0];
+            const uint4 b = reinterpret_cast<const uint4 *>(pkey + i0)[1];
+            k[0] = a.x; k[1] = a.y; k[2] = a.z; k[3] = a.w;
+            k[4] = b.x; k[5] = b.y; k[6] = b.z; k[7] = b.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) k[j] = i0 + j < hi ? pkey[i0 + j] : kInvalidKey;
         }
+        uint32_t c = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) c += k[j] != kInvalidKey;
+        uint32_t tot;
+        uint32_t o = base + block_exclusive_scan(c, sm, &tot);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (k[j] != kInvalidKey) {
+                vis_key[o] = k[j];
+                vis_pair[o] = i0 + j;
+                ++o;
+            }
         base += tot;
     }
 }
