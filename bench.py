@@ -339,6 +339,10 @@ class Step:
         t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
         self.P = [t(sc.means), t(sc.log_scales), t(sc.quats), t(sc.opacity_logits), t(sc.sh)]
         self.target = t(sc.target)
+        # the same targets as 8-bit camera values (t = round(255 x)), for the
+        # end-to-end leg that uploads keyframes as cameras deliver them
+        self.target_u8 = t(np.clip(np.rint(np.asarray(sc.target, np.float64) * 255.0), 0, 255).astype(np.uint8))
+        self.u8 = False
         self.lidar = t(sc.lidar)
         self.r = G.Renderer(sc.cameras, sc.submap_offsets, sc.sh_degree, config=cfg,
                             inst_capacity=inst_capacity or max(1 << 22, 8 * sc.n))
@@ -392,6 +396,9 @@ class Step:
             if self.ssim_lambda > 0:
                 G.gs_image_loss(r.ws, G._ptr(self.rgb), G._ptr(self.target), self.ssim_lambda, G._ptr(self.loss_rgb),
                                 G._ptr(self.g_rgb), s)
+            elif self.u8:
+                G.gs_image_l1_u8(r.ws, G._ptr(self.rgb), G._ptr(self.target_u8), G._ptr(self.loss_rgb),
+                                 G._ptr(self.g_rgb), s)
             else:
                 G.gs_image_l1(r.ws, G._ptr(self.rgb), G._ptr(self.target), G._ptr(self.loss_rgb), G._ptr(self.g_rgb),
                               s)
@@ -717,7 +724,7 @@ def main():
     # every step.
     e2e = None
     if not args.no_e2e:
-        def e2e_run(tensors):
+        def e2e_run(tensors, g):
             host = [t.cpu().pin_memory() for t in tensors]
             loss_h = torch.empty(2, pin_memory=True)
             h2d = sum(h.numel() * h.element_size() for h in host)
@@ -725,7 +732,7 @@ def main():
             def e2e_step():
                 for h, d in zip(host, tensors):
                     d.copy_(h, non_blocking=True)
-                graph.replay()
+                g.replay()
                 loss_h[0:1].copy_(step.loss_rgb[0:1], non_blocking=True)
                 loss_h[1:2].copy_(step.loss_depth, non_blocking=True)
             e_times = time_steps(torch, e2e_step, max(3, args.steps // 2), 3, flush)
@@ -733,9 +740,22 @@ def main():
             return {"value": sc.n_pix * world / (e_ms * 1e-3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": 8, "ms_per_step": e_ms}
         batch = [step.target, step.lidar, step.r.cams_dev]
-        e2e = e2e_run(batch)
-        e2e["inputs"] = "keyframe batch: target images, LiDAR returns, cameras (map resident)"
-        e2e["with_map_upload"] = e2e_run(list(step.P) + batch)
+        if args.ssim_lambda == 0:
+            # keyframes as cameras deliver them: 8-bit target images (the step's
+            # L1 reads them directly); the float-target figure is kept beside it
+            step.u8 = True
+            graph_u8 = make_graph(torch, step)
+            step.u8 = False
+            batch_u8 = [step.target_u8, step.lidar, step.r.cams_dev]
+            e2e = e2e_run(batch_u8, graph_u8)
+            e2e["inputs"] = ("keyframe batch: 8-bit target images, LiDAR returns, cameras (map resident); "
+                             "gs_image_l1_u8")
+            e2e["with_map_upload"] = e2e_run(list(step.P) + batch_u8, graph_u8)
+            e2e["float_targets"] = e2e_run(batch, graph)
+        else:
+            e2e = e2e_run(batch, graph)
+            e2e["inputs"] = "keyframe batch: target images, LiDAR returns, cameras (map resident)"
+            e2e["with_map_upload"] = e2e_run(list(step.P) + batch, graph)
 
     # roofline of the dominant kernel (the raster backward)
     peaks = {}

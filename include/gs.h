@@ -177,6 +177,14 @@ gs_status gs_depth_loss_var(gs_workspace *ws, const float *alpha, const float *d
 gs_status gs_image_l1(gs_workspace *ws, const float *rgb, const float *target, float *loss,
                       float *dL_drgb, void *stream);
 
+/* gs_image_l1 with 8-bit target images, as cameras deliver them: target
+ * (device, 3*N_pix bytes, planar like rgb) holds values t in 0..255 that
+ * stand for t / 255 (rounded as a float32 division rounds it), so that a
+ * keyframe uploads a quarter of the float bytes.  Loss and gradient equal
+ * gs_image_l1's on the float targets t / 255, bit for bit. */
+gs_status gs_image_l1_u8(gs_workspace *ws, const float *rgb, const uint8_t *target, float *loss,
+                         float *dL_drgb, void *stream);
+
 /* The photometric loss of Eq. (6) (Sec. III-C):
  * (1 - lambda) mean |rgb - target| + lambda (1 - mean SSIM).  SSIM per channel
  * plane of every view, 11x11 Gaussian window of sigma 1.5 (normalised), zero

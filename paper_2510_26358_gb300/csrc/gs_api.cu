@@ -379,6 +379,12 @@ gs_status gs_image_l1(gs_workspace *ws, const float *rgb, const float *target, f
     return launch_image_l1(ws, rgb, target, loss, dL_drgb, (cudaStream_t)stream);
 }
 
+gs_status gs_image_l1_u8(gs_workspace *ws, const float *rgb, const uint8_t *target, float *loss,
+                         float *dL_drgb, void *stream) {
+    if (!ws || !rgb || !target || !loss) return fail(GS_ERR_INVALID_ARG, "NULL argument");
+    return launch_image_l1_u8(ws, rgb, target, loss, dL_drgb, (cudaStream_t)stream);
+}
+
 gs_status gs_image_loss(gs_workspace *ws, const float *rgb, const float *target, float lambda, float *loss,
                         float *dL_drgb, void *stream) {
     if (!ws || !rgb || !target || !loss) return fail(GS_ERR_INVALID_ARG, "NULL argument");

@@ -144,6 +144,8 @@ gs_status launch_raster_bwd(gs_workspace *ws, const float *dL_drgb, const float 
 gs_status launch_depth_loss(gs_workspace *ws, int mode, const float *depth, const float *alpha,
                             const float *var, const float *lidar, int64_t n_pts, float *loss,
                             float *dL_ddepth, float *dL_dvar, cudaStream_t s);
+gs_status launch_image_l1_u8(gs_workspace *ws, const float *rgb, const uint8_t *target, float *loss,
+                             float *dL_drgb, cudaStream_t s);
 gs_status launch_image_l1(gs_workspace *ws, const float *rgb, const float *target, float *loss,
                           float *dL_drgb, cudaStream_t s);
 // Eq. (6): (1 - lambda) L1 + lambda (1 - SSIM); loss[0..2] = total, L1, 1 - SSIM

@@ -169,18 +169,30 @@ __device__ __forceinline__ float l1_term(float c, float t, float inv, float &g) 
     return fabsf(d);
 }
 
+// Target values: float as given, or 8-bit (value / 255, rounded as the
+// float division rounds it).  Four at a time: float4 or uchar4.
+__device__ __forceinline__ float target_value(float t) { return t; }
+__device__ __forceinline__ float target_value(uint8_t t) { return (float)t / 255.f; }
+__device__ __forceinline__ float4 target4(const float *t, int64_t i) { return reinterpret_cast<const float4 *>(t)[i]; }
+__device__ __forceinline__ float4 target4(const uint8_t *t, int64_t i) {
+    const uchar4 b = reinterpret_cast<const uchar4 *>(t)[i];
+    return make_float4(target_value(b.x), target_value(b.y), target_value(b.z), target_value(b.w));
+}
+
 // Four terms are added in float, each group of four into a double; the
 // block and grid sums are in double and in a fixed order.  A thread works
 // four grid strides at once (more loads in flight), in the same order.  With
 // `done` set, the last block also writes the mean to *loss (else a separate
 // kernel combines the partials).
-__global__ void __launch_bounds__(LT) k_l1_partial(const float *rgb, const float *target, int64_t n,
+template <typename TT>
+__global__ void __launch_bounds__(LT) k_l1_partial(const float *rgb, const TT *target, int64_t n,
                                                   float *grad, double *part, float inv, uint32_t *done,
                                                   float *loss) {
     constexpr int U = 4;
     __shared__ double sm[32];
     double s = 0.0;
-    const bool vec = ((((uintptr_t)rgb) | ((uintptr_t)target) | ((uintptr_t)grad)) & 15) == 0;
+    const bool vec = ((((uintptr_t)rgb) | ((uintptr_t)grad)) & 15) == 0 &&
+                     (((uintptr_t)target) & (4 * sizeof(TT) - 1)) == 0;
     const int64_t n4 = vec ? n / 4 : 0;
     const int64_t stride = (int64_t)gridDim.x * LT;
     for (int64_t i0 = (int64_t)blockIdx.x * LT + threadIdx.x; i0 < n4; i0 += U * stride) {
@@ -191,7 +203,7 @@ __global__ void __launch_bounds__(LT) k_l1_partial(const float *rgb, const float
             c[u] = t[u] = g[u] = make_float4(0.f, 0.f, 0.f, 0.f);
             if (i < n4) {
                 c[u] = reinterpret_cast<const float4 *>(rgb)[i];
-                t[u] = reinterpret_cast<const float4 *>(target)[i];
+                t[u] = target4(target, i);
                 if (grad) g[u] = reinterpret_cast<float4 *>(grad)[i];
             }
         }
@@ -206,7 +218,7 @@ __global__ void __launch_bounds__(LT) k_l1_partial(const float *rgb, const float
     }
     for (int64_t i = 4 * n4 + (int64_t)blockIdx.x * LT + threadIdx.x; i < n; i += stride) {
         float g = grad ? grad[i] : 0.f;
-        s += (double)l1_term(rgb[i], target[i], inv, g);
+        s += (double)l1_term(rgb[i], target_value(target[i]), inv, g);
         if (grad) grad[i] = g;
     }
     double t = block_sum_d(s, sm);
@@ -270,15 +282,28 @@ gs_status launch_depth_loss(gs_workspace *ws, int mode, const float *depth, cons
     return check_launch("depth_loss");
 }
 
-gs_status launch_image_l1(gs_workspace *ws, const float *rgb, const float *target, float *loss,
-                          float *dL_drgb, cudaStream_t s) {
+namespace {
+template <typename TT>
+gs_status image_l1(gs_workspace *ws, const float *rgb, const TT *target, float *loss, float *dL_drgb,
+                   cudaStream_t s) {
     int64_t n = 3 * ws->n_pix;
     int nb = ws->sort_blocks;
     StageTimer timer(ws, GS_STAGE_IMAGE_L1, s);
     ++ws->kernel_launches;
-    k_l1_partial<<<nb, LT, 0, s>>>(rgb, target, n, dL_drgb, ws->red_part, (float)(1.0 / (double)n),
-                                   &ws->st->done_l1, loss);
+    k_l1_partial<TT><<<nb, LT, 0, s>>>(rgb, target, n, dL_drgb, ws->red_part, (float)(1.0 / (double)n),
+                                       &ws->st->done_l1, loss);
     return check_launch("image_l1");
+}
+}  // namespace
+
+gs_status launch_image_l1(gs_workspace *ws, const float *rgb, const float *target, float *loss,
+                          float *dL_drgb, cudaStream_t s) {
+    return image_l1(ws, rgb, target, loss, dL_drgb, s);
+}
+
+gs_status launch_image_l1_u8(gs_workspace *ws, const float *rgb, const uint8_t *target, float *loss,
+                             float *dL_drgb, cudaStream_t s) {
+    return image_l1(ws, rgb, target, loss, dL_drgb, s);
 }
 
 gs_status launch_image_loss(gs_workspace *ws, const float *rgb, const float *target, float lambda, float *loss,
@@ -288,7 +313,7 @@ gs_status launch_image_loss(gs_workspace *ws, const float *rgb, const float *tar
     {
         StageTimer timer(ws, GS_STAGE_IMAGE_L1, s);
         ++ws->kernel_launches;
-        k_l1_partial<<<nb, LT, 0, s>>>(rgb, target, n, dL_drgb, ws->red_part,
+        k_l1_partial<float><<<nb, LT, 0, s>>>(rgb, target, n, dL_drgb, ws->red_part,
                                        (float)((1.0 - (double)lambda) / (double)n), nullptr, nullptr);
     }
     gs_status r = check_launch("image_loss");

@@ -28,7 +28,7 @@ GS_MAX_SUBMAPS = 64
 
 EXPORTED = ("gs_config_default", "gs_workspace_create", "gs_workspace_destroy", "gs_project",
             "gs_bin_sort", "gs_render_fwd", "gs_render_fwd_var", "gs_depth_loss", "gs_depth_loss_var",
-            "gs_image_l1", "gs_image_loss", "gs_render_bwd", "gs_render_bwd_var",
+            "gs_image_l1", "gs_image_l1_u8", "gs_image_loss", "gs_render_bwd", "gs_render_bwd_var",
             "gs_workspace_status", "gs_workspace_info", "gs_workspace_copy", "gs_workspace_set_profiling",
             "gs_workspace_stage_ms", "gs_image_l1_noalloc", "gs_status_string", "gs_last_error",
             "gs_lifecycle_create", "gs_lifecycle_destroy", "gs_lifecycle_run", "gs_lifecycle_status", "gs_adam_step",
@@ -121,6 +121,7 @@ def lib() -> ctypes.CDLL:
     L.gs_depth_loss.argtypes = [P, P, P, P, i64, P, P, P]
     L.gs_depth_loss_var.argtypes = [P, P, P, P, P, i64, P, P, P, P]
     L.gs_image_l1.argtypes = [P, P, P, P, P, P]
+    L.gs_image_l1_u8.argtypes = [P, P, P, P, P, P]
     L.gs_image_loss.argtypes = [P, P, P, ctypes.c_float, P, P, P]
     L.gs_render_bwd.argtypes = [P, ctypes.POINTER(GsGaussians), P, P, P, P, ctypes.POINTER(GsGrads), P]
     L.gs_render_bwd_var.argtypes = [P, ctypes.POINTER(GsGaussians), P, P, P, P, P, P, ctypes.POINTER(GsGrads), P]
@@ -154,7 +155,7 @@ def lib() -> ctypes.CDLL:
     L.gs_last_error.argtypes = []
     L.gs_last_error.restype = ctypes.c_char_p
     for name in ("gs_workspace_create", "gs_project", "gs_bin_sort", "gs_render_fwd", "gs_render_fwd_var",
-                 "gs_depth_loss", "gs_depth_loss_var", "gs_image_l1", "gs_image_loss", "gs_render_bwd",
+                 "gs_depth_loss", "gs_depth_loss_var", "gs_image_l1", "gs_image_l1_u8", "gs_image_loss", "gs_render_bwd",
                  "gs_render_bwd_var",
                  "gs_workspace_status", "gs_workspace_info",
                  "gs_workspace_copy", "gs_workspace_set_profiling", "gs_workspace_stage_ms",
@@ -429,6 +430,10 @@ def gs_image_l1(ws, rgb, target, loss, dL_drgb, stream):
     _check(lib().gs_image_l1(ws, rgb, target, loss, dL_drgb, stream), "gs_image_l1")
 
 
+def gs_image_l1_u8(ws, rgb, target_u8, loss, dL_drgb, stream):
+    _check(lib().gs_image_l1_u8(ws, rgb, target_u8, loss, dL_drgb, stream), "gs_image_l1_u8")
+
+
 def gs_image_loss(ws, rgb, target, lam, loss, dL_drgb, stream):
     _check(lib().gs_image_loss(ws, rgb, target, float(lam), loss, dL_drgb, stream), "gs_image_loss")
 
@@ -627,8 +632,11 @@ class Renderer:
         return loss
 
     def image_l1(self, rgb, target, dL_drgb=None, stream=None):
+        """Mean |rgb - target| (accumulates dL/drgb when given); an 8-bit target
+        tensor (torch.uint8) stands for target / 255."""
         loss = self.torch.zeros(1, device=self.device)
-        gs_image_l1(self.ws, _ptr(rgb), _ptr(target), _ptr(loss), _ptr(dL_drgb), _stream(stream))
+        f = gs_image_l1_u8 if target.dtype == self.torch.uint8 else gs_image_l1
+        f(self.ws, _ptr(rgb), _ptr(target), _ptr(loss), _ptr(dL_drgb), _stream(stream))
         return loss
 
     def image_loss(self, rgb, target, lam=0.2, dL_drgb=None, stream=None):

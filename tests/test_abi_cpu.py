@@ -64,6 +64,7 @@ def test_argument_errors_before_any_cuda_call(G):
     assert "submap" in G.last_error()
     assert L.gs_project(None, None, None, None) == E
     assert L.gs_image_l1_noalloc(None, None, 10, None, None, None) == E
+    assert L.gs_image_l1_u8(None, None, None, None, None, None) == E
 
 
 def _rank_main(rank, world, port, q):

@@ -189,6 +189,35 @@ def test_image_l1_parity():
     r.close()
 
 
+def test_image_l1_with_8bit_targets():
+    """gs_image_l1_u8 equals gs_image_l1 on the float targets t / 255 bit for
+    bit (loss and accumulated gradient, ragged size so the scalar tail runs),
+    and both match the oracle; ties give zero gradient."""
+    torch, dev = torch_dev()
+    G = _G()
+    cams = [S.Camera(51, 31, 50.0, 50.0, 25.0, 15.0, np.eye(3, 4), 0)]
+    r = G.Renderer(cams, [0, 1], 0, inst_capacity=1024)
+    n = 3 * 51 * 31
+    rng = np.random.default_rng(2)
+    T8 = rng.integers(0, 256, n).astype(np.uint8)
+    Tf = T8.astype(np.float32) / np.float32(255.0)  # float32 division, as the kernel divides
+    C = rng.random(n).astype(np.float32)
+    C[:20] = Tf[:20]  # exact ties
+    Cd = torch.from_numpy(C).to(dev)
+    g8 = torch.full((n,), 0.25, device=dev)  # accumulation onto existing values
+    gf = g8.clone()
+    l8 = r.image_l1(Cd, torch.from_numpy(T8).to(dev), g8)
+    lf = r.image_l1(Cd, torch.from_numpy(Tf).to(dev), gf)
+    torch.cuda.synchronize()
+    assert l8.item() == lf.item()
+    assert torch.equal(g8, gf)
+    lo, go = O.image_l1(C, Tf)
+    assert l8.item() == pytest.approx(lo, rel=1e-6)
+    # the gradient was added onto 0.25 in float32: one rounding at 0.25's ulp
+    assert np.abs(g8.cpu().numpy().astype(np.float64) - 0.25 - go).max() <= float(np.spacing(np.float32(0.25)))
+    r.close()
+
+
 # ---------------------------------------------------------------------------
 # edge cases of the C ABI
 # ---------------------------------------------------------------------------
