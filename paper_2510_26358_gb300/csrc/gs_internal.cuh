@@ -82,7 +82,7 @@ struct gs_workspace {
     float *tfin = nullptr;         // [n_pix]
     float4 *vstat = nullptr;       // [n_pix] depth (mean, var, 1/W, 0) of the variance forward
     // scratch
-    uint32_t *hist = nullptr;      // [256][sort_blocks]
+    uint32_t *hist = nullptr;      // [256][2 sort_blocks]
     uint32_t *part = nullptr;      // [sort_blocks + 1]
     uint32_t *digit_tot = nullptr; // [256] digit totals of the current radix pass
     float *pose_part = nullptr;    // [proj_blocks][max_views_per_submap][6]

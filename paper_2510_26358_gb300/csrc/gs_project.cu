@@ -428,9 +428,9 @@ __global__ void __launch_bounds__(kProjThreads) k_project_fwd(ProjArgs A) {
                 for (int kk = 0; kk < K; ++kk)
 #pragma unroll
                     for (int ch = 0; ch < 3; ++ch) acc[ch] = __fmaf_rn(__ldg(shg + 3 * kk + ch), Y[kk], acc[ch]);
-#pragma unroll
                 // a clamped channel is stored as -0: it renders as 0, and its
                 // sign bit hands the clamp decision to the backward
+#pragma unroll
                 for (int ch = 0; ch < 3; ++ch) rgb[ch] = acc[ch] < 0.f ? -0.f : acc[ch];
                 r0 = make_float4(Uf, Vf, hx, hy);
                 r1 = make_float4(l11, l12, l22, log2o);
