@@ -475,8 +475,9 @@ __global__ void k_order_scatter(const uint2 *ranges, int n_tiles, uint32_t *buck
 // One stable pass over bits [shift, shift+8) by nb blocks; swaps in/out.
 // R = 8 rounds (2048-key tiles) on twice the blocks for the instance sort
 // (64 registers: one full wave of four blocks per SM; measured 0.0725 ->
-// 0.068 ms against R = 16 on one block per two SMs' worth), R = 4 for the
-// smaller sort of the visible pairs (more blocks busy, shorter latency).
+// 0.068 ms against R = 16 on one block per two SMs' worth), R = 2 for the
+// smaller sort of the visible pairs (more blocks busy, shorter latency:
+// 0.070 -> 0.068 ms against R = 4, R = 1 0.072 ms).
 template <int R>
 gs_status radix_pass(gs_workspace *ws, uint32_t *&k, uint32_t *&v, uint32_t *&k2, uint32_t *&v2,
                      const uint32_t *n_ptr, int shift, int nb, cudaStream_t s) {
@@ -496,8 +497,8 @@ gs_status sort_configure() {
     cudaError_t e = cudaFuncSetAttribute(k_radix_scatter<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sizeof(ScatterSmem<8>));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_radix_scatter<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sizeof(ScatterSmem<4>));
+        e = cudaFuncSetAttribute(k_radix_scatter<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(ScatterSmem<2>));
     if (e != cudaSuccess) {
         set_last_error(std::string("sort_configure: ") + cudaGetErrorString(e));
         return GS_ERR_CUDA;
@@ -525,7 +526,7 @@ gs_status launch_bin_sort(gs_workspace *ws, cudaStream_t s) {
     {
     StageTimer timer(ws, GS_STAGE_DEPTH_SORT, s);
     for (int sh = 0; sh < 32; sh += 8)
-        if ((r = radix_pass<4>(ws, k, v, k2, v2, &st->n_vis, sh, nb, s)) != GS_OK) return r;
+        if ((r = radix_pass<2>(ws, k, v, k2, v2, &st->n_vis, sh, nb, s)) != GS_OK) return r;
     }
     // after 4 passes the sorted data are back in vis_key / vis_pair
     // 3. instance offsets, capacity check, emission in depth order
