@@ -240,8 +240,29 @@ __device__ __forceinline__ void ssim_epilogue(const SsimArgs &A, const PlaneTile
 }
 
 // Vertical pass of the backward and the gradient (shared by both staging paths).
+// The thread's VB output values of x, y and the gradient, loaded when the
+// kernel starts so that their latency hides behind the staging and the
+// filters (0 outside the image; those are not written).
+struct BwdOut {
+    float x[VB], y[VB], g[VB];
+};
+__device__ __forceinline__ BwdOut ssim_bwd_prefetch(const SsimArgs &A, const PlaneTile &P, int lx, int ly) {
+    BwdOut o;
+    const int gx = P.x0 + lx, oy0 = VB * ly;
+#pragma unroll
+    for (int b = 0; b < VB; ++b) {
+        const int gy = P.y0 + oy0 + b;
+        const bool in = gx < P.W && gy < P.H;
+        const int64_t e = P.base + (int64_t)gy * P.W + gx;
+        o.x[b] = in ? A.x[e] : 0.f;
+        o.y[b] = in ? A.y[e] : 0.f;
+        o.g[b] = in ? A.grad[e] : 0.f;
+    }
+    return o;
+}
+
 __device__ __forceinline__ void ssim_bwd_epilogue(const SsimArgs &A, const PlaneTile &P, const float (*sh)[IH][HW],
-                                                  int lx, int ly) {
+                                                  int lx, int ly, const BwdOut &o) {
     const int gx = P.x0 + lx, oy0 = VB * ly;
     float f[VB][3];
 #pragma unroll
@@ -263,8 +284,7 @@ __device__ __forceinline__ void ssim_bwd_epilogue(const SsimArgs &A, const Plane
         const int gy = P.y0 + oy0 + b;
         if (gx >= P.W || gy >= P.H) continue;
         const int64_t e = P.base + (int64_t)gy * P.W + gx;
-        const float xv = A.x[e], yv = A.y[e];
-        A.grad[e] += A.scale * (f[b][0] + 2.f * xv * f[b][1] + yv * f[b][2]);
+        A.grad[e] = o.g[b] + A.scale * (f[b][0] + 2.f * o.x[b] * f[b][1] + o.y[b] * f[b][2]);
     }
 }
 
@@ -309,6 +329,7 @@ __global__ void __launch_bounds__(NT) k_ssim_bwd(SsimArgs A) {
     __shared__ float sh[3][IH][HW];
     const PlaneTile P = locate(A, blockIdx.x);
     const int tid = threadIdx.x, lx = tid & 31, ly = tid >> 5;
+    const BwdOut out = ssim_bwd_prefetch(A, P, lx, ly);
     {
         float v[3][SLOADS];
 #pragma unroll
@@ -332,7 +353,7 @@ __global__ void __launch_bounds__(NT) k_ssim_bwd(SsimArgs A) {
     __syncthreads();
     for (int item = tid; item < HITEMS; item += NT) horizontal<3>(A, st, sh, item);
     __syncthreads();
-    ssim_bwd_epilogue(A, P, sh, lx, ly);
+    ssim_bwd_epilogue(A, P, sh, lx, ly, out);
 }
 
 
@@ -481,6 +502,7 @@ __global__ void __launch_bounds__(NT) k_ssim_bwd_tma(SsimArgs A, const __grid_co
         for (int q = 0; q < 3; ++q) tma_load_4d(&sd[q][0][0], &T.d[P.v], P.x0 - R - BOFF, P.y0 - R, P.ch, q, &bar);
     }
     __syncthreads();
+    const BwdOut out = ssim_bwd_prefetch(A, P, lx, ly);
     if (!tma_wait(&bar, A.flags, A.wait_ns)) return;
     for (int item = tid; item < HITEMS; item += NT) {
         const int r = item / (TX / HB), c0 = (item % (TX / HB)) * HB;
@@ -499,7 +521,7 @@ __global__ void __launch_bounds__(NT) k_ssim_bwd_tma(SsimArgs A, const __grid_co
         }
     }
     __syncthreads();
-    ssim_bwd_epilogue(A, P, sh, lx, ly);
+    ssim_bwd_epilogue(A, P, sh, lx, ly, out);
 }
 
 std::once_flag g_encode_once;
