@@ -71,8 +71,10 @@ struct RasterArgs {
 // shared-memory reads and the column part of every fragment's exponent.  A
 // pixel stops at the first fragment that would take its transmittance below
 // t_min, the thread when all of its pixels have, the CTA when all threads have.
+// The VAR variant holds four more values a pixel: at least 640 resident
+// threads an SM keeps it at 96 registers without spills (0: no minimum).
 template <int TW, int TH, int PF, bool VAR>
-__global__ void __launch_bounds__(TW * TH / PF) k_raster_fwd(RasterArgs A) {
+__global__ void __launch_bounds__(TW * TH / PF, VAR ? 640 / (TW * TH / PF) : 0) k_raster_fwd(RasterArgs A) {
     constexpr int NT = TW * TH / PF;
     static_assert(NT % 32 == 0, "the forward needs whole warps");
     extern __shared__ float4 smem[];
@@ -517,9 +519,9 @@ size_t bwd_smem(int depth) {
 
 // Pixels per thread of the forward: on the 500k orchard with 16x16 tiles
 // 1 -> 0.307 ms, 2 -> 0.268 ms, 4 -> 0.239 ms, 8 -> 0.303 ms; the VAR variant
-// (four more values a pixel) 2 -> 0.372 ms, 4 -> 0.400 ms.
+// (four more values a pixel, register bound above) 2 -> 0.370 ms, 4 -> 0.352 ms.
 template <int TW, int TH, bool VAR>
-constexpr int ppt_fwd() { return TW * TH >= 256 && !VAR ? 4 : 2; }
+constexpr int ppt_fwd() { return TW * TH >= 256 ? 4 : 2; }
 
 template <int TW, int TH, bool VAR>
 cudaError_t configure_variant(gs_workspace *ws, int &grid_f, int &grid_b) {
