@@ -441,35 +441,41 @@ __global__ void k_ranges(const uint32_t *tile, const DevState *st, uint2 *ranges
 // counting sort into kOrderBuckets length buckets; the order inside a bucket
 // is whatever the atomics give (tiles are independent, so it does not change
 // any result).
-__global__ void k_order_hist(const uint2 *ranges, int n_tiles, uint32_t *buckets) {
-    __shared__ uint32_t h[kOrderBuckets];
-    if (threadIdx.x < kOrderBuckets) h[threadIdx.x] = 0;
-    __syncthreads();
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += gridDim.x * blockDim.x) {
-        uint32_t len = ranges[t].y - ranges[t].x;
-        uint32_t b = kOrderBuckets - 1 - min((uint32_t)(kOrderBuckets - 1), len >> kOrderShift);
-        atomicAdd(&h[b], 1u);
-    }
-    __syncthreads();
-    if (threadIdx.x < kOrderBuckets && h[threadIdx.x]) atomicAdd(&buckets[threadIdx.x], h[threadIdx.x]);
+__device__ __forceinline__ uint32_t order_bucket(uint2 r) {
+    const uint32_t len = r.y - r.x;
+    return kOrderBuckets - 1 - min((uint32_t)(kOrderBuckets - 1), len >> kOrderShift);
 }
 
-__global__ void k_order_scatter(const uint2 *ranges, int n_tiles, uint32_t *buckets, uint32_t *order) {
-    __shared__ uint32_t start[kOrderBuckets];
-    if (threadIdx.x == 0) {
-        uint32_t run = 0;
-        for (int b = 0; b < kOrderBuckets; ++b) {
-            start[b] = run;
-            run += buckets[b];
+// One block: bucket counts in shared memory, their prefix, then every tile
+// placed at its bucket's cursor.
+__global__ void __launch_bounds__(1024) k_tile_order(const uint2 *ranges, int n_tiles, uint32_t *order) {
+    static_assert(kOrderBuckets == 64, "the prefix below takes two counts a lane of one warp");
+    __shared__ uint32_t cursor[kOrderBuckets];
+    const int t = threadIdx.x;
+    if (t < kOrderBuckets) cursor[t] = 0;
+    __syncthreads();
+    for (int i = t; i < n_tiles; i += blockDim.x) atomicAdd(&cursor[order_bucket(ranges[i])], 1u);
+    __syncthreads();
+    if (t < 32) {  // exclusive prefix of the kOrderBuckets (= 64) counts by one warp
+        const uint32_t a = cursor[t], b = cursor[t + 32];
+        uint32_t x = a;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (t >= o) x += y;
         }
+        const uint32_t tot_a = __shfl_sync(0xffffffffu, x, 31);
+        uint32_t z = b;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, z, o);
+            if (t >= o) z += y;
+        }
+        cursor[t] = x - a;
+        cursor[t + 32] = tot_a + z - b;
     }
     __syncthreads();
-    uint32_t *cursor = buckets + kOrderBuckets;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += gridDim.x * blockDim.x) {
-        uint32_t len = ranges[t].y - ranges[t].x;
-        uint32_t b = kOrderBuckets - 1 - min((uint32_t)(kOrderBuckets - 1), len >> kOrderShift);
-        order[start[b] + atomicAdd(&cursor[b], 1u)] = (uint32_t)t;
-    }
+    for (int i = t; i < n_tiles; i += blockDim.x) order[atomicAdd(&cursor[order_bucket(ranges[i])], 1u)] = (uint32_t)i;
 }
 
 // One stable pass over bits [shift, shift+8) by nb blocks; swaps in/out.
@@ -558,12 +564,8 @@ gs_status launch_bin_sort(gs_workspace *ws, cudaStream_t s) {
     cudaMemsetAsync(ws->ranges, 0, sizeof(uint2) * ws->n_tiles, s);
     ++ws->kernel_launches; k_ranges<<<ws->num_sms * 8, 256, 0, s>>>(ws->inst_tile, st, ws->ranges);
     // 6. raster work order
-    cudaMemsetAsync(ws->tile_buckets, 0, sizeof(uint32_t) * 2 * kOrderBuckets, s);
-    int ob = (int)std::min<int64_t>(ws->num_sms, (ws->n_tiles + 255) / 256);
     ++ws->kernel_launches;
-    k_order_hist<<<ob, 256, 0, s>>>(ws->ranges, (int)ws->n_tiles, ws->tile_buckets);
-    ++ws->kernel_launches;
-    k_order_scatter<<<ob, 256, 0, s>>>(ws->ranges, (int)ws->n_tiles, ws->tile_buckets, ws->tile_order);
+    k_tile_order<<<1, 1024, 0, s>>>(ws->ranges, (int)ws->n_tiles, ws->tile_order);
     return check_launch("ranges");
 }
 
