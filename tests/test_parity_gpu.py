@@ -24,22 +24,25 @@ GRAD_TOL = 1e-4
 MARGIN = 1e-4
 
 
-def _overlap_scene():
-    """Degree-3 box scene seen by three cameras with overlapping frusta (the
-    first camera and two seeded perturbations of it), so that many Gaussians
-    are seen by several views."""
-    sc = S.random_box_scene(8_000, 160, 120, 150.0, seed=3, sh_degree=3)
-    rng = np.random.default_rng(3)
+def _overlap_scene(n=8_000, deg=3, seed=3):
+    """Box scene seen by three cameras with overlapping frusta (the first
+    camera and two seeded perturbations of it), so that many Gaussians are
+    seen by several views."""
+    sc = S.random_box_scene(n, 160, 120, 150.0, seed=seed, sh_degree=deg)
+    rng = np.random.default_rng(seed)
     cam0 = sc.cameras[0]
     sc.cameras = [cam0] + [S.perturb_pose(cam0, rng, sigma_t=0.15, sigma_deg=4.0) for _ in range(2)]
     sc.target = rng.random(3 * sum(c.width * c.height for c in sc.cameras)).astype(np.float32)
-    sc.name = "box_overlap"
+    sc.name = f"box_overlap_deg{deg}"
     return sc
 
 
 def _scenes():
     return {
         "box_overlap": _overlap_scene(),
+        # the other SH degrees of the projection and SH adjoint kernels
+        "box_overlap_deg1": _overlap_scene(3_000, 1, 4),
+        "box_overlap_deg2": _overlap_scene(3_000, 2, 5),
         "box10k": S.random_box_scene(10_000, 320, 240, 300.0, seed=0),
         "orchard_rig": S.orchard_scene(40_000, 3, 4, 200, 120, rear=True, pose_noise=True,
                                        lidar_per_view=3000, seed=1, name="orchard_rig"),
