@@ -221,3 +221,26 @@ def test_var_empty_and_single_fragment():
     assert float(loss.cpu()[0]) == 0.0 and all(torch.count_nonzero(x).item() == 0 for x in gl)
     assert torch.count_nonzero(alp).item() == 0 and torch.count_nonzero(mean).item() == 0
     r.close()
+
+
+def test_var_tile_size_and_batch_depth_invariance():
+    """The variance rasterisers at every tile shape (their pixels per thread
+    differ) give the 16x16 images, depth mean and variance bitwise, and its
+    gradients up to the order of float atomics."""
+    sc = SCENES["orchard_rig"]
+    rng = np.random.default_rng(23)
+    n = sc.n_pix
+    up = dict(gC=rng.normal(size=3 * n), gD=0.1 * rng.normal(size=n), gA=rng.normal(size=n),
+              gmean=rng.normal(size=n), gvar=3.0 * rng.normal(size=n))
+    runs = {}
+    for (tw, th, depth) in [(16, 16, 256), (8, 8, 64), (16, 32, 128), (32, 16, 256)]:
+        g = run_gpu(sc, O.Config(tile_w=tw, tile_h=th), depth=depth, var=True, **up)
+        assert g["status"] == 0
+        runs[(tw, th, depth)] = g
+        g["renderer"].close()
+    ref = runs[(16, 16, 256)]
+    for key, g in runs.items():
+        for k in ("rgb", "depth", "alpha", "tfin", "mean", "var"):
+            assert np.array_equal(g[k], ref[k]), (key, k)
+        for k in ("g_means", "g_log_scales", "g_quats", "g_opacity_logits", "g_sh", "g_pose"):
+            assert rel_l2(g[k], ref[k]) < 1e-5, (key, k)
