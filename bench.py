@@ -167,7 +167,9 @@ def max_over_ranks(ms: float, device) -> float:
     return float(t.item())
 
 
-RASTER_SOURCES = ("paper_2510_26358_gb300/csrc/gs_raster.cu", "paper_2510_26358_gb300/csrc/gs_frag.cuh")
+# the raster kernels and the binning that makes the instance lists they read
+RASTER_SOURCES = ("paper_2510_26358_gb300/csrc/gs_raster.cu", "paper_2510_26358_gb300/csrc/gs_frag.cuh",
+                  "paper_2510_26358_gb300/csrc/gs_sort.cu")
 
 
 def raster_source_hash() -> str:
@@ -767,14 +769,18 @@ def main():
     n_inst = need
     npx = sc.n_pix
     n_tiles = step.r.info["n_tiles"]
-    # algorithmic bytes of one raster-backward launch: instance pair ids (4 B),
+    # instances in the tiles' lists (the rectangle tiles the ellipse misses
+    # are emitted, sorted last and in no list)
+    rng = step.r.buffer(G.BUF_RANGES, torch.int32).view(-1, 2).to(torch.int64)
+    n_listed = int((rng[:, 1] - rng[:, 0]).sum().item())
+    # algorithmic bytes of one raster-backward launch: listed instance pair ids (4 B),
     # visible records read once (48 B), per-pixel inputs (3 rgb + depth grads,
     # list count, final T = 24 B), tile ranges (8 B), image-space gradients of
     # the visible pairs accumulated (40 B written); the variance variant reads
     # the (mean, var, 1/W) record and the two adjoints instead of the depth
     # adjoint (44 B per pixel)
     px_bytes = 44 if args.depth_loss == "kl-var" else 24
-    alg_bytes = 4 * n_inst + 48 * nvis + px_bytes * npx + 8 * n_tiles + 40 * nvis
+    alg_bytes = 4 * n_listed + 48 * nvis + px_bytes * npx + 8 * n_tiles + 40 * nvis
     bwd_ms = kern["raster_bwd"]
     achieved = alg_bytes / (bwd_ms * 1e-3) / 1e9
     if args.depth_loss == "kl-var":
@@ -815,7 +821,8 @@ def main():
             "launches_per_step": int(launches_per_step), "roofline": roofline, "roofline_hbm": roofline_hbm,
             "per_view": per_view, "breakdown_ms": breakdown, "kernel_ms": kern, "lifecycle": lifecycle,
             "active_set": active_set,
-            "counts": {"visible_pairs": nvis, "instances": n_inst, "tiles": n_tiles}}
+            "counts": {"visible_pairs": nvis, "instances": n_inst, "listed_instances": n_listed,
+                       "tiles": n_tiles}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = {k: v for k, v in cpu_baseline(sc, args, reps=2).items()
                                 if k not in ("seconds", "pixels")}

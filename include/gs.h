@@ -130,7 +130,12 @@ gs_status gs_project(gs_workspace *ws, const gs_gaussians *g, const gs_camera *c
 /* Binning: one instance per (visible pair, covered tile), ordered by the
  * 64-bit key (global tile id << 32 | float bits of the view depth), ties by
  * (view, Gaussian index); per-tile [start, end) ranges. Stable on-device
- * radix sorts (depth of the visible pairs, then tile id of the instances). */
+ * radix sorts (depth of the visible pairs, then tile id of the instances).
+ * A tile of the pair's rectangle is covered iff the box of its pixel centres,
+ * grown by ext_abs_pad, meets the ellipse d^T Sigma'^-1 d <= 2 ln(o /
+ * alpha_min) (1 + ext_rel_pad)^2; the rectangle's other tiles are emitted
+ * with tile id 0xFFFFFFFF, sort after every list and belong to no range
+ * (the instance count and capacity cover the whole rectangles). */
 gs_status gs_bin_sort(gs_workspace *ws, void *stream);
 
 /* Front-to-back alpha compositing of every tile's list into rgb (device,
@@ -229,7 +234,8 @@ gs_status gs_workspace_info(gs_workspace *ws, int64_t *info, int32_t n_info);
  * the buffer size reported through *bytes when dst is NULL.
  * which: 0 records [n_pairs][12] f32, 1 pair depth keys [n_pairs] u32,
  * 2 tile rectangles [n_pairs][4] i16, 3 sorted instance tile ids [capacity]
- * u32, 4 sorted instance pair ids [capacity] u32, 5 tile ranges [n_tiles][2]
+ * u32 (0xFFFFFFFF, last, for a rectangle tile that is not covered), 4 sorted
+ * instance pair ids [capacity] u32, 5 tile ranges [n_tiles][2]
  * u32, 6 per-pixel list count up to the last blended fragment [N_pix] u32,
  * 7 per-pixel final T [N_pix] f32, 8 image-space gradients [n_pairs][10] f32,
  * 9 per-pixel depth (mean, var, 1/W, 0) of gs_render_fwd_var [N_pix][4] f32. */

@@ -28,10 +28,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "gs_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "liboracle.so")
 
-NCOL = 29
+NCOL = 30
 (C_VIS, C_TX0, C_TY0, C_TX1, C_TY1, C_U, C_V, C_Z, C_Z32, C_SA, C_SB, C_SC, C_QA, C_QB, C_QC,
  C_OPA, C_E, C_EX, C_EY, C_R, C_G, C_B, C_CLR, C_CLG, C_CLB, C_RGB_MARGIN, C_RECT_AMBIG,
- C_GAUSS, C_VIEW) = range(29)
+ C_GAUSS, C_VIEW, C_NTILE) = range(30)
 NGRAD = 10
 G_U, G_V, G_QA, G_QB, G_QC, G_LNO, G_R, G_G, G_B, G_Z = range(10)
 
@@ -59,7 +59,8 @@ class _Config(ctypes.Structure):
                 ("alpha_min", ctypes.c_double), ("alpha_max", ctypes.c_double),
                 ("t_min", ctypes.c_double), ("jac_clamp", ctypes.c_double),
                 ("ext_rel_pad", ctypes.c_double), ("ext_abs_pad", ctypes.c_double),
-                ("rect_eps_abs", ctypes.c_double), ("rect_eps_rel", ctypes.c_double)]
+                ("rect_eps_abs", ctypes.c_double), ("rect_eps_rel", ctypes.c_double),
+                ("tile_eps_rel", ctypes.c_double), ("tile_eps_cond", ctypes.c_double)]
 
 
 @dataclass
@@ -76,13 +77,16 @@ class Config:
     ext_abs_pad: float = 1e-2
     rect_eps_abs: float = 1e-4
     rect_eps_rel: float = 1e-5
+    tile_eps_rel: float = 1e-3
+    tile_eps_cond: float = 2.0 ** -20
 
     def c(self) -> _Config:
         # the float32 values the GPU path uses, widened exactly
         f = lambda x: float(np.float32(x))
         return _Config(self.tile_w, self.tile_h, f(self.near_z), f(self.dilation), f(self.alpha_min),
                        f(self.alpha_max), f(self.t_min), f(self.jac_clamp), f(self.ext_rel_pad),
-                       f(self.ext_abs_pad), self.rect_eps_abs, self.rect_eps_rel)
+                       f(self.ext_abs_pad), self.rect_eps_abs, self.rect_eps_rel, self.tile_eps_rel,
+                       self.tile_eps_cond)
 
 
 _lib = None

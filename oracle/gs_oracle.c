@@ -27,6 +27,13 @@
  *       its tile rectangle covers the pixel centres inside the padded
  *       axis-aligned extent of the ellipse {d : d^T Q d <= 2 ln(o/alpha_min)}.
  *       Images therefore do not depend on the tile size.
+ *   R6b a tile of that rectangle holds an instance iff the box of its pixel
+ *       centres (clipped to the image), grown by ext_abs_pad on every side,
+ *       meets the padded ellipse {d : d^T Q d <= E (1 + ext_rel_pad)^2},
+ *       E = 2 ln(o/alpha_min): the rectangle's corner tiles that the ellipse
+ *       misses hold no pixel the Gaussian reaches and get no instance.  Only
+ *       the instance lists change: every pixel with alpha >= alpha_min lies
+ *       in a kept tile, so images do not depend on this reading.
  *   R7  colour: real orthonormal SH basis without Condon-Shortley phase,
  *       ordered by l then m=-l..l, evaluated at the unit direction from the
  *       camera centre to the mean; rgb = max(0.5 + sum_k c_k Y_k, 0).
@@ -73,6 +80,9 @@ typedef struct {
     double near_z, dilation, alpha_min, alpha_max, t_min, jac_clamp;
     double ext_rel_pad, ext_abs_pad; /* padding of the extent used for tile rectangles */
     double rect_eps_abs, rect_eps_rel; /* width of the ambiguity band for rect decisions */
+    double tile_eps_rel, tile_eps_cond; /* relative band of the R6b tile decisions: rel + cond *
+                                         * (a c + b^2) / det of Sigma' (the rounding of the
+                                         * inverse grows with its condition) */
 } oc_config;
 
 /* columns of a projected record (one row of OC_NCOL doubles per pair) */
@@ -85,8 +95,9 @@ enum {
     C_R, C_G, C_B,                        /* colour */
     C_CLR, C_CLG, C_CLB,                  /* 1 where the colour is clamped at 0 */
     C_RGB_MARGIN,                         /* min |0.5 + sum c Y| over channels */
-    C_RECT_AMBIG,                         /* 1 if a rect decision lies inside the eps band */
+    C_RECT_AMBIG,                         /* 1 if a rect or tile decision lies inside the eps band */
     C_GAUSS, C_VIEW,                      /* Gaussian index, view index */
+    C_NTILE,                              /* tiles of the rectangle that hold an instance (R6b) */
     OC_NCOL
 };
 
@@ -273,6 +284,45 @@ static int64_t hi_tile(double a, int W, int tw) {
     return (int64_t)p / tw;
 }
 
+/* R6b: minimum of d^T Q d over the box [x0, x1] x [y0, y1] of offsets d from
+ * the mean.  Q is positive definite, so the minimum is 0 when the box holds
+ * the mean and otherwise lies on one of the four edges, where q is a convex
+ * parabola along the edge minimised at its stationary point clamped to the
+ * edge. */
+static double box_min_q(const double *r, double x0, double x1, double y0, double y1) {
+    double qa = r[C_QA], qb = r[C_QB], qc = r[C_QC];
+    if (x0 <= 0.0 && 0.0 <= x1 && y0 <= 0.0 && 0.0 <= y1) return 0.0;
+    double best = INFINITY;
+    double xs[2] = {x0, x1}, ys[2] = {y0, y1};
+    for (int i = 0; i < 2; ++i) {
+        double x = xs[i], y = dmin(dmax(-qb * x / qc, y0), y1); /* edge dx = x */
+        best = dmin(best, qa * x * x + 2.0 * qb * x * y + qc * y * y);
+        y = ys[i];
+        x = dmin(dmax(-qb * y / qa, x0), x1); /* edge dy = y */
+        best = dmin(best, qa * x * x + 2.0 * qb * x * y + qc * y * y);
+    }
+    return best;
+}
+
+/* R6b: minimum of d^T Q d over the pixel centres of tile (tx, ty), clipped
+ * to the image, with the box grown by `grow` pixels on every side */
+static double tile_min_q(const double *r, int64_t tx, int64_t ty, const oc_camera *cam,
+                         const oc_config *cfg, double grow) {
+    int64_t X0 = tx * cfg->tile_w, Y0 = ty * cfg->tile_h;
+    int64_t X1 = (X0 + cfg->tile_w < cam->width ? X0 + cfg->tile_w : cam->width) - 1;
+    int64_t Y1 = (Y0 + cfg->tile_h < cam->height ? Y0 + cfg->tile_h : cam->height) - 1;
+    return box_min_q(r, (double)X0 + 0.5 - r[C_U] - grow, (double)X1 + 0.5 - r[C_U] + grow,
+                     (double)Y0 + 0.5 - r[C_V] - grow, (double)Y1 + 0.5 - r[C_V] + grow);
+}
+
+static double tile_threshold(const double *r, const oc_config *cfg) {
+    return r[C_E] * (1.0 + cfg->ext_rel_pad) * (1.0 + cfg->ext_rel_pad);
+}
+
+static int tile_kept(const double *r, int64_t tx, int64_t ty, const oc_camera *cam, const oc_config *cfg) {
+    return tile_min_q(r, tx, ty, cam, cfg, cfg->ext_abs_pad) <= tile_threshold(r, cfg);
+}
+
 static void project_pair(const double *mu, const double *ls, const double *q, double omega,
                          const double *sh, int sh_degree, const oc_camera *cam,
                          const oc_config *cfg, double *rec) {
@@ -363,6 +413,23 @@ static void project_pair(const double *mu, const double *ls, const double *q, do
     rec[C_TY0] = (double)lo_tile(ya, th);
     rec[C_TY1] = (double)hi_tile(yb, cam->height, th);
     rec[C_VIS] = 1.0;
+    /* R6b: kept tiles, and whether a small perturbation of a tile's box (the
+     * pixel band of the rectangle decisions) or of the threshold (relative
+     * band eta) changes a decision */
+    {
+        double thr = tile_threshold(rec, cfg);
+        double eps = cfg->rect_eps_abs + cfg->rect_eps_rel * (dmax(ex, ey) + dmax(tw, th));
+        double eta = cfg->tile_eps_rel + cfg->tile_eps_cond * (a * c + b * b) / det;
+        int64_t kept = 0;
+        for (int64_t ty = (int64_t)rec[C_TY0]; ty <= (int64_t)rec[C_TY1]; ++ty)
+            for (int64_t tx = (int64_t)rec[C_TX0]; tx <= (int64_t)rec[C_TX1]; ++tx) {
+                kept += tile_kept(rec, tx, ty, cam, cfg);
+                int hi = tile_min_q(rec, tx, ty, cam, cfg, cfg->ext_abs_pad + eps) <= thr * (1.0 + eta);
+                int lo = tile_min_q(rec, tx, ty, cam, cfg, cfg->ext_abs_pad - eps) <= thr * (1.0 - eta);
+                if (hi != lo) rec[C_RECT_AMBIG] = 1.0;
+            }
+        rec[C_NTILE] = (double)kept;
+    }
     /* R7: view-dependent colour from the camera centre C = -R^T t */
     double Cb[3];
     for (int i = 0; i < 3; ++i) Cb[i] = -(RbT[3 * i + 0] * T[3] + RbT[3 * i + 1] * T[7] + RbT[3 * i + 2] * T[11]);
@@ -420,20 +487,21 @@ static int inst_cmp(const void *pa, const void *pb) {
 
 static uint32_t float_bits(float f) { uint32_t u; memcpy(&u, &f, 4); return u; }
 
-/* Count instances: sum over visible pairs of their rectangle areas. */
+/* Count instances: sum over visible pairs of their kept tiles (R6b). */
 int64_t oracle_count_instances(int64_t n_pairs, const double *rec) {
     int64_t total = 0;
     for (int64_t p = 0; p < n_pairs; ++p) {
         const double *r = rec + p * OC_NCOL;
         if (r[C_VIS] == 0.0) continue;
-        total += (int64_t)(r[C_TX1] - r[C_TX0] + 1) * (int64_t)(r[C_TY1] - r[C_TY0] + 1);
+        total += (int64_t)r[C_NTILE];
     }
     return total;
 }
 
-/* Emit one key per (visible pair, covered tile) in pair order with the tiles of
- * a rectangle row-major, key = (global tile << 32) | bits(z32); stable sort by
- * key; ranges[2t], ranges[2t+1] = [first, end) of tile t (0,0 when empty). */
+/* Emit one key per (visible pair, kept tile of its rectangle, R6b) in pair
+ * order with the tiles of a rectangle row-major, key = (global tile << 32) |
+ * bits(z32); stable sort by key; ranges[2t], ranges[2t+1] = [first, end) of
+ * tile t (0,0 when empty). */
 int oracle_bin(int n_views, const oc_camera *cams, const int64_t *submap_offsets,
                const oc_config *cfg, const double *rec, uint64_t *keys_out, int64_t *vals_out,
                int64_t *ranges) {
@@ -452,6 +520,7 @@ int oracle_bin(int n_views, const oc_camera *cams, const int64_t *submap_offsets
             uint32_t zb = float_bits((float)r[C_Z32]);
             for (int64_t ty = (int64_t)r[C_TY0]; ty <= (int64_t)r[C_TY1]; ++ty)
                 for (int64_t tx = (int64_t)r[C_TX0]; tx <= (int64_t)r[C_TX1]; ++tx) {
+                    if (!tile_kept(r, tx, ty, &cams[v], cfg)) continue;
                     uint64_t tile = (uint64_t)(V[v].tile_off + ty * V[v].ntx + tx);
                     I[m].key = (tile << 32) | zb;
                     I[m].seq = m;

@@ -211,8 +211,10 @@ gs_status gs_workspace_create(const gs_camera *cams, int32_t n_views, const int6
     ws->n_pairs = pair_off;
     ws->n_tiles = tile_off;
     ws->n_pix = pix_off;
+    // bits of the largest value n_tiles (not n_tiles - 1): the sort then
+    // orders the dropped instances' kInvalidKey after every real tile id
     ws->tile_bits = 0;
-    while ((1ll << ws->tile_bits) < ws->n_tiles) ++ws->tile_bits;
+    while ((1ll << ws->tile_bits) <= ws->n_tiles) ++ws->tile_bits;
     int maxv = 1;
     for (int s = 0; s < n_submaps; ++s) maxv = std::max(maxv, nviews[s]);
     ws->max_views_per_submap = maxv;

@@ -358,6 +358,51 @@ __global__ void __launch_bounds__(T) k_instance_offsets(const DevState *st, cons
 // window-start table (the pairs owning its first slot and the next window's),
 // stages them in shared memory, and every thread writes one instance per
 // step, locating its pair by binary search in the stage.
+//
+// A rectangle tile that the Gaussian's padded alpha >= alpha_min ellipse
+// misses (about a fifth of them on wide scenes: the corners of the rectangles
+// of large or tilted ellipses) is written with tile id kInvalidKey.  The tile
+// sort puts these after every real tile (the sort covers whole bytes above
+// the highest tile id), the ranges skip them, and the rasterisers never walk
+// them.
+
+// Does the tile whose pixels span [X0, X1] x [Y0, Y1] hold an instance of the
+// pair with record r0 = (U, V, hx, hy), r1 = (l11, l12, l22, log2 o)?  The
+// rasterisers keep a fragment where log2 o - |t|^2 >= log2 alpha_min, with
+// t = L d, L = [[l11, l12], [0, l22]] and d = (px - U + hx, py - V + hy) the
+// offset of pixel (px, py)'s centre from the mean.  The tile is kept iff the
+// minimum of |L d|^2 over the box of its pixel centres, grown by ext_abs_pad,
+// is within (log2 o - log2 alpha_min) (1 + ext_rel_pad)^2: the same padding as
+// the rectangle's extents, which dwarfs the rounding of this test and of the
+// rasterisers' own evaluation, so a dropped tile has no fragment to keep.  The
+// minimum of the convex quadratic is 0 when the box holds the mean, else it
+// lies on an edge, at the edge's stationary point clamped to the edge.
+__device__ __forceinline__ bool tile_reached(const float4 r0, const float4 r1, int X0, int X1, int Y0, int Y1,
+                                             const Consts &k) {
+    const float ax = __fadd_rn((float)X0 - r0.x, r0.z) - k.ext_abs_pad;
+    const float bx = __fadd_rn((float)X1 - r0.x, r0.z) + k.ext_abs_pad;
+    const float ay = __fadd_rn((float)Y0 - r0.y, r0.w) - k.ext_abs_pad;
+    const float by = __fadd_rn((float)Y1 - r0.y, r0.w) + k.ext_abs_pad;
+    if (ax <= 0.f && bx >= 0.f && ay <= 0.f && by >= 0.f) return true;
+    const float l11 = r1.x, l12 = r1.y, l22 = r1.z;
+    const float pad = 1.f + k.ext_rel_pad;
+    const float thr = (r1.w - k.log2_alpha_min) * pad * pad;
+    const float sy = -l11 * l12 / (l12 * l12 + l22 * l22);  // stationary dy / dx on an edge dx = const
+    const float sx = -l12 / l11;                            // stationary dx / dy on an edge dy = const
+    float m = INFINITY;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const float cx = e ? bx : ax;
+        const float dy = fminf(fmaxf(sy * cx, ay), by);
+        const float t1 = l11 * cx + l12 * dy, t2 = l22 * dy;
+        m = fminf(m, t1 * t1 + t2 * t2);
+        const float cy = e ? by : ay;
+        const float dx = fminf(fmaxf(sx * cy, ax), bx);
+        const float u1 = l11 * dx + l12 * cy, u2 = l22 * cy;
+        m = fminf(m, u1 * u1 + u2 * u2);
+    }
+    return m <= thr;
+}
 
 __device__ __forceinline__ uint32_t last_le(const uint32_t *a, uint32_t n, uint32_t x) {
     // largest i < n with a[i] <= x (a nondecreasing, a[0] <= x)
@@ -370,14 +415,14 @@ __device__ __forceinline__ uint32_t last_le(const uint32_t *a, uint32_t n, uint3
 }
 
 __global__ void __launch_bounds__(T) k_emit_instances(const uint32_t *vis_pair, const short4 *rect,
-                                                     const ViewInfo *views, int n_views,
-                                                     const DevState *st, const uint32_t *ioff,
+                                                     const float4 *rec, const ViewInfo *views, int n_views,
+                                                     const Consts k, const DevState *st, const uint32_t *ioff,
                                                      const uint32_t *win_pair, uint32_t *inst_tile,
                                                      uint32_t *inst_val) {
     __shared__ uint32_t s_off[kEmitWindow];
     __shared__ uint32_t s_pair[kEmitWindow];
     __shared__ short4 s_rect[kEmitWindow];
-    __shared__ int2 s_view[kEmitWindow];  // (tile_off, ntx) of the pair's view
+    __shared__ int4 s_view[kEmitWindow];  // (tile_off, ntx, W, H) of the pair's view
     __shared__ uint32_t s_range[2];
     if (st->flags & kFlagCapacity) return;
     const uint32_t n = st->n_vis, total = st->n_inst;
@@ -400,37 +445,44 @@ __global__ void __launch_bounds__(T) k_emit_instances(const uint32_t *vis_pair, 
         }
         __syncthreads();
         const uint32_t s0 = s_range[0], np = s_range[1] - s0 + 1;  // np <= window: every pair has >= 1 slot
-        for (uint32_t k = t; k < np; k += T) {
-            const uint32_t pair = vis_pair[s0 + k];
+        for (uint32_t j = t; j < np; j += T) {
+            const uint32_t pair = vis_pair[s0 + j];
             int lo_v = 0, hi_v = n_views - 1;
             while (lo_v < hi_v) {
                 int mid = (lo_v + hi_v + 1) >> 1;
                 if ((uint32_t)views[mid].pair_off <= pair) lo_v = mid; else hi_v = mid - 1;
             }
-            s_off[k] = ioff[s0 + k];
-            s_pair[k] = pair;
-            s_rect[k] = rect[pair];
-            s_view[k] = make_int2(views[lo_v].tile_off, views[lo_v].ntx);
+            s_off[j] = ioff[s0 + j];
+            s_pair[j] = pair;
+            s_rect[j] = rect[pair];
+            s_view[j] = make_int4(views[lo_v].tile_off, views[lo_v].ntx, views[lo_v].W, views[lo_v].H);
         }
         __syncthreads();
         for (uint32_t o = o0 + t; o < o1; o += T) {
             const uint32_t a = last_le(s_off, np, o);
             const short4 r = s_rect[a];
-            const int2 vw = s_view[a];
+            const int4 vw = s_view[a];
+            const uint32_t pair = s_pair[a];
             const int wdt = (int)r.z - (int)r.x + 1;
             const int local = (int)(o - s_off[a]);
             const int ty = r.y + local / wdt, tx = r.x + local % wdt;
-            inst_tile[o] = (uint32_t)(vw.x + ty * vw.y + tx);
-            inst_val[o] = s_pair[a];
+            const int X0 = tx * k.tile_w, Y0 = ty * k.tile_h;
+            const bool keep = tile_reached(__ldg(rec + 3 * pair), __ldg(rec + 3 * pair + 1), X0,
+                                           min(X0 + k.tile_w, vw.z) - 1, Y0, min(Y0 + k.tile_h, vw.w) - 1, k);
+            inst_tile[o] = keep ? (uint32_t)(vw.x + ty * vw.y + tx) : kInvalidKey;
+            inst_val[o] = pair;
         }
         __syncthreads();
     }
 }
 
-__global__ void k_ranges(const uint32_t *tile, const DevState *st, uint2 *ranges) {
+// [start, end) of every tile's run in the sorted instances; the dropped
+// rectangle tiles (kInvalidKey, sorted last) belong to no tile
+__global__ void k_ranges(const uint32_t *tile, const DevState *st, uint32_t n_tiles, uint2 *ranges) {
     uint32_t n = st->n_inst;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         uint32_t t = tile[i];
+        if (t >= n_tiles) continue;
         if (i == 0 || tile[i - 1] != t) ranges[t].x = i;
         if (i + 1 == n || tile[i + 1] != t) ranges[t].y = i + 1;
     }
@@ -549,8 +601,8 @@ gs_status launch_bin_sort(gs_workspace *ws, cudaStream_t s) {
     ++ws->kernel_launches; k_instance_offsets<<<nb, T, 0, s>>>(st, ws->part, nb, ws->ioff, ws->win_pair,
                                                                   (uint32_t)(ws->inst_cap / kEmitWindow + 2));
     ++ws->kernel_launches;
-    k_emit_instances<<<4 * ws->num_sms, T, 0, s>>>(v, ws->rect, ws->views, ws->n_views, st, ws->ioff, ws->win_pair,
-                                                   tk, tv);
+    k_emit_instances<<<4 * ws->num_sms, T, 0, s>>>(v, ws->rect, ws->rec, ws->views, ws->n_views, ws->consts, st,
+                                                   ws->ioff, ws->win_pair, tk, tv);
     if ((r = check_launch("emit")) != GS_OK) return r;
     }
     // 4. stable sort of the instances by tile id
@@ -562,7 +614,8 @@ gs_status launch_bin_sort(gs_workspace *ws, cudaStream_t s) {
     // 5. ranges
     StageTimer timer(ws, GS_STAGE_RANGES, s);
     cudaMemsetAsync(ws->ranges, 0, sizeof(uint2) * ws->n_tiles, s);
-    ++ws->kernel_launches; k_ranges<<<ws->num_sms * 8, 256, 0, s>>>(ws->inst_tile, st, ws->ranges);
+    ++ws->kernel_launches;
+    k_ranges<<<ws->num_sms * 8, 256, 0, s>>>(ws->inst_tile, st, (uint32_t)ws->n_tiles, ws->ranges);
     // 6. raster work order
     ++ws->kernel_launches;
     k_tile_order<<<1, 1024, 0, s>>>(ws->ranges, (int)ws->n_tiles, ws->tile_order);

@@ -57,8 +57,14 @@ def run_gpu(sc, ocfg: O.Config, gC=None, gD=None, gA=None, depth=256, inst_capac
     out["pkey"] = r.buffer(G.BUF_PAIR_KEYS, torch.int32).cpu().numpy().view(np.uint32)
     out["rect"] = r.buffer(G.BUF_RECTS, torch.int16).cpu().numpy().reshape(-1, 4)
     m = min(n_inst, r.info["inst_capacity"]) if st == G.GS_OK else 0
-    out["inst_tile"] = r.buffer(G.BUF_INST_TILES, torch.int32).cpu().numpy().view(np.uint32)[:m]
-    out["inst_pair"] = r.buffer(G.BUF_INST_PAIRS, torch.int32).cpu().numpy().view(np.uint32)[:m]
+    tiles = r.buffer(G.BUF_INST_TILES, torch.int32).cpu().numpy().view(np.uint32)[:m]
+    pairs = r.buffer(G.BUF_INST_PAIRS, torch.int32).cpu().numpy().view(np.uint32)[:m]
+    # the rectangle tiles that the ellipse misses carry tile id 0xFFFFFFFF and
+    # sort after every real tile: the lists proper are the prefix
+    kept = int(np.count_nonzero(tiles != 0xFFFFFFFF))
+    assert np.all(tiles[kept:] == 0xFFFFFFFF), "dropped instances not sorted last"
+    out["inst_tile"], out["inst_pair"] = tiles[:kept], pairs[:kept]
+    out["dropped_pair"] = pairs[kept:]
     out["ranges"] = r.buffer(G.BUF_RANGES, torch.int32).cpu().numpy().view(np.uint32).reshape(-1, 2)
     out["last"] = r.buffer(G.BUF_LAST, torch.int32).cpu().numpy().view(np.uint32)
     out["tfin"] = r.buffer(G.BUF_TFIN, torch.float32).cpu().numpy()

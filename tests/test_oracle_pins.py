@@ -9,8 +9,11 @@ sign, a transposed operand or a wrong index in the oracle fails at least one:
   colour                    SH orthonormality by quadrature; DC reproduces rgb
   compositing               single-Gaussian closed form; stacked-alpha closed
                             form with the stop rule; sum of weights = alpha
-  binning                   keys rebuilt with numpy's stable sort; brute-force
-                            renderer (no tiles) equal bitwise for 3 tile sizes
+  binning                   keys rebuilt with numpy's stable sort, each tile's
+                            test redone as a bounded least-squares problem
+                            (scipy's BVLS); every pixel with alpha >= alpha_min
+                            in a kept tile (brute force); brute-force renderer
+                            (no tiles) equal bitwise for 3 tile sizes
   backward                  central differences of every parameter type and
                             every pose twist; translation identity
   losses (Eqs. 6-7)         KL by numerical integration; FD of both losses
@@ -34,6 +37,7 @@ from paper_2510_26358_gb300 import scenes as S
 
 scipy = pytest.importorskip("scipy")
 from scipy.spatial.transform import Rotation  # noqa: E402
+from scipy.optimize import lsq_linear  # noqa: E402
 
 
 CFG = O.Config()
@@ -264,9 +268,15 @@ def test_keys_rebuilt_with_numpy_stable_sort():
     cams = O.as_float32_cameras(sc.cameras)
     rec = O.project(P, cams, cfg)
     keys, vals, ranges = O.bin(P, cams, cfg, rec)
-    # independent rebuild: per view, per visible pair, per tile; then argsort
+    cc = cfg.c()
+    rho, kappa = cc.ext_rel_pad, cc.ext_abs_pad
+    # independent rebuild: per view, per visible pair, per tile of its
+    # rectangle; the tile is kept iff min ||L d||^2 over the tile's grown box
+    # of pixel-centre offsets d (Q = L^T L) is within the padded threshold,
+    # solved as bounded linear least squares; then argsort
     ek, ev = [], []
     toff, poff = 0, 0
+    n_rect = n_reach = 0
     for v, c in enumerate(cams):
         ntx, nty = -(-c.width // 8), -(-c.height // 8)
         ng = int(sc.submap_offsets[c.submap + 1] - sc.submap_offsets[c.submap])
@@ -274,14 +284,31 @@ def test_keys_rebuilt_with_numpy_stable_sort():
             r = rec[poff + k]
             if r[O.C_VIS] == 0:
                 continue
+            Q = np.array([[r[O.C_QA], r[O.C_QB]], [r[O.C_QB], r[O.C_QC]]])
+            L = np.linalg.cholesky(Q).T
+            thr = r[O.C_E] * (1 + rho) ** 2
             zb = np.array([r[O.C_Z32]], np.float32).view(np.uint32)[0]
             for ty in range(int(r[O.C_TY0]), int(r[O.C_TY1]) + 1):
                 for tx in range(int(r[O.C_TX0]), int(r[O.C_TX1]) + 1):
-                    ek.append((np.uint64(toff + ty * ntx + tx) << np.uint64(32)) | np.uint64(zb))
-                    ev.append(poff + k)
+                    n_rect += 1
+                    px = np.arange(tx * 8, min(tx * 8 + 8, c.width)) + 0.5 - r[O.C_U]
+                    py = np.arange(ty * 8, min(ty * 8 + 8, c.height)) + 0.5 - r[O.C_V]
+                    lo, hi = [px[0] - kappa, py[0] - kappa], [px[-1] + kappa, py[-1] + kappa]
+                    qmin = 2 * lsq_linear(L, np.zeros(2), bounds=(lo, hi), method="bvls").cost
+                    assert abs(qmin - thr) > 1e-9 * thr  # no decision this close in the fixture
+                    # brute force: a pixel where the Gaussian reaches alpha_min lies in a kept tile
+                    dx, dy = np.meshgrid(px, py)
+                    reach = (Q[0, 0] * dx * dx + 2 * Q[0, 1] * dx * dy + Q[1, 1] * dy * dy <= r[O.C_E]).any()
+                    assert qmin <= thr or not reach
+                    if qmin <= thr:
+                        n_reach += reach
+                        ek.append((np.uint64(toff + ty * ntx + tx) << np.uint64(32)) | np.uint64(zb))
+                        ev.append(poff + k)
         toff += ntx * nty
         poff += ng
     ek, ev = np.array(ek, np.uint64), np.array(ev, np.int64)
+    # the fixture exercises both outcomes: corner tiles dropped, most kept ones reached
+    assert n_rect - len(ek) >= 50 and n_reach > 0.8 * len(ek), (n_rect, len(ek), n_reach)
     order = np.argsort(ek, kind="stable")
     assert np.array_equal(keys, ek[order]) and np.array_equal(vals, ev[order])
     tiles = (keys >> np.uint64(32)).astype(np.int64)

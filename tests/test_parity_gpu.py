@@ -120,6 +120,19 @@ def test_keys_and_ranges_bit_exact(case):
     keep_o = ~np.isin(ovals, amb_pairs)
     assert np.array_equal(gkeys[keep_g], okeys[keep_o]), "sorted keys differ"
     assert np.array_equal(gp[keep_g], ovals[keep_o]), "instance order differs"
+    # every rectangle tile is emitted once, listed or dropped; the dropped
+    # ones are the tiles the oracle's exact test rejects
+    vis_g = g["pkey"] != 0xFFFFFFFF
+    rect = g["rect"].astype(np.int64)
+    area = np.where(vis_g, (rect[:, 2] - rect[:, 0] + 1) * (rect[:, 3] - rect[:, 1] + 1), 0)
+    n = len(area)
+    drop_g = np.bincount(g["dropped_pair"].astype(np.int64), minlength=n)
+    assert np.array_equal(np.bincount(gp, minlength=n) + drop_g, area)
+    vis_o = rec[:, O.C_VIS] > 0
+    rect_o = (rec[:, O.C_TX1] - rec[:, O.C_TX0] + 1) * (rec[:, O.C_TY1] - rec[:, O.C_TY0] + 1)
+    drop_o = np.where(vis_o, rect_o - rec[:, O.C_NTILE], 0).astype(np.int64)
+    ok = ~np.isin(np.arange(n), amb_pairs)
+    assert np.array_equal(drop_g[ok], drop_o[ok])
     if len(amb_pairs) == 0:
         assert np.array_equal(g["ranges"].astype(np.int64), case["ranges"])
     else:
@@ -129,7 +142,8 @@ def test_keys_and_ranges_bit_exact(case):
             s, e = g["ranges"][t]
             assert np.all(tiles[s:e] == t)
         assert g["ranges"][:, 1].astype(np.int64).sum() - g["ranges"][:, 0].astype(np.int64).sum() == len(tiles)
-    print(f"[{case['name']}] instances {len(gkeys)}, ambiguous pairs {len(amb_pairs)}")
+    print(f"[{case['name']}] instances {len(gkeys)} listed, {drop_g.sum()} dropped, "
+          f"ambiguous pairs {len(amb_pairs)}")
 
 
 def test_forward_images(case):
