@@ -53,6 +53,25 @@ def test_tile_size_and_batch_depth_invariance():
             assert rel_l2(g[k], ref[k]) < 1e-5, (key, k)
 
 
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (32, 16)])
+def test_plain_forward_matches_scalar_variance_forward_bitwise(tile):
+    """The plain forward works its pixels in packed f32x2 pairs, the variance
+    forward one pixel at a time; both must give the same images, final
+    transmittance and list counts bit for bit (one and two pairs a thread)."""
+    sc = _scene()
+    cfg = O.Config(tile_w=tile[0], tile_h=tile[1])
+    g0 = run_gpu(sc, cfg, depth=64)
+    g1 = run_gpu(sc, cfg, depth=64, var=True)
+    try:
+        assert g0["status"] == 0 and g1["status"] == 0
+        for k in ("rgb", "depth", "tfin", "last"):
+            assert np.array_equal(g0[k].view(np.uint32), g1[k].view(np.uint32)), k
+        assert (g0["last"] > 0).mean() > 0.3
+    finally:
+        g0["renderer"].close()
+        g1["renderer"].close()
+
+
 def test_graph_replay_matches_eager():
     torch, dev = torch_dev()
     G = _G()
