@@ -10,6 +10,8 @@ Parity status per function (see the pins in ``tests/test_oracle_pins.py``):
   project      pinned: closed forms (covariance eigen-structure, isotropic
                on-axis image covariance, pinhole), SH orthonormality, FD of J
   bin          pinned: brute-force renderer equality, independent key rebuild
+               with every tile decision redone by bounded least squares, every
+               reached pixel in a kept tile (brute force)
   render_fwd   pinned: single-Gaussian closed form, T invariants, brute force
   render_bwd   pinned: central finite differences, translation identity
   depth_loss   pinned: KL closed form vs numerical integration, FD
