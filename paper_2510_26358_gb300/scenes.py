@@ -169,6 +169,23 @@ def random_box_scene(n=10_000, width=320, height=240, f=300.0, seed=0,
                  name=f"box{n}_{width}x{height}")
 
 
+def needle_scene(n=4_000, width=160, height=120, f=150.0, seed=6, long_log_scale=(-2.2, -0.8),
+                 thin_log_scale=(-6.0, -5.0)) -> Scene:
+    """The box scene with needle-shaped Gaussians: one axis log-uniform in
+    `long_log_scale`, the other two in `thin_log_scale` (below the pixel, so
+    the image covariance is a long ellipse about as wide as the dilation),
+    random orientations.  Their tile rectangles are mostly corners the
+    ellipse misses, and their image covariances are badly conditioned."""
+    sc = random_box_scene(n, width, height, f, seed=seed)
+    rng = np.random.Generator(np.random.PCG64(seed + 1000))
+    ls = np.empty((n, 3))
+    ls[:, 0] = rng.uniform(*long_log_scale, n)
+    ls[:, 1:] = rng.uniform(*thin_log_scale, (n, 2))
+    sc.log_scales = ls.astype(np.float32)
+    sc.name = f"needles{n}_{width}x{height}"
+    return sc
+
+
 # ----------------------------------------------------------------------------
 # orchard scenes
 # ----------------------------------------------------------------------------

@@ -248,10 +248,14 @@ def test_weights_sum_to_alpha():
 # binning and tiling
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("tile", [(8, 8), (16, 16), (16, 32)])
-def test_tiled_equals_brute_force(tile):
+@pytest.mark.parametrize("tile,scene", [((8, 8), "box"), ((16, 16), "box"), ((16, 32), "box"),
+                                        ((8, 8), "needles")])
+def test_tiled_equals_brute_force(tile, scene):
     cfg = O.Config(tile_w=tile[0], tile_h=tile[1])
-    sc = S.random_box_scene(500, 72, 56, 60.0, seed=11, sh_degree=3)
+    if scene == "box":
+        sc = S.random_box_scene(500, 72, 56, 60.0, seed=11, sh_degree=3)
+    else:  # most rectangle tiles dropped by the tile-exact rule
+        sc = S.needle_scene(400, 72, 56, 60.0, seed=12)
     P = O.Params.from_scene(sc)
     cams = O.as_float32_cameras(sc.cameras)
     rec, keys, vals, ranges, out = O.forward(P, cams, cfg)
@@ -261,9 +265,13 @@ def test_tiled_equals_brute_force(tile):
     assert out["nblend"].max() >= 3
 
 
-def test_keys_rebuilt_with_numpy_stable_sort():
+@pytest.mark.parametrize("scene", ["submaps", "needles"])
+def test_keys_rebuilt_with_numpy_stable_sort(scene):
     cfg = O.Config(tile_w=8, tile_h=8)
-    sc = S.uneven_submaps(3, 200, 800, seed=4, scale=1.0, resolutions=((48, 40), (64, 32)))
+    if scene == "submaps":
+        sc = S.uneven_submaps(3, 200, 800, seed=4, scale=1.0, resolutions=((48, 40), (64, 32)))
+    else:  # long thin ellipses: most rectangle tiles dropped, badly conditioned covariances
+        sc = S.needle_scene(600, 96, 72, 90.0, seed=7)
     P = O.Params.from_scene(sc)
     cams = O.as_float32_cameras(sc.cameras)
     rec = O.project(P, cams, cfg)
