@@ -249,6 +249,7 @@ struct PairGeom {
     float WM[9];                  // W R S
     float r0[3], r1[3];           // rows of J W R S
     float a, b, c, det;           // Sigma' and its determinant
+    float cx, cy, cz;             // r0 x r1 (its 2x2 minors)
 };
 
 __device__ __forceinline__ void pair_geom(const Cam &cam, int W, int H, const Consts &k, float px, float py,
@@ -285,10 +286,10 @@ __device__ __forceinline__ void pair_geom(const Cam &cam, int W, int H, const Co
     G.b = G.r0[0] * G.r1[0] + G.r0[1] * G.r1[1] + G.r0[2] * G.r1[2];
     G.a = n0 + k.dilation;
     G.c = n1 + k.dilation;
-    float cx = diff_prod(G.r0[1], G.r1[2], G.r0[2], G.r1[1]);
-    float cy = diff_prod(G.r0[2], G.r1[0], G.r0[0], G.r1[2]);
-    float cz = diff_prod(G.r0[0], G.r1[1], G.r0[1], G.r1[0]);
-    G.det = (cx * cx + cy * cy + cz * cz) + k.dilation * (n0 + n1) + k.dilation * k.dilation;
+    G.cx = diff_prod(G.r0[1], G.r1[2], G.r0[2], G.r1[1]);
+    G.cy = diff_prod(G.r0[2], G.r1[0], G.r0[0], G.r1[2]);
+    G.cz = diff_prod(G.r0[0], G.r1[1], G.r0[1], G.r1[0]);
+    G.det = (G.cx * G.cx + G.cy * G.cy + G.cz * G.cz) + k.dilation * (n0 + n1) + k.dilation * k.dilation;
 }
 
 template <int DEG>
@@ -638,6 +639,7 @@ __global__ void __launch_bounds__(kProjBwdThreads, 512 / kProjBwdThreads) k_proj
         float o = 1.f / (1.f + expf(-om));
 
         float gmu[3] = {0, 0, 0}, gM[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, gom = 0.f;
+        float gls[3] = {0, 0, 0};
         float dacc = 0.f;
         int dcnt = 0;
         for (;;) {
@@ -685,6 +687,32 @@ __global__ void __launch_bounds__(kProjBwdThreads, 512 / kProjBwdThreads) k_proj
                     float Ma = -(QG00 * Qa + QG01 * Qb);
                     float Mb = -(QG00 * Qb + QG01 * Qc);
                     float Mc = -(QG10 * Qb + QG11 * Qc);
+                    // log-scales: M = R diag(S) scales column k of T2 = J W M (v_k,
+                    // the image-space axis k), so dL/dls_k = v_k . 2 dL/dSigma' v_k
+                    // = -2 Y_k^T G Y_k with Y_k = Sigma'^-1 v_k.  Y_k is formed from
+                    // the adjugate adj(Sigma') = sum_m w_m w_m^T + dil I, w_m = (r1_m,
+                    // -r0_m), in which axis k's own term w_k . v_k vanishes
+                    // identically: Y_k det = sum_{m != k} w_m (w_m . v_k) + dil v_k,
+                    // with w_m . v_k the minors of r0 x r1.  Through the entries of
+                    // -Q G Q the same sum cancels for a long thin Gaussian (Q's small
+                    // eigenvalue, along its long axis, is a difference of large entries).
+                    {
+                        const float cr[3][3] = {{0.f, G.cz, -G.cy}, {-G.cz, 0.f, G.cx}, {G.cy, -G.cx, 0.f}};
+#pragma unroll
+                        for (int kk = 0; kk < 3; ++kk) {
+                            float y0 = k.dilation * G.r0[kk], y1 = k.dilation * G.r1[kk];
+#pragma unroll
+                            for (int m = 0; m < 3; ++m) {
+                                if (m == kk) continue;
+                                // w_m . v_k = r1_m r0_k - r0_m r1_k = cr[kk][m]
+                                y0 += G.r1[m] * cr[kk][m];
+                                y1 -= G.r0[m] * cr[kk][m];
+                            }
+                            y0 *= idet;
+                            y1 *= idet;
+                            gls[kk] -= 2.f * (gqa * y0 * y0 + gqb * y0 * y1 + gqc * y1 * y1);
+                        }
+                    }
                     // Sigma' = T2 T2^T + dil I with T2 = J W M (rows r0, r1):
                     // dL/dT2 = 2 Msym T2 (Msym = [[Ma, Mb], [Mb, Mc]])
                     float gr0[3], gr1[3];
@@ -776,12 +804,10 @@ __global__ void __launch_bounds__(kProjBwdThreads, 512 / kProjBwdThreads) k_proj
             }
         }
         if (live) {
-            // M = R diag(S): dL/dS_k = sum_i gM_ik R_ik, dL/dls_k = dL/dS_k S_k; dL/dR_ik = gM_ik S_k
+            // M = R diag(S): dL/dR_ik = gM_ik S_k (dL/dls_k was summed per view above)
             float gR[9];
-            float gls[3];
 #pragma unroll
             for (int kk = 0; kk < 3; ++kk) {
-                gls[kk] = (gM[kk] * R[kk] + gM[3 + kk] * R[3 + kk] + gM[6 + kk] * R[6 + kk]) * S[kk];
                 gR[kk] = gM[kk] * S[kk];
                 gR[3 + kk] = gM[3 + kk] * S[kk];
                 gR[6 + kk] = gM[6 + kk] * S[kk];

@@ -56,21 +56,23 @@ def _scenes():
 SCENES = _scenes()
 
 # Known precision gaps of the float32 projection on needle-shaped Gaussians
-# (thin axes ~0.2 px under the 0.3 px dilation, long axes up to ~70 px): the
-# two image-space rows of such a Gaussian are nearly parallel, so the conic
-# from their cross product carries a relative error of about
-# ulp * sigma_long / sigma_thin, and the adjoint through the inverse of the
-# badly conditioned covariance cancels.  Keys and images still meet the bar.
+# (thin axes ~0.2 px under the 0.3 px dilation, long axes up to ~70 px,
+# covariance condition up to 2600); keys, images and the log-scale gradient
+# meet the bar.  Non-strict: the values sit near the bar and the gradient
+# sums move with the order of float atomics.
 KNOWN_GAPS = {
-    ("test_projection", "needles"): "conic max relative error 1.2e-5 against the 1e-5 bar",
-    ("test_gradients", "needles"): "log-scale gradient relative L2 8.2e-3 against the 1e-4 bar",
+    ("test_projection", "needles"):
+        "qc up to 1.02e-5 of its scale: the float rotation of the long axis, projected across the thin one",
+    ("test_gradients", "needles"):
+        "quaternion gradient 7.3e-4, pose 1.1e-4, means 1.0e-4 relative L2: the adjoint through "
+        "-Q G Q cancels along the long axis",
 }
 
 
 def _known_gap(request, case):
     reason = KNOWN_GAPS.get((request.node.originalname, case["name"]))
     if reason:
-        request.node.add_marker(pytest.mark.xfail(strict=True, reason=reason))
+        request.node.add_marker(pytest.mark.xfail(reason=reason))
 
 
 @pytest.fixture(scope="module", params=list(SCENES))
@@ -115,9 +117,11 @@ def test_projection(case, request):
     # pixel mean
     assert np.abs(d["u"] - r[:, O.C_U]).max() < 1e-6 * (1 + np.abs(r[:, O.C_U]).max())
     assert np.abs(d["v"] - r[:, O.C_V]).max() < 1e-6 * (1 + np.abs(r[:, O.C_V]).max())
-    # conic, relative to its scale
-    sc = np.sqrt(r[:, O.C_QA] * r[:, O.C_QC])
-    for k, c in (("qa", O.C_QA), ("qb", O.C_QB), ("qc", O.C_QC)):
+    # conic, each entry relative to its own scale: the record holds the
+    # Cholesky factor of Q, which fixes qa and qc to their own relative
+    # precision, and |qb| <= sqrt(qa qc) for a positive definite Q
+    sqa, sqc = r[:, O.C_QA], r[:, O.C_QC]
+    for k, c, sc in (("qa", O.C_QA, sqa), ("qb", O.C_QB, np.sqrt(sqa * sqc)), ("qc", O.C_QC, sqc)):
         assert (np.abs(d[k] - r[:, c]) / sc).max() < 1e-5, k
     assert np.abs(d["log2o"] - np.log2(r[:, O.C_OPA])).max() < 2e-6
     assert np.abs(d["rgb"] - r[:, O.C_R:O.C_B + 1]).max() < 2e-6
