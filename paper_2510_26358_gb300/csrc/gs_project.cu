@@ -678,24 +678,21 @@ __global__ void __launch_bounds__(kProjBwdThreads, 512 / kProjBwdThreads) k_proj
                     const float gdir[3] = {gd4.x, gd4.y, gd4.z};
                     float dd = d[0] * gdir[0] + d[1] * gdir[1] + d[2] * gdir[2];
                     float gw[3] = {(gdir[0] - d[0] * dd) * iw, (gdir[1] - d[1] * dd) * iw, (gdir[2] - d[2] * dd) * iw};
-                    // dL/dSigma' = -Q G Q with Q = Sigma'^-1, G = [[gqa, gqb/2], [gqb/2, gqc]]
-                    float idet = 1.f / G.det;
-                    float Qa = G.c * idet, Qb = -G.b * idet, Qc = G.a * idet;
-                    float hb = 0.5f * gqb;
-                    float QG00 = Qa * gqa + Qb * hb, QG01 = Qa * hb + Qb * gqc;
-                    float QG10 = Qb * gqa + Qc * hb, QG11 = Qb * hb + Qc * gqc;
-                    float Ma = -(QG00 * Qa + QG01 * Qb);
-                    float Mb = -(QG00 * Qb + QG01 * Qc);
-                    float Mc = -(QG10 * Qb + QG11 * Qc);
-                    // log-scales: M = R diag(S) scales column k of T2 = J W M (v_k,
-                    // the image-space axis k), so dL/dls_k = v_k . 2 dL/dSigma' v_k
-                    // = -2 Y_k^T G Y_k with Y_k = Sigma'^-1 v_k.  Y_k is formed from
-                    // the adjugate adj(Sigma') = sum_m w_m w_m^T + dil I, w_m = (r1_m,
-                    // -r0_m), in which axis k's own term w_k . v_k vanishes
-                    // identically: Y_k det = sum_{m != k} w_m (w_m . v_k) + dil v_k,
-                    // with w_m . v_k the minors of r0 x r1.  Through the entries of
-                    // -Q G Q the same sum cancels for a long thin Gaussian (Q's small
-                    // eigenvalue, along its long axis, is a difference of large entries).
+                    // Sigma' = T2 T2^T + dil I with T2 = J W M, rows r0, r1 and columns
+                    // v_k (the image-space axes), Q = Sigma'^-1, G = [[gqa, gqb/2],
+                    // [gqb/2, gqc]]: dL/dSigma' = -Q G Q, so column k of dL/dT2 is
+                    // 2 dL/dSigma' v_k = -2 Q G Y_k with Y_k = Q v_k, and
+                    // dL/dls_k = v_k . (column k) = -2 Y_k^T G Y_k (M = R diag(S)
+                    // scales column k).  Q is applied through the adjugate
+                    // adj(Sigma') = sum_m w_m w_m^T + dil I, w_m = (r1_m, -r0_m): in
+                    // Y_k det = sum_{m != k} w_m (w_m . v_k) + dil v_k axis k's own term
+                    // vanishes identically, and w_m . v_k are the minors of r0 x r1.
+                    // The entries of -Q G Q would cancel for a long thin Gaussian (Q's
+                    // small eigenvalue, along its long axis, is a difference of large
+                    // entries).
+                    const float idet = 1.f / G.det;
+                    const float hb = 0.5f * gqb;
+                    float gr0[3], gr1[3];
                     {
                         const float cr[3][3] = {{0.f, G.cz, -G.cy}, {-G.cz, 0.f, G.cx}, {G.cy, -G.cx, 0.f}};
 #pragma unroll
@@ -710,16 +707,19 @@ __global__ void __launch_bounds__(kProjBwdThreads, 512 / kProjBwdThreads) k_proj
                             }
                             y0 *= idet;
                             y1 *= idet;
-                            gls[kk] -= 2.f * (gqa * y0 * y0 + gqb * y0 * y1 + gqc * y1 * y1);
-                        }
-                    }
-                    // Sigma' = T2 T2^T + dil I with T2 = J W M (rows r0, r1):
-                    // dL/dT2 = 2 Msym T2 (Msym = [[Ma, Mb], [Mb, Mc]])
-                    float gr0[3], gr1[3];
+                            const float z0 = gqa * y0 + hb * y1, z1 = hb * y0 + gqc * y1;  // G Y_k
+                            gls[kk] -= 2.f * (z0 * y0 + z1 * y1);
+                            // Q z = (sum_m w_m (w_m . z) + dil z) / det
+                            float q0 = k.dilation * z0, q1 = k.dilation * z1;
 #pragma unroll
-                    for (int j = 0; j < 3; ++j) {
-                        gr0[j] = 2.f * (Ma * G.r0[j] + Mb * G.r1[j]);
-                        gr1[j] = 2.f * (Mb * G.r0[j] + Mc * G.r1[j]);
+                            for (int m = 0; m < 3; ++m) {
+                                const float wz = G.r1[m] * z0 - G.r0[m] * z1;
+                                q0 += G.r1[m] * wz;
+                                q1 -= G.r0[m] * wz;
+                            }
+                            gr0[kk] = -2.f * q0 * idet;
+                            gr1[kk] = -2.f * q1 * idet;
+                        }
                     }
                     // T2 = J WM: rows r0 = J00 WM0 + J02 WM2, r1 = J11 WM1 + J12 WM2
                     float gJ00 = gr0[0] * G.WM[0] + gr0[1] * G.WM[1] + gr0[2] * G.WM[2];

@@ -55,24 +55,21 @@ def _scenes():
 
 SCENES = _scenes()
 
-# Known precision gaps of the float32 projection on needle-shaped Gaussians
+# Known precision gap of the float32 projection on needle-shaped Gaussians
 # (thin axes ~0.2 px under the 0.3 px dilation, long axes up to ~70 px,
-# covariance condition up to 2600); keys, images and the log-scale gradient
-# meet the bar.  Non-strict: the values sit near the bar and the gradient
-# sums move with the order of float atomics.
+# covariance condition up to 2600); keys, images and gradients meet the bar.
+# Strict: the projection has no atomics, so the value is reproducible and a
+# fix shows as a pass.
 KNOWN_GAPS = {
     ("test_projection", "needles"):
         "qc up to 1.02e-5 of its scale: the float rotation of the long axis, projected across the thin one",
-    ("test_gradients", "needles"):
-        "quaternion gradient 7.3e-4, pose 1.1e-4, means 1.0e-4 relative L2: the adjoint through "
-        "-Q G Q cancels along the long axis",
 }
 
 
 def _known_gap(request, case):
     reason = KNOWN_GAPS.get((request.node.originalname, case["name"]))
     if reason:
-        request.node.add_marker(pytest.mark.xfail(reason=reason))
+        request.node.add_marker(pytest.mark.xfail(strict=True, reason=reason))
 
 
 @pytest.fixture(scope="module", params=list(SCENES))
@@ -183,8 +180,7 @@ def test_forward_images(case):
     assert (~keep).sum() <= 0.01 * keep.size
 
 
-def test_gradients(case, request):
-    _known_gap(request, case)
+def test_gradients(case):
     g, go = case["gpu"], case["go"]
     res = {}
     for k in ("means", "log_scales", "quats", "opacity_logits", "sh", "pose", "dens_acc"):
