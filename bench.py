@@ -173,11 +173,17 @@ RASTER_SOURCES = ("paper_2510_26358_gb300/csrc/gs_raster.cu", "paper_2510_26358_
 
 
 def raster_source_hash() -> str:
+    """sha1 of the code of RASTER_SOURCES with comments and whitespace removed,
+    so that an edit of a comment does not void a recorded measurement."""
     import hashlib
+    import re
     h = hashlib.sha1()
     for f in RASTER_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, f)) as fh:
+            code = fh.read()
+        code = re.sub(r"/\*.*?\*/", " ", code, flags=re.S)
+        code = re.sub(r"//[^\n]*", " ", code)
+        h.update(" ".join(code.split()).encode())
     return h.hexdigest()[:16]
 
 

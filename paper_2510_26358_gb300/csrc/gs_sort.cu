@@ -1,12 +1,15 @@
 // Binning: one instance per (visible pair, covered tile), ordered by the
 // 64-bit key (global tile << 32 | float bits of depth), ties by pair order.
+// A pair's rectangle tiles are all emitted; those its alpha >= alpha_min
+// ellipse misses carry the invalid tile id (see the emission below).
 //
 // Instead of radix-sorting 64-bit keys over every instance, the visible pairs
 // are first sorted by their 32-bit depth key (N_vis elements), the instances
-// are then emitted in that order, and a stable sort by tile id alone (only the
-// ceil(log2 n_tiles) bits that can be set) finishes the job.  Stability makes
-// the result identical to the stable 64-bit sort: within a tile the instances
-// stay in (depth, pair) order.  Per-tile ranges come from key changes.
+// are then emitted in that order, and a stable sort by tile id alone (the
+// bits of the value n_tiles, so that the invalid id sorts after every real
+// one) finishes the job.  Stability makes the result identical to the stable
+// 64-bit sort: within a tile the instances stay in (depth, pair) order.
+// Per-tile ranges come from key changes.
 //
 // Every count lives on the device (capacity overflow sets a flag), so the
 // sequence needs no host round trip and can be captured in a CUDA graph.  All
