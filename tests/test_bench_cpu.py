@@ -1,0 +1,68 @@
+"""Host logic of bench.py that decides whether the recorded ncu traffic still
+describes the timed kernel: the source hash ignores comments and whitespace
+but not code, and a record taken on other code, another workload or another
+tile size is not reported."""
+import importlib.util
+import json
+import os
+import shutil
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bench():
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    b = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(b)
+    return b
+
+
+@pytest.fixture
+def tree(tmp_path):
+    """A copy of the hashed sources and the traffic record, with bench.py's
+    ROOT pointed at it."""
+    b = _bench()
+    for f in b.RASTER_SOURCES:
+        os.makedirs(tmp_path / os.path.dirname(f), exist_ok=True)
+        shutil.copy(os.path.join(ROOT, f), tmp_path / f)
+    os.makedirs(tmp_path / "profiles")
+    shutil.copy(os.path.join(ROOT, "profiles", "ncu_traffic.json"), tmp_path / "profiles" / "ncu_traffic.json")
+    b.ROOT = str(tmp_path)
+    return b, tmp_path
+
+
+def _edit(path, fn):
+    with open(path) as f:
+        s = f.read()
+    with open(path, "w") as f:
+        f.write(fn(s))
+
+
+def test_hash_ignores_comments_and_whitespace_not_code(tree):
+    b, root = tree
+    h0 = b.raster_source_hash()
+    src = root / b.RASTER_SOURCES[0]
+    _edit(src, lambda s: "// a new comment line\n/* and a\n   block */\n" + s.replace("\n", "\n  ", 5))
+    assert b.raster_source_hash() == h0
+    _edit(src, lambda s: s + "\nstatic const int kChanged = 1;\n")
+    assert b.raster_source_hash() != h0
+
+
+def test_traffic_reported_only_for_the_recorded_code_workload_and_tile(tree):
+    b, root = tree
+    rec = json.load(open(root / "profiles" / "ncu_traffic.json"))["k_raster_bwd"]
+    cfg = rec["config"]
+    # the committed record matches the committed sources
+    traffic, note = b.measured_traffic("k_raster_bwd", rec["workload"], cfg)
+    assert traffic == rec["dram_bytes_per_launch"] and note == rec["command"]
+    # the batch depth does not change the backward's traffic; the tile size does
+    tile = cfg.split("/")[0]
+    assert b.measured_traffic("k_raster_bwd", rec["workload"], tile + "/64")[0] == traffic
+    assert b.measured_traffic("k_raster_bwd", rec["workload"], "8x8/128")[0] is None
+    assert b.measured_traffic("k_raster_bwd", "another_workload", cfg)[0] is None
+    # code changed since the capture
+    _edit(root / b.RASTER_SOURCES[-1], lambda s: s + "\nstatic const int kChanged = 1;\n")
+    traffic, note = b.measured_traffic("k_raster_bwd", rec["workload"], cfg)
+    assert traffic is None and "changed" in note
