@@ -179,7 +179,7 @@ def raster_source_hash() -> str:
     import re
     h = hashlib.sha1()
     for f in RASTER_SOURCES:
-        with open(os.path.join(ROOT, f)) as fh:
+        with open(os.path.join(ROOT, f), encoding="utf-8") as fh:
             code = fh.read()
         code = re.sub(r"/\*.*?\*/", " ", code, flags=re.S)
         code = re.sub(r"//[^\n]*", " ", code)
