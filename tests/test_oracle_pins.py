@@ -315,6 +315,19 @@ def test_keys_rebuilt_with_numpy_stable_sort(scene):
         toff += ntx * nty
         poff += ng
     ek, ev = np.array(ek, np.uint64), np.array(ev, np.int64)
+    # convexity: in every rectangle row a pair's kept tiles are those whose
+    # grown box overlaps the one x-interval of the ellipse within the row's
+    # strip, so they form a single run
+    toffs = np.cumsum([0] + [-(-c.width // 8) * -(-c.height // 8) for c in cams])
+    ntxs = [-(-c.width // 8) for c in cams]
+    tiles_o = (keys >> np.uint64(32)).astype(np.int64)
+    for pair in np.unique(vals):
+        t = tiles_o[vals == pair]
+        v = int(np.searchsorted(toffs, t[0], side="right") - 1)
+        tx, ty = (t - toffs[v]) % ntxs[v], (t - toffs[v]) // ntxs[v]
+        for row in np.unique(ty):
+            xs = np.sort(tx[ty == row])
+            assert np.array_equal(xs, np.arange(xs[0], xs[-1] + 1))
     # the fixture exercises both outcomes: corner tiles dropped, most kept ones reached
     assert n_rect - len(ek) >= 50 and n_reach > 0.8 * len(ek), (n_rect, len(ek), n_reach)
     order = np.argsort(ek, kind="stable")
