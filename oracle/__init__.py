@@ -12,6 +12,9 @@ Parity status per function (see the pins in ``tests/test_oracle_pins.py``):
   bin          pinned: brute-force renderer equality, independent key rebuild
                with every tile decision redone by bounded least squares, every
                reached pixel in a kept tile (brute force)
+  tile_decisions32 / bin_decided (the binning stage alone, from float32
+               projection outputs): pinned by the same key rebuild with the
+               decisions redone by bounded least squares on the float inputs
   render_fwd   pinned: single-Gaussian closed form, T invariants, brute force
   render_bwd   pinned: central finite differences, translation identity
   depth_loss   pinned: KL closed form vs numerical integration, FD
@@ -44,7 +47,7 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
         subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off",
-                               "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
+                               "-fno-fast-math", "-fopenmp", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -128,8 +131,24 @@ def lib():
         _lib.oracle_cov3d.restype = i32
         _lib.oracle_sh_basis.argtypes = [i32, P, P]
         _lib.oracle_layout.restype = i64
+        _lib.oracle_rect_tiles32.argtypes = [i64, P, P]
+        _lib.oracle_rect_tiles32.restype = i64
+        _lib.oracle_tile_decisions32.argtypes = [i32, P, P, P, i64, P, P, P, P, P]
+        _lib.oracle_bin_decided.argtypes = [i32, P, P, P, i64, P, P, P, P, P, P]
+        _lib.oracle_bin_decided.restype = i64
+        _lib.oracle_set_threads.argtypes = [i32]
+        _lib.oracle_get_threads.restype = i32
         assert _lib.oracle_layout() == NCOL * 100 + NGRAD, "oracle column layout mismatch"
     return _lib
+
+
+def set_threads(n: int) -> int:
+    """Host threads of the oracle's per-pair and per-pixel loops (default 1,
+    which reproduces results bit for bit; more threads change only the order
+    of the backward's additions).  Returns the previous value."""
+    prev = int(lib().oracle_get_threads())
+    lib().oracle_set_threads(int(n))
+    return prev
 
 
 def _p(a: np.ndarray):
@@ -225,6 +244,45 @@ def bin(P: Params, cams, cfg: Config, rec: np.ndarray):
     lib().oracle_bin(len(cams), ca, _p(P.submap_offsets), ctypes.byref(cc), _p(rec), _p(keys),
                      _p(vals), _p(ranges))
     return keys[:n_inst], vals[:n_inst], ranges[:T]
+
+
+def tile_decisions32(P: Params, cams, cfg: Config, rec32, rect, pkey):
+    """The binning stage alone, from the float32 path's projection outputs
+    (records [n_pairs][12] f32, rectangles [n_pairs][4] i16, depth keys
+    [n_pairs] u32): R6b's decision for every rectangle tile of every visible
+    pair, taken exactly from those float inputs, in emission order.  Returns
+    (keep int8 [D], margin float64 [D]): |margin| of a few float ulps marks a
+    decision a float32 evaluation may take the other way."""
+    ca, cc = cameras(cams), cfg.c()
+    rec32 = np.ascontiguousarray(rec32, np.float32).reshape(-1, 12)
+    rect = np.ascontiguousarray(rect, np.int16).reshape(-1, 4)
+    pkey = np.ascontiguousarray(pkey, np.uint32)
+    n_p = rec32.shape[0]
+    D = int(lib().oracle_rect_tiles32(n_p, _p(rect), _p(pkey)))
+    dec = np.zeros(max(D, 1), np.int8)
+    margin = np.zeros(max(D, 1))
+    lib().oracle_tile_decisions32(len(cams), ca, _p(P.submap_offsets), ctypes.byref(cc), n_p, _p(rec32),
+                                  _p(rect), _p(pkey), _p(dec), _p(margin))
+    return dec[:D], margin[:D]
+
+
+def bin_decided(P: Params, cams, cfg: Config, rect, pkey, dec):
+    """Keys (uint64), pair of each instance (int64) and per-tile ranges [T, 2]
+    of the stable key sort, from the float32 path's rectangles and depth keys
+    and one keep decision per rectangle tile (emission order)."""
+    ca, cc = cameras(cams), cfg.c()
+    rect = np.ascontiguousarray(rect, np.int16).reshape(-1, 4)
+    pkey = np.ascontiguousarray(pkey, np.uint32)
+    dec = np.ascontiguousarray(dec, np.int8)
+    n_keep = int(np.count_nonzero(dec))
+    keys = np.zeros(max(n_keep, 1), np.uint64)
+    vals = np.zeros(max(n_keep, 1), np.int64)
+    T = n_tiles(cams, cfg)
+    ranges = np.zeros((max(T, 1), 2), np.int64)
+    m = lib().oracle_bin_decided(len(cams), ca, _p(P.submap_offsets), ctypes.byref(cc), rect.shape[0], _p(rect),
+                                 _p(pkey), _p(dec), _p(keys), _p(vals), _p(ranges))
+    assert m == n_keep
+    return keys[:m], vals[:m], ranges[:T]
 
 
 def _npix(cams):

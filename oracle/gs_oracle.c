@@ -107,6 +107,24 @@ enum { G_U = 0, G_V, G_QA, G_QB, G_QC, G_LNO, G_R, G_G, G_B, G_Z, OC_NGRAD };
 /* layout check for the Python wrapper: OC_NCOL*100 + OC_NGRAD */
 int64_t oracle_layout(void) { return (int64_t)OC_NCOL * 100 + OC_NGRAD; }
 
+/* Host threads of the per-pair and per-pixel loops (OpenMP when compiled with
+ * it).  Each pair and each pixel is computed alone, exactly as with one
+ * thread; only the order in which the backward adds contributions of
+ * different pixels into one pair's gradient (and of different pairs into a
+ * view's pose gradient) depends on the threads, so results with more than
+ * one thread can differ from the one-thread results by rounding.  Default 1. */
+static int oc_threads = 1;
+void oracle_set_threads(int n) { oc_threads = n > 0 ? n : 1; }
+int oracle_get_threads(void) { return oc_threads; }
+
+/* a += v, atomic when several threads may add to the same location */
+static void acc_add(double *a, double v) {
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+    *a += v;
+}
+
 /* ------------------------------------------------------------------------ */
 /* small helpers                                                            */
 /* ------------------------------------------------------------------------ */
@@ -289,8 +307,7 @@ static int64_t hi_tile(double a, int W, int tw) {
  * the mean and otherwise lies on one of the four edges, where q is a convex
  * parabola along the edge minimised at its stationary point clamped to the
  * edge. */
-static double box_min_q(const double *r, double x0, double x1, double y0, double y1) {
-    double qa = r[C_QA], qb = r[C_QB], qc = r[C_QC];
+static double box_min_quad(double qa, double qb, double qc, double x0, double x1, double y0, double y1) {
     if (x0 <= 0.0 && 0.0 <= x1 && y0 <= 0.0 && 0.0 <= y1) return 0.0;
     double best = INFINITY;
     double xs[2] = {x0, x1}, ys[2] = {y0, y1};
@@ -311,8 +328,9 @@ static double tile_min_q(const double *r, int64_t tx, int64_t ty, const oc_camer
     int64_t X0 = tx * cfg->tile_w, Y0 = ty * cfg->tile_h;
     int64_t X1 = (X0 + cfg->tile_w < cam->width ? X0 + cfg->tile_w : cam->width) - 1;
     int64_t Y1 = (Y0 + cfg->tile_h < cam->height ? Y0 + cfg->tile_h : cam->height) - 1;
-    return box_min_q(r, (double)X0 + 0.5 - r[C_U] - grow, (double)X1 + 0.5 - r[C_U] + grow,
-                     (double)Y0 + 0.5 - r[C_V] - grow, (double)Y1 + 0.5 - r[C_V] + grow);
+    return box_min_quad(r[C_QA], r[C_QB], r[C_QC], (double)X0 + 0.5 - r[C_U] - grow,
+                        (double)X1 + 0.5 - r[C_U] + grow, (double)Y0 + 0.5 - r[C_V] - grow,
+                        (double)Y1 + 0.5 - r[C_V] + grow);
 }
 
 static double tile_threshold(const double *r, const oc_config *cfg) {
@@ -460,7 +478,8 @@ int oracle_project(int64_t n, const double *means, const double *log_scales, con
     oc_view *V = (oc_view *)malloc(sizeof(oc_view) * (n_views > 0 ? n_views : 1));
     make_views(n_views, cams, submap_offsets, cfg, V);
     int K = (sh_degree + 1) * (sh_degree + 1);
-    for (int v = 0; v < n_views; ++v)
+    for (int v = 0; v < n_views; ++v) {
+#pragma omp parallel for schedule(dynamic, 1024) num_threads(oc_threads)
         for (int64_t k = 0; k < V[v].ng; ++k) {
             int64_t g = V[v].g0 + k;
             double *r = rec + (V[v].pair_off + k) * OC_NCOL;
@@ -469,6 +488,7 @@ int oracle_project(int64_t n, const double *means, const double *log_scales, con
             r[C_GAUSS] = (double)g;
             r[C_VIEW] = (double)v;
         }
+    }
     free(V);
     return 0;
 }
@@ -496,6 +516,22 @@ int64_t oracle_count_instances(int64_t n_pairs, const double *rec) {
         total += (int64_t)r[C_NTILE];
     }
     return total;
+}
+
+/* Stable sort of the emitted instances I[0..m) by key, then the keys, the
+ * pair of each instance and ranges[2t], ranges[2t+1] = [first, end) of every
+ * tile t (0,0 when empty). */
+static void sort_and_range(oc_inst *I, int64_t m, int64_t n_tiles, uint64_t *keys_out, int64_t *vals_out,
+                           int64_t *ranges) {
+    qsort(I, (size_t)m, sizeof(oc_inst), inst_cmp);
+    for (int64_t t = 0; t < 2 * n_tiles; ++t) ranges[t] = 0;
+    for (int64_t i = 0; i < m; ++i) {
+        keys_out[i] = I[i].key;
+        vals_out[i] = I[i].pair;
+        int64_t t = (int64_t)(I[i].key >> 32);
+        if (i == 0 || (I[i - 1].key >> 32) != (uint64_t)t) ranges[2 * t] = i;
+        if (i == m - 1 || (I[i + 1].key >> 32) != (uint64_t)t) ranges[2 * t + 1] = i + 1;
+    }
 }
 
 /* Emit one key per (visible pair, kept tile of its rectangle, R6b) in pair
@@ -528,18 +564,128 @@ int oracle_bin(int n_views, const oc_camera *cams, const int64_t *submap_offsets
                     ++m;
                 }
         }
-    qsort(I, (size_t)n_inst, sizeof(oc_inst), inst_cmp);
-    for (int64_t t = 0; t < 2 * n_tiles; ++t) ranges[t] = 0;
-    for (int64_t i = 0; i < n_inst; ++i) {
-        keys_out[i] = I[i].key;
-        vals_out[i] = I[i].pair;
-        int64_t t = (int64_t)(I[i].key >> 32);
-        if (i == 0 || (I[i - 1].key >> 32) != (uint64_t)t) ranges[2 * t] = i;
-        if (i == n_inst - 1 || (I[i + 1].key >> 32) != (uint64_t)t) ranges[2 * t + 1] = i + 1;
-    }
+    sort_and_range(I, m, n_tiles, keys_out, vals_out, ranges);
     free(I);
     free(V);
     return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* stage-isolated binning: R6b and the sort from given float32 records      */
+/* ------------------------------------------------------------------------ */
+
+/* The binning stage alone, on the projection outputs of the float32 path:
+ * per pair the record (U, V, hx, hy | l11, l12, l22, log2 o | r, g, b, z) of
+ * 12 floats, the tile rectangle (tx0, ty0, tx1, ty1) as int16 and the depth
+ * key (float bits of z, 0xFFFFFFFF for a pair that is not visible).  The pixel
+ * mean is u = U + 1/2 - hx, v = V + 1/2 - hy, so that the offset of pixel
+ * centre (X + 1/2, Y + 1/2) from it is (X - U + hx, Y - V + hy); L is the
+ * upper Cholesky factor [[l11, l12], [0, l22]] of Q log2(e)/2, so that
+ * log2 alpha = log2 o - |L d|^2 before the clamp.  R6b keeps a rectangle tile
+ * iff min over the box of its pixel-centre offsets (clipped to the image,
+ * grown by ext_abs_pad) of |L d|^2 <= (log2 o - log2 alpha_min)(1 +
+ * ext_rel_pad)^2.  Here that minimum and that threshold are taken exactly (in
+ * double, from the float inputs; products of two floats are exact in double). */
+
+static int rec32_visible(const int16_t *rect, uint32_t pkey) {
+    return pkey != 0xFFFFFFFFu && rect[2] >= rect[0] && rect[3] >= rect[1];
+}
+
+/* Number of rectangle tiles of the visible pairs (the decisions to take). */
+int64_t oracle_rect_tiles32(int64_t n_pairs, const int16_t *rect, const uint32_t *pkey) {
+    int64_t total = 0;
+    for (int64_t p = 0; p < n_pairs; ++p)
+        if (rec32_visible(rect + 4 * p, pkey[p]))
+            total += (int64_t)(rect[4 * p + 2] - rect[4 * p] + 1) * (rect[4 * p + 3] - rect[4 * p + 1] + 1);
+    return total;
+}
+
+/* R6b decision of every rectangle tile of every visible pair, in emission
+ * order (pairs in order, each rectangle row-major): dec = 1 keep, 0 drop.
+ * margin[i] = (threshold - minimum) / scale, where scale bounds the size of
+ * the terms a float32 evaluation of the same test rounds: the threshold's
+ * factors and the largest |L d|^2 over the box corners.  A float32 evaluation
+ * can take the other decision only where |margin| is a few float ulps. */
+int oracle_tile_decisions32(int n_views, const oc_camera *cams, const int64_t *submap_offsets,
+                            const oc_config *cfg, int64_t n_pairs, const float *rec32, const int16_t *rect,
+                            const uint32_t *pkey, int8_t *dec, double *margin) {
+    oc_view *V = (oc_view *)malloc(sizeof(oc_view) * (n_views > 0 ? n_views : 1));
+    make_views(n_views, cams, submap_offsets, cfg, V);
+    double l2amin = log2(cfg->alpha_min);
+    double pad = 1.0 + cfg->ext_rel_pad;
+    int64_t m = 0;
+    for (int v = 0; v < n_views; ++v)
+        for (int64_t k = 0; k < V[v].ng; ++k) {
+            int64_t p = V[v].pair_off + k;
+            if (p >= n_pairs) break;
+            const int16_t *rc = rect + 4 * p;
+            if (!rec32_visible(rc, pkey[p])) continue;
+            const float *r = rec32 + 12 * p;
+            double U = r[0], Vv = r[1], hx = r[2], hy = r[3];
+            double l11 = r[4], l12 = r[5], l22 = r[6], log2o = r[7];
+            /* |L d|^2 = qa dx^2 + 2 qb dx dy + qc dy^2 */
+            double qa = l11 * l11, qb = l11 * l12, qc = l12 * l12 + l22 * l22;
+            double thr = (log2o - l2amin) * pad * pad;
+            for (int64_t ty = rc[1]; ty <= rc[3]; ++ty)
+                for (int64_t tx = rc[0]; tx <= rc[2]; ++tx) {
+                    int64_t X0 = tx * cfg->tile_w, Y0 = ty * cfg->tile_h;
+                    int64_t X1 = (X0 + cfg->tile_w < cams[v].width ? X0 + cfg->tile_w : cams[v].width) - 1;
+                    int64_t Y1 = (Y0 + cfg->tile_h < cams[v].height ? Y0 + cfg->tile_h : cams[v].height) - 1;
+                    double ax = ((double)X0 - U + hx) - cfg->ext_abs_pad;
+                    double bx = ((double)X1 - U + hx) + cfg->ext_abs_pad;
+                    double ay = ((double)Y0 - Vv + hy) - cfg->ext_abs_pad;
+                    double by = ((double)Y1 - Vv + hy) + cfg->ext_abs_pad;
+                    double mq = box_min_quad(qa, qb, qc, ax, bx, ay, by);
+                    double big = 0.0;
+                    for (int c = 0; c < 4; ++c) {
+                        double x = (c & 1) ? bx : ax, y = (c & 2) ? by : ay;
+                        double t1 = fabs(l11 * x) + fabs(l12 * y), t2 = fabs(l22 * y);
+                        big = dmax(big, t1 * t1 + t2 * t2);
+                    }
+                    double scale = big + (fabs(log2o) + fabs(l2amin)) * pad * pad;
+                    dec[m] = mq <= thr;
+                    margin[m] = (thr - mq) / scale;
+                    ++m;
+                }
+        }
+    free(V);
+    return 0;
+}
+
+/* Instances, keys and ranges from the float32 path's projection outputs and
+ * one decision per rectangle tile (emission order, as oracle_tile_decisions32
+ * writes them): key = (global tile << 32) | pkey, stable sort by key,
+ * per-tile [first, end).  Returns the number of instances. */
+int64_t oracle_bin_decided(int n_views, const oc_camera *cams, const int64_t *submap_offsets,
+                           const oc_config *cfg, int64_t n_pairs, const int16_t *rect, const uint32_t *pkey,
+                           const int8_t *dec, uint64_t *keys_out, int64_t *vals_out, int64_t *ranges) {
+    oc_view *V = (oc_view *)malloc(sizeof(oc_view) * (n_views > 0 ? n_views : 1));
+    make_views(n_views, cams, submap_offsets, cfg, V);
+    int64_t n_tiles = oracle_count_tiles(n_views, cams, cfg);
+    int64_t n_dec = oracle_rect_tiles32(n_pairs, rect, pkey);
+    oc_inst *I = (oc_inst *)malloc(sizeof(oc_inst) * (n_dec > 0 ? n_dec : 1));
+    int64_t m = 0, d = 0;
+    for (int v = 0; v < n_views; ++v)
+        for (int64_t k = 0; k < V[v].ng; ++k) {
+            int64_t p = V[v].pair_off + k;
+            if (p >= n_pairs) break;
+            const int16_t *rc = rect + 4 * p;
+            if (!rec32_visible(rc, pkey[p])) continue;
+            for (int64_t ty = rc[1]; ty <= rc[3]; ++ty)
+                for (int64_t tx = rc[0]; tx <= rc[2]; ++tx) {
+                    if (dec[d++]) {
+                        uint64_t tile = (uint64_t)(V[v].tile_off + ty * V[v].ntx + tx);
+                        I[m].key = (tile << 32) | pkey[p];
+                        I[m].seq = m;
+                        I[m].pair = p;
+                        ++m;
+                    }
+                }
+        }
+    sort_and_range(I, m, n_tiles, keys_out, vals_out, ranges);
+    free(I);
+    free(V);
+    return m;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -631,6 +777,7 @@ int oracle_render_fwd(int n_views, const oc_camera *cams, const int64_t *submap_
     make_views(n_views, cams, submap_offsets, cfg, V);
     for (int v = 0; v < n_views; ++v) {
         int64_t W = cams[v].width, H = cams[v].height;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(oc_threads)
         for (int64_t y = 0; y < H; ++y)
             for (int64_t x = 0; x < W; ++x) {
                 int64_t t = V[v].tile_off + (y / cfg->tile_h) * V[v].ntx + x / cfg->tile_w;
@@ -657,6 +804,7 @@ int oracle_render_depth_dist(int n_views, const oc_camera *cams, const int64_t *
     make_views(n_views, cams, submap_offsets, cfg, V);
     for (int v = 0; v < n_views; ++v) {
         int64_t W = cams[v].width, H = cams[v].height;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(oc_threads)
         for (int64_t y = 0; y < H; ++y)
             for (int64_t x = 0; x < W; ++x) {
                 int64_t t = V[v].tile_off + (y / cfg->tile_h) * V[v].ntx + x / cfg->tile_w;
@@ -685,6 +833,7 @@ int oracle_render_fwd_pixels(int n_views, const oc_camera *cams, const int64_t *
                              int64_t *last, double *margin) {
     oc_view *V = (oc_view *)malloc(sizeof(oc_view) * (n_views > 0 ? n_views : 1));
     make_views(n_views, cams, submap_offsets, cfg, V);
+#pragma omp parallel for schedule(dynamic, 64) num_threads(oc_threads)
     for (int64_t k = 0; k < n_sel; ++k) {
         int v = 0;
         while (v + 1 < n_views && V[v + 1].pix_off <= pix[k]) ++v;
@@ -993,19 +1142,19 @@ static void pixel_adjoint(const double *rec, const int64_t *cand, int64_t n, dou
                    gmean * dmu_dw + gvar * dvar_dw;
         double dal = Tb[j] * h - suffix / (1.0 - al[j]);
         suffix += w * h;
-        g[G_R] += w * gC[0]; g[G_G] += w * gC[1]; g[G_B] += w * gC[2];
-        g[G_Z] += w * gD + gmean * dmu_dz + gvar * dvar_dz;
+        acc_add(&g[G_R], w * gC[0]); acc_add(&g[G_G], w * gC[1]); acc_add(&g[G_B], w * gC[2]);
+        acc_add(&g[G_Z], w * gD + gmean * dmu_dz + gvar * dvar_dz);
         if (raw[j] > cfg->alpha_max) continue; /* clamped: no dependence on o, pw */
         /* alpha = o exp(pw): dalpha/dln(o) = alpha, dalpha/dpw = alpha */
         double gpw = dal * al[j];
-        g[G_LNO] += gpw;
+        acc_add(&g[G_LNO], gpw);
         double dx = px - r[C_U], dy = py - r[C_V];
         /* pw = -1/2 (qa dx^2 + 2 qb dx dy + qc dy^2), d = pixel - mean */
-        g[G_QA] += -0.5 * gpw * dx * dx;
-        g[G_QB] += -gpw * dx * dy;
-        g[G_QC] += -0.5 * gpw * dy * dy;
-        g[G_U] += gpw * (r[C_QA] * dx + r[C_QB] * dy);
-        g[G_V] += gpw * (r[C_QB] * dx + r[C_QC] * dy);
+        acc_add(&g[G_QA], -0.5 * gpw * dx * dx);
+        acc_add(&g[G_QB], -gpw * dx * dy);
+        acc_add(&g[G_QC], -0.5 * gpw * dy * dy);
+        acc_add(&g[G_U], gpw * (r[C_QA] * dx + r[C_QB] * dy));
+        acc_add(&g[G_V], gpw * (r[C_QB] * dx + r[C_QC] * dy));
     }
     free(bl); free(al); free(raw); free(Tb);
 }
@@ -1199,6 +1348,7 @@ int oracle_render_bwd(int64_t n, const double *means, const double *log_scales, 
     make_views(n_views, cams, submap_offsets, cfg, V);
     for (int v = 0; v < n_views; ++v) {
         int64_t W = cams[v].width, H = cams[v].height;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(oc_threads)
         for (int64_t y = 0; y < H; ++y)
             for (int64_t x = 0; x < W; ++x) {
                 int64_t pix = V[v].pix_off + y * W + x, local = y * W + x;
@@ -1214,19 +1364,29 @@ int oracle_render_bwd(int64_t n, const double *means, const double *log_scales, 
             }
     }
     int K = (sh_degree + 1) * (sh_degree + 1);
-    for (int v = 0; v < n_views; ++v)
-        for (int64_t k = 0; k < V[v].ng; ++k) {
-            int64_t p = V[v].pair_off + k, g = V[v].g0 + k;
-            const double *r = rec + p * OC_NCOL;
-            if (r[C_VIS] == 0.0) continue;
-            const double *gg = g2d + p * OC_NGRAD;
-            project_adjoint(means + 3 * g, log_scales + 3 * g, quats + 4 * g, opacity_logits[g],
-                            sh + (int64_t)3 * K * g, sh_degree, &cams[v], cfg, r, gg,
-                            g_means + 3 * g, g_ls + 3 * g, g_quats + 4 * g, g_om + g,
-                            g_sh + (int64_t)3 * K * g, g_pose + 6 * v);
-            if (dens_acc) dens_acc[g] += sqrt(gg[G_U] * gg[G_U] + gg[G_V] * gg[G_V]);
-            if (dens_cnt) dens_cnt[g] += 1.0;
+    /* a Gaussian appears once per view, so the pairs of one view update
+     * disjoint parameter rows; each thread sums its pairs' pose terms apart */
+    for (int v = 0; v < n_views; ++v) {
+#pragma omp parallel num_threads(oc_threads)
+        {
+            double pose_t[6] = {0, 0, 0, 0, 0, 0};
+#pragma omp for schedule(dynamic, 1024)
+            for (int64_t k = 0; k < V[v].ng; ++k) {
+                int64_t p = V[v].pair_off + k, g = V[v].g0 + k;
+                const double *r = rec + p * OC_NCOL;
+                if (r[C_VIS] == 0.0) continue;
+                const double *gg = g2d + p * OC_NGRAD;
+                project_adjoint(means + 3 * g, log_scales + 3 * g, quats + 4 * g, opacity_logits[g],
+                                sh + (int64_t)3 * K * g, sh_degree, &cams[v], cfg, r, gg,
+                                g_means + 3 * g, g_ls + 3 * g, g_quats + 4 * g, g_om + g,
+                                g_sh + (int64_t)3 * K * g, pose_t);
+                /* R14: image-space gradient magnitude at the projected centre, pixels */
+                if (dens_acc) dens_acc[g] += sqrt(gg[G_U] * gg[G_U] + gg[G_V] * gg[G_V]);
+                if (dens_cnt) dens_cnt[g] += 1.0;
+            }
+            for (int i = 0; i < 6; ++i) acc_add(&g_pose[6 * v + i], pose_t[i]);
         }
+    }
     free(V);
     return 0;
 }
