@@ -347,6 +347,100 @@ def test_keys_rebuilt_with_numpy_stable_sort(scene):
         assert gs.min() >= sc.submap_offsets[c.submap] and gs.max() < sc.submap_offsets[c.submap + 1]
 
 
+def _float32_records(rec):
+    """Projection outputs in the float32 path's layout, made from the FP64
+    oracle's records: (U, V, hx, hy | l11, l12, l22, log2 o | r, g, b, z) with
+    U = floor(u), hx = U + 1/2 - u, L the upper Cholesky factor of
+    Q log2(e)/2; the tile rectangles; depth keys (0xFFFFFFFF: not visible)."""
+    n = rec.shape[0]
+    out = np.zeros((n, 12), np.float32)
+    rect = np.zeros((n, 4), np.int16)
+    pkey = np.full(n, 0xFFFFFFFF, np.uint32)
+    s2 = math.log2(math.e) / 2
+    for i, r in enumerate(rec):
+        if r[O.C_VIS] == 0:
+            continue
+        U, V = math.floor(r[O.C_U]), math.floor(r[O.C_V])
+        l11 = math.sqrt(r[O.C_QA] * s2)
+        l12 = r[O.C_QB] * s2 / l11
+        l22 = math.sqrt(r[O.C_QC] * s2 - l12 * l12)
+        out[i] = (U, V, U + 0.5 - r[O.C_U], V + 0.5 - r[O.C_V], l11, l12, l22, math.log2(r[O.C_OPA]),
+                  r[O.C_R], r[O.C_G], r[O.C_B], r[O.C_Z32])
+        rect[i] = (r[O.C_TX0], r[O.C_TY0], r[O.C_TX1], r[O.C_TY1])
+        pkey[i] = np.float32(r[O.C_Z32]).view(np.uint32)
+    return out, rect, pkey
+
+
+@pytest.mark.parametrize("scene", ["submaps", "needles"])
+def test_stage_isolated_binning_rebuilt(scene):
+    """The binning stage on float32 projection outputs: every rectangle
+    tile's R6b decision redone as bounded least squares on the float inputs
+    (the box of pixel-centre offsets X - U + hx, grown by ext_abs_pad, and L
+    as given), keys rebuilt with numpy's stable sort, ranges from the sorted
+    tile ids; and on records made from the FP64 projection the decisions
+    agree with the end-to-end binning wherever neither is near its threshold."""
+    cfg = O.Config(tile_w=8, tile_h=8)
+    if scene == "submaps":
+        sc = S.uneven_submaps(3, 200, 800, seed=4, scale=1.0, resolutions=((48, 40), (64, 32)))
+    else:
+        sc = S.needle_scene(600, 96, 72, 90.0, seed=7)
+    P = O.Params.from_scene(sc)
+    cams = O.as_float32_cameras(sc.cameras)
+    rec = O.project(P, cams, cfg)
+    rec32, rect, pkey = _float32_records(rec)
+    dec, margin = O.tile_decisions32(P, cams, cfg, rec32, rect, pkey)
+    cc = cfg.c()
+    rho, kappa, l2amin = cc.ext_rel_pad, cc.ext_abs_pad, math.log2(cc.alpha_min)
+    ek, ev, exp_dec = [], [], []
+    toff, poff = 0, 0
+    for v, c in enumerate(cams):
+        ntx, nty = -(-c.width // 8), -(-c.height // 8)
+        ng = int(sc.submap_offsets[c.submap + 1] - sc.submap_offsets[c.submap])
+        for k in range(ng):
+            p = poff + k
+            if pkey[p] == 0xFFFFFFFF:
+                continue
+            r = rec32[p].astype(np.float64)
+            L = np.array([[r[4], r[5]], [0.0, r[6]]])
+            thr = (r[7] - l2amin) * (1 + rho) ** 2
+            for ty in range(int(rect[p, 1]), int(rect[p, 3]) + 1):
+                for tx in range(int(rect[p, 0]), int(rect[p, 2]) + 1):
+                    X1, Y1 = min(tx * 8 + 8, c.width) - 1, min(ty * 8 + 8, c.height) - 1
+                    lo = [tx * 8 - r[0] + r[2] - kappa, ty * 8 - r[1] + r[3] - kappa]
+                    hi = [X1 - r[0] + r[2] + kappa, Y1 - r[1] + r[3] + kappa]
+                    qmin = 2 * lsq_linear(L, np.zeros(2), bounds=(lo, hi), method="bvls").cost
+                    assert abs(qmin - thr) > 1e-9 * (abs(thr) + 1)  # no decision this close in the fixture
+                    keep = qmin <= thr
+                    exp_dec.append(keep)
+                    if keep:
+                        ek.append((np.uint64(toff + ty * ntx + tx) << np.uint64(32)) | np.uint64(pkey[p]))
+                        ev.append(p)
+        toff += ntx * nty
+        poff += ng
+    exp_dec = np.array(exp_dec, bool)
+    assert np.array_equal(dec.astype(bool), exp_dec)
+    assert np.all(np.sign(margin[margin != 0]) == np.where(exp_dec, 1, -1)[margin != 0])
+    assert (~exp_dec).sum() >= 50 and exp_dec.sum() >= 50
+    keys, vals, ranges = O.bin_decided(P, cams, cfg, rect, pkey, dec)
+    ek, ev = np.array(ek, np.uint64), np.array(ev, np.int64)
+    order = np.argsort(ek, kind="stable")
+    assert np.array_equal(keys, ek[order]) and np.array_equal(vals, ev[order])
+    tiles = (keys >> np.uint64(32)).astype(np.int64)
+    T = ranges.shape[0]
+    first = np.searchsorted(tiles, np.arange(T), side="left")
+    last = np.searchsorted(tiles, np.arange(T), side="right")
+    empty = first == last
+    assert np.array_equal(ranges[~empty, 0], first[~empty]) and np.array_equal(ranges[~empty, 1], last[~empty])
+    assert np.all(ranges[empty] == 0)
+    # against the end-to-end binning (FP64 projection): the same instances
+    # except where the end-to-end band marks the pair
+    k0, v0, _ = O.bin(P, cams, cfg, rec)
+    amb = np.nonzero(rec[:, O.C_RECT_AMBIG] > 0)[0]
+    a = ~np.isin(vals, amb)
+    b = ~np.isin(v0, amb)
+    assert np.array_equal(keys[a], k0[b]) and np.array_equal(vals[a], v0[b])
+
+
 # ---------------------------------------------------------------------------
 # backward: central differences and the translation identity
 # ---------------------------------------------------------------------------
@@ -461,6 +555,137 @@ def test_translation_identity():
     lhs = cams[0].T_cw[:, :3] @ g["means"].sum(0)
     assert np.allclose(g["pose"][0, :3], lhs, rtol=1e-10, atol=1e-10)
     assert np.abs(g["pose"][0, 3:]).max() > 0
+
+
+# ---------------------------------------------------------------------------
+# image-space gradients and the densification statistic (Sec. III-B: the
+# image-space gradient magnitude at the projected splat centre)
+# ---------------------------------------------------------------------------
+
+# record column perturbed for each component of the per-pair image-space
+# gradient (the opacity enters through ln o)
+_G2D_COLS = {O.G_U: O.C_U, O.G_V: O.C_V, O.G_QA: O.C_QA, O.G_QB: O.C_QB, O.G_QC: O.C_QC, O.G_LNO: O.C_OPA,
+             O.G_R: O.C_R, O.G_G: O.C_G, O.G_B: O.C_B, O.G_Z: O.C_Z}
+
+
+def test_image_space_gradients_and_densify_statistic_fd():
+    """Each of the ten image-space gradient components of a pair (mean u, v;
+    conic qa, qb, qc; ln o; colour; depth) against central differences of
+    the loss with that record entry moved and the tile lists kept; then the
+    densification statistic against the same differences: for every
+    Gaussian, the sum over the views where it is visible of the Euclidean
+    norm of (dL/du, dL/dv) in pixels, and the number of those views."""
+    sc = S.random_box_scene(300, 56, 44, 50.0, seed=21, sh_degree=1)
+    rng = np.random.default_rng(21)
+    cam0 = sc.cameras[0]
+    cams = O.as_float32_cameras([cam0, S.perturb_pose(cam0, rng, sigma_t=0.1, sigma_deg=3.0)])
+    P = O.Params.from_scene(sc)
+    rec, keys, vals, ranges, out = O.forward(P, cams, CFG)
+    npx = sum(c.width * c.height for c in cams)
+    wC, wD, wA = rng.normal(size=3 * npx), 0.1 * rng.normal(size=npx), rng.normal(size=npx)
+    rgb_pix = np.concatenate([np.tile(np.arange(c.width * c.height) + sum(d.width * d.height for d in cams[:v]), 3)
+                              for v, c in enumerate(cams)])
+    vis = np.nonzero(rec[:, O.C_VIS] > 0)[0]
+    gauss = rec[:, O.C_GAUSS].astype(int)
+    shared = [g for g in np.unique(gauss[vis]) if (gauss[vis] == g).sum() == 2]
+    assert len(shared) >= 20
+
+    def loss_with(rec_p, mask):
+        o = O.render_fwd(P, cams, CFG, rec_p, vals, ranges)
+        return (wC * mask[rgb_pix]) @ o["rgb"] + (wD * mask) @ o["depth"] + (wA * mask) @ o["alpha"], o["sig"]
+
+    def fd(p, col, h):
+        rp, rm = rec.copy(), rec.copy()
+        if col == O.C_OPA:        # d/d ln o
+            rp[p, col] *= math.exp(h)
+            rm[p, col] *= math.exp(-h)
+        else:
+            rp[p, col] += h
+            rm[p, col] -= h
+        ones = np.ones(npx, bool)
+        _, sp = loss_with(rp, ones)
+        _, sm = loss_with(rm, ones)
+        keep = sp == sm           # pixels whose blended set does not change
+        lp, _ = loss_with(rp, keep)
+        lm, _ = loss_with(rm, keep)
+        return (lp - lm) / (2 * h), keep
+
+    h = 1e-6
+    picked = list(rng.choice(vis, 12, replace=False))
+    for g in shared[:10]:
+        picked += list(np.nonzero((gauss == g) & (rec[:, O.C_VIS] > 0))[0])
+    fd_uv, clean = {}, {}
+    for p in picked:
+        comps = {}
+        masks = []
+        for k, col in _G2D_COLS.items():
+            comps[k], keep = fd(p, col, h)
+            masks.append(keep)
+        keep = np.logical_and.reduce(masks)
+        go = O.render_bwd(P, cams, CFG, rec, vals, ranges, wC * keep[rgb_pix], wD * keep, wA * keep)
+        g2d = go["g2d"][p]
+        scale = max(abs(g2d).max(), 1e-12)
+        for k in _G2D_COLS:
+            assert abs(comps[k] - g2d[k]) <= 1e-6 * scale + 1e-9, (p, k, comps[k], g2d[k])
+        fd_uv[p] = (comps[O.G_U], comps[O.G_V])
+        clean[p] = bool(keep.all())    # no pixel's blended set changed under the moves
+    # the statistic of the Gaussians seen by both views whose moves flip no pixel
+    go = O.render_bwd(P, cams, CFG, rec, vals, ranges, wC, wD, wA)
+    n_ok = 0
+    for g in shared[:10]:
+        pairs = np.nonzero((gauss == g) & (rec[:, O.C_VIS] > 0))[0]
+        if not all(clean[p] for p in pairs):
+            continue
+        ref = sum(math.hypot(*fd_uv[p]) for p in pairs)
+        assert abs(go["dens_acc"][g] - ref) <= 1e-6 * ref, (g, go["dens_acc"][g], ref)
+        assert go["dens_cnt"][g] == len(pairs) == 2
+        n_ok += 1
+    assert n_ok >= 3
+
+
+def test_densify_statistic_closed_form():
+    """One isotropic Gaussian seen twice (two identical views) under the loss
+    L = sum over pixel centres of w * A, with w a smooth bump (3 px wide,
+    polynomial-tilted) that vanishes long before the alpha >= alpha_min edge
+    of the Gaussian's support.  Since alpha depends on (pixel - mean),
+    dL/du = -sum w d(alpha)/dx = sum alpha dw/dx, because the lattice sum of
+    the derivative of the smooth, rapidly decaying w alpha is 0 (to ~1e-12
+    for these widths); likewise dL/dv = sum alpha dw/dy.  The statistic is
+    then the sum over the two views of the Euclidean norm of (dL/du, dL/dv)
+    in pixels (not squared, not normalised), the count is 2, and a third
+    camera that looks away adds nothing."""
+    W, H, f, z = 96, 96, 80.0, 4.0
+    s_world = 6.0 * z / f                         # 6 px image standard deviation before the dilation
+    o = 0.9
+    mu = np.array([[0.25 * z / f, -0.5 * z / f, z]])
+    P = _params(mu, np.log([s_world] * 3), [1, 0, 0, 0], math.log(o / (1 - o)), np.zeros(3))
+    T_away = np.concatenate([np.diag([-1.0, 1.0, -1.0]), np.zeros((3, 1))], 1)
+    cams = O.as_float32_cameras([_cam(W, H, f), _cam(W, H, f), _cam(W, H, f, T=T_away)])
+    rec, keys, vals, ranges, out = O.forward(P, cams, CFG)
+    npx = W * H
+    # pinhole mean of the Gaussian, the bump 1.3 px right of and 0.7 px above it
+    u = f * mu[0, 0] / z + W / 2
+    v = f * mu[0, 1] / z + H / 2
+    u0, v0, b = u + 1.3, v - 0.7, 3.0
+    X, Y = np.meshgrid(np.arange(W) + 0.5, np.arange(H) + 0.5)
+    ex, ey = (X - u0) / b, (Y - v0) / b
+    bump = np.exp(-0.5 * (ex * ex + ey * ey))
+    poly = 1.0 + 0.5 * ex + 0.3 * ey
+    w = (bump * poly).ravel()
+    dw_dx = (bump * (0.5 / b - ex / b * poly)).ravel()
+    dw_dy = (bump * (0.3 / b - ey / b * poly)).ravel()
+    A = out["alpha"][:npx]
+    exp_u, exp_v = A @ dw_dx, A @ dw_dy
+    g = O.render_bwd(P, cams, CFG, rec, vals, ranges, np.zeros(9 * npx), np.zeros(3 * npx),
+                     np.concatenate([w, w, np.zeros(npx)]))
+    scale = math.hypot(exp_u, exp_v)
+    assert abs(exp_u) > 0.05 and abs(exp_v) > 0.05
+    for p in (0, 1):
+        assert abs(g["g2d"][p, O.G_U] - exp_u) <= 1e-8 * scale, (g["g2d"][p, O.G_U], exp_u)
+        assert abs(g["g2d"][p, O.G_V] - exp_v) <= 1e-8 * scale, (g["g2d"][p, O.G_V], exp_v)
+    assert rec[2, O.C_VIS] == 0
+    assert g["dens_cnt"][0] == 2
+    assert abs(g["dens_acc"][0] - 2 * scale) <= 1e-8 * scale
 
 
 # ---------------------------------------------------------------------------
