@@ -81,6 +81,74 @@ def run_gpu(sc, ocfg: O.Config, gC=None, gD=None, gA=None, depth=256, inst_capac
     return out
 
 
+# A float32 evaluation of the tile test (tile_reached in the binning kernel)
+# rounds its box edges, products and threshold: its value of (threshold -
+# minimum) is off from the exact one on the same float inputs by at most
+# about 16 float ulps of the scale oracle.tile_decisions32 divides by.  Four
+# times that is the band inside which either decision is correct.
+TILE_BAND = 64 * 2.0 ** -24
+
+
+def rect_tile_codes(sc, ocfg: O.Config, rect, pkey):
+    """(pair, global tile) of every rectangle tile of every visible pair, in
+    the emission order of oracle.tile_decisions32, as pair * n_tiles + tile."""
+    rect = np.asarray(rect, np.int64).reshape(-1, 4)
+    ng = [int(sc.submap_offsets[c.submap + 1] - sc.submap_offsets[c.submap]) for c in sc.cameras]
+    pair_view = np.repeat(np.arange(len(sc.cameras)), ng)
+    ntx = np.array([-(-c.width // ocfg.tile_w) for c in sc.cameras], np.int64)
+    nty = np.array([-(-c.height // ocfg.tile_h) for c in sc.cameras], np.int64)
+    toff = np.concatenate([[0], np.cumsum(ntx * nty)])
+    T = int(toff[-1])
+    vis = (np.asarray(pkey) != 0xFFFFFFFF) & (rect[:, 2] >= rect[:, 0]) & (rect[:, 3] >= rect[:, 1])
+    p = np.nonzero(vis)[0]
+    w = rect[p, 2] - rect[p, 0] + 1
+    area = w * (rect[p, 3] - rect[p, 1] + 1)
+    rp = np.repeat(p, area)
+    j = np.arange(int(area.sum())) - np.repeat(np.cumsum(area) - area, area)
+    ww = np.repeat(w, area)
+    ty = np.repeat(rect[p, 1], area) + j // ww
+    tx = np.repeat(rect[p, 0], area) + j % ww
+    v = pair_view[rp]
+    return rp * T + toff[v] + ty * ntx[v] + tx, T
+
+
+def check_binning_stage(sc, ocfg: O.Config, g, P=None, cams=None):
+    """The binning stage against the oracle, bit for bit: the oracle takes
+    the CUDA path's own float32 projection outputs (records, rectangles,
+    depth keys), decides every rectangle tile exactly (R6b) and sorts.  Tile
+    decisions must agree except inside TILE_BAND, where the CUDA path's
+    decision is taken; then the sorted keys, instance order and per-tile
+    ranges must be identical.  Returns (decisions, decisions in the band)."""
+    P = P if P is not None else O.Params.from_scene(sc)
+    cams = cams if cams is not None else O.as_float32_cameras(sc.cameras)
+    dec, margin = O.tile_decisions32(P, cams, ocfg, g["rec"], g["rect"], g["pkey"])
+    codes, T = rect_tile_codes(sc, ocfg, g["rect"], g["pkey"])
+    assert codes.shape == dec.shape
+    gp = g["inst_pair"].astype(np.int64)
+    gdec = np.isin(codes, gp * T + g["inst_tile"].astype(np.int64))
+    band = np.abs(margin) < TILE_BAND
+    bad = (gdec != dec.astype(bool)) & ~band
+    assert not bad.any(), f"{int(bad.sum())} tile decisions differ outside the band"
+    resolved = np.where(band, gdec, dec.astype(bool)).astype(np.int8)
+    keys, vals, ranges = O.bin_decided(P, cams, ocfg, g["rect"], g["pkey"], resolved)
+    gkeys = (g["inst_tile"].astype(np.uint64) << np.uint64(32)) | g["pkey"][gp].astype(np.uint64)
+    assert np.array_equal(gkeys, keys), "sorted keys differ"
+    assert np.array_equal(gp, vals), "instance order differs"
+    assert np.array_equal(g["ranges"].astype(np.int64), ranges), "tile ranges differ"
+    # every rectangle tile is emitted once, listed or dropped
+    drop = np.bincount(g["dropped_pair"].astype(np.int64), minlength=len(g["pkey"]))
+    assert drop.sum() + len(gp) == len(dec)
+    return int(len(dec)), int(band.sum())
+
+
+def end_to_end_key_mismatch(g, keys, vals, T):
+    """Instances on one side only, against the FP64 oracle's own projection
+    and binning: (pair, tile) pairs in the symmetric difference."""
+    a = g["inst_pair"].astype(np.int64) * T + g["inst_tile"].astype(np.int64)
+    b = vals.astype(np.int64) * T + (keys >> np.uint64(32)).astype(np.int64)
+    return int(np.setxor1d(a, b).size)
+
+
 def run_oracle(sc, ocfg: O.Config):
     P = O.Params.from_scene(sc)
     cams = O.as_float32_cameras(sc.cameras)

@@ -1,6 +1,7 @@
 """Parity at the benchmark's full size, in the benchmark's launch configuration
 (orchard, 500k Gaussians, three 1280x720 views, SH degree 3, 16x16 tiles,
-batch depth 256): every projected pair and every sort key is compared; the
+batch depth 256): every projected pair is compared, and the binning stage
+bit for bit (keys, instance order, ranges) on the CUDA path's projection; the
 images on 20k sampled pixels (the oracle composites those pixels one by one);
 the gradients with upstream gradients non-zero only on those sampled pixels
 (the oracle's adjoint skips the others)."""
@@ -9,7 +10,8 @@ import pytest
 
 import oracle as O
 from paper_2510_26358_gb300 import scenes as S
-from tests.gpu_helpers import decode_records, pixel_weights, rel_l2, run_gpu
+from tests.gpu_helpers import (check_binning_stage, decode_records, end_to_end_key_mismatch, pixel_weights,
+                               rel_l2, run_gpu)
 
 pytestmark = pytest.mark.gpu
 
@@ -47,13 +49,13 @@ def test_fullsize_projection_and_keys(full):
     d = decode_records(g["rec"][both])
     assert np.array_equal(g["pkey"][both], rec[both, O.C_Z32].astype(np.float32).view(np.uint32))
     assert np.abs(d["u"] - rec[both, O.C_U]).max() < 2e-6 * 1280
-    amb_pairs = np.nonzero(amb)[0]
-    gp = g["inst_pair"].astype(np.int64)
-    gkeys = (g["inst_tile"].astype(np.uint64) << np.uint64(32)) | g["pkey"][gp].astype(np.uint64)
-    kg, ko = ~np.isin(gp, amb_pairs), ~np.isin(full["vals"], amb_pairs)
-    assert np.array_equal(gkeys[kg], full["keys"][ko])
-    assert np.array_equal(gp[kg], full["vals"][ko])
-    print(f"full size: {both.sum()} visible pairs, {len(gkeys)} instances, {len(amb_pairs)} ambiguous")
+    # the binning stage, bit for bit on the CUDA path's own projection outputs
+    n_dec, n_band = check_binning_stage(full["sc"], O.Config(), g)
+    mism = end_to_end_key_mismatch(g, full["keys"], full["vals"], full["ranges"].shape[0])
+    print(f"full size: {both.sum()} visible pairs, {len(g['inst_pair'])} listed instances of {n_dec} rectangle "
+          f"tiles, {n_band} decisions in the float band; end to end {mism} instances differ "
+          f"({amb.sum()} pairs in the FP64 band)")
+    assert n_band <= 1e-4 * n_dec
 
 
 def test_fullsize_sampled_pixels(full):

@@ -1,15 +1,16 @@
 """The larger workloads at full size: the pose-refinement rig (1M Gaussians,
 four perturbed 1440x1080 cameras), the uneven batch (8 submaps with
 log-uniform Gaussian counts, 24 views of mixed resolution) and the large
-keyframe map (4M Gaussians, six 1920x1200 views).  Every projected pair and
-every sort key is compared with the oracle, and 2000 sampled pixels are
-composited by the oracle one by one."""
+keyframe map (4M Gaussians, six 1920x1200 views).  Every projected pair is
+compared with the oracle, the binning stage bit for bit on the CUDA path's own
+projection outputs, and 2000 sampled pixels are composited by the oracle one
+by one."""
 import numpy as np
 import pytest
 
 import oracle as O
 from paper_2510_26358_gb300 import scenes as S
-from tests.gpu_helpers import decode_records, run_gpu
+from tests.gpu_helpers import check_binning_stage, decode_records, end_to_end_key_mismatch, run_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -32,11 +33,9 @@ def test_workload_full_size(name):
         assert np.array_equal(g["pkey"][both], rec[both, O.C_Z32].astype(np.float32).view(np.uint32))
         d = decode_records(g["rec"][both])
         assert np.abs(d["u"] - rec[both, O.C_U]).max() < 1e-6 * 2048
-        amb_pairs = np.nonzero(amb)[0]
-        gp = g["inst_pair"].astype(np.int64)
-        gkeys = (g["inst_tile"].astype(np.uint64) << np.uint64(32)) | g["pkey"][gp].astype(np.uint64)
-        kg, ko = ~np.isin(gp, amb_pairs), ~np.isin(vals, amb_pairs)
-        assert np.array_equal(gkeys[kg], keys[ko]) and np.array_equal(gp[kg], vals[ko])
+        n_dec, n_band = check_binning_stage(sc, ocfg, g, P, cams)
+        assert n_band <= 1e-4 * n_dec
+        mism = end_to_end_key_mismatch(g, keys, vals, ranges.shape[0])
         rng = np.random.default_rng(2)
         pix = np.sort(rng.choice(sc.n_pix, 2000, replace=False))
         o = O.render_fwd_pixels(P, cams, ocfg, rec, vals, ranges, pix)
@@ -49,7 +48,8 @@ def test_workload_full_size(name):
         e_rgb = np.abs(rgb - o["rgb"])[keep].max()
         e_a = np.abs(g["alpha"][pix] - o["alpha"])[keep].max()
         e_d = np.abs(g["depth"][pix] - o["depth"])[keep].max()
-        print(f"{name}: {both.sum()} visible, {len(gkeys)} instances, {amb.sum()} ambiguous; "
+        print(f"{name}: {both.sum()} visible, {len(g['inst_pair'])} instances, {n_band} of {n_dec} tile decisions "
+              f"in the float band, {mism} differ end to end ({amb.sum()} pairs in the FP64 band); "
               f"rgb {e_rgb:.2e} alpha {e_a:.2e} depth {e_d:.2e}")
         assert e_rgb <= 1e-5 and e_a <= 1e-5 and e_d <= 1e-5
     finally:
