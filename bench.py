@@ -7,9 +7,12 @@ cameras, the L1 photometric loss (Eq. 6, lambda = 0) and the LiDAR depth loss
 (Eq. 7), then the full backward to every Gaussian parameter and every camera
 pose.  The metric is rendered megapixels per second over the whole step.
 
-Default workload: the 500k-Gaussian orchard (3 rows of 8 trees, trunk
-cylinders + canopy balls, SH degree 3) seen by a 3-camera rig of 1280x720,
-with 20k LiDAR returns per view and an L1 depth term.  Synthetic, seeded.
+Default workload: the large keyframe map, 4M Gaussians over a 9-row x 40 m
+orchard (trunk cylinders + canopy balls, SH degree 3) seen by two 3-camera
+rigs of 1920x1200, with the KL depth-consistency term of Eq. 7 on 100k LiDAR
+returns per view and the per-Gaussian densification statistics accumulated
+in the backward.  ``--workload orchard500k --depth-loss l1`` runs the 500k
+orchard (3 x 1280x720, 20k returns a view).  Synthetic, seeded.
 
 Arms:
   default            the batched path: one CUDA graph per step covering every
@@ -48,13 +51,16 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="orchard500k")
+    ap.add_argument("--workload", default="orchard4m")
     ap.add_argument("--tile", default="auto", help="WxH, or auto to let the autotuner pick tile and depth")
     ap.add_argument("--depth", type=int, default=256)
     ap.add_argument("--no-per-view", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--cpu-sample", type=int, default=640, help="crop width (px) per view for the oracle sample")
+    ap.add_argument("--cpu-sample", type=int, default=0,
+                    help="crop width (px) of each view in the oracle sample (0: full frames)")
+    ap.add_argument("--cpu-views", type=int, default=-1,
+                    help="views in the oracle sample (0: all; -1: the workload's default)")
     ap.add_argument("--ssim-lambda", type=float, default=0.0,
                     help="weight lambda of the SSIM term of Eq. 6 (0: L1 image loss only)")
     ap.add_argument("--adam", action="store_true",
@@ -63,7 +69,7 @@ def parse():
                     help="also time one map-lifecycle pass (prune, reset, split / clone) on the workload")
     ap.add_argument("--active-set", action="store_true",
                     help="also time voxel-hash insertion of a point batch, LRU selection and an offload to host memory")
-    ap.add_argument("--depth-loss", default="l1", choices=list(DEPTH_LOSSES),
+    ap.add_argument("--depth-loss", default="kl", choices=list(DEPTH_LOSSES),
                     help="depth term of the step: l1, kl (Eq. 7, fixed sigma_u) or kl-var (Eq. 7 with the "
                          "rendered variance: forward and backward with the central depth moment)")
     return ap.parse_args()
@@ -510,15 +516,25 @@ def kernel_breakdown(torch, G, step, steps, flush):
 # reference arm and CPU baseline: the FP64 oracle on a bounded sample
 # ---------------------------------------------------------------------------
 
-def oracle_sample(sc, crop_w):
-    """The workload's cameras cropped to a centred window crop_w wide (same
-    aspect ratio): same scene, same Gaussians, fewer pixels."""
+# The oracle's sample of each workload: full frames of every view for the
+# small box scene and the 500k orchard; one full view of the larger ones (the
+# FP64 step over all six 1920x1200 views of the 4M map takes minutes).
+ORACLE_VIEWS = {"box10k": 0, "orchard500k": 0, "orchard1m_pose": 1, "submaps8": 1, "orchard4m": 1}
+
+
+def oracle_sample(sc, crop_w=0, n_views=0):
+    """The cameras the oracle renders: the first ``n_views`` views (0: all),
+    each cropped to a centred window ``crop_w`` wide of the same aspect ratio
+    (0: the full frame).  Same scene, same Gaussians, fewer pixels.  Returns
+    (cameras, their view indices in the workload)."""
+    idx = list(range(len(sc.cameras) if n_views <= 0 else min(n_views, len(sc.cameras))))
     cams = []
-    for c in sc.cameras:
-        w = min(crop_w, c.width)
-        h = max(1, int(round(w * c.height / c.width)))
-        cams.append(c.crop(int(c.cx) - w // 2, int(c.cy) - h // 2, w, h))
-    return cams
+    for v in idx:
+        c = sc.cameras[v]
+        w = c.width if crop_w <= 0 else min(crop_w, c.width)
+        h = c.height if crop_w <= 0 else max(1, int(round(w * c.height / c.width)))
+        cams.append(c.crop(int(c.cx) - w // 2, int(c.cy) - h // 2, w, h) if (w, h) != (c.width, c.height) else c)
+    return cams, idx
 
 
 def run_oracle_step(O, P, cams, cfg, lidar_full, sc, depth_loss="l1", ssim_lambda=0.0, adam=False):
@@ -548,28 +564,52 @@ def run_oracle_step(O, P, cams, cfg, lidar_full, sc, depth_loss="l1", ssim_lambd
     return npx
 
 
-def cpu_baseline(sc, args, reps=1):
+def oracle_threads() -> int:
+    """Every host core of the machine (the oracle's loops over pairs and
+    pixels run on OpenMP threads)."""
+    return os.cpu_count() or 1
+
+
+def cpu_baseline(sc, args, reps=1, state=None):
+    """The FP64 oracle's full step on the sample of ``oracle_sample``, on all
+    host cores.  ``state`` (a dict) keeps the widened parameters between calls."""
     import oracle as O
     O.build()
-    cams = O.as_float32_cameras(oracle_sample(sc, args.cpu_sample))
-    P = O.Params.from_scene(sc)
-    # LiDAR returns re-expressed in the crops' pixel coordinates
-    lid = sc.lidar.astype(np.float64).copy()
-    for v, (c, cc) in enumerate(zip(sc.cameras, cams)):
-        m = lid[:, 3] == v
-        lid[m, 0] -= (c.cx - cc.cx)
-        lid[m, 1] -= (c.cy - cc.cy)
+    cores = oracle_threads()
+    O.set_threads(cores)
+    n_views = args.cpu_views if args.cpu_views >= 0 else ORACLE_VIEWS.get(sc.name, 1)
+    sel, idx = oracle_sample(sc, args.cpu_sample, n_views)
+    cams = O.as_float32_cameras(sel)
+    if state is not None and "P" in state:
+        P = state["P"]
+    else:
+        P = O.Params.from_scene(sc)
+        if state is not None:
+            state["P"] = P
+    # the sample's LiDAR returns, re-expressed in its (cropped) views
+    lid_all = sc.lidar.astype(np.float64)
+    parts = []
+    for j, (v, cc) in enumerate(zip(idx, cams)):
+        c = sc.cameras[v]
+        m = lid_all[lid_all[:, 3] == v].copy()
+        m[:, 0] -= (c.cx - cc.cx)
+        m[:, 1] -= (c.cy - cc.cy)
+        m[:, 3] = j
+        parts.append(m)
+    lid = np.concatenate(parts) if parts else np.zeros((0, 4))
     cfg = O.Config()
     t0 = time.perf_counter()
     npx = 0
     for _ in range(reps):
         npx += run_oracle_step(O, P, cams, cfg, lid, sc, args.depth_loss, args.ssim_lambda, args.adam)
     dt = time.perf_counter() - t0
-    sample = (f"FP64 oracle, full step (project all {sc.n} Gaussians x {len(cams)} views, bin, forward, "
-              f"{loss_label(args)}, backward) on centred {cams[0].width}x{cams[0].height} crops "
-              f"of every view, "
-              f"{reps} step(s), {dt:.1f} s")
-    return {"value": npx / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+    full = all((c.width, c.height) == (sc.cameras[v].width, sc.cameras[v].height) for v, c in zip(idx, cams))
+    frames = "full frames" if full else f"centred {cams[0].width}x{cams[0].height} crops"
+    views = "every view" if len(idx) == len(sc.cameras) else f"{len(idx)} of the {len(sc.cameras)} views"
+    sample = (f"FP64 oracle on {cores} host threads, full step (project all {sc.n} Gaussians x {len(cams)} "
+              f"view(s), bin, forward, {loss_label(args)}, backward) on {frames} of {views}, "
+              f"{npx} pixels, {reps} step(s), {dt:.1f} s")
+    return {"value": npx / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
             "seconds": dt, "pixels": npx}
 
 
@@ -581,11 +621,12 @@ def run_reference(args):
     sc = scenes.workload(args.workload)
     # warm-up and timed steps, each a bounded sample of the workload
     cb = None
+    state = {}
     for _ in range(args.warmup):
-        cpu_baseline(sc, args)
+        cpu_baseline(sc, args, state=state)
     vals, secs, pix = [], 0.0, 0
     for _ in range(args.steps):
-        cb = cpu_baseline(sc, args)
+        cb = cpu_baseline(sc, args, state=state)
         secs += cb["seconds"]
         pix += cb["pixels"]
     value = pix / secs / 1e6
@@ -593,7 +634,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(sc, args),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cb["sample"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
+                             "sample": cb["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0

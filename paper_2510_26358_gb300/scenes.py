@@ -289,6 +289,36 @@ def _ray_hits(origin, dirs, trees):
     return best
 
 
+def _scan_hits(origin, dirs, n_beams, az, trees):
+    """_ray_hits over a beams x azimuths grid of rays (row-major), testing each
+    tree only against the azimuths that can reach it: a tree's trunk and
+    canopy lie inside the vertical cylinder of radius CANOPY_RADIUS about its
+    axis, which a ray from ``origin`` meets only within asin(R / d) of the
+    tree's bearing (d the horizontal distance; every azimuth when d <= R).
+    The window is widened by 1e-3 rad, so every ray that hits the tree is
+    tested, and the nearest hit of each ray is the same as testing all trees."""
+    n_az = len(az)
+    best = np.full(len(dirs), np.inf)
+    o = np.asarray(origin, np.float64)
+    step = 2 * math.pi / n_az
+    beam_base = (np.arange(n_beams) * n_az)[:, None]
+    for tree in trees:
+        dx, dy = tree[0] - o[0], tree[1] - o[1]
+        d = math.hypot(dx, dy)
+        if d <= CANOPY_RADIUS + 1e-6:
+            sel = np.arange(len(dirs))
+        else:
+            half = math.asin(CANOPY_RADIUS / d) + 1e-3
+            c = math.atan2(dy, dx)
+            k0 = int(math.floor((c - half) / step))
+            k1 = int(math.ceil((c + half) / step))
+            ks = np.unique(np.arange(k0, k1 + 1) % n_az)
+            sel = (beam_base + ks[None, :]).ravel()
+        t = _ray_hits(o, dirs[sel], np.asarray([tree]))
+        best[sel] = np.minimum(best[sel], t)
+    return best
+
+
 def lidar_scan(rng, origin, trees, cameras, per_view, n_beams=32,
                elev=(-25.0, 15.0), n_az=2048, max_az=65536, near=0.2):
     """32-beam spinning scan from ``origin`` ray-cast against the trunk
@@ -304,9 +334,7 @@ def lidar_scan(rng, origin, trees, cameras, per_view, n_beams=32,
         az = np.linspace(0, 2 * math.pi, n_az, endpoint=False)
         E, Az = np.meshgrid(elevs, az, indexing="ij")
         dirs = np.stack([np.cos(E) * np.cos(Az), np.cos(E) * np.sin(Az), np.sin(E)], -1).reshape(-1, 3)
-        dist = np.full(len(dirs), np.inf)
-        for i in range(0, len(dirs), 1 << 16):
-            dist[i:i + (1 << 16)] = _ray_hits(origin, dirs[i:i + (1 << 16)], near_trees)
+        dist = _scan_hits(origin, dirs, n_beams, az, near_trees)
         ok = np.isfinite(dist)
         pts = np.asarray(origin)[None, :] + dirs[ok] * dist[ok, None]
         per_cam = []
