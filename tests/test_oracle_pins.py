@@ -28,6 +28,7 @@ sign, a transposed operand or a wrong index in the oracle fails at least one:
 """
 import copy
 import math
+import os
 
 import numpy as np
 import pytest
@@ -536,6 +537,87 @@ def test_fd_orchard_crop_posed_rig():
     res = _fd_case(sc, cams, 3, seed=2)
     _assert_fd(res)
     assert sum(1 for r in res if r[0].startswith("pose")) == 24
+
+
+def test_fd_pose_rig_config_step():
+    """Central differences with the pose-refinement workload's own step
+    h = 1e-4, on that workload: the 1M-Gaussian orchard and its four
+    perturbed 1440x1080 cameras, each cropped to a 64x48 window; the
+    Gaussians are restricted to those visible in a crop (the others have no
+    instance in any crop's tiles and so no effect on the images).  All 24
+    pose twists, and 13 entries of each parameter type among the Gaussians
+    that blend somewhere (most visible ones sit behind saturated pixels and
+    have no gradient).  A rotation of 1e-4 moves the image by ~0.13 px, so
+    the plain differences carry an O(h^2) truncation of ~1e-2 of the
+    gradient; Richardson's extrapolation (4 D(h/2) - D(h)) / 3 removes it,
+    and that must agree with the analytic gradient to 1e-4.  Pixels whose
+    blended set changes in any of the four evaluations are masked on both
+    sides."""
+    from tests.rig_crop import pose_rig_crop, visible_subset
+    sc = pose_rig_crop()
+    cams = O.as_float32_cameras(sc.cameras)
+    prev = O.set_threads(os.cpu_count() or 1)
+    try:
+        rec = O.project(O.Params.from_scene(sc), cams, CFG)
+        sub = visible_subset(sc, np.unique(rec[rec[:, O.C_VIS] > 0, O.C_GAUSS].astype(np.int64)))
+        P = O.Params.from_scene(sub)
+        npx = sub.n_pix
+        rng = np.random.default_rng(5)
+        wC, wD, wA = rng.normal(size=3 * npx), 0.1 * rng.normal(size=npx), rng.normal(size=npx)
+        rgb_pix = np.concatenate([np.tile(np.arange(c.width * c.height) + sum(d.width * d.height for d in cams[:v]), 3)
+                                  for v, c in enumerate(cams)])
+        r0, k0, v0, rg0, o0 = O.forward(P, cams, CFG)
+        g_all = O.render_bwd(P, cams, CFG, r0, v0, rg0, wC, wD, wA)
+        blending = np.nonzero(np.abs(g_all["opacity_logits"]) > 1e-8 * np.abs(g_all["opacity_logits"]).max())[0]
+        assert len(blending) >= 200
+
+        def loss(o, keep):
+            return (wC * keep[rgb_pix]) @ o["rgb"] + (wD * keep) @ o["depth"] + (wA * keep) @ o["alpha"]
+
+        def richardson(move):
+            """move(s) -> (Params, cameras) displaced by s along the direction."""
+            h = 1e-4
+            outs = {s: O.forward(*move(s), CFG)[4] for s in (h, -h, h / 2, -h / 2)}
+            keep = np.logical_and.reduce([o["sig"] == o0["sig"] for o in outs.values()])
+            d1 = (loss(outs[h], keep) - loss(outs[-h], keep)) / (2 * h)
+            d2 = (loss(outs[h / 2], keep) - loss(outs[-h / 2], keep)) / h
+            return d1, (4 * d2 - d1) / 3, keep
+
+        results = []
+        for name in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+            for _ in range(13):
+                gi = int(rng.choice(blending))
+                A = getattr(P, name)
+                idx = (gi,) + tuple(int(rng.integers(0, n)) for n in A.shape[1:])
+
+                def move(s, name=name, idx=idx):
+                    Pm = P.copy()
+                    getattr(Pm, name)[idx] += s
+                    return Pm, cams
+                d1, dr, keep = richardson(move)
+                an = O.render_bwd(P, cams, CFG, r0, v0, rg0, wC * keep[rgb_pix], wD * keep, wA * keep)[name][idx]
+                results.append((name, dr, an, int((~keep).sum())))
+        raw = []
+        for v in range(len(cams)):
+            for k in range(6):
+                def move(s, v=v, k=k):
+                    cm = copy.deepcopy(cams)
+                    xi = np.zeros(6)
+                    xi[k] = s
+                    cm[v].T_cw = _se3_left(cams[v].T_cw, xi)
+                    return P, cm
+                d1, dr, keep = richardson(move)
+                an = O.render_bwd(P, cams, CFG, r0, v0, rg0, wC * keep[rgb_pix], wD * keep, wA * keep)["pose"][v, k]
+                results.append((f"pose{v}.{k}", dr, an, int((~keep).sum())))
+                raw.append(abs(d1 - an) / max(abs(an), 1e-12))
+    finally:
+        O.set_threads(prev)
+    assert sum(1 for r in results if r[0].startswith("pose")) == 24
+    zero = [r for r in results if r[2] == 0]
+    print("entries with a zero gradient (clamped colour channels):", [(r[0], r[1]) for r in zero])
+    assert len(zero) <= 8 and all(r[0] == "sh" and r[1] == 0 for r in zero)
+    _assert_fd(results, rtol=1e-4)
+    print(f"plain central differences at h = 1e-4: pose error up to {max(raw):.1e} of the gradient")
 
 
 def test_translation_identity():
