@@ -52,7 +52,8 @@ typedef enum {
     GS_ERR_INVALID_ARG = 1, /* a pointer, size or configuration value is out of range */
     GS_ERR_CAPACITY = 2,    /* more (view, Gaussian, tile) instances than the workspace holds */
     GS_ERR_CUDA = 3,        /* a CUDA runtime call failed (message: gs_last_error) */
-    GS_ERR_STATE = 4        /* calls out of order (e.g. gs_render_fwd before gs_bin_sort) */
+    GS_ERR_STATE = 4,       /* calls out of order (e.g. gs_render_fwd before gs_bin_sort) */
+    GS_ERR_TIMEOUT = 5      /* a bounded device-side wait ran out (the step's results are not valid) */
 } gs_status;
 
 /* One pinhole camera (80 bytes). */
@@ -221,8 +222,10 @@ gs_status gs_render_bwd_var(gs_workspace *ws, const gs_gaussians *g, const gs_ca
                             void *stream);
 
 /* Synchronise `stream` and report device-side conditions: returns
- * GS_ERR_CAPACITY if the last gs_bin_sort needed more instances than the
- * capacity. Any out pointer may be NULL. */
+ * GS_ERR_TIMEOUT if a bounded device-side wait ran out since the last
+ * gs_bin_sort (the outputs of that step are not valid), else GS_ERR_CAPACITY
+ * if the last gs_bin_sort needed more instances than the capacity. Any out
+ * pointer may be NULL. */
 gs_status gs_workspace_status(gs_workspace *ws, void *stream, int64_t *n_instances, int64_t *n_visible);
 
 /* Sizes of the workspace: info[0] n_pairs, [1] n_tiles, [2] n_pix, [3]
@@ -242,8 +245,7 @@ gs_status gs_workspace_info(gs_workspace *ws, int64_t *info, int32_t n_info);
 gs_status gs_workspace_copy(gs_workspace *ws, int32_t which, void *dst, int64_t *bytes, void *stream);
 
 /* gs_image_l1 for callers that cannot allocate device memory (the paper has
- * no counterpart: this is a deployment variant of the L1 term of Eq. (6)).
- * Some callers may not call cudaMalloc: a hard real-time mapping loop whose
+ * no counterpart).  Some callers may not call cudaMalloc: a hard real-time mapping loop whose
  * memory is fixed at start-up (cudaMalloc can block and synchronise the
  * device), or code embedded in a host program that only hands over its
  * buffers.  This call needs no workspace and allocates nothing: its only
@@ -255,8 +257,10 @@ gs_status gs_workspace_copy(gs_workspace *ws, int32_t which, void *dst, int64_t 
  * n beyond GS_IMAGE_L1_NOALLOC_BLOCKS * GS_IMAGE_L1_NOALLOC_CHUNK returns
  * GS_ERR_INVALID_ARG without launching anything.  The first call on a device
  * (made with that device current) resolves the array's address once; make
- * it before any stream capture.  All calls share the array: calls whose
- * kernels overlap on the GPU race on it. */
+ * it before any stream capture.  After a device reset (cudaDeviceReset) the
+ * next call resolves it again, so that call too belongs outside a capture.
+ * All calls share the array: calls whose kernels overlap on the GPU race on
+ * it. */
 #define GS_IMAGE_L1_NOALLOC_BLOCKS 1024
 #define GS_IMAGE_L1_NOALLOC_CHUNK 65536
 gs_status gs_image_l1_noalloc(const float *rgb, const float *target, int64_t n, float *loss,
@@ -401,7 +405,7 @@ gs_status gs_partition(gs_voxel *vx, const int32_t *flags, int64_t n, int32_t sh
  * kernels waits on an mbarrier for at most a second): one block waits on a
  * barrier that no copy will ever complete for limit_ns (1 .. 2e9), then sets
  * the workspace's time-out flag and writes *result (device int32) = 1.
- * gs_workspace_status then reports GS_ERR_CUDA until the next gs_bin_sort. */
+ * gs_workspace_status then reports GS_ERR_TIMEOUT until the next gs_bin_sort. */
 gs_status gs_selftest_wait_timeout(gs_workspace *ws, int64_t limit_ns, int32_t *result, void *stream);
 
 /* Sets count (0..16) device buffers to zero in one launch: ptrs[i] (device)

@@ -125,6 +125,7 @@ const char *gs_status_string(gs_status s) {
         case GS_ERR_CAPACITY: return "instance capacity exceeded";
         case GS_ERR_CUDA: return "CUDA error";
         case GS_ERR_STATE: return "call out of order";
+        case GS_ERR_TIMEOUT: return "a bounded device-side wait timed out";
     }
     return "unknown status";
 }
@@ -432,7 +433,7 @@ gs_status gs_workspace_status(gs_workspace *ws, void *stream, int64_t *n_instanc
     if (e != cudaSuccess) return fail(GS_ERR_CUDA, std::string("status: ") + cudaGetErrorString(e));
     if (n_instances) *n_instances = (int64_t)h.n_inst_needed;
     if (n_visible) *n_visible = (int64_t)h.n_vis;
-    if (h.flags & kFlagTimeout) return fail(GS_ERR_CUDA, "a device-side wait for a TMA copy timed out");
+    if (h.flags & kFlagTimeout) return fail(GS_ERR_TIMEOUT, "a device-side wait for a TMA copy timed out");
     return (h.flags & kFlagCapacity) ? GS_ERR_CAPACITY : GS_OK;
 }
 

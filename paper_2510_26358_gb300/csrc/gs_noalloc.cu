@@ -12,9 +12,14 @@
 // Set-up: the first call on a device (with that device current) resolves the
 // array's device address with cudaGetSymbolAddress and caches it; make that
 // first call before any stream capture.  Later calls reuse the address and
-// call nothing that allocates.  All calls share the array, so calls whose
-// kernels overlap on the GPU race on it; every partial a call reads is first
-// written by that same call, so nothing needs clearing between calls.
+// call nothing that allocates.  The cached address is checked on every call
+// (cudaPointerGetAttributes: still device memory of this device): after a
+// device reset has unloaded the library's module, the check fails and the
+// call resolves the address again, so the first call after a reset is a
+// set-up call too and also belongs outside any stream capture.  All calls
+// share the array, so calls whose kernels overlap on the GPU race on it;
+// every partial a call reads is first written by that same call, so nothing
+// needs clearing between calls.
 #include <mutex>
 #include <string>
 
@@ -85,6 +90,15 @@ gs_status partials_address(double **out) {
         return GS_ERR_INVALID_ARG;
     }
     std::lock_guard<std::mutex> lock(g_setup_mutex);
+    if (g_partials_addr[dev]) {
+        // still this device's memory?  (a device reset unloads the module)
+        cudaPointerAttributes a{};
+        e = cudaPointerGetAttributes(&a, g_partials_addr[dev]);
+        if (e != cudaSuccess || a.type != cudaMemoryTypeDevice || a.device != dev) {
+            (void)cudaGetLastError();  // the failed query is not an error of this call
+            g_partials_addr[dev] = nullptr;
+        }
+    }
     if (!g_partials_addr[dev]) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_l1_partials);

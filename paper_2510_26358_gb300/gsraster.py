@@ -19,7 +19,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libgsraster.so")
 
-GS_OK, GS_ERR_INVALID_ARG, GS_ERR_CAPACITY, GS_ERR_CUDA, GS_ERR_STATE = range(5)
+GS_OK, GS_ERR_INVALID_ARG, GS_ERR_CAPACITY, GS_ERR_CUDA, GS_ERR_STATE, GS_ERR_TIMEOUT = range(6)
 GS_MAX_VIEWS = 64
 GS_MAX_SUBMAPS = 64
 # gs_workspace_copy buffer ids

@@ -370,7 +370,7 @@ def test_device_wait_timeout_is_reported():
     assert int(res.item()) == 1
     with pytest.raises(G.GsError) as ei:
         st = r.status()
-    assert ei.value.status == G.GS_ERR_CUDA
+    assert ei.value.status == G.GS_ERR_TIMEOUT
     r.forward(*P)
     assert r.status()[0] == G.GS_OK
     r.close()
