@@ -16,7 +16,9 @@
 // depth key uses double: GB300's FP64 rate is a small fraction of its FP32
 // rate, and the visible pairs are a sparse subset of every warp.
 // The image covariance is built from the rows of J W R S, its determinant
-// through the Lagrange identity (a sum of squares), so no step cancels.
+// through the Lagrange identity (a sum of squares) with the minors taken by
+// the Binet-Cauchy identity from the camera and the Gaussian's axes, so no
+// step cancels, not even for a long thin Gaussian.
 //
 // Backward (chain rule through the same steps), over chunks of one submap:
 // each block first packs the chunk's Gaussians that some view sees (most are
@@ -105,14 +107,6 @@ __device__ __forceinline__ void sh_basis_grad(float x, float y, float z, float d
         dY[14][2] = kC3e * (x * x - y * y);
         dY[15][0] = 3.f * kC3a * (x * x - y * y); dY[15][1] = -6.f * kC3a * x * y;
     }
-}
-
-// a*b - c*d with one rounding error (Kahan's difference of products)
-__device__ __forceinline__ float diff_prod(float a, float b, float c, float d) {
-    float w = c * d;
-    float e = __fmaf_rn(-c, d, w);
-    float f = __fmaf_rn(a, b, -w);
-    return f + e;
 }
 
 struct Cam {
@@ -220,6 +214,36 @@ __device__ __forceinline__ float quat_rot(const float q[4], float qh[4], float R
     return qn;
 }
 
+// The rotation of q correctly rounded to float, R = M(q) / |q|^2 with the
+// quadratic entries of M formed in double (products of floats are exact in
+// double).  Used for strongly anisotropic Gaussians: a long axis s_L rounded
+// by an ulp leans by ~1e-7 rad, which its projection onto a thin image
+// direction turns into an error of the thin variance relative to itself of
+// ~1e-7 s_L / s_thin (1e-5 for a 180:1 needle); correct rounding keeps each
+// entry's error at half an ulp.
+__device__ __forceinline__ void quat_rot_rn(const float q[4], float R[9]) {
+    const double w = q[0], x = q[1], y = q[2], z = q[3];
+    const double ww = w * w, xx = x * x, yy = y * y, zz = z * z;
+    const double inv = 1.0 / ((ww + xx) + (yy + zz));
+    const double i2 = 2.0 * inv;
+    R[0] = (float)(((ww + xx) - (yy + zz)) * inv);
+    R[1] = (float)((x * y - w * z) * i2);
+    R[2] = (float)((x * z + w * y) * i2);
+    R[3] = (float)((x * y + w * z) * i2);
+    R[4] = (float)(((ww + yy) - (xx + zz)) * inv);
+    R[5] = (float)((y * z - w * x) * i2);
+    R[6] = (float)((x * z - w * y) * i2);
+    R[7] = (float)((y * z + w * x) * i2);
+    R[8] = (float)(((ww + zz) - (xx + yy)) * inv);
+}
+
+// Axis-scale ratio above which the rotation is formed by quat_rot_rn: a float
+// rotation leaves the thin variance ~6e-8 x the ratio off, 1.9e-6 at 32:1 (the
+// bar is 1e-5), and the double path costs a warp its FP64 instructions
+// whenever one lane takes it (a threshold of 8:1 sent most warps of the
+// orchard's trunks and canopies there: projection 0.54 -> 0.77 ms at 4M).
+constexpr float kAnisoLogRatio = 3.4657359f;  // ln 32
+
 struct ProjArgs {
     const float *means, *log_scales, *quats, *opac, *sh;
     int64_t n;
@@ -253,7 +277,7 @@ struct PairGeom {
 };
 
 __device__ __forceinline__ void pair_geom(const Cam &cam, int W, int H, const Consts &k, float px, float py,
-                                          float pz, const float M[9], PairGeom &G) {
+                                          float pz, const float R[9], const float S[3], PairGeom &G) {
     G.pxf = px;
     G.pyf = py;
     G.pzf = pz;
@@ -271,11 +295,15 @@ __device__ __forceinline__ void pair_geom(const Cam &cam, int W, int H, const Co
     G.J11 = cam.fy * iz;
     G.J12 = -cam.fy * G.tyc * iz2;
     const float *T = cam.T;
+    // U = W R: the Gaussian's unit axes in camera coordinates (columns); W R S = U S
+    float U[9];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int j = 0; j < 3; ++j)
-            G.WM[3 * i + j] = T[4 * i + 0] * M[j] + T[4 * i + 1] * M[3 + j] + T[4 * i + 2] * M[6 + j];
+        for (int j = 0; j < 3; ++j) {
+            U[3 * i + j] = T[4 * i + 0] * R[j] + T[4 * i + 1] * R[3 + j] + T[4 * i + 2] * R[6 + j];
+            G.WM[3 * i + j] = U[3 * i + j] * S[j];
+        }
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         G.r0[j] = G.J00 * G.WM[j] + G.J02 * G.WM[6 + j];
@@ -286,9 +314,18 @@ __device__ __forceinline__ void pair_geom(const Cam &cam, int W, int H, const Co
     G.b = G.r0[0] * G.r1[0] + G.r0[1] * G.r1[1] + G.r0[2] * G.r1[2];
     G.a = n0 + k.dilation;
     G.c = n1 + k.dilation;
-    G.cx = diff_prod(G.r0[1], G.r1[2], G.r0[2], G.r1[1]);
-    G.cy = diff_prod(G.r0[2], G.r1[0], G.r0[0], G.r1[2]);
-    G.cz = diff_prod(G.r0[0], G.r1[1], G.r0[1], G.r1[0]);
+    // r0 x r1, whose components are the 2x2 minors of T2 = J U S: by the
+    // Binet-Cauchy identity the minor of columns (k, l) is
+    //   s_k s_l (j0 x j1) . (u_k x u_l) = s_k s_l (j0 x j1) . u_m
+    // for (k, l, m) cyclic (the columns u of a rotation: u_k x u_l = u_m), with
+    // j0 = (J00, 0, J02), j1 = (0, J11, J12) the rows of J.  Taken from the
+    // entries of r0 and r1 instead, a minor of a long thin Gaussian is a
+    // difference of products of its long axis's large terms: their rounding
+    // (about an ulp of s_long^2) swamps the true value s_long s_thin.
+    const float nx = -G.J02 * G.J11, ny = -G.J00 * G.J12, nz = G.J00 * G.J11;
+    G.cx = S[1] * S[2] * (nx * U[0] + ny * U[3] + nz * U[6]);
+    G.cy = S[2] * S[0] * (nx * U[1] + ny * U[4] + nz * U[7]);
+    G.cz = S[0] * S[1] * (nx * U[2] + ny * U[5] + nz * U[8]);
     G.det = (G.cx * G.cx + G.cy * G.cy + G.cz * G.cz) + k.dilation * (n0 + n1) + k.dilation * k.dilation;
 }
 
@@ -331,11 +368,8 @@ __global__ void __launch_bounds__(kProjThreads) k_project_fwd(ProjArgs A) {
     float qh[4], R[9];
     float qn = quat_rot(q, qh, R);
     float S[3] = {expf(ls[0]), expf(ls[1]), expf(ls[2])};
-    float M[9];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) M[3 * i + j] = R[3 * i + j] * S[j];
+    if (fmaxf(ls[0], fmaxf(ls[1], ls[2])) - fminf(ls[0], fminf(ls[1], ls[2])) > kAnisoLogRatio && qn > 0.f)
+        quat_rot_rn(q, R);
     // ln o = -ln(1 + e^-omega); support threshold E = 2 ln(o / alpha_min)
     // largest axis scale, for the conservative frustum test below
     const float smax = fmaxf(S[0], fmaxf(S[1], S[2]));
@@ -390,7 +424,7 @@ __global__ void __launch_bounds__(kProjThreads) k_project_fwd(ProjArgs A) {
                 vis = false;
         }
         if (vis) {
-            pair_geom(cam, vi.W, vi.H, k, pxx.x, pyy.x, pzz.x, M, G);
+            pair_geom(cam, vi.W, vi.H, k, pxx.x, pyy.x, pzz.x, R, S, G);
             vis = G.det > 0.f;
         }
         if (vis) {
@@ -631,11 +665,8 @@ __global__ void __launch_bounds__(kProjBwdThreads, 512 / kProjBwdThreads) k_proj
         float qh[4], R[9];
         float qn = quat_rot(q, qh, R);
         float S[3] = {expf(ls[0]), expf(ls[1]), expf(ls[2])};
-        float M[9];
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int j = 0; j < 3; ++j) M[3 * i + j] = R[3 * i + j] * S[j];
+        if (fmaxf(ls[0], fmaxf(ls[1], ls[2])) - fminf(ls[0], fminf(ls[1], ls[2])) > kAnisoLogRatio && qn > 0.f)
+            quat_rot_rn(q, R);  // the forward's rotation
         float o = 1.f / (1.f + expf(-om));
 
         float gmu[3] = {0, 0, 0}, gM[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, gom = 0.f;
@@ -659,7 +690,7 @@ __global__ void __launch_bounds__(kProjBwdThreads, 512 / kProjBwdThreads) k_proj
                     PairGeom G;
                     pair_geom(cam, vi.W, vi.H, k, view_coord_ff(cam.T, mu[0], mu[1], mu[2]).x,
                               view_coord_ff(cam.T + 4, mu[0], mu[1], mu[2]).x, view_coord_ff(cam.T + 8, mu[0], mu[1], mu[2]).x,
-                              M, G);
+                              R, S, G);
                     const float p[3] = {G.pxf, G.pyf, G.pzf};
                     const float *T = cam.T;
                     float gp[3] = {0.f, 0.f, gz};

@@ -10,7 +10,7 @@ counted; their upstream gradients are zeroed on both sides.  The binning is
 checked as a stage: the oracle bins the CUDA path's own float32 projection
 outputs, so that keys, instance order and ranges compare bit for bit (tile
 decisions within a few float ulps of their threshold take the CUDA path's
-side, and are counted).  One case is a known gap (KNOWN_GAPS below).
+side, and are counted).
 """
 import numpy as np
 import pytest
@@ -58,15 +58,9 @@ def _scenes():
 
 SCENES = _scenes()
 
-# Known precision gap of the float32 projection on needle-shaped Gaussians
-# (thin axes ~0.2 px under the 0.3 px dilation, long axes up to ~70 px,
-# covariance condition up to 2600); keys, images and gradients meet the bar.
-# Strict: the projection has no atomics, so the value is reproducible and a
-# fix shows as a pass.
-KNOWN_GAPS = {
-    ("test_projection", "needles"):
-        "qc up to 1.02e-5 of its scale: the float rotation of the long axis, projected across the thin one",
-}
+# Known precision gaps (none at present): (test name, scene) -> reason, run
+# as strict xfails so that a fix shows as a pass.
+KNOWN_GAPS = {}
 
 
 def _known_gap(request, case):
