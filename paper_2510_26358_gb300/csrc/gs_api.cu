@@ -238,6 +238,8 @@ gs_status gs_workspace_create(const gs_camera *cams, int32_t n_views, const int6
     }
     ws->proj_blocks = blocks;
     ws->sort_blocks = std::min(4 * kSortThreads, 2 * ws->num_sms);
+    // the radix scan takes at most 4 kSortThreads blocks
+    ws->wide_blocks = std::min(4 * kSortThreads, 6 * ws->num_sms);
 
     // constants
     Consts &k = ws->consts;
@@ -282,8 +284,9 @@ gs_status gs_workspace_create(const gs_camera *cams, int32_t n_views, const int6
     GS_ALLOC(ws->last, (size_t)ws->n_pix);
     GS_ALLOC(ws->tfin, (size_t)ws->n_pix);
     GS_ALLOC(ws->vstat, (size_t)ws->n_pix);
-    GS_ALLOC(ws->hist, (size_t)256 * 2 * ws->sort_blocks);  // the instance sort runs 2 x sort_blocks
-    GS_ALLOC(ws->part, (size_t)ws->sort_blocks + 1);
+    // the instance sort runs 2 x sort_blocks, the compaction and depth sort wide_blocks
+    GS_ALLOC(ws->hist, (size_t)256 * std::max(2 * ws->sort_blocks, ws->wide_blocks));
+    GS_ALLOC(ws->part, (size_t)std::max(ws->sort_blocks, ws->wide_blocks) + 1);
     GS_ALLOC(ws->digit_tot, (size_t)256);
     GS_ALLOC(ws->pose_part, (size_t)std::max(1, blocks) * maxv * 6);
     GS_ALLOC(ws->red_part, (size_t)2 * ws->sort_blocks);

@@ -39,6 +39,7 @@ struct DevState {
     uint32_t depth_valid;
     uint32_t done_l1, done_depth;  // finished blocks of the loss reductions (the last one finishes)
     uint32_t pad[5];
+    unsigned long long frag_count[4];  // gs_workspace_fragment_counts
 };
 constexpr uint32_t kFlagCapacity = 1u;
 constexpr int kEmitWindow = 1024;      // output slots per emission window
@@ -53,6 +54,7 @@ struct gs_workspace {
     gs::Consts consts{};
     int64_t n = 0, n_pairs = 0, n_tiles = 0, n_pix = 0, inst_cap = 0;
     int32_t tile_bits = 0, sort_blocks = 0, proj_blocks = 0, max_views_per_submap = 0;
+    int32_t wide_blocks = 0;  // blocks of the compaction and of the depth sort (short, latency-bound chains)
     int32_t raster_grid_fwd = 0, raster_grid_bwd = 0, raster_grid_fwd_var = 0, raster_grid_bwd_var = 0;
     size_t bytes = 0;
     int64_t kernel_launches = 0;  // kernels enqueued by this workspace so far
@@ -81,8 +83,8 @@ struct gs_workspace {
     float *tfin = nullptr;         // [n_pix]
     float4 *vstat = nullptr;       // [n_pix] depth (mean, var, 1/W, 0) of the variance forward
     // scratch
-    uint32_t *hist = nullptr;      // [256][2 sort_blocks]
-    uint32_t *part = nullptr;      // [sort_blocks + 1]
+    uint32_t *hist = nullptr;      // [256][max(2 sort_blocks, wide_blocks)]
+    uint32_t *part = nullptr;      // [max(sort_blocks, wide_blocks) + 1]
     uint32_t *digit_tot = nullptr; // [256] digit totals of the current radix pass
     float *pose_part = nullptr;    // [proj_blocks][max_views_per_submap][6]
     double *red_part = nullptr;    // [2][sort_blocks] loss partials

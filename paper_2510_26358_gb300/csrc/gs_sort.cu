@@ -128,10 +128,10 @@ __global__ void __launch_bounds__(T) k_compact_visible(const uint32_t *pkey, uin
     uint32_t lo, hi;
     chunk_range(n, blockIdx.x, nb, kCompactStep, lo, hi);
     uint32_t base = part[blockIdx.x];
-    for (uint32_t t0 = lo; t0 < hi; t0 += kCompactStep) {
-        // this thread's 8 consecutive keys, in pair order
+    // this thread's 8 consecutive keys of a step, in pair order; the next
+    // step's keys are loaded before this step's block-wide scan
+    auto load8 = [&](uint32_t t0, uint32_t k[8]) {
         const uint32_t i0 = t0 + 8 * threadIdx.x;
-        uint32_t k[8];
         if (i0 + 8 <= hi) {
             const uint4 a = reinterpret_cast<const uint4 *>(pkey + i0)[0];
             const uint4 b = reinterpret_cast<const uint4 *>(pkey + i0)[1];
@@ -141,6 +141,15 @@ __global__ void __launch_bounds__(T) k_compact_visible(const uint32_t *pkey, uin
 #pragma unroll
             for (int j = 0; j < 8; ++j) k[j] = i0 + j < hi ? pkey[i0 + j] : kInvalidKey;
         }
+    };
+    uint32_t kn[8];
+    if (lo < hi) load8(lo, kn);
+    for (uint32_t t0 = lo; t0 < hi; t0 += kCompactStep) {
+        const uint32_t i0 = t0 + 8 * threadIdx.x;
+        uint32_t k[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) k[j] = kn[j];
+        if (t0 + kCompactStep < hi) load8(t0 + kCompactStep, kn);
         uint32_t c = 0;
 #pragma unroll
         for (int j = 0; j < 8; ++j) c += k[j] != kInvalidKey;
@@ -417,20 +426,30 @@ __device__ __forceinline__ uint32_t last_le(const uint32_t *a, uint32_t n, uint3
     return lo;
 }
 
-__global__ void __launch_bounds__(T) k_emit_instances(const uint32_t *vis_pair, const short4 *rect,
-                                                     const float4 *rec, const ViewInfo *views, int n_views,
-                                                     const Consts k, const DevState *st, const uint32_t *ioff,
-                                                     const uint32_t *win_pair, uint32_t *inst_tile,
-                                                     uint32_t *inst_val) {
+// Blocks of the emission an SM keeps resident: a window's staging is a short
+// chain of dependent loads (slot owners, pair ids, rectangles) that every
+// thread of the block waits for, so several blocks per SM hide it.
+constexpr int kEmitBlocksPerSM = 6;
+
+__global__ void __launch_bounds__(T, kEmitBlocksPerSM) k_emit_instances(
+    const uint32_t *vis_pair, const short4 *rect, const float4 *rec, const ViewInfo *views, int n_views,
+    const Consts k, const DevState *st, const uint32_t *ioff, const uint32_t *win_pair, uint32_t *inst_tile,
+    uint32_t *inst_val) {
     __shared__ uint32_t s_off[kEmitWindow];
     __shared__ uint32_t s_pair[kEmitWindow];
     __shared__ short4 s_rect[kEmitWindow];
-    __shared__ int4 s_view[kEmitWindow];  // (tile_off, ntx, W, H) of the pair's view
+    __shared__ uint8_t s_vidx[kEmitWindow];
+    __shared__ int4 s_view[GS_MAX_VIEWS];    // (tile_off, ntx, W, H)
+    __shared__ int32_t s_poff[GS_MAX_VIEWS];  // first pair of each view
     __shared__ uint32_t s_range[2];
     if (st->flags & kFlagCapacity) return;
     const uint32_t n = st->n_vis, total = st->n_inst;
     const uint32_t windows = (total + kEmitWindow - 1) / kEmitWindow;
     const int t = threadIdx.x;
+    for (int v = t; v < n_views; v += T) {
+        s_view[v] = make_int4(views[v].tile_off, views[v].ntx, views[v].W, views[v].H);
+        s_poff[v] = views[v].pair_off;
+    }
     for (uint32_t wdw = blockIdx.x; wdw < windows; wdw += gridDim.x) {
         const uint32_t o0 = wdw * kEmitWindow;
         const uint32_t o1 = min(o0 + kEmitWindow, total);
@@ -453,18 +472,18 @@ __global__ void __launch_bounds__(T) k_emit_instances(const uint32_t *vis_pair, 
             int lo_v = 0, hi_v = n_views - 1;
             while (lo_v < hi_v) {
                 int mid = (lo_v + hi_v + 1) >> 1;
-                if ((uint32_t)views[mid].pair_off <= pair) lo_v = mid; else hi_v = mid - 1;
+                if ((uint32_t)s_poff[mid] <= pair) lo_v = mid; else hi_v = mid - 1;
             }
             s_off[j] = ioff[s0 + j];
             s_pair[j] = pair;
             s_rect[j] = rect[pair];
-            s_view[j] = make_int4(views[lo_v].tile_off, views[lo_v].ntx, views[lo_v].W, views[lo_v].H);
+            s_vidx[j] = (uint8_t)lo_v;
         }
         __syncthreads();
         for (uint32_t o = o0 + t; o < o1; o += T) {
             const uint32_t a = last_le(s_off, np, o);
             const short4 r = s_rect[a];
-            const int4 vw = s_view[a];
+            const int4 vw = s_view[s_vidx[a]];
             const uint32_t pair = s_pair[a];
             const int wdt = (int)r.z - (int)r.x + 1;
             const int local = (int)(o - s_off[a]);
@@ -481,13 +500,30 @@ __global__ void __launch_bounds__(T) k_emit_instances(const uint32_t *vis_pair, 
 
 // [start, end) of every tile's run in the sorted instances; the dropped
 // rectangle tiles (kInvalidKey, sorted last) belong to no tile
+// (a thread takes four consecutive ids with one 16-byte load, plus the ids
+// on either side)
 __global__ void k_ranges(const uint32_t *tile, const DevState *st, uint32_t n_tiles, uint2 *ranges) {
-    uint32_t n = st->n_inst;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        uint32_t t = tile[i];
-        if (t >= n_tiles) continue;
-        if (i == 0 || tile[i - 1] != t) ranges[t].x = i;
-        if (i + 1 == n || tile[i + 1] != t) ranges[t].y = i + 1;
+    const uint32_t n = st->n_inst;
+    const uint32_t n4 = (n + 3) / 4;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += gridDim.x * blockDim.x) {
+        const uint32_t i0 = 4 * q;
+        uint32_t t[6];
+        t[0] = i0 > 0 ? tile[i0 - 1] : kInvalidKey;
+        if (i0 + 4 <= n) {
+            const uint4 v = reinterpret_cast<const uint4 *>(tile)[q];
+            t[1] = v.x; t[2] = v.y; t[3] = v.z; t[4] = v.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) t[1 + j] = i0 + j < n ? tile[i0 + j] : kInvalidKey;
+        }
+        t[5] = i0 + 4 < n ? tile[i0 + 4] : kInvalidKey;
+#pragma unroll
+        for (int j = 1; j <= 4; ++j) {
+            const uint32_t i = i0 + j - 1;
+            if (i >= n || t[j] >= n_tiles) continue;
+            if (t[j - 1] != t[j]) ranges[t[j]].x = i;
+            if (t[j + 1] != t[j]) ranges[t[j]].y = i + 1;
+        }
     }
 }
 
@@ -560,6 +596,7 @@ gs_status sort_configure() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_radix_scatter<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sizeof(ScatterSmem<2>));
+
     if (e != cudaSuccess) {
         set_last_error(std::string("sort_configure: ") + cudaGetErrorString(e));
         return GS_ERR_CUDA;
@@ -572,13 +609,15 @@ gs_status launch_bin_sort(gs_workspace *ws, cudaStream_t s) {
     uint32_t n_pairs = (uint32_t)ws->n_pairs;
     DevState *st = ws->st;
     cudaMemsetAsync(&st->n_vis, 0, sizeof(uint32_t) * 2 + sizeof(unsigned long long) + sizeof(uint32_t), s);
-    // 1. compaction of visible pairs
+    // 1. compaction of visible pairs (more blocks than the other stages: each
+    //    block's chunk is a chain of block-wide scans)
     gs_status r;
+    const int nw = ws->wide_blocks;
     {
     StageTimer timer(ws, GS_STAGE_COMPACT, s);
-    ++ws->kernel_launches; k_count_visible<<<nb, T, 0, s>>>(ws->pkey, n_pairs, ws->part, nb);
-    ++ws->kernel_launches; k_scan_parts<<<1, T, 0, s>>>(ws->part, nb, &st->n_vis, st, 0, 0);
-    ++ws->kernel_launches; k_compact_visible<<<nb, T, 0, s>>>(ws->pkey, n_pairs, ws->part, nb, ws->vis_key, ws->vis_pair);
+    ++ws->kernel_launches; k_count_visible<<<nw, T, 0, s>>>(ws->pkey, n_pairs, ws->part, nw);
+    ++ws->kernel_launches; k_scan_parts<<<1, T, 0, s>>>(ws->part, nw, &st->n_vis, st, 0, 0);
+    ++ws->kernel_launches; k_compact_visible<<<nw, T, 0, s>>>(ws->pkey, n_pairs, ws->part, nw, ws->vis_key, ws->vis_pair);
     r = check_launch("compact");
     if (r != GS_OK) return r;
     }
@@ -586,8 +625,11 @@ gs_status launch_bin_sort(gs_workspace *ws, cudaStream_t s) {
     uint32_t *k = ws->vis_key, *v = ws->vis_pair, *k2 = ws->vis_key_alt, *v2 = ws->vis_pair_alt;
     {
     StageTimer timer(ws, GS_STAGE_DEPTH_SORT, s);
+    // (blocks grow with the pairs: a tenth of them or so are visible; more
+    // blocks than keys to fill them only lengthen the digit-table scans)
+    const int nd = (int)std::min<int64_t>(nw, std::max<int64_t>(nb, ws->n_pairs / 16384));
     for (int sh = 0; sh < 32; sh += 8)
-        if ((r = radix_pass<2>(ws, k, v, k2, v2, &st->n_vis, sh, nb, s)) != GS_OK) return r;
+        if ((r = radix_pass<2>(ws, k, v, k2, v2, &st->n_vis, sh, nd, s)) != GS_OK) return r;
     }
     // after 4 passes the sorted data are back in vis_key / vis_pair
     // 3. instance offsets, capacity check, emission in depth order
@@ -604,8 +646,8 @@ gs_status launch_bin_sort(gs_workspace *ws, cudaStream_t s) {
     ++ws->kernel_launches; k_instance_offsets<<<nb, T, 0, s>>>(st, ws->part, nb, ws->ioff, ws->win_pair,
                                                                   (uint32_t)(ws->inst_cap / kEmitWindow + 2));
     ++ws->kernel_launches;
-    k_emit_instances<<<4 * ws->num_sms, T, 0, s>>>(v, ws->rect, ws->rec, ws->views, ws->n_views, ws->consts, st,
-                                                   ws->ioff, ws->win_pair, tk, tv);
+    k_emit_instances<<<kEmitBlocksPerSM * ws->num_sms, T, 0, s>>>(v, ws->rect, ws->rec, ws->views, ws->n_views,
+                                                                    ws->consts, st, ws->ioff, ws->win_pair, tk, tv);
     if ((r = check_launch("emit")) != GS_OK) return r;
     }
     // 4. stable sort of the instances by tile id
@@ -618,7 +660,7 @@ gs_status launch_bin_sort(gs_workspace *ws, cudaStream_t s) {
     StageTimer timer(ws, GS_STAGE_RANGES, s);
     cudaMemsetAsync(ws->ranges, 0, sizeof(uint2) * ws->n_tiles, s);
     ++ws->kernel_launches;
-    k_ranges<<<ws->num_sms * 8, 256, 0, s>>>(ws->inst_tile, st, (uint32_t)ws->n_tiles, ws->ranges);
+    k_ranges<<<ws->num_sms * 4, 256, 0, s>>>(ws->inst_tile, st, (uint32_t)ws->n_tiles, ws->ranges);
     // 6. raster work order
     ++ws->kernel_launches;
     k_tile_order<<<1, 1024, 0, s>>>(ws->ranges, (int)ws->n_tiles, ws->tile_order);
