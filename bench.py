@@ -193,10 +193,13 @@ def raster_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def measured_traffic(kernel: str, workload: str, config: str):
+def measured_traffic(kernel: str, workload: str, config: str, alg_bytes=None):
     """DRAM bytes (read + write) per launch of `kernel` from the committed ncu
-    summary, if it was captured on this workload and configuration from the
-    current raster sources; otherwise None."""
+    summary, if it was captured from the current raster sources with the same
+    tile size (the batch depth does not change what the backward stages).  On
+    another workload it is scaled by the ratio of algorithmic bytes per launch
+    (the kernel's traffic grows with the units it processes), when the record
+    holds its own algorithmic bytes; otherwise None."""
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
             rec = json.load(f)[kernel]
@@ -204,21 +207,137 @@ def measured_traffic(kernel: str, workload: str, config: str):
         return None, "no ncu capture recorded"
     if rec.get("source_sha1") != raster_source_hash():
         return None, "kernel changed since the ncu capture"
-    # the backward stages the same list entries (those up to the last blended
-    # fragment) whatever the batch depth, so the tile size fixes its traffic
-    if rec.get("workload") != workload or rec.get("config", "").split("/")[0] != config.split("/")[0]:
+    if rec.get("config", "").split("/")[0] != config.split("/")[0]:
         return None, f"ncu capture was on {rec.get('workload')} {rec.get('config')}"
-    return int(rec["dram_bytes_per_launch"]), rec.get("command", "")
+    if rec.get("workload") == workload:
+        return int(rec["dram_bytes_per_launch"]), rec.get("command", "")
+    if alg_bytes and rec.get("algorithmic_bytes"):
+        scaled = int(rec["dram_bytes_per_launch"] * alg_bytes / rec["algorithmic_bytes"])
+        return scaled, (f"scaled from the {rec['workload']} capture ({rec['dram_bytes_per_launch']} B for "
+                        f"{rec['algorithmic_bytes']} algorithmic B) by algorithmic bytes: {rec.get('command', '')}")
+    return None, f"ncu capture was on {rec.get('workload')} {rec.get('config')}"
 
 
-# FP32 operations (an FMA counts 2) the backward needs per (pixel, fragment)
-# evaluation, from the adjoint's steps: offset to the mean 2, exponent through
-# the Cholesky factor 8, alpha clamp 1, T recovery 2, weight 1, h 8, dL/dalpha
-# 3, suffix sum 2, colour and depth gradients 8, dL/dpw 1, opacity gradient 1,
-# conic and mean moments 12 = 49 (plus two MUFU operations, ex2 and rcp).
-FLOPS_PER_FRAGMENT_BWD = 49
-# extra per evaluation for the depth mean and variance adjoints: dz 1, h 4, dL/dz 4
-FLOPS_PER_FRAGMENT_VAR = 9
+# FP32 operations of the rasterisers per (pixel, list entry), from their
+# steps (an FMA counts 2).  Every entry a pixel walks: offset to the mean 2,
+# exponent through the Cholesky factor 8 (then one MUFU ex2 where it blends).
+EVAL_FLOPS = 10
+# every fragment the backward blends: alpha clamp 1, T recovery 2, weight 1,
+# h 8, dL/dalpha 3, suffix sum 2, colour and depth gradients 8, dL/dpw 1,
+# opacity gradient 1, conic and mean moments 12 (plus one MUFU rcp)
+BWD_BLEND_FLOPS = 39
+# extra per blend of the variance backward: dz 1, h 4, dL/dz 4
+VAR_BLEND_FLOPS = 9
+# every fragment the forward blends: alpha clamp 1, T update 2, weight 1,
+# colour and depth sums 8
+FWD_BLEND_FLOPS = 12
+
+
+def measure_alu_peaks(torch, G, dev, n_sm, reps=5):
+    """FP32 FMA, packed f32x2 FMA and MUFU ex2 / rcp rates of this GPU from
+    the library's probe: 8 blocks of 256 threads per SM, each thread running
+    long independent chains of one instruction; best of `reps` launches
+    timed with CUDA events.  Returns TFLOP/s (FMA kinds) and T op/s (MUFU)."""
+    sink = torch.zeros(1, device=dev)
+    blocks = 8 * n_sm
+    out = {}
+    for kind, (name, ops_per_round) in G.ALU_PROBE_KINDS.items():
+        iters = 1 << 15 if kind < 2 else 1 << 13
+        G.gs_alu_probe(kind, blocks, 64, sink)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * reps)]
+        torch.cuda.synchronize()
+        for r in range(reps):
+            ev[2 * r].record()
+            G.gs_alu_probe(kind, blocks, iters, sink)
+            ev[2 * r + 1].record()
+        torch.cuda.synchronize()
+        best = min(ev[2 * r].elapsed_time(ev[2 * r + 1]) for r in range(reps))
+        out[name] = blocks * 256 * iters * ops_per_round / (best * 1e-3) / 1e12
+    out["unit"] = "TFLOP/s (FMA kinds, an FMA = 2), T op/s (MUFU)"
+    out["how"] = f"gs_alu_probe: {blocks} blocks x 256 threads, 8 independent chains, best of {reps}"
+    return out
+
+
+def stage_bytes(u, args):
+    """Algorithmic (unique) bytes each library stage must move: every array
+    read or written once, repeated reads of a record assumed to hit L2, a
+    radix sort counted at one pass (read and write key + value)."""
+    P = 4 * (3 + 3 + 4 + 1 + 3 * u["sh_coeffs"])
+    var = args.depth_loss == "kl-var"
+    return {
+        # geometry of every Gaussian (44 B), SH of those seen, per pair the
+        # depth key and rectangle, per visible pair its 48-byte record
+        "project": 44 * u["N"] + (P - 44) * u["touched"] + 12 * u["pairs"] + 48 * u["visible"],
+        # every pair's key read, the visible (key, pair) written
+        "compact": 4 * u["pairs"] + 8 * u["visible"],
+        "depth_sort": 16 * u["visible"],
+        # per visible pair its id, rectangle and the 32 B of record the tile
+        # test reads; per instance (tile, pair) written
+        "emit": 44 * u["visible"] + 8 * u["instances"],
+        "tile_sort": 16 * u["instances"],
+        # tile ids read; ranges and the work order written
+        "ranges": 4 * u["instances"] + 12 * u["tiles"],
+        # ranges, listed pair ids, records once; rgb, depth, alpha, count, T written
+        "raster_fwd": 8 * u["tiles"] + 4 * u["listed"] + 48 * u["visible"] + (28 + (24 if var else 0)) * u["pix"],
+        # rgb and (float) target read, gradient read and written
+        "image_l1": 48 * u["pix"],
+        # returns read, depth and alpha gathered, dL/dD read and written
+        "depth_loss": 32 * u["lidar"],
+        "zero_grad": 40 * u["visible"],
+        # ranges, listed pair ids, records once, per-pixel inputs, image-space gradients written
+        "raster_bwd": 8 * u["tiles"] + 4 * u["listed"] + 48 * u["visible"] + (44 if var else 24) * u["pix"]
+        + 40 * u["visible"],
+        # params of the seen Gaussians read and their gradients read and written;
+        # per visible pair its image-space gradient and view-direction gradient
+        # (written by the SH adjoint, read by the geometric one); densify statistics
+        "project_bwd": 3 * P * u["touched"] + (40 + 32) * u["visible"] + 16 * u["touched"],
+    }
+
+
+def roofline_report(u, kern, step_ms, hbm_peak, hbm_src, alu, args, tw, th):
+    """Per-stage HBM rooflines, the step's, and the raster kernels' FP32
+    rooflines against the measured FMA rate."""
+    b = stage_bytes(u, args)
+    stages = {}
+    for k, nbytes in b.items():
+        t = kern.get(k)
+        if not t or t <= 0:
+            continue
+        gbs = nbytes / (t * 1e-3) / 1e9
+        stages[k] = {"bound": "hbm", "algorithmic_bytes": int(nbytes), "ms": t, "achieved": gbs, "unit": "GB/s",
+                     "frac": gbs / hbm_peak}
+    # the survey's floor for a whole iteration (each array touched once)
+    P = 4 * (3 + 3 + 4 + 1 + 3 * u["sh_coeffs"])
+    B = (3 * u["touched"] * P + 260 * u["visible"] + 52 * u["instances"] + 88 * u["pix"] + 20 * u["lidar"]
+         + 8 * u["touched"])
+    step = {"bound": "hbm", "algorithmic_bytes": int(B), "ms": step_ms, "achieved": B / (step_ms * 1e-3) / 1e9,
+            "peak": hbm_peak, "unit": "GB/s", "frac": B / (step_ms * 1e-3) / 1e9 / hbm_peak,
+            "stage_bytes_sum": int(sum(b.values())),
+            "formula": "3 N_touched P + 260 N_vis + 52 N_inst + 88 N_pix + 20 N_L + 8 N_touched"}
+    fp32 = max(alu["fp32_fma"], alu["fp32x2_fma"])
+    var = args.depth_loss == "kl-var"
+    walked, blends = u["pixel_entries"], u["pixel_blends"]
+    fl_bwd = walked * EVAL_FLOPS + blends * (BWD_BLEND_FLOPS + (VAR_BLEND_FLOPS if var else 0))
+    fl_fwd = walked * EVAL_FLOPS + blends * FWD_BLEND_FLOPS
+    for k, fl in (("raster_bwd", fl_bwd), ("raster_fwd", fl_fwd)):
+        if k in stages:
+            a = fl / (stages[k]["ms"] * 1e-3) / 1e12
+            stages[k]["alu"] = {"bound": "alu", "flops": int(fl), "achieved": a, "peak": fp32, "unit": "TFLOP/s",
+                                "frac": a / fp32}
+    t = kern["raster_bwd"]
+    a = fl_bwd / (t * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": "k_raster_bwd", "achieved": a, "peak": fp32, "unit": "TFLOP/s",
+                "frac": a / fp32, "ms": t, "flops": int(fl_bwd),
+                "work": f"{walked} (pixel, entry) pairs walked x {EVAL_FLOPS} + {blends} blended x "
+                        f"{BWD_BLEND_FLOPS + (VAR_BLEND_FLOPS if var else 0)} FP32 operations",
+                "peak_source": "measured FP32 FMA rate (gs_alu_probe, the larger of scalar and packed f32x2)"}
+    hb = b["raster_bwd"] / (t * 1e-3) / 1e9
+    roofline_hbm = {"bound": "hbm", "kernel": "k_raster_bwd", "achieved": hb, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": hb / hbm_peak, "algorithmic_bytes": int(b["raster_bwd"]), "ms": t,
+                    "peak_source": hbm_src}
+    for v in stages.values():
+        v["peak"] = hbm_peak
+    return {"roofline": roofline, "roofline_hbm": roofline_hbm, "step": step, "stages": stages, "bytes": b}
 
 
 def lifecycle_timing(torch, G, step, sc, dev, reps=5):
@@ -807,56 +926,32 @@ def main():
             e2e["inputs"] = "keyframe batch: target images, LiDAR returns, cameras (map resident)"
             e2e["with_map_upload"] = e2e_run(list(step.P) + batch, graph)
 
-    # roofline of the dominant kernel (the raster backward)
+    # rooflines: every library stage against its bound, the dominant kernel
+    # (the raster backward) against the measured FP32 rate
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    n_inst = need
-    npx = sc.n_pix
-    n_tiles = step.r.info["n_tiles"]
-    # instances in the tiles' lists (the rectangle tiles the ellipse misses
-    # are emitted, sorted last and in no list)
+    hbm_src = "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6800 GB/s"
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu = measure_alu_peaks(torch, G, dev, n_sm)
+    frag = G.gs_workspace_fragment_counts(step.r.ws)
     rng = step.r.buffer(G.BUF_RANGES, torch.int32).view(-1, 2).to(torch.int64)
-    n_listed = int((rng[:, 1] - rng[:, 0]).sum().item())
-    # algorithmic bytes of one raster-backward launch: listed instance pair ids (4 B),
-    # visible records read once (48 B), per-pixel inputs (3 rgb + depth grads,
-    # list count, final T = 24 B), tile ranges (8 B), image-space gradients of
-    # the visible pairs accumulated (40 B written); the variance variant reads
-    # the (mean, var, 1/W) record and the two adjoints instead of the depth
-    # adjoint (44 B per pixel)
-    px_bytes = 44 if args.depth_loss == "kl-var" else 24
-    alg_bytes = 4 * n_listed + 48 * nvis + px_bytes * npx + 8 * n_tiles + 40 * nvis
-    bwd_ms = kern["raster_bwd"]
-    achieved = alg_bytes / (bwd_ms * 1e-3) / 1e9
+    units = dict(N=sc.n, views=len(sc.cameras), pairs=step.r.info["n_pairs"], visible=nvis, instances=need,
+                 listed=int((rng[:, 1] - rng[:, 0]).sum().item()), tiles=step.r.info["n_tiles"], pix=sc.n_pix,
+                 lidar=int(sc.lidar.shape[0]), touched=int((step.grads["densify_cnt"] > 0).sum().item()),
+                 sh_coeffs=(sc.sh_degree + 1) ** 2, **frag)
+    rep = roofline_report(units, kern, ms, hbm_peak, hbm_src, alu, args, tw, th)
+    roofline, roofline_hbm = rep["roofline"], rep["roofline_hbm"]
     if args.depth_loss == "kl-var":
         traffic, traffic_note = None, "the ncu capture covers the kernel without the depth variance"
     else:
-        traffic, traffic_note = measured_traffic("k_raster_bwd", sc.name, f"{tw}x{th}/{args.depth}")
-    roofline_hbm = {"bound": "hbm", "kernel": "k_raster_bwd",
-                    "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                    "traffic": traffic, "traffic_source": traffic_note,
-                    "algorithmic_bytes": int(alg_bytes), "ms": bwd_ms,
-                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6800 GB/s"}
-    # The raster backward is bound by FP32 arithmetic and issue, not DRAM (ncu:
-    # 77 % issue, ALU + FMA pipes busiest, DRAM 2 %): its roofline is the
-    # fragment rate.  Algorithmic work = (pixel, fragment) evaluations the
-    # adjoint needs, sum over pixels of the list count up to the last blended
-    # fragment, times FLOPS_PER_FRAGMENT_BWD; peak = SMs x 128 FP32 lanes x 2
-    # (FMA) x the sampled maximum SM clock.
-    n_frag = int(step.r.buffer(G.BUF_LAST, torch.int32).to(torch.int64).sum().item())
-    flops = n_frag * (FLOPS_PER_FRAGMENT_BWD + (FLOPS_PER_FRAGMENT_VAR if args.depth_loss == "kl-var" else 0))
-    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-    f_max = (clocks or {}).get("sm_max_mhz") or 2070.0
-    alu_peak = n_sm * 128 * 2 * f_max * 1e6 / 1e12
-    alu_achieved = flops / (bwd_ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "kernel": "k_raster_bwd", "achieved": alu_achieved, "peak": alu_peak,
-                "unit": "TFLOP/s", "frac": alu_achieved / alu_peak, "traffic": traffic,
-                "traffic_source": traffic_note, "fragments": n_frag,
-                "flops_per_fragment": flops / max(1, n_frag), "ms": bwd_ms,
-                "peak_source": f"derived: {n_sm} SMs x 128 FP32 lanes x 2 x {f_max:.0f} MHz (sampled max clock)"}
+        traffic, traffic_note = measured_traffic("k_raster_bwd", sc.name, f"{tw}x{th}/{args.depth}",
+                                                 rep["bytes"]["raster_bwd"])
+    for r_ in (roofline, roofline_hbm):
+        r_["traffic"], r_["traffic_source"] = traffic, traffic_note
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -867,10 +962,9 @@ def main():
                                                                 "ms": tuned["timings"]}),
             "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches_per_step * args.steps),
             "launches_per_step": int(launches_per_step), "roofline": roofline, "roofline_hbm": roofline_hbm,
+            "step_roofline": rep["step"], "kernel_rooflines": rep["stages"], "alu_peaks": alu,
             "per_view": per_view, "breakdown_ms": breakdown, "kernel_ms": kern, "lifecycle": lifecycle,
-            "active_set": active_set,
-            "counts": {"visible_pairs": nvis, "instances": n_inst, "listed_instances": n_listed,
-                       "tiles": n_tiles}}
+            "active_set": active_set, "counts": units}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = {k: v for k, v in cpu_baseline(sc, args, reps=2).items()
                                 if k not in ("seconds", "pixels")}

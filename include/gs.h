@@ -437,6 +437,30 @@ enum {
 gs_status gs_workspace_set_profiling(gs_workspace *ws, int32_t on);
 gs_status gs_workspace_stage_ms(gs_workspace *ws, float *ms, int32_t n);
 
+/* ------------------------------------------------------------------------ */
+/* Measurement (the paper times nothing on this path: these calls give the  */
+/* rates and counts the benchmark's rooflines are quoted against; neither   */
+/* runs inside the mapping step).                                            */
+/* ------------------------------------------------------------------------ */
+
+/* Arithmetic-rate probe: blocks x 256 threads each run `iters` rounds of 8
+ * independent dependency chains of one instruction: kind 0 FP32 FMA (2
+ * FLOP), 1 packed f32x2 FMA (4 FLOP), 2 MUFU ex2.approx, 3 MUFU rcp.approx.
+ * The caller times the launch; operations = blocks * 256 * iters * 8.
+ * sink (device, 1 float) is written only in a case that never occurs.
+ * Enqueued on `stream`; GS_ERR_INVALID_ARG for kind outside 0..3 or
+ * blocks, iters < 1. */
+gs_status gs_alu_probe(int32_t kind, int32_t blocks, int32_t iters, float *sink, void *stream);
+
+/* Fragment counts of the last forward (call after gs_render_fwd; GS_ERR_STATE
+ * before): every pixel's tile list is walked up to the count the forward
+ * kept, with the rasterisers' own alpha evaluation, and counts (host, 4
+ * int64) receives [0] (pixel, entry) pairs walked, [1] of those blended
+ * (alpha >= alpha_min), [2] (tile, entry) pairs walked (the longest count of
+ * each tile), [3] (tile, entry) pairs that some pixel of the tile blends.
+ * Synchronises `stream`. */
+gs_status gs_workspace_fragment_counts(gs_workspace *ws, int64_t *counts, void *stream);
+
 const char *gs_status_string(gs_status s);
 /* Text of the last CUDA error seen by this thread's calls ("" if none). */
 const char *gs_last_error(void);

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgsraster.so")
-SOURCES = ["gs_api.cu", "gs_project.cu", "gs_sort.cu", "gs_raster.cu", "gs_loss.cu", "gs_ssim.cu", "gs_lifecycle.cu", "gs_voxel.cu", "gs_noalloc.cu"]
+SOURCES = ["gs_api.cu", "gs_project.cu", "gs_sort.cu", "gs_raster.cu", "gs_loss.cu", "gs_ssim.cu", "gs_lifecycle.cu", "gs_voxel.cu", "gs_noalloc.cu", "gs_probe.cu"]
 HEADERS = [os.path.join(CSRC, "gs_internal.cuh"), os.path.join(CSRC, "gs_frag.cuh"), os.path.join(CSRC, "gs_scan.cuh"),
            os.path.join(ROOT, "include", "gs.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -33,7 +33,8 @@ EXPORTED = ("gs_config_default", "gs_workspace_create", "gs_workspace_destroy", 
             "gs_workspace_stage_ms", "gs_image_l1_noalloc", "gs_status_string", "gs_last_error",
             "gs_lifecycle_create", "gs_lifecycle_destroy", "gs_lifecycle_run", "gs_lifecycle_status", "gs_adam_step",
             "gs_voxel_keys", "gs_voxel_create", "gs_voxel_destroy", "gs_voxel_insert", "gs_voxel_status",
-            "gs_active_select", "gs_partition", "gs_selftest_wait_timeout", "gs_zero_buffers")
+            "gs_active_select", "gs_partition", "gs_selftest_wait_timeout", "gs_zero_buffers", "gs_alu_probe",
+            "gs_workspace_fragment_counts")
 GS_LC_PRUNE, GS_LC_DENSIFY, GS_LC_RESET = 1, 2, 4
 PARAM_FIELDS = ("means", "log_scales", "quats", "opacity_logits", "sh")
 IMAGE_L1_NOALLOC_MAX = 1024 * 65536  # GS_IMAGE_L1_NOALLOC_BLOCKS * GS_IMAGE_L1_NOALLOC_CHUNK
@@ -150,6 +151,8 @@ def lib() -> ctypes.CDLL:
     L.gs_partition.argtypes = [P, P, i64, i32, PA, P, P, PA, P, P, PA, P, P, P, P]
     L.gs_selftest_wait_timeout.argtypes = [P, i64, P, P]
     L.gs_zero_buffers.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int64), i32, P]
+    L.gs_alu_probe.argtypes = [i32, i32, i32, P, P]
+    L.gs_workspace_fragment_counts.argtypes = [P, ctypes.POINTER(ctypes.c_int64), P]
     L.gs_status_string.argtypes = [i32]
     L.gs_status_string.restype = ctypes.c_char_p
     L.gs_last_error.argtypes = []
@@ -161,7 +164,8 @@ def lib() -> ctypes.CDLL:
                  "gs_workspace_copy", "gs_workspace_set_profiling", "gs_workspace_stage_ms",
                  "gs_image_l1_noalloc", "gs_lifecycle_create", "gs_lifecycle_run", "gs_lifecycle_status",
                  "gs_adam_step", "gs_voxel_keys", "gs_voxel_create", "gs_voxel_insert", "gs_voxel_status",
-                 "gs_active_select", "gs_partition", "gs_selftest_wait_timeout", "gs_zero_buffers"):
+                 "gs_active_select", "gs_partition", "gs_selftest_wait_timeout", "gs_zero_buffers", "gs_alu_probe",
+                 "gs_workspace_fragment_counts"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -362,6 +366,24 @@ def gs_zero_buffers(tensors, stream=None):
     ptrs = (ctypes.c_void_p * max(1, len(ts)))(*[t.data_ptr() for t in ts])
     sizes = (ctypes.c_int64 * max(1, len(ts)))(*[t.numel() * t.element_size() for t in ts])
     _check(lib().gs_zero_buffers(ptrs, sizes, len(ts), _stream(stream)), "gs_zero_buffers")
+
+
+# operations per lane and round of gs_alu_probe's kinds (FMA = 2 FLOP) and
+# their names
+ALU_PROBE_KINDS = {0: ("fp32_fma", 2 * 8), 1: ("fp32x2_fma", 4 * 8), 2: ("mufu_ex2", 8), 3: ("mufu_rcp", 8)}
+
+
+def gs_alu_probe(kind: int, blocks: int, iters: int, sink, stream=None):
+    """One launch of the arithmetic-rate probe (see include/gs.h)."""
+    _check(lib().gs_alu_probe(int(kind), int(blocks), int(iters), _ptr(sink), _stream(stream)), "gs_alu_probe")
+
+
+def gs_workspace_fragment_counts(ws, stream=None) -> dict:
+    """(pixel, entry) pairs walked and blended, (tile, entry) pairs walked and
+    with a blend, for the last forward (synchronises)."""
+    c = (ctypes.c_int64 * 4)()
+    _check(lib().gs_workspace_fragment_counts(ws, c, _stream(stream)), "gs_workspace_fragment_counts")
+    return dict(pixel_entries=int(c[0]), pixel_blends=int(c[1]), tile_entries=int(c[2]), tile_active=int(c[3]))
 
 
 def status_string(s: int) -> str:

@@ -66,3 +66,36 @@ def test_traffic_reported_only_for_the_recorded_code_workload_and_tile(tree):
     _edit(root / b.RASTER_SOURCES[-1], lambda s: s + "\nstatic const int kChanged = 1;\n")
     traffic, note = b.measured_traffic("k_raster_bwd", rec["workload"], cfg)
     assert traffic is None and "changed" in note
+
+
+def test_traffic_scaled_to_another_workload_by_algorithmic_bytes(tree):
+    b, root = tree
+    path = root / "profiles" / "ncu_traffic.json"
+    recs = json.load(open(path))
+    rec = recs["k_raster_bwd"]
+    rec["algorithmic_bytes"] = 1000
+    json.dump(recs, open(path, "w"))
+    traffic, note = b.measured_traffic("k_raster_bwd", "another_workload", rec["config"], 3000)
+    assert traffic == 3 * rec["dram_bytes_per_launch"] and "scaled" in note
+    assert b.measured_traffic("k_raster_bwd", "another_workload", rec["config"])[0] is None
+
+
+def test_stage_bytes_and_report_use_every_stage():
+    b = _bench()
+
+    class A:
+        depth_loss, ssim_lambda = "kl", 0.0
+    u = dict(N=100, views=2, pairs=200, visible=50, instances=400, listed=300, tiles=10, pix=1000, lidar=20,
+             touched=40, sh_coeffs=16, pixel_entries=5000, pixel_blends=2000, tile_entries=100, tile_active=80)
+    kern = {k: 0.01 for k in ("project", "compact", "depth_sort", "emit", "tile_sort", "ranges", "raster_fwd",
+                               "image_l1", "depth_loss", "zero_grad", "raster_bwd", "project_bwd")}
+    alu = {"fp32_fma": 60.0, "fp32x2_fma": 70.0}
+    rep = b.roofline_report(u, kern, 0.2, 6000.0, "test", alu, A, 16, 16)
+    assert set(rep["stages"]) == set(kern)
+    bw = rep["roofline"]
+    assert bw["peak"] == 70.0
+    assert bw["flops"] == 5000 * b.EVAL_FLOPS + 2000 * b.BWD_BLEND_FLOPS
+    P = 4 * (11 + 48)
+    B = 3 * 40 * P + 260 * 50 + 52 * 400 + 88 * 1000 + 20 * 20 + 8 * 40
+    assert rep["step"]["algorithmic_bytes"] == B
+    assert abs(rep["step"]["frac"] - B / 0.2e-3 / 1e9 / 6000.0) < 1e-12
