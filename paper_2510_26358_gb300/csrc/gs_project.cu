@@ -7,9 +7,10 @@
 // One thread per Gaussian loops over the cameras of its submap, so the 3-D
 // covariance and the parameter loads are shared by all views.
 //
-// Precision: the view-space depth is the double-precision dot product
+// Precision: the view-space depth key is the double-precision dot product
 // ((R0 mu0 + R1 mu1) + R2 mu2) + t (exact products of float inputs), rounded to
-// float for the sort key, so keys are reproducible bit for bit.  The pixel
+// float, so keys are reproducible bit for bit; it is read off the float-float
+// depth wherever that determines it (all but about one pair in 2^14).  The pixel
 // mean is formed in float-float arithmetic (error-free products and sums,
 // about 48 bits) and kept as an integer pixel plus a small float offset, so
 // that per-fragment offsets are exact integers plus that offset.  Only the
@@ -174,6 +175,34 @@ __device__ __forceinline__ float2 ff_pinhole(float f, float2 x, float2 z, float 
     return renorm(s, __fadd_rn(__fadd_rn(ea, es), __fmul_rn(f, q1)));
 }
 
+// The depth key z32 = float(D) and the near-plane decision D > near, where D
+// is the double sum ((W0 mu0 + W1 mu1) + W2 mu2) + t (products of floats are
+// exact in double, so D is within 3 ulps (2^-53) of the terms' magnitudes
+// `mag` of the exact sum), taken from the float-float z = hi + lo of the same
+// sum (within ~40 x 2^-48 mag of it) wherever that decides them: hi is
+// float(D) when z lies farther than 2^-38 mag inside hi's rounding interval,
+// and D > near when z - near exceeds 2^-38 mag in either direction.  Only
+// the rare pair closer than that to a rounding boundary or to the near plane
+// (about one in 2^14) computes D itself, so the FP64 pipe (a small fraction
+// of the FP32 rate, and paid by the whole warp for any lane) stays idle.
+// Returns the decision; z32 receives the key when it is visible.
+__device__ __forceinline__ bool depth_key(const float *Tz, const float mu[3], float2 z, float near, float &z32) {
+    const float mag = fabsf(Tz[0] * mu[0]) + fabsf(Tz[1] * mu[1]) + fabsf(Tz[2] * mu[2]) + fabsf(Tz[3]);
+    const float margin = mag * 0x1p-38f;
+    const float d = __fadd_rn(__fsub_rn(z.x, near), z.y);
+    if (z.x > 0.f && fabsf(d) > margin) {
+        const float up = __int_as_float(__float_as_int(z.x) + 1), dn = __int_as_float(__float_as_int(z.x) - 1);
+        const float half = 0.5f * (z.y >= 0.f ? up - z.x : z.x - dn);
+        if (fabsf(z.y) < half - margin) {
+            z32 = z.x;
+            return d > 0.f;
+        }
+    }
+    const double D = view_coord(Tz, mu[0], mu[1], mu[2]);
+    z32 = __double2float_rn(D);
+    return D > (double)near;
+}
+
 // floor / ceil of hi + lo (|lo| <= ulp(hi) / 2, |hi| < 2^23): a non-integer
 // hi keeps its floor / ceil; an integer hi moves by one if lo points away
 __device__ __forceinline__ float floor_ff(float2 v) {
@@ -220,8 +249,9 @@ __device__ __forceinline__ float quat_rot(const float q[4], float qh[4], float R
 // by an ulp leans by ~1e-7 rad, which its projection onto a thin image
 // direction turns into an error of the thin variance relative to itself of
 // ~1e-7 s_L / s_thin (1e-5 for a 180:1 needle); correct rounding keeps each
-// entry's error at half an ulp.
-__device__ __forceinline__ void quat_rot_rn(const float q[4], float R[9]) {
+// entry's error at half an ulp.  Not inlined: its double-precision code in the
+// body of the projection kernels, even untaken, slowed them by a sixth.
+__device__ __noinline__ void quat_rot_rn(const float q[4], float R[9]) {
     const double w = q[0], x = q[1], y = q[2], z = q[3];
     const double ww = w * w, xx = x * x, yy = y * y, zz = z * z;
     const double inv = 1.0 / ((ww + xx) + (yy + zz));
@@ -261,6 +291,7 @@ struct ProjArgs {
     float *gm, *gls, *gq, *gom, *gsh, *pose_part, *dens_acc;
     float4 *gdir;     // [pairs] dL/d(view direction) of the colour (x, y, z, unused)
     int32_t *dens_cnt;
+    int32_t overwrite;  // gradients written (=) instead of accumulated, zeros for unseen Gaussians
 };
 
 // Projection of one pair in float after the exact depth: Jacobian, image
@@ -385,44 +416,49 @@ __global__ void __launch_bounds__(kProjThreads) k_project_fwd(ProjArgs A) {
         const ViewInfo vi = A.views[v];
         int64_t pair = (int64_t)vi.pair_off + (g - vi.g0);
         Cam cam = load_cam(A.cams, v);
-        // float estimate of the view depth: pairs clearly behind the near plane
-        // skip the exact double-precision depth (the margin dwarfs the float error)
+        // float estimate of the view point: pairs clearly behind the near plane
+        // or clearly outside the image skip the float-float mean and the exact
+        // depth key (measured: projection 0.543 -> 0.491 ms on orchard4m)
+        const float x_est = __fmaf_rn(cam.T[2], mu[2], __fmaf_rn(cam.T[1], mu[1], __fmaf_rn(cam.T[0], mu[0], cam.T[3])));
+        const float y_est = __fmaf_rn(cam.T[6], mu[2], __fmaf_rn(cam.T[5], mu[1], __fmaf_rn(cam.T[4], mu[0], cam.T[7])));
         const float z_est = __fmaf_rn(cam.T[10], mu[2], __fmaf_rn(cam.T[9], mu[1], __fmaf_rn(cam.T[8], mu[0], cam.T[11])));
-        bool vis = qn > 0.f && E > 0.f && z_est > k.near_z - 1e-5f * (mabs + fabsf(cam.T[11]) + 1.f);
-        double pz = 0.0;
+        const float tabs = fabsf(cam.T[3]) + fabsf(cam.T[7]) + fabsf(cam.T[11]);
+        bool vis = qn > 0.f && E > 0.f && z_est > k.near_z - 1e-5f * (mabs + tabs + 1.f);
+        if (vis) {
+            // The rows of W R S have norm <= smax, so Sigma'_xx <= (|J00| + |J02|)^2 smax^2 + dil:
+            // a pair whose mean lies farther outside the image than that bound on the
+            // support's half-extent (plus margins for these float estimates) has no pixel.
+            // Each estimate is within 4 ulps of (mabs + |t|) of the exact coordinate.
+            const float iz = 1.f / z_est;
+            const float limx = k.jac_clamp * fmaxf(cam.cx, (float)vi.W - cam.cx) / cam.fx;
+            const float limy = k.jac_clamp * fmaxf(cam.cy, (float)vi.H - cam.cy) / cam.fy;
+            const float tx = fminf(fmaxf(x_est * iz, -limx), limx), ty = fminf(fmaxf(y_est * iz, -limy), limy);
+            const float jx = cam.fx * iz * (1.f + fabsf(tx)), jy = cam.fy * iz * (1.f + fabsf(ty));
+            const float bx = sqrtf(E * (jx * jx * smax * smax + k.dilation)) * 1.01f * (1.f + k.ext_rel_pad) +
+                             k.ext_abs_pad + 1.f;
+            const float by = sqrtf(E * (jy * jy * smax * smax + k.dilation)) * 1.01f * (1.f + k.ext_rel_pad) +
+                             k.ext_abs_pad + 1.f;
+            const float uf = cam.fx * x_est * iz + cam.cx, vf = cam.fy * y_est * iz + cam.cy;
+            const float est = 1e-6f * (mabs + tabs) * iz * (1.f + fabsf(x_est * iz) + fabsf(y_est * iz));
+            const float mu_ = 1e-4f * (fabsf(uf) + fabsf(vf));
+            const float mx = mu_ + cam.fx * est, my = mu_ + cam.fy * est;
+            if (uf < 0.5f - bx - mx || uf > (float)vi.W - 0.5f + bx + mx ||
+                vf < 0.5f - by - my || vf > (float)vi.H - 0.5f + by + my)
+                vis = false;
+        }
+        float z32 = 0.f;
         float2 pxx = make_float2(0.f, 0.f), pyy = pxx, pzz = pxx;
         if (vis) {
-            pz = view_coord(cam.T + 8, mu[0], mu[1], mu[2]);  // the exact depth, for the key
-            vis = pz > (double)k.near_z;
+            pzz = view_coord_ff(cam.T + 8, mu[0], mu[1], mu[2]);
+            vis = depth_key(cam.T + 8, mu, pzz, k.near_z, z32);  // the exact depth key (R10)
         }
         if (vis) {
             pxx = view_coord_ff(cam.T, mu[0], mu[1], mu[2]);
             pyy = view_coord_ff(cam.T + 4, mu[0], mu[1], mu[2]);
-            pzz = view_coord_ff(cam.T + 8, mu[0], mu[1], mu[2]);
         }
         PairGeom G;
         float4 r0 = make_float4(0, 0, 0, 0), r1 = r0, r2 = r0;
         short4 rc = make_short4(1, 1, 0, 0);
-        if (vis) {
-            // The rows of W R S have norm <= smax, so Sigma'_xx <= (|J00| + |J02|)^2 smax^2 + dil:
-            // a pair whose mean lies farther outside the image than that bound on the
-            // support's half-extent (plus a margin for this float estimate) has no pixel.
-            float zf = pzz.x, xf = pxx.x, yf = pyy.x;
-            float iz = 1.f / zf;
-            float limx = k.jac_clamp * fmaxf(cam.cx, (float)vi.W - cam.cx) / cam.fx;
-            float limy = k.jac_clamp * fmaxf(cam.cy, (float)vi.H - cam.cy) / cam.fy;
-            float tx = fminf(fmaxf(xf * iz, -limx), limx), ty = fminf(fmaxf(yf * iz, -limy), limy);
-            float jx = cam.fx * iz * (1.f + fabsf(tx)), jy = cam.fy * iz * (1.f + fabsf(ty));
-            float bx = sqrtf(E * (jx * jx * smax * smax + k.dilation)) * 1.01f * (1.f + k.ext_rel_pad) +
-                       k.ext_abs_pad + 1.f;
-            float by = sqrtf(E * (jy * jy * smax * smax + k.dilation)) * 1.01f * (1.f + k.ext_rel_pad) +
-                       k.ext_abs_pad + 1.f;
-            float uf = cam.fx * xf * iz + cam.cx, vf = cam.fy * yf * iz + cam.cy;
-            float mu_ = 1e-4f * (fabsf(uf) + fabsf(vf));
-            if (uf < 0.5f - bx - mu_ || uf > (float)vi.W - 0.5f + bx + mu_ ||
-                vf < 0.5f - by - mu_ || vf > (float)vi.H - 0.5f + by + mu_)
-                vis = false;
-        }
         if (vis) {
             pair_geom(cam, vi.W, vi.H, k, pxx.x, pyy.x, pzz.x, R, S, G);
             vis = G.det > 0.f;
@@ -469,7 +505,7 @@ __global__ void __launch_bounds__(kProjThreads) k_project_fwd(ProjArgs A) {
                 for (int ch = 0; ch < 3; ++ch) rgb[ch] = acc[ch] < 0.f ? -0.f : acc[ch];
                 r0 = make_float4(Uf, Vf, hx, hy);
                 r1 = make_float4(l11, l12, l22, log2o);
-                r2 = make_float4(rgb[0], rgb[1], rgb[2], __double2float_rn(pz));
+                r2 = make_float4(rgb[0], rgb[1], rgb[2], z32);
             }
         }
         if (vis) {
@@ -499,8 +535,9 @@ __device__ __forceinline__ int submap_of_block(const ProjArgs &A, int b) {
 // the one barrier; positions come from per-warp ballots.  Returns the count
 // (the same in every thread); the whole block must call it.  s_cnt holds
 // kProjBwdChunk / 32 counters.
+template <class Unseen>
 __device__ int chunk_visible(const ProjArgs &A, int s, const SubmapInfo &sub, int64_t c0, int *s_item,
-                             unsigned long long *s_mask, uint32_t *s_cnt) {
+                             unsigned long long *s_mask, uint32_t *s_cnt, Unseen unseen) {
     constexpr int F = kProjBwdChunk / kProjBwdThreads, NW = kProjBwdThreads / 32;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     unsigned long long m[F];
@@ -514,6 +551,13 @@ __device__ int chunk_visible(const ProjArgs &A, int s, const SubmapInfo &sub, in
             const int loc = f * kProjBwdThreads + threadIdx.x;
             if (c0 + loc < sub.ng && pk[loc] != kInvalidKey) m[f] |= 1ull << kv;
         }
+    }
+    // the chunk's Gaussians that no view sees (in overwrite mode their
+    // gradient rows are written here, as zeros)
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+        const int loc = f * kProjBwdThreads + threadIdx.x;
+        if (c0 + loc < sub.ng && m[f] == 0ull) unseen(sub.g0 + c0 + loc);
     }
     uint32_t bal[F];
 #pragma unroll
@@ -561,7 +605,18 @@ __global__ void __launch_bounds__(kProjBwdThreads) k_sh_bwd(ProjArgs A) {
     const int b = blockIdx.x, s = submap_of_block(A, b);
     const SubmapInfo sub = A.subs[s];
     const int64_t c0 = (int64_t)(b - sub.block0) * kProjBwdChunk;
-    const int n_items = chunk_visible(A, s, sub, c0, s_item, s_mask, s_scan);
+    const int n_items = chunk_visible(A, s, sub, c0, s_item, s_mask, s_scan, [&](int64_t gu) {
+        if (!A.overwrite) return;
+        if constexpr ((3 * K) % 4 == 0) {  // rows of a 16-byte multiple (degrees 1 and 3)
+            float4 *row = reinterpret_cast<float4 *>(A.gsh + gu * (3 * K));
+#pragma unroll
+            for (int i = 0; i < 3 * K / 4; ++i) row[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        } else {
+            float *row = A.gsh + gu * (3 * K);
+#pragma unroll
+            for (int i = 0; i < 3 * K; ++i) row[i] = 0.f;
+        }
+    });
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int grp = lane / 3, ch = lane - 3 * grp, lead = 3 * grp;  // lanes 30, 31 idle
     for (int base = wid * GPW; base < n_items; base += NWARP * GPW) {
@@ -622,8 +677,13 @@ __global__ void __launch_bounds__(kProjBwdThreads) k_sh_bwd(ProjArgs A) {
         }
         if (live) {
             float *gsh = A.gsh + g * (3 * K) + ch;
+            if (A.overwrite) {
 #pragma unroll
-            for (int kk = 0; kk < K; ++kk) gsh[3 * kk] += gacc[kk];
+                for (int kk = 0; kk < K; ++kk) gsh[3 * kk] = gacc[kk];
+            } else {
+#pragma unroll
+                for (int kk = 0; kk < K; ++kk) gsh[3 * kk] += gacc[kk];
+            }
         }
     }
 }
@@ -643,8 +703,20 @@ __global__ void __launch_bounds__(kProjBwdThreads, 512 / kProjBwdThreads) k_proj
     const int64_t c0 = (int64_t)(b - sub.block0) * kProjBwdChunk;
     for (int i = tid; i < sub.nviews * NWARP * 6; i += kProjBwdThreads) red[i] = 0.f;
 
-    // 1. the chunk's Gaussians that some view sees
-    const int n_items = chunk_visible(A, s, sub, c0, s_item, s_mask, s_scan);
+    // 1. the chunk's Gaussians that some view sees (in overwrite mode the
+    //    others' rows get zeros)
+    const int n_items = chunk_visible(A, s, sub, c0, s_item, s_mask, s_scan, [&](int64_t gu) {
+        if (!A.overwrite) return;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) A.gm[3 * gu + i] = 0.f;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) A.gls[3 * gu + i] = 0.f;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) A.gq[4 * gu + i] = 0.f;
+        A.gom[gu] = 0.f;
+        if (A.dens_acc) A.dens_acc[gu] = 0.f;
+        if (A.dens_cnt) A.dens_cnt[gu] = 0;
+    });
 
     // 2. each warp takes 32 of them at a time; a lane walks the views of its
     //    Gaussian in order and is the only writer of its gradients
@@ -857,14 +929,14 @@ __global__ void __launch_bounds__(kProjBwdThreads, 512 / kProjBwdThreads) k_proj
             float gq[4] = {(gw_ - w * dq) * iq, (gx_ - x * dq) * iq, (gy_ - y * dq) * iq, (gz_ - z * dq) * iq};
 
 #pragma unroll
-            for (int i = 0; i < 3; ++i) A.gm[3 * g + i] += gmu[i];
+            for (int i = 0; i < 3; ++i) A.gm[3 * g + i] = (A.overwrite ? 0.f : A.gm[3 * g + i]) + gmu[i];
 #pragma unroll
-            for (int i = 0; i < 3; ++i) A.gls[3 * g + i] += gls[i];
+            for (int i = 0; i < 3; ++i) A.gls[3 * g + i] = (A.overwrite ? 0.f : A.gls[3 * g + i]) + gls[i];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) A.gq[4 * g + i] += gq[i];
-            A.gom[g] += gom;
-            if (A.dens_acc) A.dens_acc[g] += dacc;
-            if (A.dens_cnt) A.dens_cnt[g] += dcnt;
+            for (int i = 0; i < 4; ++i) A.gq[4 * g + i] = (A.overwrite ? 0.f : A.gq[4 * g + i]) + gq[i];
+            A.gom[g] = (A.overwrite ? 0.f : A.gom[g]) + gom;
+            if (A.dens_acc) A.dens_acc[g] = (A.overwrite ? 0.f : A.dens_acc[g]) + dacc;
+            if (A.dens_cnt) A.dens_cnt[g] = (A.overwrite ? 0 : A.dens_cnt[g]) + dcnt;
         }
     }
     __syncthreads();
@@ -879,7 +951,7 @@ __global__ void __launch_bounds__(kProjBwdThreads, 512 / kProjBwdThreads) k_proj
 // pose[v][i] += sum over the blocks of v's submap of the partials of v's slot;
 // one block per (view, component), fixed summation order
 __global__ void __launch_bounds__(256) k_pose_reduce(const float *pose_part, const ViewInfo *views,
-                                                    const SubmapInfo *subs, int maxv, float *pose) {
+                                                    const SubmapInfo *subs, int maxv, float *pose, int overwrite) {
     __shared__ double sm[8];
     const int v = blockIdx.x / 6, i = blockIdx.x % 6;
     const ViewInfo vi = views[v];
@@ -894,7 +966,7 @@ __global__ void __launch_bounds__(256) k_pose_reduce(const float *pose_part, con
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int w = 0; w < 8; ++w) t += sm[w];
-        pose[6 * v + i] += (float)t;
+        pose[6 * v + i] = (overwrite ? 0.f : pose[6 * v + i]) + (float)t;
     }
 }
 
@@ -949,6 +1021,7 @@ gs_status launch_project_bwd(gs_workspace *ws, const gs_gaussians *g, const gs_c
     A.dens_acc = out->densify_acc;
     A.dens_cnt = out->densify_cnt;
     A.gdir = ws->gdir;
+    A.overwrite = out->overwrite;
     StageTimer timer(ws, GS_STAGE_PROJECT_BWD, s);
     if (ws->proj_blocks > 0) {
         size_t smem = sizeof(float) * ws->max_views_per_submap * (kProjBwdThreads / 32) * 6;
@@ -970,7 +1043,7 @@ gs_status launch_project_bwd(gs_workspace *ws, const gs_gaussians *g, const gs_c
     if (out->pose) {
         ++ws->kernel_launches;
         k_pose_reduce<<<6 * ws->n_views, 256, 0, s>>>(ws->pose_part, ws->views, ws->subs,
-                                                      ws->max_views_per_submap, out->pose);
+                                                      ws->max_views_per_submap, out->pose, out->overwrite);
         return check_launch("pose_reduce");
     }
     return GS_OK;
