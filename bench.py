@@ -502,8 +502,10 @@ class Step:
             self.adam_v = [torch.zeros_like(p) for p in self.P]
 
     def zero(self):
-        # one library launch for every gradient buffer the step accumulates into
-        self.G.gs_zero_buffers([self.g_rgb, self.g_depth, *self.g_var, *self.grads.values()])
+        # one library launch for the image-space gradient buffers the losses
+        # accumulate into; the backward writes the parameter gradients
+        # (gs_grads.overwrite), so those need no clearing
+        self.G.gs_zero_buffers([self.g_rgb, self.g_depth, *self.g_var])
 
     # stage-by-stage so that the breakdown can put events between them
     def stages(self):
@@ -546,7 +548,7 @@ class Step:
         def bwd():
             gg = self.grads
             grads = G.GsGrads(*(gg[k].data_ptr() for k in ("means", "log_scales", "quats", "opacity_logits", "sh",
-                                                            "pose", "densify_acc", "densify_cnt")))
+                                                            "pose", "densify_acc", "densify_cnt")), 1, 0)
             if self.var:
                 G.gs_render_bwd_var(r.ws, r.gaussians(*self.P), G._ptr(r.cams_dev), G._ptr(self.g_rgb),
                                     None, None, *(G._ptr(x) for x in self.g_var), grads, G._stream())

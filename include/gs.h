@@ -27,7 +27,8 @@
  *    rgb[3*pix_off[v] .. 3*pix_off[v] + 3*W*H) as [3][H][W]; depth and alpha
  *    occupy [pix_off[v] .. pix_off[v] + W*H) as [H][W]; pix_off[v] is the sum
  *    of W*H over the views before v.
- *  - Gradients are accumulated (+=) into the caller's buffers.
+ *  - Gradients are accumulated (+=) into the caller's buffers, or written
+ *    (gs_grads.overwrite).
  *  - Errors: argument errors return at once and enqueue nothing. Conditions
  *    found on the device (instance capacity exceeded, a bounded device wait
  *    that ran out) set a flag in the workspace that lasts until the next
@@ -90,14 +91,20 @@ typedef struct {
     int64_t n; /* must equal submap_offsets[n_submaps] given at workspace creation */
 } gs_gaussians;
 
-/* Gradient outputs (device, accumulated). pose, densify_acc and densify_cnt
- * may be NULL. densify_acc[g] += ||dL/d(u,v)|| (pixels) and densify_cnt[g] += 1
- * for every view in which Gaussian g is visible. */
+/* Gradient outputs (device). pose, densify_acc and densify_cnt may be NULL.
+ * densify_acc[g] gets ||dL/d(u,v)|| (pixels) and densify_cnt[g] 1 for every
+ * view in which Gaussian g is visible (the densification statistic of Sec.
+ * III-B).  overwrite = 0: every output is accumulated (+=) into the caller's
+ * values; overwrite = 1: every output is written (=), zeros for the rows of
+ * Gaussians that no view sees, so the buffers need no clearing before the
+ * call (one write of each row instead of a clear and a read-modify-write). */
 typedef struct {
     float *means, *log_scales, *quats, *opacity_logits, *sh;
     float *pose;        /* [n_views][6]: dL/d(rho, phi) of the left perturbation exp(xi^) T_cw */
     float *densify_acc; /* [N] */
     int32_t *densify_cnt; /* [N] */
+    int32_t overwrite;  /* 0 accumulate, 1 write */
+    int32_t reserved;   /* must be 0 */
 } gs_grads;
 
 typedef struct gs_workspace gs_workspace;

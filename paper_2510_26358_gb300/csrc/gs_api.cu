@@ -405,6 +405,8 @@ gs_status gs_render_bwd(gs_workspace *ws, const gs_gaussians *g, const gs_camera
     if (r != GS_OK) return r;
     if (ws->n > 0 && (!out->means || !out->log_scales || !out->quats || !out->opacity_logits || !out->sh))
         return fail(GS_ERR_INVALID_ARG, "a gradient pointer is NULL");
+    if ((out->overwrite != 0 && out->overwrite != 1) || out->reserved != 0)
+        return fail(GS_ERR_INVALID_ARG, "gs_grads.overwrite must be 0 or 1 and reserved 0");
     if (!ws->rendered) return fail(GS_ERR_STATE, "gs_render_bwd before gs_render_fwd");
     cudaStream_t s = (cudaStream_t)stream;
     r = launch_raster_bwd(ws, dL_drgb, dL_ddepth, dL_dalpha, false, nullptr, nullptr, s);
@@ -420,6 +422,8 @@ gs_status gs_render_bwd_var(gs_workspace *ws, const gs_gaussians *g, const gs_ca
     if (r != GS_OK) return r;
     if (ws->n > 0 && (!out->means || !out->log_scales || !out->quats || !out->opacity_logits || !out->sh))
         return fail(GS_ERR_INVALID_ARG, "a gradient pointer is NULL");
+    if ((out->overwrite != 0 && out->overwrite != 1) || out->reserved != 0)
+        return fail(GS_ERR_INVALID_ARG, "gs_grads.overwrite must be 0 or 1 and reserved 0");
     if (!ws->rendered_var)
         return fail(GS_ERR_STATE, "gs_render_bwd_var needs gs_render_fwd_var as the last forward");
     cudaStream_t s = (cudaStream_t)stream;

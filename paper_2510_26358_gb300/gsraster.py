@@ -71,7 +71,8 @@ class GsGaussians(ctypes.Structure):
 class GsGrads(ctypes.Structure):
     _fields_ = [("means", ctypes.c_void_p), ("log_scales", ctypes.c_void_p), ("quats", ctypes.c_void_p),
                 ("opacity_logits", ctypes.c_void_p), ("sh", ctypes.c_void_p), ("pose", ctypes.c_void_p),
-                ("densify_acc", ctypes.c_void_p), ("densify_cnt", ctypes.c_void_p)]
+                ("densify_acc", ctypes.c_void_p), ("densify_cnt", ctypes.c_void_p), ("overwrite", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class GsParamArrays(ctypes.Structure):
@@ -611,26 +612,31 @@ class Renderer:
         return rgb, depth, alpha
 
     def backward(self, means, log_scales, quats, opacity_logits, sh, dL_drgb, dL_ddepth, dL_dalpha=None,
-                 grads=None, stream=None, pose=True, densify=True, var=False, dL_dmean=None, dL_dvar=None):
-        """Accumulates gradients into ``grads`` (dict of tensors; allocated zeroed if None).  With ``var``
-        the adjoints of the depth mean and variance are taken too (after ``forward(var=True)``)."""
+                 grads=None, stream=None, pose=True, densify=True, var=False, dL_dmean=None, dL_dvar=None,
+                 overwrite=None):
+        """Gradients into ``grads`` (dict of tensors): accumulated, or written when ``overwrite``.  If
+        ``grads`` is None they are allocated uninitialised and written (``overwrite`` defaults to
+        True then, else to False).  With ``var`` the adjoints of the depth mean and variance are
+        taken too (after ``forward(var=True)``)."""
         torch = self.torch
         s = _stream(stream)
         g = self.gaussians(means, log_scales, quats, opacity_logits, sh)
+        if overwrite is None:
+            overwrite = grads is None
         if grads is None:
-            grads = dict(means=torch.zeros_like(means), log_scales=torch.zeros_like(log_scales),
-                         quats=torch.zeros_like(quats), opacity_logits=torch.zeros_like(opacity_logits),
-                         sh=torch.zeros_like(sh))
+            new = torch.empty_like if overwrite else torch.zeros_like
+            grads = dict(means=new(means), log_scales=new(log_scales), quats=new(quats),
+                         opacity_logits=new(opacity_logits), sh=new(sh))
             if pose:
-                grads["pose"] = torch.zeros(self.n_views, 6, device=self.device)
+                grads["pose"] = new(torch.empty(self.n_views, 6, device=self.device))
             if densify:
-                grads["densify_acc"] = torch.zeros(self.n, device=self.device)
-                grads["densify_cnt"] = torch.zeros(self.n, dtype=torch.int32, device=self.device)
+                grads["densify_acc"] = new(torch.empty(self.n, device=self.device))
+                grads["densify_cnt"] = new(torch.empty(self.n, dtype=torch.int32, device=self.device))
         gg = GsGrads(grads["means"].data_ptr(), grads["log_scales"].data_ptr(), grads["quats"].data_ptr(),
                      grads["opacity_logits"].data_ptr(), grads["sh"].data_ptr(),
                      grads["pose"].data_ptr() if "pose" in grads else None,
                      grads["densify_acc"].data_ptr() if "densify_acc" in grads else None,
-                     grads["densify_cnt"].data_ptr() if "densify_cnt" in grads else None)
+                     grads["densify_cnt"].data_ptr() if "densify_cnt" in grads else None, int(bool(overwrite)), 0)
         if var:
             gs_render_bwd_var(self.ws, g, _ptr(self.cams_dev), _ptr(dL_drgb), _ptr(dL_ddepth), _ptr(dL_dalpha),
                               _ptr(dL_dmean), _ptr(dL_dvar), gg, s)

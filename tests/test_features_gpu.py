@@ -394,3 +394,49 @@ def test_zero_buffers():
     assert int(torch.count_nonzero(f)) == 0
     with pytest.raises(G.GsError):
         G.gs_zero_buffers([torch.ones(4, device=dev)] * 17)
+
+
+def test_written_gradients_equal_accumulated_onto_zero():
+    """gs_grads.overwrite = 1 writes every output (zeros for the Gaussians no
+    view sees) and equals accumulating onto zeroed buffers, up to the order
+    of the raster backward's float atomics (each call sums its image-space
+    gradients in its own order); with overwrite = 0 the outputs are added onto
+    what the buffers held."""
+    torch, dev = torch_dev()
+    G = _G()
+    sc = _scene()
+    gC, gD, gA = _upstream(sc)
+    P = params_to_dev(sc)
+    r = G.Renderer(sc.cameras, sc.submap_offsets, sc.sh_degree, inst_capacity=1 << 22)
+    try:
+        r.forward(*P)
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev)
+        up = (t(gC), t(gD), t(gA))
+        keys = ("means", "log_scales", "quats", "opacity_logits", "sh", "pose", "densify_acc", "densify_cnt")
+        zeros = r.backward(*P, *up, overwrite=False)  # allocated zeroed, accumulated
+        poison = {k: (torch.full_like(v, float("nan")) if v.dtype == torch.float32 else torch.full_like(v, -7))
+                  for k, v in zeros.items()}
+        written = r.backward(*P, *up, grads=poison, overwrite=True)
+        base = {k: (torch.randn_like(v) if v.dtype == torch.float32 else torch.full_like(v, 3)) for k, v in zeros.items()}
+        summed = r.backward(*P, *up, grads={k: v.clone() for k, v in base.items()}, overwrite=False)
+        torch.cuda.synchronize()
+        seen = zeros["densify_cnt"] > 0
+        assert 0 < int(seen.sum()) < sc.n  # both kinds of rows occur
+        close = lambda a, b: float((a.double() - b.double()).abs().max()) <= 1e-5 * float(b.double().abs().max())
+        for k in keys:
+            assert not torch.isnan(written[k].float()).any(), k  # every row written
+            assert close(written[k], zeros[k]), k
+            # the unseen Gaussians' rows are exactly zero
+            if k not in ("pose",):
+                assert torch.all(written[k][~seen] == 0), k
+        assert torch.equal(written["densify_cnt"], zeros["densify_cnt"])
+        for k in ("means", "log_scales", "quats", "sh", "opacity_logits", "pose", "densify_acc"):
+            assert close(summed[k] - base[k], zeros[k]), k  # added onto what the buffers held
+        assert torch.equal(summed["densify_cnt"], base["densify_cnt"] + zeros["densify_cnt"])
+        # an invalid mode is refused
+        gg = G.GsGrads(*(zeros[k].data_ptr() for k in keys), 2, 0)
+        st = G.lib().gs_render_bwd(r.ws, r.gaussians(*P), G._ptr(r.cams_dev), G._ptr(up[0]), G._ptr(up[1]),
+                                   None, ctypes.byref(gg), G._stream())
+        assert st == G.GS_ERR_INVALID_ARG
+    finally:
+        r.close()
