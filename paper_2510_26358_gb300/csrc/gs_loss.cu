@@ -39,6 +39,20 @@ __device__ __forceinline__ double block_sum_d(double v, double *sm) {
     return t;
 }
 
+// A thread's running sum in float with Kahan's compensation (error about 2
+// ulps of the sum whatever the number of terms): the FP64 pipe, a small
+// fraction of the FP32 rate on this GPU, is kept for the block and grid sums.
+struct KahanF {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float y = __fsub_rn(x, c);
+        const float t = __fadd_rn(s, y);
+        c = __fsub_rn(__fsub_rn(t, s), y);
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
 // Called by every thread after thread 0 has written the block's partial:
 // true in the one block that finishes last (it then sees every partial, and
 // puts the counter back to 0 for the next launch when it is done with it).
@@ -100,26 +114,29 @@ __device__ __forceinline__ int64_t lidar_pixel(const DepthArgs &A, int64_t i, fl
 
 __global__ void __launch_bounds__(LT) k_depth_partial(DepthArgs A) {
     __shared__ double sm[32];
-    double s = 0.0, c = 0.0;
+    KahanF sf;
+    double s = 0.0;
+    uint32_t c = 0;
     for (int64_t i = (int64_t)blockIdx.x * LT + threadIdx.x; i < A.n_pts; i += (int64_t)gridDim.x * LT) {
         float z;
         int64_t pix = lidar_pixel(A, i, z);
         if (pix < 0) continue;
-        double D = A.depth[pix], d = D - (double)z;
+        const float d = __fsub_rn(A.depth[pix], z);
         if (A.mode == 0) {
-            s += fabs(d);
+            sf.add(fabsf(d));
         } else if (A.mode == 2) {
-            s += var_term(D, A.var[pix], z, A.sigma_L, A.sigma_U).kl;
+            s += var_term(A.depth[pix], A.var[pix], z, A.sigma_L, A.sigma_U).kl;
         } else {
             // the KL's point-independent part (its log and constants) is added
             // once per valid point at the end: double logs and divisions per
             // point kept the FP64 pipe busy for tens of microseconds
-            s += d * d;
+            sf.add(__fmul_rn(d, d));
         }
-        c += 1.0;
+        ++c;
     }
+    s += sf.value();
     double ts = block_sum_d(s, sm);
-    double tc = block_sum_d(c, sm);
+    double tc = block_sum_d((double)c, sm);
     if (threadIdx.x == 0) {
         A.part[blockIdx.x] = ts;
         A.part[A.nb + blockIdx.x] = tc;
@@ -128,13 +145,13 @@ __global__ void __launch_bounds__(LT) k_depth_partial(DepthArgs A) {
     // the last block: grid sums in a fixed order (each thread a fixed strided
     // set, then a fixed tree), the loss and the gradient scale
     s = 0.0;
-    c = 0.0;
+    double cd = 0.0;
     for (int i = threadIdx.x; i < A.nb; i += LT) {
         s += A.part[i];
-        c += A.part[A.nb + i];
+        cd += A.part[A.nb + i];
     }
     ts = block_sum_d(s, sm);
-    tc = block_sum_d(c, sm);
+    tc = block_sum_d(cd, sm);
     if (threadIdx.x == 0) {
         double scale = tc > 0.0 ? (double)A.lambda / tc : 0.0;
         if (A.mode == 1) {
@@ -186,9 +203,10 @@ __device__ __forceinline__ float4 target4(const uint8_t *t, int64_t i) {
     return make_float4(target_value(b.x), target_value(b.y), target_value(b.z), target_value(b.w));
 }
 
-// Four terms are added in float, each group of four into a double; the
-// block and grid sums are in double and in a fixed order.  A thread works
-// four grid strides at once (more loads in flight), in the same order.  With
+// Four terms are added in float, each group of four into a thread's
+// compensated float sum; the block and grid sums are in double and in a
+// fixed order.  A thread works four grid strides at once (more loads in
+// flight), in the same order.  With
 // `done` set, the last block also writes the mean to *loss (else a separate
 // kernel combines the partials).
 template <typename TT>
@@ -197,7 +215,7 @@ __global__ void __launch_bounds__(LT) k_l1_partial(const float *rgb, const TT *t
                                                   float *loss) {
     constexpr int U = 4;
     __shared__ double sm[32];
-    double s = 0.0;
+    KahanF s;
     const bool vec = ((((uintptr_t)rgb) | ((uintptr_t)grad)) & 15) == 0 &&
                      (((uintptr_t)target) & (4 * sizeof(TT) - 1)) == 0;
     const int64_t n4 = vec ? n / 4 : 0;
@@ -218,22 +236,22 @@ __global__ void __launch_bounds__(LT) k_l1_partial(const float *rgb, const TT *t
         for (int u = 0; u < U; ++u) {
             const int64_t i = i0 + u * stride;
             if (i >= n4) break;
-            s += (double)(l1_term(c[u].x, t[u].x, inv, g[u].x) + l1_term(c[u].y, t[u].y, inv, g[u].y) +
-                          l1_term(c[u].z, t[u].z, inv, g[u].z) + l1_term(c[u].w, t[u].w, inv, g[u].w));
+            s.add(l1_term(c[u].x, t[u].x, inv, g[u].x) + l1_term(c[u].y, t[u].y, inv, g[u].y) +
+                  l1_term(c[u].z, t[u].z, inv, g[u].z) + l1_term(c[u].w, t[u].w, inv, g[u].w));
             if (grad) reinterpret_cast<float4 *>(grad)[i] = g[u];
         }
     }
     for (int64_t i = 4 * n4 + (int64_t)blockIdx.x * LT + threadIdx.x; i < n; i += stride) {
         float g = grad ? grad[i] : 0.f;
-        s += (double)l1_term(rgb[i], target_value(target[i]), inv, g);
+        s.add(l1_term(rgb[i], target_value(target[i]), inv, g));
         if (grad) grad[i] = g;
     }
-    double t = block_sum_d(s, sm);
+    double t = block_sum_d(s.value(), sm);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
     if (!done || !last_block(done)) return;
-    s = 0.0;
-    for (int i = threadIdx.x; i < (int)gridDim.x; i += LT) s += part[i];
-    t = block_sum_d(s, sm);
+    double sd = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += LT) sd += part[i];
+    t = block_sum_d(sd, sm);
     if (threadIdx.x == 0) {
         *loss = (float)(t / (double)n);
         *done = 0u;
