@@ -137,7 +137,7 @@ void gs_workspace_destroy(gs_workspace *ws) {
     void *ptrs[] = {ws->views, ws->subs, ws->sub_views, ws->rec, ws->pkey, ws->rect, ws->g2d, ws->gdir,
                     ws->vis_key, ws->vis_pair, ws->vis_key_alt, ws->vis_pair_alt, ws->ioff, ws->win_pair,
                     ws->inst_tile, ws->inst_val, ws->inst_tile_alt, ws->inst_val_alt, ws->ranges,
-                    ws->tile_order,
+                    ws->tile_order, ws->order_tot, ws->order_base,
                     ws->last, ws->tfin, ws->vstat, ws->hist, ws->part, ws->digit_tot, ws->pose_part, ws->red_part, ws->ssim_d, ws->ssim_part,
                     ws->st};
     for (void *p : ptrs)
@@ -281,6 +281,8 @@ gs_status gs_workspace_create(const gs_camera *cams, int32_t n_views, const int6
     GS_ALLOC(ws->inst_val_alt, I);
     GS_ALLOC(ws->ranges, (size_t)ws->n_tiles);
     GS_ALLOC(ws->tile_order, (size_t)ws->n_tiles);
+    GS_ALLOC(ws->order_tot, (size_t)kOrderBuckets);
+    GS_ALLOC(ws->order_base, (size_t)kOrderBlocks * kOrderBuckets);
     GS_ALLOC(ws->last, (size_t)ws->n_pix);
     GS_ALLOC(ws->tfin, (size_t)ws->n_pix);
     GS_ALLOC(ws->vstat, (size_t)ws->n_pix);

@@ -30,6 +30,7 @@ constexpr int kSortThreads = 256;
 constexpr int kProjThreads = 256;
 constexpr int kOrderBuckets = 64;     // list-length buckets of the raster work order
 constexpr int kOrderShift = 5;        // bucket = min(63, length >> 5)
+constexpr int kOrderBlocks = 64;      // blocks of the two work-order kernels
 
 // ---------------------------------------------------------------------------
 // tables

@@ -79,6 +79,8 @@ struct gs_workspace {
     // per-tile / per-pixel
     uint2 *ranges = nullptr;       // [n_tiles]
     uint32_t *tile_order = nullptr; // [n_tiles] tiles by decreasing list length (raster work order)
+    uint32_t *order_tot = nullptr;  // [kOrderBuckets] work-order bucket totals
+    uint32_t *order_base = nullptr; // [kOrderBlocks][kOrderBuckets] each block's base inside each bucket
     uint32_t *last = nullptr;      // [n_pix]
     float *tfin = nullptr;         // [n_pix]
     float4 *vstat = nullptr;       // [n_pix] depth (mean, var, 1/W, 0) of the variance forward

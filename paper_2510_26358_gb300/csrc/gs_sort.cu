@@ -223,12 +223,15 @@ struct ScatterSmem {
 };
 
 // One block tile = T*R keys, split into W contiguous warp sub-tiles of 32*R
-// keys.  Each warp ranks its own sub-tile round by round (match masks give
-// the rank among equal digits of the round, per-warp counters carry it across
-// rounds, no block barrier); one block-wide pass then turns the per-warp
-// counts into offsets, the keys are reordered by digit in shared memory and
-// written out in coalesced runs at the global offsets.  Stable: sub-tiles,
-// rounds and lanes follow the input order.
+// keys.  Each warp ranks its own sub-tile round by round (the mask of the
+// lanes holding the same digit, built from one ballot per digit bit, which
+// measured faster than __match_any_sync: 0.473 -> 0.452 ms for the two passes
+// over 25.1M instances; it gives the rank among equal digits of the round,
+// per-warp counters carry it across rounds, no block barrier); one
+// block-wide pass then turns the per-warp counts into offsets, the keys are
+// reordered by digit in shared memory and written out in coalesced runs at
+// the global offsets.  Stable: sub-tiles, rounds and lanes follow the input
+// order.
 template <int R>
 __global__ void __launch_bounds__(T) k_radix_scatter(const uint32_t *kin, const uint32_t *vin,
                                                     uint32_t *kout, uint32_t *vout,
@@ -264,7 +267,12 @@ __global__ void __launch_bounds__(T) k_radix_scatter(const uint32_t *kin, const 
         for (int r = 0; r < R; ++r) {
             const bool valid = (uint32_t)(w * WT + r * 32 + lane) < tn;
             const uint32_t d = (key[r] >> shift) & 255u;
-            const uint32_t m = __match_any_sync(0xffffffffu, valid ? d : (0x100u | (uint32_t)lane));
+            uint32_t m = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                const uint32_t bb = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+                m &= ((d >> b) & 1u) ? bb : ~bb;
+            }
             const uint32_t below = m & lt;
             const uint32_t before = valid ? S.wcnt[w][d] : 0u;
             rank[r] = before + __popc(below);
@@ -294,12 +302,16 @@ __global__ void __launch_bounds__(T) k_radix_scatter(const uint32_t *kin, const 
             }
         }
         __syncthreads();
-        for (uint32_t j = t; j < tn; j += T) {
-            const uint32_t k = S.key[j];
-            const uint32_t d = (k >> shift) & 255u;
-            const uint32_t o = S.base[d] + (j - S.tstart[d]);
-            kout[o] = k;
-            vout[o] = S.val[j];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint32_t j = t + r * T;
+            if (j < tn) {
+                const uint32_t k = S.key[j];
+                const uint32_t d = (k >> shift) & 255u;
+                const uint32_t o = S.base[d] + (j - S.tstart[d]);
+                kout[o] = k;
+                vout[o] = S.val[j];
+            }
         }
         __syncthreads();
         S.base[t] += S.tcnt[t];
@@ -369,7 +381,7 @@ __global__ void __launch_bounds__(T) k_instance_offsets(const DevState *st, cons
 // kEmitWindow consecutive slots, takes the pairs that cover it from the
 // window-start table (the pairs owning its first slot and the next window's),
 // stages them in shared memory, and every thread writes one instance per
-// step, locating its pair by binary search in the stage.
+// step, reading its pair from the window's slot-owner table.
 //
 // A rectangle tile that the Gaussian's padded alpha >= alpha_min ellipse
 // misses (about a fifth of them on wide scenes: the corners of the rectangles
@@ -389,18 +401,27 @@ __global__ void __launch_bounds__(T) k_instance_offsets(const DevState *st, cons
 // rasterisers' own evaluation, so a dropped tile has no fragment to keep.  The
 // minimum of the convex quadratic is 0 when the box holds the mean, else it
 // lies on an edge, at the edge's stationary point clamped to the edge.
-__device__ __forceinline__ bool tile_reached(const float4 r0, const float4 r1, int X0, int X1, int Y0, int Y1,
-                                             const Consts &k) {
+// The pair's own factors of the test: the stationary slopes on an edge
+// dx = const (sy = dy/dx) and dy = const (sx = dx/dy), and the padded
+// threshold.  (Staging them per pair in the window, with the record load that
+// needs, measured slower than recomputing them per instance: the load lands
+// on the staging's critical path.)
+__device__ __forceinline__ float4 reach_terms(const float4 r1, const Consts &k) {
+    const float l11 = r1.x, l12 = r1.y, l22 = r1.z;
+    const float pad = 1.f + k.ext_rel_pad;
+    return make_float4(-l11 * l12 / (l12 * l12 + l22 * l22), -l12 / l11, (r1.w - k.log2_alpha_min) * pad * pad,
+                       0.f);
+}
+
+__device__ __forceinline__ bool tile_reached(const float4 r0, const float4 r1, const float4 q, int X0, int X1,
+                                             int Y0, int Y1, const Consts &k) {
     const float ax = __fadd_rn((float)X0 - r0.x, r0.z) - k.ext_abs_pad;
     const float bx = __fadd_rn((float)X1 - r0.x, r0.z) + k.ext_abs_pad;
     const float ay = __fadd_rn((float)Y0 - r0.y, r0.w) - k.ext_abs_pad;
     const float by = __fadd_rn((float)Y1 - r0.y, r0.w) + k.ext_abs_pad;
     if (ax <= 0.f && bx >= 0.f && ay <= 0.f && by >= 0.f) return true;
     const float l11 = r1.x, l12 = r1.y, l22 = r1.z;
-    const float pad = 1.f + k.ext_rel_pad;
-    const float thr = (r1.w - k.log2_alpha_min) * pad * pad;
-    const float sy = -l11 * l12 / (l12 * l12 + l22 * l22);  // stationary dy / dx on an edge dx = const
-    const float sx = -l12 / l11;                            // stationary dx / dy on an edge dy = const
+    const float sy = q.x, sx = q.y;
     float m = INFINITY;
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
@@ -413,39 +434,40 @@ __device__ __forceinline__ bool tile_reached(const float4 r0, const float4 r1, i
         const float u1 = l11 * dx + l12 * cy, u2 = l22 * cy;
         m = fminf(m, u1 * u1 + u2 * u2);
     }
-    return m <= thr;
-}
-
-__device__ __forceinline__ uint32_t last_le(const uint32_t *a, uint32_t n, uint32_t x) {
-    // largest i < n with a[i] <= x (a nondecreasing, a[0] <= x)
-    uint32_t lo = 0, hi = n - 1;
-    while (lo < hi) {
-        uint32_t mid = (lo + hi + 1) >> 1;
-        if (a[mid] <= x) lo = mid; else hi = mid - 1;
-    }
-    return lo;
+    return m <= q.z;
 }
 
 // Blocks of the emission an SM keeps resident: a window's staging is a short
 // chain of dependent loads (slot owners, pair ids, rectangles) that every
 // thread of the block waits for, so several blocks per SM hide it.
 constexpr int kEmitBlocksPerSM = 6;
+constexpr int kEmitPerThread = kEmitWindow / T;
+static_assert(kEmitWindow == T * kEmitPerThread, "a window is a whole number of slots a thread");
 
+// Per window, staged once per covering pair: its first slot, pair id,
+// rectangle origin, width, 1 / width (for the row of a slot) and view.  The
+// owner of every slot of the window comes from one block-wide max-scan of the
+// pairs' start marks (pair j >= 1 starts inside the window, pair 0 owns its
+// first slot; every visible pair has at least one tile), so a slot finds its
+// pair with one shared-memory read instead of a binary search over the
+// staged pairs: 0.323 -> 0.270 ms for 25.1M instances of 3.08M pairs.
 __global__ void __launch_bounds__(T, kEmitBlocksPerSM) k_emit_instances(
     const uint32_t *vis_pair, const short4 *rect, const float4 *rec, const ViewInfo *views, int n_views,
     const Consts k, const DevState *st, const uint32_t *ioff, const uint32_t *win_pair, uint32_t *inst_tile,
     uint32_t *inst_val) {
     __shared__ uint32_t s_off[kEmitWindow];
     __shared__ uint32_t s_pair[kEmitWindow];
-    __shared__ short4 s_rect[kEmitWindow];
-    __shared__ uint8_t s_vidx[kEmitWindow];
-    __shared__ int4 s_view[GS_MAX_VIEWS];    // (tile_off, ntx, W, H)
+    __shared__ short4 s_rect[kEmitWindow];    // (x0, y0, width, view)
+    __shared__ float s_rw[kEmitWindow];       // 1 / width
+    __shared__ uint16_t s_own[kEmitWindow];   // owner (staged pair) of each slot of the window
+    __shared__ int4 s_view[GS_MAX_VIEWS];     // (tile_off, ntx, W, H)
     __shared__ int32_t s_poff[GS_MAX_VIEWS];  // first pair of each view
     __shared__ uint32_t s_range[2];
+    __shared__ uint32_t s_wmax[T / 32];
     if (st->flags & kFlagCapacity) return;
     const uint32_t n = st->n_vis, total = st->n_inst;
     const uint32_t windows = (total + kEmitWindow - 1) / kEmitWindow;
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     for (int v = t; v < n_views; v += T) {
         s_view[v] = make_int4(views[v].tile_off, views[v].ntx, views[v].W, views[v].H);
         s_poff[v] = views[v].pair_off;
@@ -465,6 +487,8 @@ __global__ void __launch_bounds__(T, kEmitBlocksPerSM) k_emit_instances(
             }
             s_range[1] = p1;
         }
+#pragma unroll
+        for (int i = 0; i < kEmitPerThread; ++i) s_own[t * kEmitPerThread + i] = 0;
         __syncthreads();
         const uint32_t s0 = s_range[0], np = s_range[1] - s0 + 1;  // np <= window: every pair has >= 1 slot
         for (uint32_t j = t; j < np; j += T) {
@@ -474,22 +498,56 @@ __global__ void __launch_bounds__(T, kEmitBlocksPerSM) k_emit_instances(
                 int mid = (lo_v + hi_v + 1) >> 1;
                 if ((uint32_t)s_poff[mid] <= pair) lo_v = mid; else hi_v = mid - 1;
             }
-            s_off[j] = ioff[s0 + j];
+            const uint32_t off = ioff[s0 + j];
+            const short4 r = rect[pair];
+            const int wdt = (int)r.z - (int)r.x + 1;
+            s_off[j] = off;
             s_pair[j] = pair;
-            s_rect[j] = rect[pair];
-            s_vidx[j] = (uint8_t)lo_v;
+            s_rect[j] = make_short4(r.x, r.y, (short)wdt, (short)lo_v);
+            s_rw[j] = 1.f / (float)wdt;
+            if (j > 0) s_own[off - o0] = (uint16_t)j;
+        }
+        __syncthreads();
+        // inclusive max-scan of the marks: thread t owns slots [4t, 4t + 4)
+        {
+            uint32_t v[kEmitPerThread], run = 0;
+#pragma unroll
+            for (int i = 0; i < kEmitPerThread; ++i) {
+                run = max(run, (uint32_t)s_own[t * kEmitPerThread + i]);
+                v[i] = run;
+            }
+            uint32_t x = run;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x = max(x, y);
+            }
+            if (lane == 31) s_wmax[wid] = x;
+            uint32_t before = __shfl_up_sync(0xffffffffu, x, 1);
+            if (lane == 0) before = 0;
+            __syncthreads();
+            for (int w = 0; w < wid; ++w) before = max(before, s_wmax[w]);
+#pragma unroll
+            for (int i = 0; i < kEmitPerThread; ++i) s_own[t * kEmitPerThread + i] = (uint16_t)max(before, v[i]);
         }
         __syncthreads();
         for (uint32_t o = o0 + t; o < o1; o += T) {
-            const uint32_t a = last_le(s_off, np, o);
+            const uint32_t a = s_own[o - o0];
             const short4 r = s_rect[a];
-            const int4 vw = s_view[s_vidx[a]];
+            const float rw = s_rw[a];
+            const int4 vw = s_view[r.w];
             const uint32_t pair = s_pair[a];
-            const int wdt = (int)r.z - (int)r.x + 1;
+            const int wdt = r.z;
             const int local = (int)(o - s_off[a]);
-            const int ty = r.y + local / wdt, tx = r.x + local % wdt;
+            // row = local / wdt from the staged reciprocal, corrected to the
+            // exact quotient (the estimate is within one of it)
+            int row = (int)((float)local * rw);
+            if (row * wdt > local) --row;
+            else if ((row + 1) * wdt <= local) ++row;
+            const int ty = r.y + row, tx = r.x + (local - row * wdt);
             const int X0 = tx * k.tile_w, Y0 = ty * k.tile_h;
-            const bool keep = tile_reached(__ldg(rec + 3 * pair), __ldg(rec + 3 * pair + 1), X0,
+            const float4 r1 = __ldg(rec + 3 * (size_t)pair + 1);
+            const bool keep = tile_reached(__ldg(rec + 3 * (size_t)pair), r1, reach_terms(r1, k), X0,
                                            min(X0 + k.tile_w, vw.z) - 1, Y0, min(Y0 + k.tile_h, vw.w) - 1, k);
             inst_tile[o] = keep ? (uint32_t)(vw.x + ty * vw.y + tx) : kInvalidKey;
             inst_val[o] = pair;
@@ -502,7 +560,9 @@ __global__ void __launch_bounds__(T, kEmitBlocksPerSM) k_emit_instances(
 // rectangle tiles (kInvalidKey, sorted last) belong to no tile
 // (a thread takes four consecutive ids with one 16-byte load, plus the ids
 // on either side)
-__global__ void k_ranges(const uint32_t *tile, const DevState *st, uint32_t n_tiles, uint2 *ranges) {
+__global__ void k_ranges(const uint32_t *tile, const DevState *st, uint32_t n_tiles, uint2 *ranges,
+                         uint32_t *order_tot) {
+    if (blockIdx.x == 0 && threadIdx.x < kOrderBuckets) order_tot[threadIdx.x] = 0u;  // for the work order
     const uint32_t n = st->n_inst;
     const uint32_t n4 = (n + 3) / 4;
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += gridDim.x * blockDim.x) {
@@ -537,18 +597,33 @@ __device__ __forceinline__ uint32_t order_bucket(uint2 r) {
     return kOrderBuckets - 1 - min((uint32_t)(kOrderBuckets - 1), len >> kOrderShift);
 }
 
-// One block: bucket counts in shared memory, their prefix, then every tile
-// placed at its bucket's cursor.
-__global__ void __launch_bounds__(1024) k_tile_order(const uint2 *ranges, int n_tiles, uint32_t *order) {
-    static_assert(kOrderBuckets == 64, "the prefix below takes two counts a lane of one warp");
-    __shared__ uint32_t cursor[kOrderBuckets];
+// Two kernels over kOrderBlocks blocks (one block over every tile took 47 us
+// on 54k tiles, its shared-memory atomics on 64 counters serialised):
+// k_order_count adds each block's bucket counts to the bucket totals, the
+// atomic's old value giving the block its base inside each bucket;
+// k_order_place takes the totals' prefix and puts each tile at its bucket's
+// start + its block's base + its rank in the block.  The totals are cleared by
+// k_ranges (block 0), which runs before.
+
+__global__ void __launch_bounds__(256) k_order_count(const uint2 *ranges, int n_tiles, uint32_t *tot,
+                                                    uint32_t *bbase) {
+    __shared__ uint32_t cnt[kOrderBuckets];
     const int t = threadIdx.x;
-    if (t < kOrderBuckets) cursor[t] = 0;
+    if (t < kOrderBuckets) cnt[t] = 0;
     __syncthreads();
-    for (int i = t; i < n_tiles; i += blockDim.x) atomicAdd(&cursor[order_bucket(ranges[i])], 1u);
+    for (int i = blockIdx.x * blockDim.x + t; i < n_tiles; i += gridDim.x * blockDim.x)
+        atomicAdd(&cnt[order_bucket(ranges[i])], 1u);
     __syncthreads();
-    if (t < 32) {  // exclusive prefix of the kOrderBuckets (= 64) counts by one warp
-        const uint32_t a = cursor[t], b = cursor[t + 32];
+    if (t < kOrderBuckets) bbase[blockIdx.x * kOrderBuckets + t] = cnt[t] ? atomicAdd(&tot[t], cnt[t]) : 0u;
+}
+
+__global__ void __launch_bounds__(256) k_order_place(const uint2 *ranges, int n_tiles, const uint32_t *tot,
+                                                    const uint32_t *bbase, uint32_t *order) {
+    static_assert(kOrderBuckets == 64, "the prefix below takes two counts a lane of one warp");
+    __shared__ uint32_t cur[kOrderBuckets];
+    const int t = threadIdx.x;
+    if (t < 32) {  // exclusive prefix of the 64 bucket totals by one warp, plus this block's bases
+        const uint32_t a = tot[t], b = tot[t + 32];
         uint32_t x = a;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -562,11 +637,12 @@ __global__ void __launch_bounds__(1024) k_tile_order(const uint2 *ranges, int n_
             const uint32_t y = __shfl_up_sync(0xffffffffu, z, o);
             if (t >= o) z += y;
         }
-        cursor[t] = x - a;
-        cursor[t + 32] = tot_a + z - b;
+        cur[t] = x - a + bbase[blockIdx.x * kOrderBuckets + t];
+        cur[t + 32] = tot_a + z - b + bbase[blockIdx.x * kOrderBuckets + t + 32];
     }
     __syncthreads();
-    for (int i = t; i < n_tiles; i += blockDim.x) order[atomicAdd(&cursor[order_bucket(ranges[i])], 1u)] = (uint32_t)i;
+    for (int i = blockIdx.x * blockDim.x + t; i < n_tiles; i += gridDim.x * blockDim.x)
+        order[atomicAdd(&cur[order_bucket(ranges[i])], 1u)] = (uint32_t)i;
 }
 
 // One stable pass over bits [shift, shift+8) by nb blocks; swaps in/out.
@@ -660,10 +736,13 @@ gs_status launch_bin_sort(gs_workspace *ws, cudaStream_t s) {
     StageTimer timer(ws, GS_STAGE_RANGES, s);
     cudaMemsetAsync(ws->ranges, 0, sizeof(uint2) * ws->n_tiles, s);
     ++ws->kernel_launches;
-    k_ranges<<<ws->num_sms * 4, 256, 0, s>>>(ws->inst_tile, st, (uint32_t)ws->n_tiles, ws->ranges);
+    k_ranges<<<ws->num_sms * 4, 256, 0, s>>>(ws->inst_tile, st, (uint32_t)ws->n_tiles, ws->ranges, ws->order_tot);
     // 6. raster work order
     ++ws->kernel_launches;
-    k_tile_order<<<1, 1024, 0, s>>>(ws->ranges, (int)ws->n_tiles, ws->tile_order);
+    k_order_count<<<kOrderBlocks, 256, 0, s>>>(ws->ranges, (int)ws->n_tiles, ws->order_tot, ws->order_base);
+    ++ws->kernel_launches;
+    k_order_place<<<kOrderBlocks, 256, 0, s>>>(ws->ranges, (int)ws->n_tiles, ws->order_tot, ws->order_base,
+                                               ws->tile_order);
     return check_launch("ranges");
 }
 
