@@ -215,7 +215,11 @@ gs_status gs_image_loss(gs_workspace *ws, const float *rgb, const float *target,
  * then chains to the parameters and, through the projection, to each
  * camera's pose twist.  dL_drgb, dL_ddepth (device, planar like the outputs),
  * dL_dalpha (device, nullable).  g and cams_dev must be those of the
- * preceding gs_project. */
+ * preceding gs_project.  The image-space gradient rows the backward adds into
+ * are cleared by gs_project (next to the records it writes); only a further
+ * backward of the same projection launches a clearing kernel of its own.  (A
+ * CUDA graph that holds the first backward after a projection but not the
+ * projection itself does not clear those rows when it is replayed.) */
 gs_status gs_render_bwd(gs_workspace *ws, const gs_gaussians *g, const gs_camera *cams_dev,
                         const float *dL_drgb, const float *dL_ddepth, const float *dL_dalpha,
                         const gs_grads *out, void *stream);

@@ -96,6 +96,7 @@ struct gs_workspace {
     gs::DevState *st = nullptr;
     // host-side order checks
     bool projected = false, binned = false, rendered = false, rendered_var = false;
+    bool g2d_clear = false;  // the last projection cleared g2d and no backward has run since
     // optional per-stage timing (events recorded around each kernel group)
     bool profiling = false;
     cudaEvent_t ev[2 * GS_NUM_STAGES] = {};

@@ -286,6 +286,7 @@ struct ProjArgs {
     float4 *rec;
     uint32_t *pkey;
     short4 *rect;
+    float *g2d_zero;  // forward: the image-space gradient rows of the visible pairs, cleared here
     // backward
     const float *g2d;
     float *gm, *gls, *gq, *gom, *gsh, *pose_part, *dens_acc;
@@ -512,6 +513,12 @@ __global__ void __launch_bounds__(kProjThreads) k_project_fwd(ProjArgs A) {
             A.rec[3 * pair + 0] = r0;
             A.rec[3 * pair + 1] = r1;
             A.rec[3 * pair + 2] = r2;
+            // the backward's atomics add into these rows: cleared next to the
+            // record (neighbouring threads, neighbouring rows) instead of by a
+            // gather over the sorted visible pairs later
+            float2 *row = reinterpret_cast<float2 *>(A.g2d_zero + pair * kGrad);
+#pragma unroll
+            for (int i = 0; i < kGrad / 2; ++i) row[i] = make_float2(0.f, 0.f);
         }
         A.rect[pair] = rc;
         A.pkey[pair] = vis ? __float_as_uint(r2.w) : kInvalidKey;
@@ -997,6 +1004,8 @@ ProjArgs make_args(gs_workspace *ws, const gs_gaussians *g, const gs_camera *cam
 gs_status launch_project_fwd(gs_workspace *ws, const gs_gaussians *g, const gs_camera *cams,
                              cudaStream_t s) {
     ProjArgs A = make_args(ws, g, cams);
+    A.g2d_zero = ws->g2d;
+    ws->g2d_clear = true;  // (set before the early return: no pair, nothing to clear)
     if (ws->n == 0) return GS_OK;
     StageTimer timer(ws, GS_STAGE_PROJECT, s);
     int grid = (int)((ws->n + kProjThreads - 1) / kProjThreads);

@@ -495,7 +495,8 @@ __global__ void __launch_bounds__(TW * TH / PPT, 512 / (TW * TH / PPT)) k_raster
     }
 }
 
-// zero the image-space gradients of the visible pairs
+// zero the image-space gradients of the visible pairs (a backward that does
+// not follow its projection directly)
 __global__ void k_zero_g2d(const uint32_t *vis_pair, const DevState *st, float *g2d) {
     uint32_t n = st->n_vis;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n * kGrad; i += gridDim.x * blockDim.x)
@@ -639,13 +640,16 @@ gs_status launch_raster_bwd(gs_workspace *ws, const float *dL_drgb, const float 
         A.dL_dvar = dL_dvar;
     }
     A.g2d = ws->g2d;
-    {
+    // the projection clears the rows; a second backward of the same
+    // projection clears them itself
+    if (!ws->g2d_clear) {
         StageTimer timer(ws, GS_STAGE_ZERO_GRAD, s);
         ++ws->kernel_launches;
         k_zero_g2d<<<ws->num_sms * 4, 256, 0, s>>>(ws->vis_pair, ws->st, ws->g2d);
+        gs_status r = check_launch("zero_g2d");
+        if (r != GS_OK) return r;
     }
-    gs_status r = check_launch("zero_g2d");
-    if (r != GS_OK) return r;
+    ws->g2d_clear = false;
     cudaMemsetAsync(A.counter, 0, sizeof(uint32_t), s);
     int tw = ws->cfg.tile_w, th = ws->cfg.tile_h;
     if (tw == 8 && th == 8) return run_bwd<8, 8>(ws, A, s);

@@ -327,6 +327,12 @@ __device__ __forceinline__ uint32_t rect_tiles(short4 r) {
     return (nx > 0 && ny > 0) ? (uint32_t)(nx * ny) : 0u;
 }
 
+// Both kernels below split the sorted visible pairs into the same per-block
+// chunks of whole kOffsetStep steps: a thread takes four consecutive pairs a
+// step (four independent rectangle gathers in flight; one block-wide scan per
+// step of the offsets), on the compaction's wide grid.
+constexpr int kOffsetStep = 4 * T;
+
 // instance count of every sorted visible pair (into ioff) and of every block's chunk
 __global__ void __launch_bounds__(T) k_count_instances(const uint32_t *vis_pair, const short4 *rect,
                                                       const DevState *st, uint32_t *ioff, uint32_t *part,
@@ -334,12 +340,22 @@ __global__ void __launch_bounds__(T) k_count_instances(const uint32_t *vis_pair,
     __shared__ uint32_t sm[32];
     uint32_t n = st->n_vis;
     uint32_t lo, hi;
-    chunk_range(n, blockIdx.x, nb, T, lo, hi);
+    chunk_range(n, blockIdx.x, nb, kOffsetStep, lo, hi);
     uint32_t c = 0;
-    for (uint32_t i = lo + threadIdx.x; i < hi; i += T) {
-        uint32_t k = rect_tiles(rect[vis_pair[i]]);
-        ioff[i] = k;
-        c += k;
+    for (uint32_t i0 = lo + 4 * threadIdx.x; i0 < hi; i0 += kOffsetStep) {
+        uint32_t pr[4];
+        short4 rc[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) pr[u] = i0 + u < hi ? vis_pair[i0 + u] : 0u;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) rc[u] = i0 + u < hi ? rect[pr[u]] : make_short4(1, 1, 0, 0);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (i0 + u >= hi) break;
+            const uint32_t k = rect_tiles(rc[u]);
+            ioff[i0 + u] = k;
+            c += k;
+        }
     }
     uint32_t tot;
     block_exclusive_scan(c, sm, &tot);
@@ -357,19 +373,24 @@ __global__ void __launch_bounds__(T) k_instance_offsets(const DevState *st, cons
     if (st->flags & kFlagCapacity) return;
     uint32_t n = st->n_vis;
     uint32_t lo, hi;
-    chunk_range(n, blockIdx.x, nb, T, lo, hi);
+    chunk_range(n, blockIdx.x, nb, kOffsetStep, lo, hi);
     uint32_t base = part[blockIdx.x];
-    for (uint32_t t0 = lo; t0 < hi; t0 += T) {
-        uint32_t i = t0 + threadIdx.x;
-        uint32_t c = i < hi ? ioff[i] : 0u;
+    for (uint32_t t0 = lo; t0 < hi; t0 += kOffsetStep) {
+        const uint32_t i0 = t0 + 4 * threadIdx.x;
+        uint32_t c[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) c[u] = i0 + u < hi ? ioff[i0 + u] : 0u;
         uint32_t tot;
-        uint32_t ex = block_exclusive_scan(c, sm, &tot);
-        if (i < hi) {
-            const uint32_t start = base + ex;
+        uint32_t start = base + block_exclusive_scan(c[0] + c[1] + c[2] + c[3], sm, &tot);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t i = i0 + u;
+            if (i >= hi) break;
             ioff[i] = start;
             for (uint32_t w = (start + kEmitWindow - 1) / kEmitWindow;
-                 c > 0 && w < n_win && w * (uint64_t)kEmitWindow < (uint64_t)start + c; ++w)
+                 c[u] > 0 && w < n_win && w * (uint64_t)kEmitWindow < (uint64_t)start + c[u]; ++w)
                 win_pair[w] = i;
+            start += c[u];
         }
         base += tot;
     }
@@ -717,9 +738,9 @@ gs_status launch_bin_sort(gs_workspace *ws, cudaStream_t s) {
     uint32_t *tv2 = (passes & 1) ? ws->inst_val : ws->inst_val_alt;
     {
     StageTimer timer(ws, GS_STAGE_EMIT, s);
-    ++ws->kernel_launches; k_count_instances<<<nb, T, 0, s>>>(v, ws->rect, st, ws->ioff, ws->part, nb);
-    ++ws->kernel_launches; k_scan_parts<<<1, T, 0, s>>>(ws->part, nb, nullptr, st, (uint64_t)ws->inst_cap, 1);
-    ++ws->kernel_launches; k_instance_offsets<<<nb, T, 0, s>>>(st, ws->part, nb, ws->ioff, ws->win_pair,
+    ++ws->kernel_launches; k_count_instances<<<nw, T, 0, s>>>(v, ws->rect, st, ws->ioff, ws->part, nw);
+    ++ws->kernel_launches; k_scan_parts<<<1, T, 0, s>>>(ws->part, nw, nullptr, st, (uint64_t)ws->inst_cap, 1);
+    ++ws->kernel_launches; k_instance_offsets<<<nw, T, 0, s>>>(st, ws->part, nw, ws->ioff, ws->win_pair,
                                                                   (uint32_t)(ws->inst_cap / kEmitWindow + 2));
     ++ws->kernel_launches;
     k_emit_instances<<<kEmitBlocksPerSM * ws->num_sms, T, 0, s>>>(v, ws->rect, ws->rec, ws->views, ws->n_views,

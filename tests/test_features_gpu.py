@@ -401,7 +401,9 @@ def test_written_gradients_equal_accumulated_onto_zero():
     view sees) and equals accumulating onto zeroed buffers, up to the order
     of the raster backward's float atomics (each call sums its image-space
     gradients in its own order); with overwrite = 0 the outputs are added onto
-    what the buffers held."""
+    what the buffers held.  The three backwards follow one projection: the
+    first adds into the image-space rows the projection cleared, the later
+    ones clear the rows themselves (else they would add onto the first's)."""
     torch, dev = torch_dev()
     G = _G()
     sc = _scene()
