@@ -69,6 +69,9 @@ def parse():
                     help="also time one map-lifecycle pass (prune, reset, split / clone) on the workload")
     ap.add_argument("--active-set", action="store_true",
                     help="also time voxel-hash insertion of a point batch, LRU selection and an offload to host memory")
+    ap.add_argument("--once", action="store_true",
+                    help="run the step twice (sizing, then one more) and exit without timing: a short program "
+                         "for profilers, whose launches are exactly one step's after the first")
     ap.add_argument("--depth-loss", default="kl", choices=list(DEPTH_LOSSES),
                     help="depth term of the step: l1, kl (Eq. 7, fixed sigma_u) or kl-var (Eq. 7 with the "
                          "rendered variance: forward and backward with the central depth moment)")
@@ -266,8 +269,9 @@ def stage_bytes(u, args):
     var = args.depth_loss == "kl-var"
     return {
         # geometry of every Gaussian (44 B), SH of those seen, per pair the
-        # depth key and rectangle, per visible pair its 48-byte record
-        "project": 44 * u["N"] + (P - 44) * u["touched"] + 12 * u["pairs"] + 48 * u["visible"],
+        # depth key and rectangle, per visible pair its 48-byte record and its
+        # image-space gradient row cleared (40 B)
+        "project": 44 * u["N"] + (P - 44) * u["touched"] + 12 * u["pairs"] + 88 * u["visible"],
         # every pair's key read, the visible (key, pair) written
         "compact": 4 * u["pairs"] + 8 * u["visible"],
         "depth_sort": 16 * u["visible"],
@@ -283,14 +287,16 @@ def stage_bytes(u, args):
         "image_l1": 48 * u["pix"],
         # returns read, depth and alpha gathered, dL/dD read and written
         "depth_loss": 32 * u["lidar"],
+        # (only a second backward of one projection clears the rows itself)
         "zero_grad": 40 * u["visible"],
         # ranges, listed pair ids, records once, per-pixel inputs, image-space gradients written
         "raster_bwd": 8 * u["tiles"] + 4 * u["listed"] + 48 * u["visible"] + (44 if var else 24) * u["pix"]
         + 40 * u["visible"],
-        # params of the seen Gaussians read and their gradients read and written;
-        # per visible pair its image-space gradient and view-direction gradient
-        # (written by the SH adjoint, read by the geometric one); densify statistics
-        "project_bwd": 3 * P * u["touched"] + (40 + 32) * u["visible"] + 16 * u["touched"],
+        # params of the seen Gaussians read; every Gaussian's gradient row and
+        # densification statistic written (the step writes them, zeros for the
+        # unseen); per visible pair its image-space gradient and view-direction
+        # gradient (written by the SH adjoint, read by the geometric one)
+        "project_bwd": P * u["touched"] + (P + 8) * u["N"] + (40 + 32) * u["visible"],
     }
 
 
@@ -531,12 +537,10 @@ class Step:
             if self.ssim_lambda > 0:
                 G.gs_image_loss(r.ws, G._ptr(self.rgb), G._ptr(self.target), self.ssim_lambda, G._ptr(self.loss_rgb),
                                 G._ptr(self.g_rgb), s)
-            elif self.u8:
-                G.gs_image_l1_u8(r.ws, G._ptr(self.rgb), G._ptr(self.target_u8), G._ptr(self.loss_rgb),
-                                 G._ptr(self.g_rgb), s)
             else:
-                G.gs_image_l1(r.ws, G._ptr(self.rgb), G._ptr(self.target), G._ptr(self.loss_rgb), G._ptr(self.g_rgb),
-                              s)
+                (G.gs_image_l1_u8 if self.u8 else G.gs_image_l1)(r.ws, G._ptr(self.rgb),
+                                                                  G._ptr(self.target_u8 if self.u8 else self.target),
+                                                                  G._ptr(self.loss_rgb), G._ptr(self.g_rgb), s)
             if self.var:
                 G.gs_depth_loss_var(r.ws, G._ptr(self.alpha), G._ptr(self.dist[0]), G._ptr(self.dist[1]),
                                     G._ptr(self.lidar), self.lidar.shape[0], G._ptr(self.loss_depth),
@@ -788,6 +792,8 @@ def main():
     sc = scenes.workload(args.workload, seed=rank)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
 
+    step_runs = [0]  # steps run while sizing (each launches every kernel of a step once)
+
     def build_step(tw, th, depth):
         """A Step whose instance capacity fits the scene (sized from a first run)."""
         cfg = G.gs_config_default(tile_w=tw, tile_h=th, batch_depth=depth,
@@ -795,12 +801,14 @@ def main():
         mom = args.depth_loss == "kl-var"
         st_ = Step(G, torch, sc, cfg, dev, var=mom, ssim_lambda=args.ssim_lambda, adam=args.adam)
         st_.run()
+        step_runs[0] += 1
         code, need_, _ = st_.r.status()
         if code == G.GS_ERR_CAPACITY or need_ > st_.r.info["inst_capacity"]:
             st_.r.close()
             st_ = Step(G, torch, sc, cfg, dev, inst_capacity=int(need_ * 1.25) + 1024, var=mom,
                        ssim_lambda=args.ssim_lambda, adam=args.adam)
             st_.run()
+            step_runs[0] += 1
         return st_
 
     tuned = None
@@ -824,6 +832,14 @@ def main():
     step = build_step(tw, th, args.depth)
     st, need, nvis = step.r.status()
     assert st == G.GS_OK, G.status_string(st)
+    if args.once:
+        step.run()
+        torch.cuda.synchronize()
+        assert step.r.status()[0] == G.GS_OK
+        step.r.close()
+        # a profiler skips this many launches of a kernel to reach the last step's
+        print(json.dumps({"once": True, "steps_before_last": step_runs[0]}))
+        return 0
 
     # launches per step, from the library's own counter
     k0 = G.gs_workspace_info(step.r.ws)["kernel_launches"]

@@ -96,6 +96,8 @@ def test_stage_bytes_and_report_use_every_stage():
     assert bw["peak"] == 70.0
     assert bw["flops"] == 5000 * b.EVAL_FLOPS + 2000 * b.BWD_BLEND_FLOPS
     P = 4 * (11 + 48)
+    assert rep["bytes"]["project_bwd"] == P * 40 + (P + 8) * 100 + 72 * 50
+    assert rep["bytes"]["project"] == 44 * 100 + (P - 44) * 40 + 12 * 200 + 88 * 50
     B = 3 * 40 * P + 260 * 50 + 52 * 400 + 88 * 1000 + 20 * 20 + 8 * 40
     assert rep["step"]["algorithmic_bytes"] == B
     assert abs(rep["step"]["frac"] - B / 0.2e-3 / 1e9 / 6000.0) < 1e-12
