@@ -213,10 +213,26 @@ __global__ void __launch_bounds__(T) k_radix_scan(uint32_t *hist, int nb, uint32
     if (t == 0) dtot[blockIdx.x] = tot;
 }
 
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, uint32_t src_bytes) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Tiles of 2048 keys and more are copied into shared memory asynchronously,
+// one tile ahead (tile k lands in buffer k & 1 while tile k - 1 is worked;
+// the buffer then holds tile k's reordered run): 0.452 -> 0.433 ms for the
+// two passes over 25.1M instances.  The depth sort's 512-key tiles load into
+// registers (the copy ahead measured 0.175 -> 0.179 ms there).
+template <int R>
+constexpr bool kScatterAhead = R >= 8;
+
 template <int R>
 struct ScatterSmem {
-    uint32_t key[T * R];
-    uint32_t val[T * R];
+    uint32_t key[kScatterAhead<R> ? 2 : 1][T * R];
+    uint32_t val[kScatterAhead<R> ? 2 : 1][T * R];
     uint32_t wcnt[W][256];  // per-warp digit counts, then per-warp digit offsets
     uint32_t base[256], tcnt[256], tstart[256];
     uint32_t scan[32];
@@ -251,8 +267,35 @@ __global__ void __launch_bounds__(T) k_radix_scatter(const uint32_t *kin, const 
         S.base[t] = digit_base + hist[t * nb + blockIdx.x];
     }
     const uint32_t lt = lanemask_lt();
-    for (uint32_t t0 = lo; t0 < hi; t0 += TILE) {
+    // asynchronous copy of the tile at t1 into buffer bi in sixteen-byte
+    // pieces of keys and of values (consecutive threads, consecutive pieces),
+    // the tail's short piece zero-filled (only its in-range bytes are read)
+    auto fetch = [&](uint32_t t1, int bi) {
+        const uint32_t tn1 = min((uint32_t)TILE, hi - t1);
+#pragma unroll
+        for (int q = 0; q < (TILE / 4 + T - 1) / T; ++q) {
+            if (q * T + t >= TILE / 4) break;
+            const uint32_t e = 4 * (q * T + t);  // first key of the piece
+            const uint32_t nbytes = e < tn1 ? 4u * min(4u, tn1 - e) : 0u;
+            const uint32_t src = t1 + (e < tn1 ? e : 0u);
+            cp_async16(&S.key[bi][e], kin + src, nbytes);
+            cp_async16(&S.val[bi][e], vin + src, nbytes);
+        }
+        cp_async_commit();
+    };
+    constexpr bool AHEAD = kScatterAhead<R>;
+    if constexpr (AHEAD) fetch(lo, 0);
+    int bi = 0;
+    for (uint32_t t0 = lo; t0 < hi; t0 += TILE, bi = AHEAD ? bi ^ 1 : 0) {
         const uint32_t tn = min((uint32_t)TILE, hi - t0);
+        if constexpr (AHEAD) {
+            if (t0 + TILE < hi) {
+                fetch(t0 + TILE, bi ^ 1);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+        }
 #pragma unroll
         for (int j = 0; j < W; ++j) S.wcnt[j][t] = 0;
         __syncthreads();
@@ -260,8 +303,8 @@ __global__ void __launch_bounds__(T) k_radix_scatter(const uint32_t *kin, const 
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const uint32_t i = w * WT + r * 32 + lane;
-            key[r] = i < tn ? kin[t0 + i] : 0u;
-            val[r] = i < tn ? vin[t0 + i] : 0u;
+            key[r] = i >= tn ? 0u : AHEAD ? S.key[bi][i] : kin[t0 + i];
+            val[r] = i >= tn ? 0u : AHEAD ? S.val[bi][i] : vin[t0 + i];
         }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -297,8 +340,8 @@ __global__ void __launch_bounds__(T) k_radix_scatter(const uint32_t *kin, const 
             if ((uint32_t)(w * WT + r * 32 + lane) < tn) {
                 const uint32_t d = (key[r] >> shift) & 255u;
                 const uint32_t lp = S.tstart[d] + S.wcnt[w][d] + rank[r];
-                S.key[lp] = key[r];
-                S.val[lp] = val[r];
+                S.key[bi][lp] = key[r];
+                S.val[bi][lp] = val[r];
             }
         }
         __syncthreads();
@@ -306,11 +349,11 @@ __global__ void __launch_bounds__(T) k_radix_scatter(const uint32_t *kin, const 
         for (int r = 0; r < R; ++r) {
             const uint32_t j = t + r * T;
             if (j < tn) {
-                const uint32_t k = S.key[j];
+                const uint32_t k = S.key[bi][j];
                 const uint32_t d = (k >> shift) & 255u;
                 const uint32_t o = S.base[d] + (j - S.tstart[d]);
                 kout[o] = k;
-                vout[o] = S.val[j];
+                vout[o] = S.val[bi][j];
             }
         }
         __syncthreads();
