@@ -247,7 +247,9 @@ gs_status gs_workspace_info(gs_workspace *ws, int64_t *info, int32_t n_info);
 /* Copy an internal buffer to `dst` (device) for inspection; bytes must equal
  * the buffer size reported through *bytes when dst is NULL.
  * which: 0 records [n_pairs][12] f32, 1 pair depth keys [n_pairs] u32,
- * 2 tile rectangles [n_pairs][4] i16, 3 sorted instance tile ids [capacity]
+ * 2 tile rectangles [n_pairs][4] i16 (records and rectangles are written for
+ * the visible pairs only, those whose depth key is not 0xFFFFFFFF; the
+ * others hold whatever an earlier projection left), 3 sorted instance tile ids [capacity]
  * u32 (0xFFFFFFFF, last, for a rectangle tile that is not covered), 4 sorted
  * instance pair ids [capacity] u32, 5 tile ranges [n_tiles][2]
  * u32, 6 per-pixel list count up to the last blended fragment [N_pix] u32,
