@@ -723,8 +723,11 @@ __global__ void __launch_bounds__(kProjBwdThreads) k_sh_bwd(ProjArgs A) {
     }
 }
 
+// Five blocks an SM (96 registers, a few spilled outside the view loop):
+// orchard4m 0.657 -> 0.635 ms for the two adjoint kernels, against four
+// blocks at 116 registers; six (80 registers) spill inside the loop.
 template <int DEG>
-__global__ void __launch_bounds__(kProjBwdThreads, 512 / kProjBwdThreads) k_project_bwd(ProjArgs A) {
+__global__ void __launch_bounds__(kProjBwdThreads, 5) k_project_bwd(ProjArgs A) {
     constexpr int NWARP = kProjBwdThreads / 32;
     extern __shared__ float red[];  // [views of the submap][warps][6] pose twist sums
     __shared__ int s_item[kProjBwdChunk];                  // chunk index of a visible Gaussian
