@@ -287,7 +287,8 @@ gs_status gs_workspace_create(const gs_camera *cams, int32_t n_views, const int6
     GS_ALLOC(ws->tfin, (size_t)ws->n_pix);
     GS_ALLOC(ws->vstat, (size_t)ws->n_pix);
     // the instance sort runs 2 x sort_blocks, the compaction and depth sort wide_blocks
-    GS_ALLOC(ws->hist, (size_t)256 * std::max(2 * ws->sort_blocks, ws->wide_blocks));
+    ws->hist_cols = std::max(2 * ws->sort_blocks, ws->wide_blocks);
+    GS_ALLOC(ws->hist, (size_t)256 * ws->hist_cols);
     GS_ALLOC(ws->part, (size_t)std::max(ws->sort_blocks, ws->wide_blocks) + 1);
     GS_ALLOC(ws->digit_tot, (size_t)256);
     GS_ALLOC(ws->pose_part, (size_t)std::max(1, blocks) * maxv * 6);

@@ -85,7 +85,8 @@ struct gs_workspace {
     float *tfin = nullptr;         // [n_pix]
     float4 *vstat = nullptr;       // [n_pix] depth (mean, var, 1/W, 0) of the variance forward
     // scratch
-    uint32_t *hist = nullptr;      // [256][max(2 sort_blocks, wide_blocks)]
+    uint32_t *hist = nullptr;      // [256][hist_cols]
+    int32_t hist_cols = 0;         // max(2 sort_blocks, wide_blocks): the most blocks a radix pass may run
     uint32_t *part = nullptr;      // [max(sort_blocks, wide_blocks) + 1]
     uint32_t *digit_tot = nullptr; // [256] digit totals of the current radix pass
     float *pose_part = nullptr;    // [proj_blocks][max_views_per_submap][6]

@@ -718,6 +718,12 @@ __global__ void __launch_bounds__(256) k_order_place(const uint2 *ranges, int n_
 template <int R>
 gs_status radix_pass(gs_workspace *ws, uint32_t *&k, uint32_t *&v, uint32_t *&k2, uint32_t *&v2,
                      const uint32_t *n_ptr, int shift, int nb, cudaStream_t s) {
+    // the digit table has a column per block, and the scan takes at most 4 T
+    if (nb < 1 || nb > ws->hist_cols || nb > 4 * T) {
+        set_last_error("radix_pass: " + std::to_string(nb) + " blocks exceed the digit table (" +
+                       std::to_string(ws->hist_cols) + " columns)");
+        return GS_ERR_INVALID_ARG;
+    }
     ++ws->kernel_launches; k_radix_hist<<<nb, T, 0, s>>>(k, n_ptr, shift, ws->hist, nb, T * R);
     ++ws->kernel_launches; k_radix_scan<<<256, T, 0, s>>>(ws->hist, nb, ws->digit_tot);
     ++ws->kernel_launches;
