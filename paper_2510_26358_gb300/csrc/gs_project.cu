@@ -681,14 +681,16 @@ __global__ void __launch_bounds__(kProjBwdThreads) k_sh_bwd(ProjArgs A) {
                 const int v = A.sub_views[s * A.maxv + kv];
                 const ViewInfo vi = A.views[v];
                 pair = (int64_t)vi.pair_off + (g - vi.g0);
+                // the forward marked a clamped channel by the sign of its colour
+                // (both loads issued before the camera's arithmetic)
+                const float cf = reinterpret_cast<const float *>(A.rec + 3 * pair + 2)[ch];
+                const float graw = A.g2d[pair * kGrad + G_R + ch];
                 const Cam cam = load_cam(A.cams, v);
                 float w[3], wn;
                 view_dir(cam, mu, w, wn);
                 const float iw = 1.f / wn;
                 const float d[3] = {w[0] * iw, w[1] * iw, w[2] * iw};
-                // the forward marked a clamped channel by the sign of its colour
-                const float cf = reinterpret_cast<const float *>(A.rec + 3 * pair + 2)[ch];
-                const float gc = signbit(cf) ? 0.f : A.g2d[pair * kGrad + G_R + ch];
+                const float gc = signbit(cf) ? 0.f : graw;
                 float Y[16], dY[16][3];
                 sh_basis<DEG>(d[0], d[1], d[2], Y);
                 sh_basis_grad<DEG>(d[0], d[1], d[2], dY);
@@ -796,6 +798,9 @@ __global__ void __launch_bounds__(kProjBwdThreads, 5) k_project_bwd(ProjArgs A) 
                     const float *gg = A.g2d + pair * kGrad;
                     float gu = gg[G_U], gv = gg[G_V], gqa = gg[G_QA], gqb = gg[G_QB], gqc = gg[G_QC];
                     float glno = gg[G_LNO], gz = gg[G_Z];
+                    // view-direction gradient of the colour, from the SH adjoint
+                    // (loaded with the image-space row, before the pair's geometry)
+                    const float4 gd4 = A.gdir[pair];
                     Cam cam = load_cam(A.cams, v);
                     PairGeom G;
                     pair_geom(cam, vi.W, vi.H, k, view_coord_ff(cam.T, mu[0], mu[1], mu[2]).x,
@@ -814,8 +819,6 @@ __global__ void __launch_bounds__(kProjBwdThreads, 5) k_project_bwd(ProjArgs A) 
                     view_dir(cam, mu, w, wn);
                     float iw = 1.f / wn;
                     float d[3] = {w[0] * iw, w[1] * iw, w[2] * iw};
-                    // view-direction gradient of the colour, from the SH adjoint
-                    const float4 gd4 = A.gdir[pair];
                     const float gdir[3] = {gd4.x, gd4.y, gd4.z};
                     float dd = d[0] * gdir[0] + d[1] * gdir[1] + d[2] * gdir[2];
                     float gw[3] = {(gdir[0] - d[0] * dd) * iw, (gdir[1] - d[1] * dd) * iw, (gdir[2] - d[2] * dd) * iw};
