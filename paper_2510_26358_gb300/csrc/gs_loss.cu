@@ -99,17 +99,49 @@ __device__ __forceinline__ VarTerm var_term(double mu, double var, double z, dou
     return t;
 }
 
-// returns the pixel index or -1 if the return is not valid
-__device__ __forceinline__ int64_t lidar_pixel(const DepthArgs &A, int64_t i, float &z) {
-    const float4 L = reinterpret_cast<const float4 *>(A.lidar)[i];
-    int v = (int)L.w;
-    z = L.z;
-    if (!(L.w >= 0.f) || v >= A.n_views) return -1;
-    const ViewInfo vi = A.views[v];
-    if (!(L.x >= 0.f && L.x < (float)vi.W && L.y >= 0.f && L.y < (float)vi.H && L.z > A.near_z)) return -1;
-    int64_t pix = vi.pix_off + (int64_t)floorf(L.y) * vi.W + (int64_t)floorf(L.x);
-    if (!(A.alpha[pix] > 0.f)) return -1;
-    return pix;
+// Validity of a return: its view exists, it lies inside that image, z > near_z
+// and alpha > 0 at pixel (floor u, floor v).  Four returns a thread at a time, i0 + u * stride (u = 0..3): the returns,
+// then their pixels' alpha, depth (and variance) gathers, are all in flight
+// together; the terms are then taken in the order of the one-at-a-time loop
+// (i0, i0 + stride, ...), so the sums are unchanged.
+constexpr int kDepthBatch = 4;
+
+struct DepthGather {
+    int64_t pix[kDepthBatch];  // -1: not a valid return
+    float z[kDepthBatch], dep[kDepthBatch], var[kDepthBatch];
+};
+
+__device__ __forceinline__ void gather_returns(const DepthArgs &A, int64_t i0, int64_t stride, DepthGather &G) {
+    float4 L[kDepthBatch];
+#pragma unroll
+    for (int u = 0; u < kDepthBatch; ++u) {
+        const int64_t i = i0 + u * stride;
+        L[u] = i < A.n_pts ? reinterpret_cast<const float4 *>(A.lidar)[i] : make_float4(0.f, 0.f, 0.f, -1.f);
+    }
+    float al[kDepthBatch];
+#pragma unroll
+    for (int u = 0; u < kDepthBatch; ++u) {
+        G.pix[u] = -1;
+        G.z[u] = L[u].z;
+        al[u] = 0.f;
+        G.dep[u] = G.var[u] = 0.f;
+        const int v = (int)L[u].w;
+        if (!(L[u].w >= 0.f) || v >= A.n_views) continue;
+        const ViewInfo vi = A.views[v];
+        if (!(L[u].x >= 0.f && L[u].x < (float)vi.W && L[u].y >= 0.f && L[u].y < (float)vi.H && L[u].z > A.near_z))
+            continue;
+        G.pix[u] = vi.pix_off + (int64_t)floorf(L[u].y) * vi.W + (int64_t)floorf(L[u].x);
+    }
+#pragma unroll
+    for (int u = 0; u < kDepthBatch; ++u) {
+        if (G.pix[u] < 0) continue;
+        al[u] = A.alpha[G.pix[u]];
+        G.dep[u] = A.depth[G.pix[u]];
+        if (A.mode == 2) G.var[u] = A.var[G.pix[u]];
+    }
+#pragma unroll
+    for (int u = 0; u < kDepthBatch; ++u)
+        if (!(al[u] > 0.f)) G.pix[u] = -1;
 }
 
 __global__ void __launch_bounds__(LT) k_depth_partial(DepthArgs A) {
@@ -117,22 +149,27 @@ __global__ void __launch_bounds__(LT) k_depth_partial(DepthArgs A) {
     KahanF sf;
     double s = 0.0;
     uint32_t c = 0;
-    for (int64_t i = (int64_t)blockIdx.x * LT + threadIdx.x; i < A.n_pts; i += (int64_t)gridDim.x * LT) {
-        float z;
-        int64_t pix = lidar_pixel(A, i, z);
-        if (pix < 0) continue;
-        const float d = __fsub_rn(A.depth[pix], z);
-        if (A.mode == 0) {
-            sf.add(fabsf(d));
-        } else if (A.mode == 2) {
-            s += var_term(A.depth[pix], A.var[pix], z, A.sigma_L, A.sigma_U).kl;
-        } else {
-            // the KL's point-independent part (its log and constants) is added
-            // once per valid point at the end: double logs and divisions per
-            // point kept the FP64 pipe busy for tens of microseconds
-            sf.add(__fmul_rn(d, d));
+    const int64_t stride = (int64_t)gridDim.x * LT;
+    for (int64_t i0 = (int64_t)blockIdx.x * LT + threadIdx.x; i0 < A.n_pts; i0 += kDepthBatch * stride) {
+        DepthGather G;
+        gather_returns(A, i0, stride, G);
+#pragma unroll
+        for (int u = 0; u < kDepthBatch; ++u) {
+            if (G.pix[u] < 0) continue;
+            const float d = __fsub_rn(G.dep[u], G.z[u]);
+            if (A.mode == 0) {
+                sf.add(fabsf(d));
+            } else if (A.mode == 2) {
+                s += var_term(G.dep[u], G.var[u], G.z[u], A.sigma_L, A.sigma_U).kl;
+            } else {
+                // the KL's point-independent part (its log and constants) is
+                // added once per valid point at the end: double logs and
+                // divisions per point kept the FP64 pipe busy for tens of
+                // microseconds
+                sf.add(__fmul_rn(d, d));
+            }
+            ++c;
         }
-        ++c;
     }
     s += sf.value();
     double ts = block_sum_d(s, sm);
@@ -170,20 +207,25 @@ __global__ void __launch_bounds__(LT) k_depth_grad(DepthArgs A) {
     const float scale = A.st->depth_scale;
     if (scale == 0.f) return;
     const float iv = 1.f / (A.sigma_U * A.sigma_U);
-    for (int64_t i = (int64_t)blockIdx.x * LT + threadIdx.x; i < A.n_pts; i += (int64_t)gridDim.x * LT) {
-        float z;
-        int64_t pix = lidar_pixel(A, i, z);
-        if (pix < 0) continue;
-        if (A.mode == 2) {
-            const VarTerm t = var_term(A.depth[pix], A.var[pix], z, A.sigma_L, A.sigma_U);
-            const double k = scale;
-            if (A.grad) atomicAdd(A.grad + pix, (float)(k * t.dmu));
-            if (A.grad_var) atomicAdd(A.grad_var + pix, (float)(k * t.dvar));
-            continue;
+    const int64_t stride = (int64_t)gridDim.x * LT;
+    for (int64_t i0 = (int64_t)blockIdx.x * LT + threadIdx.x; i0 < A.n_pts; i0 += kDepthBatch * stride) {
+        DepthGather G;
+        gather_returns(A, i0, stride, G);
+#pragma unroll
+        for (int u = 0; u < kDepthBatch; ++u) {
+            const int64_t pix = G.pix[u];
+            if (pix < 0) continue;
+            if (A.mode == 2) {
+                const VarTerm t = var_term(G.dep[u], G.var[u], G.z[u], A.sigma_L, A.sigma_U);
+                const double k = scale;
+                if (A.grad) atomicAdd(A.grad + pix, (float)(k * t.dmu));
+                if (A.grad_var) atomicAdd(A.grad_var + pix, (float)(k * t.dvar));
+                continue;
+            }
+            float d = G.dep[u] - G.z[u];
+            float g = A.mode == 0 ? (d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f)) : d * iv;
+            atomicAdd(A.grad + pix, scale * g);
         }
-        float d = A.depth[pix] - z;
-        float g = A.mode == 0 ? (d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f)) : d * iv;
-        atomicAdd(A.grad + pix, scale * g);
     }
 }
 
