@@ -473,8 +473,11 @@ __global__ void __launch_bounds__(T) k_instance_offsets(const DevState *st, cons
 __device__ __forceinline__ float4 reach_terms(const float4 r1, const Consts &k) {
     const float l11 = r1.x, l12 = r1.y, l22 = r1.z;
     const float pad = 1.f + k.ext_rel_pad;
-    return make_float4(-l11 * l12 / (l12 * l12 + l22 * l22), -l12 / l11, (r1.w - k.log2_alpha_min) * pad * pad,
-                       0.f);
+    // (the slopes by the fast division, within 2 ulps: the quadratic is
+    // stationary there, so a slope off by e moves the edge minimum by O(e^2);
+    // orchard4m emission 0.239 -> 0.228 ms)
+    return make_float4(__fdividef(-l11 * l12, l12 * l12 + l22 * l22), __fdividef(-l12, l11),
+                       (r1.w - k.log2_alpha_min) * pad * pad, 0.f);
 }
 
 __device__ __forceinline__ bool tile_reached(const float4 r0, const float4 r1, const float4 q, int X0, int X1,
