@@ -715,9 +715,8 @@ __global__ void __launch_bounds__(256) k_order_place(const uint2 *ranges, int n_
 // One stable pass over bits [shift, shift+8) by nb blocks; swaps in/out.
 // R = 8 rounds (2048-key tiles) on twice the blocks for the instance sort
 // (64 registers: one full wave of four blocks per SM; measured 0.0725 ->
-// 0.068 ms against R = 16 on one block per two SMs' worth), R = 2 for the
-// smaller sort of the visible pairs (more blocks busy, shorter latency:
-// 0.070 -> 0.068 ms against R = 4, R = 1 0.072 ms).
+// 0.068 ms against R = 16 on one block per two SMs' worth), R = 2 or 4 for
+// the smaller sort of the visible pairs (see its launch).
 template <int R>
 gs_status radix_pass(gs_workspace *ws, uint32_t *&k, uint32_t *&v, uint32_t *&k2, uint32_t *&v2,
                      const uint32_t *n_ptr, int shift, int nb, cudaStream_t s) {
@@ -777,8 +776,14 @@ gs_status launch_bin_sort(gs_workspace *ws, cudaStream_t s) {
     // (blocks grow with the pairs: a tenth of them or so are visible; more
     // blocks than keys to fill them only lengthen the digit-table scans)
     const int nd = (int)std::min<int64_t>(nw, std::max<int64_t>(nb, ws->n_pairs / 16384));
+    // four keys a thread once the blocks hold several tiles each (orchard4m,
+    // 3.08 M visible of 24 M pairs: 0.175 -> 0.164 ms), two below (orchard500k,
+    // 148k of 1.5 M: 0.063 ms against 0.065 with four)
+    const bool wide = ws->n_pairs >= (int64_t)8 << 20;
     for (int sh = 0; sh < 32; sh += 8)
-        if ((r = radix_pass<2>(ws, k, v, k2, v2, &st->n_vis, sh, nd, s)) != GS_OK) return r;
+        if ((r = wide ? radix_pass<4>(ws, k, v, k2, v2, &st->n_vis, sh, nd, s)
+                      : radix_pass<2>(ws, k, v, k2, v2, &st->n_vis, sh, nd, s)) != GS_OK)
+            return r;
     }
     // after 4 passes the sorted data are back in vis_key / vis_pair
     // 3. instance offsets, capacity check, emission in depth order
@@ -809,7 +814,9 @@ gs_status launch_bin_sort(gs_workspace *ws, cudaStream_t s) {
     StageTimer timer(ws, GS_STAGE_RANGES, s);
     cudaMemsetAsync(ws->ranges, 0, sizeof(uint2) * ws->n_tiles, s);
     ++ws->kernel_launches;
-    k_ranges<<<ws->num_sms * 4, 256, 0, s>>>(ws->inst_tile, st, (uint32_t)ws->n_tiles, ws->ranges, ws->order_tot);
+    // (eight blocks an SM, every thread resident: 0.054 -> 0.044 ms with the
+    // work order on orchard4m's 25.1 M instances, against four)
+    k_ranges<<<ws->num_sms * 8, 256, 0, s>>>(ws->inst_tile, st, (uint32_t)ws->n_tiles, ws->ranges, ws->order_tot);
     // 6. raster work order
     ++ws->kernel_launches;
     k_order_count<<<kOrderBlocks, 256, 0, s>>>(ws->ranges, (int)ws->n_tiles, ws->order_tot, ws->order_base);
