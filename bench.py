@@ -973,6 +973,8 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            # (value is from the mean step time; the median, for a median-based reading)
+            "ms_per_step_median": float(np.median(times)),
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(workload_config(sc, args, f"{tw}x{th}", args.depth),
                            autotune=None if tuned is None else {"chosen": f"{tw}x{th}/{args.depth}",

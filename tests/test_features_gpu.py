@@ -442,3 +442,36 @@ def test_written_gradients_equal_accumulated_onto_zero():
         assert st == G.GS_ERR_INVALID_ARG
     finally:
         r.close()
+
+
+def test_projection_with_unaligned_sh_rows_matches_aligned():
+    """The projection reads each SH row in 16-byte pieces when the SH array
+    starts on a 16-byte boundary and one coefficient at a time otherwise, in
+    the same order: the images are bitwise equal, and so are the gradients'
+    rows of the Gaussians no view sees (zeros) and the densification counts."""
+    torch, dev = torch_dev()
+    G = _G()
+    sc = _scene()
+    gC, gD, gA = _upstream(sc)
+    P = params_to_dev(sc)
+    r = G.Renderer(sc.cameras, sc.submap_offsets, sc.sh_degree, inst_capacity=1 << 22)
+    try:
+        ref = [x.clone() for x in r.forward(*P)]
+        buf = torch.empty(P[4].numel() + 1, device=dev)
+        sh_u = buf[1:].view_as(P[4])
+        sh_u.copy_(P[4])
+        assert sh_u.data_ptr() % 16 != 0
+        out = r.forward(*P[:4], sh_u)
+        torch.cuda.synchronize()
+        for a, b in zip(out, ref):
+            assert torch.equal(a, b)
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev)
+        g_u = r.backward(*P[:4], sh_u, t(gC), t(gD), t(gA))
+        r.forward(*P)
+        g_a = r.backward(*P, t(gC), t(gD), t(gA))
+        torch.cuda.synchronize()
+        assert torch.equal(g_u["densify_cnt"], g_a["densify_cnt"])
+        scale = float(g_a["sh"].double().abs().max())
+        assert float((g_u["sh"].double() - g_a["sh"].double()).abs().max()) <= 1e-5 * scale
+    finally:
+        r.close()
