@@ -312,7 +312,7 @@ def roofline_report(u, kern, step_ms, hbm_peak, hbm_src, alu, args, tw, th):
         gbs = nbytes / (t * 1e-3) / 1e9
         stages[k] = {"bound": "hbm", "algorithmic_bytes": int(nbytes), "ms": t, "achieved": gbs, "unit": "GB/s",
                      "frac": gbs / hbm_peak}
-    # the survey's floor for a whole iteration (each array touched once)
+    # the floor for a whole iteration: each array of the step touched once
     P = 4 * (3 + 3 + 4 + 1 + 3 * u["sh_coeffs"])
     B = (3 * u["touched"] * P + 260 * u["visible"] + 52 * u["instances"] + 88 * u["pix"] + 20 * u["lidar"]
          + 8 * u["touched"])
