@@ -294,6 +294,7 @@ struct ProjArgs {
     int32_t *dens_cnt;
     int32_t overwrite;  // gradients written (=) instead of accumulated, zeros for unseen Gaussians
     int32_t sh_vec;     // the SH array starts on a 16-byte boundary
+    int32_t gsh_vec;    // the SH gradient array starts on a 16-byte boundary
 };
 
 // Projection of one pair in float after the exact depth: Jacobian, image
@@ -637,21 +638,33 @@ __global__ void __launch_bounds__(kProjBwdThreads) k_sh_bwd(ProjArgs A) {
     __shared__ int s_item[kProjBwdChunk];
     __shared__ unsigned long long s_mask[kProjBwdChunk];
     __shared__ uint32_t s_scan[kProjBwdChunk / 32];
+    __shared__ uint8_t s_unseen[kProjBwdChunk];
+    constexpr int R4 = (3 * K) % 4 == 0 ? 3 * K / 4 : 1;
+    const bool vec = (3 * K) % 4 == 0 && A.gsh_vec;
     const int b = blockIdx.x, s = submap_of_block(A, b);
     const SubmapInfo sub = A.subs[s];
     const int64_t c0 = (int64_t)(b - sub.block0) * kProjBwdChunk;
+    for (int i = threadIdx.x; i < kProjBwdChunk; i += kProjBwdThreads) s_unseen[i] = 0;
+    __syncthreads();
     const int n_items = chunk_visible(A, s, sub, c0, s_item, s_mask, s_scan, [&](int64_t gu) {
         if (!A.overwrite) return;
-        if constexpr ((3 * K) % 4 == 0) {  // rows of a 16-byte multiple (degrees 1 and 3)
-            float4 *row = reinterpret_cast<float4 *>(A.gsh + gu * (3 * K));
-#pragma unroll
-            for (int i = 0; i < 3 * K / 4; ++i) row[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        } else {
-            float *row = A.gsh + gu * (3 * K);
-#pragma unroll
-            for (int i = 0; i < 3 * K; ++i) row[i] = 0.f;
+        if (vec) {
+            s_unseen[gu - sub.g0 - c0] = 1;  // cleared by the whole block below
+            return;
         }
+        float *row = A.gsh + gu * (3 * K);
+#pragma unroll
+        for (int i = 0; i < 3 * K; ++i) row[i] = 0.f;
     });
+    // the unseen rows, consecutive threads on consecutive 16-byte pieces (a
+    // thread writing a whole row of its own Gaussian spread each store over 32
+    // rows: orchard4m SH and geometric adjoints 0.586 -> 0.529 ms)
+    if (vec && A.overwrite) {
+        const int nloc = (int)min((int64_t)kProjBwdChunk, sub.ng - c0);
+        float4 *rows = reinterpret_cast<float4 *>(A.gsh + (sub.g0 + c0) * (3 * K));
+        for (int i = threadIdx.x; i < nloc * R4; i += kProjBwdThreads)
+            if (s_unseen[i / R4]) rows[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int grp = lane / 3, ch = lane - 3 * grp, lead = 3 * grp;  // lanes 30, 31 idle
     for (int base = wid * GPW; base < n_items; base += NWARP * GPW) {
@@ -1066,6 +1079,7 @@ gs_status launch_project_bwd(gs_workspace *ws, const gs_gaussians *g, const gs_c
     A.dens_cnt = out->densify_cnt;
     A.gdir = ws->gdir;
     A.overwrite = out->overwrite;
+    A.gsh_vec = (((uintptr_t)out->sh) & 15) == 0;
     StageTimer timer(ws, GS_STAGE_PROJECT_BWD, s);
     if (ws->proj_blocks > 0) {
         size_t smem = sizeof(float) * ws->max_views_per_submap * (kProjBwdThreads / 32) * 6;

@@ -447,8 +447,11 @@ def test_written_gradients_equal_accumulated_onto_zero():
 def test_projection_with_unaligned_sh_rows_matches_aligned():
     """The projection reads each SH row in 16-byte pieces when the SH array
     starts on a 16-byte boundary and one coefficient at a time otherwise, in
-    the same order: the images are bitwise equal, and so are the gradients'
-    rows of the Gaussians no view sees (zeros) and the densification counts."""
+    the same order: the images are bitwise equal.  The SH adjoint clears the
+    unseen Gaussians' gradient rows in 16-byte pieces only when the caller's
+    gradient array is aligned: with SH values and SH gradients both one float
+    past a boundary the gradients equal the aligned ones, the unseen rows are
+    zeros, and the densification counts are equal."""
     torch, dev = torch_dev()
     G = _G()
     sc = _scene()
@@ -466,11 +469,19 @@ def test_projection_with_unaligned_sh_rows_matches_aligned():
         for a, b in zip(out, ref):
             assert torch.equal(a, b)
         t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev)
-        g_u = r.backward(*P[:4], sh_u, t(gC), t(gD), t(gA))
         r.forward(*P)
         g_a = r.backward(*P, t(gC), t(gD), t(gA))
+        r.forward(*P[:4], sh_u)
+        g_buf = torch.full((P[4].numel() + 1,), float("nan"), device=dev)
+        grads = {k: torch.empty_like(v) for k, v in g_a.items()}
+        grads["sh"] = g_buf[1:].view_as(g_a["sh"])
+        assert grads["sh"].data_ptr() % 16 != 0
+        g_u = r.backward(*P[:4], sh_u, t(gC), t(gD), t(gA), grads=grads, overwrite=True)
         torch.cuda.synchronize()
         assert torch.equal(g_u["densify_cnt"], g_a["densify_cnt"])
+        assert not torch.isnan(g_u["sh"]).any()
+        unseen = g_a["densify_cnt"] == 0
+        assert int(unseen.sum()) > 0 and torch.all(g_u["sh"][unseen] == 0)
         scale = float(g_a["sh"].double().abs().max())
         assert float((g_u["sh"].double() - g_a["sh"].double()).abs().max()) <= 1e-5 * scale
     finally:
