@@ -640,6 +640,11 @@ __global__ void __launch_bounds__(kProjBwdThreads) k_sh_bwd(ProjArgs A) {
     __shared__ uint32_t s_scan[kProjBwdChunk / 32];
     __shared__ uint8_t s_unseen[kProjBwdChunk];
     constexpr int R4 = (3 * K) % 4 == 0 ? 3 * K / 4 : 1;
+    // the warp's ten gradient rows staged for 16-byte stores (orchard4m
+    // adjoints 0.529 -> 0.518 ms); a row stride of R4 + 1 pieces keeps the
+    // groups' lanes on different banks
+    constexpr int SR = 4 * (R4 + 1);
+    __shared__ __align__(16) float s_out[kProjBwdThreads / 32][GPW * SR];
     const bool vec = (3 * K) % 4 == 0 && A.gsh_vec;
     const int b = blockIdx.x, s = submap_of_block(A, b);
     const SubmapInfo sub = A.subs[s];
@@ -725,7 +730,23 @@ __global__ void __launch_bounds__(kProjBwdThreads) k_sh_bwd(ProjArgs A) {
             }
             if (act && ch == 0) A.gdir[pair] = make_float4(gd[0], gd[1], gd[2], 0.f);
         }
-        if (live) {
+        if (vec && A.overwrite) {
+            float *so = s_out[wid];
+            if (live) {
+#pragma unroll
+                for (int kk = 0; kk < K; ++kk) so[grp * SR + 3 * kk + ch] = gacc[kk];
+            }
+            __syncwarp();
+            for (int i = lane; i < GPW * R4; i += 32) {
+                const int r = i / R4, q = i - r * R4;
+                if (base + r < n_items) {
+                    const int64_t gr = sub.g0 + c0 + s_item[base + r];
+                    reinterpret_cast<float4 *>(A.gsh + gr * (3 * K))[q] =
+                        reinterpret_cast<const float4 *>(so + r * SR)[q];
+                }
+            }
+            __syncwarp();
+        } else if (live) {
             float *gsh = A.gsh + g * (3 * K) + ch;
             if (A.overwrite) {
 #pragma unroll
