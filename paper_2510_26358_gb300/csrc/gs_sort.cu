@@ -221,13 +221,14 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// Tiles of 2048 keys and more are copied into shared memory asynchronously,
+// Tiles of 1024 keys and more are copied into shared memory asynchronously,
 // one tile ahead (tile k lands in buffer k & 1 while tile k - 1 is worked;
 // the buffer then holds tile k's reordered run): 0.452 -> 0.433 ms for the
-// two passes over 25.1M instances.  The depth sort's 512-key tiles load into
-// registers (the copy ahead measured 0.175 -> 0.179 ms there).
+// two passes over 25.1M instances, 0.165 -> 0.154 ms for the depth sort's
+// 1024-key tiles over 3.08M pairs.  512-key tiles load into registers (the
+// copy ahead measured 0.175 -> 0.179 ms there).
 template <int R>
-constexpr bool kScatterAhead = R >= 8;
+constexpr bool kScatterAhead = R >= 4;
 
 template <int R>
 struct ScatterSmem {
